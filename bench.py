@@ -1,0 +1,326 @@
+"""Throughput benchmark of the batched SQP/ADMM OCP solver on one node.
+
+Default workload: kinematic-bicycle racing, B = 1024 instances, N = 50,
+implicit midpoint dynamics, L1+L2-softened track constraint, control-rate
+cost, 10 SQP x 50 ADMM iterations (FP32 on the GPU).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+One step = one forward solve of the whole batch (every instance, every SQP and
+ADMM iteration); a second timed pass measures forward + backward.  Inputs are
+resident in HBM; the L2 is flushed (a 512 MB write) between timed steps.  The
+`e2e` figure times the host-memory entry point (tmpc_solve_host): copy of every
+parameter array from pinned host memory, the solve, and the copy of the whole
+solution back.  `--impl reference` times the FP64 CPU oracle (the baseline arm)
+on a bounded sample of the same workload on the host cores.
+
+Under torchrun (N > 1) every rank solves its own batch on its own GPU (weak
+scaling, no collective on the data path); rank 0 prints one JSON line with the
+max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "OCP solves/sec (fwd and fwd+bwd) at 1e-5 KKT residual; % of HBM/FP32 roofline"
+UNIT = "solves/s"
+
+# algorithmic FP32 work of the path, per stage (racing model, n = 8, nx = 6, ng = 4),
+# counted from the dense block operations of the method ("Roofline"):
+FLOP_ADMM_STAGE = 970.0     # one ADMM iteration (eta, S solve, A x~, relax/project/dual)
+FLOP_FACTOR_STAGE = 4600.0  # one block LDL' factorisation stage (Theta, Phi, Delta, inverse, Omega)
+FLOP_LIN_STAGE = 400.0      # one linearisation stage (Jacobians, shifted bounds)
+SMS, FP32_LANES = 152, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--batch", type=int, default=1024)
+    ap.add_argument("--horizon", type=int, default=50)
+    ap.add_argument("--cpu-sample", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-bwd", action="store_true", help="time the forward pass only")
+    ap.add_argument("--skip-e2e", action="store_true", help="skip the host-memory end-to-end timing")
+    return ap.parse_args()
+
+
+def workload(args, rank=0):
+    import workloads as w
+    return w.racing(B=args.batch, N=args.horizon, seed=1002 + 7919 * rank)
+
+
+def config_of(args, pb):
+    return {"workload": f"kinematic-bicycle racing B={pb.B} N={pb.N_max} (implicit midpoint, "
+                        f"L1+L2 soft track row, rate cost), {pb.opts.max_sqp} SQP x {pb.opts.max_admm} ADMM",
+            "batch": pb.B, "horizon": pb.N_max, "nx": pb.nx, "nu": pb.nu, "ng": pb.ng,
+            "sqp_iters": pb.opts.max_sqp, "admm_iters": pb.opts.max_admm,
+            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{args.gpus}"}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (baseline / reference arm)
+# ----------------------------------------------------------------------------
+_WORKER_BATCH = None
+
+
+def _init_worker(B, N, seed):
+    global _WORKER_BATCH
+    import workloads as w
+    _WORKER_BATCH = w.racing(B=B, N=N, seed=seed)
+
+
+def _oracle_one(i):
+    from oracle import sqp
+    pb = _WORKER_BATCH
+    inst = pb.instance(i % pb.B)
+    t = time.perf_counter()
+    sqp.solve(inst, pb.opts)
+    return time.perf_counter() - t
+
+
+def oracle_rate(args, n_inst, cores):
+    """Solve n_inst instances of the workload with the FP64 oracle on `cores`
+    processes; returns (solves/s, wall seconds, summed CPU seconds).  Instance
+    generation happens once per worker, before the timed map."""
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_init_worker, initargs=(n_inst, args.horizon, 1002)) as pool:
+        pool.map(_oracle_one, range(cores), chunksize=1)   # imports, warm caches
+        t = time.perf_counter()
+        times = pool.map(_oracle_one, range(n_inst), chunksize=1)
+        wall = time.perf_counter() - t
+    return n_inst / wall, wall, float(np.sum(times))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    per_step = max(cores, min(args.cpu_sample, 4 * cores))
+    for _ in range(max(args.warmup, 0) and 1):
+        oracle_rate(args, cores, cores)
+    vals, walls = [], []
+    for _ in range(args.steps):
+        v, wall, _ = oracle_rate(args, per_step, cores)
+        vals.append(v)
+        walls.append(wall)
+    value = float(np.median(vals))
+    pb = workload(args)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.median(walls)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(args, pb),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} instances of the workload per step, FP64 numpy/scipy oracle, "
+                                       f"one process per core"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip().lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def algorithmic_flops(pb, stats):
+    """FP32 flops the method needs for the solves just run (counts from the stats)."""
+    T = pb.N.astype(np.float64) + 1.0
+    admm = stats[:, 1].astype(np.float64)
+    fact = stats[:, 5].astype(np.float64)
+    sqp = stats[:, 0].astype(np.float64)
+    return float(np.sum(T * (admm * FLOP_ADMM_STAGE + fact * FLOP_FACTOR_STAGE + (sqp + 1) * FLOP_LIN_STAGE)))
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        n = max(cores, args.cpu_sample)
+        v, wall, cpu_s = oracle_rate(args, n, cores)
+        cpu_base = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                    "sample": f"{n} instances of the same workload (FP64 numpy/scipy oracle, one process per core, "
+                              f"{cpu_s:.1f} s CPU)"}
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2606_24039_gb300 import Solver, build, tensors_from_batch
+    build.build()
+    pb = workload(args, rank)
+    s = Solver.from_batch(pb, device="cuda")
+    sol = s.alloc_solution("cuda")
+    dLdz = torch.randn((pb.B, pb.N_max + 1, pb.n), device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        s.tmpc_solve(s.x0, sol)
+
+    def step_fb():
+        s.tmpc_solve(s.x0, sol)
+        s.tmpc_backward(s.x0, sol, dLdz)
+
+    for _ in range(args.warmup):
+        step()
+        if not args.skip_bwd:
+            step_fb()
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        times = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        return times
+
+    with Clocks(local) as clk:
+        t_fwd = timed(step)
+        t_fb = timed(step_fb) if not args.skip_bwd else [float("nan")]
+    clocks = clk.summary()
+    stats = sol["stats"].cpu().numpy()
+    status = sol["status"].cpu().numpy()
+    kkt = stats[:, 6]
+
+    # end to end through the host-memory entry point
+    hp = {k: (v.cpu().pin_memory() if v is not None else None) for k, v in tensors_from_batch(pb, "cpu").items()}
+    ho = {k: v.cpu().pin_memory() for k, v in s.alloc_solution("cpu").items()}
+    h2d = sum(v.numel() * v.element_size() for v in hp.values() if v is not None)
+    d2h = sum(v.numel() * v.element_size() for v in ho.values())
+    for _ in range(0 if args.skip_e2e else max(1, args.warmup)):
+        s.tmpc_solve_host(hp, hp["x0"], ho)
+    e2e_t = [float("nan")]
+    for _ in range(0 if args.skip_e2e else args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        s.tmpc_solve_host(hp, hp["x0"], ho)
+        e2e_t.append(time.perf_counter() - t)
+    e2e_t = [v for v in e2e_t if v == v] or [float("nan")]
+
+    ms_f = float(np.mean(t_fwd))
+    ms_fb = float(np.mean(t_fb))
+    ms_e2e = 1e3 * float(np.mean(e2e_t))
+    if world > 1:
+        red = torch.tensor([ms_f, ms_fb, ms_e2e], device="cuda")
+        dist.all_reduce(red, op=dist.ReduceOp.MAX)
+        ms_f, ms_fb, ms_e2e = red.tolist()
+    total = pb.B * world
+    value = total / (ms_f * 1e-3)
+    flops = algorithmic_flops(pb, stats)
+    achieved = flops / (ms_f * 1e-3) / 1e12
+    peak_clock = 2070.0
+    peak = SMS * FP32_LANES * 2 * peak_clock * 1e6 / 1e12
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_f, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(args, pb),
+            "fwd_bwd": {"value": total / (ms_fb * 1e-3), "unit": UNIT, "ms_per_step": ms_fb},
+            "clocks": clocks,
+            "e2e": {"value": total / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_note": "FP32 FMA peak = 152 SM x 128 lanes x 2 flop x 2070 MHz (derived)"},
+            "cpu_baseline": cpu_base,
+            "quality": {"kkt_median": float(np.median(kkt)), "kkt_p90": float(np.percentile(kkt, 90)),
+                        "frac_kkt_le_1e-5": float(np.mean(kkt <= 1e-5)),
+                        "status_counts": {str(k): int(v) for k, v in zip(*np.unique(status, return_counts=True))},
+                        "admm_iters_mean": float(stats[:, 1].mean()), "factorizations_mean": float(stats[:, 5].mean())},
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * tmpc.h -- C ABI of the batched, differentiable OCP solver (GB300, sm_103a).
+ *
+ * The library solves B independent optimal-control problems (the OCP of
+ * Section II-A / Appendix A of the paper) with SQP (Algorithm 1): at each SQP
+ * iterate the QP of Section III-A / Appendix B is built and solved by the ADMM
+ * scheme of Algorithm 3 (Section III-B, Appendix C), whose primal system
+ * S x = eta (Eq. admm:schur) is factored once per SQP step and per accepted
+ * rho and reused; the next iterate is chosen by the line search of Appendix D.
+ * The backward pass is the active-set implicit differentiation of Algorithm 2
+ * (Section III-D, Appendix E).
+ *
+ * Conventions for every call
+ *  - Plain C types only.  Array arguments are DEVICE pointers (CUDA global
+ *    memory) unless the name of the call ends in _host.  All float arrays are
+ *    contiguous, row-major FP32; integer arrays are int32.  The caller owns
+ *    every array it passes; the handle owns its workspace.
+ *  - Padded batch layout with layout maxima (Nmax, nx, nu, ng) from tmpc_dims:
+ *    stage arrays are [B][Nmax+1][...]; an instance i uses stages 0..N[i] and
+ *    the leading (nx_i, nu_i, ng_i) entries of its model: a stage vector
+ *    z[t] holds the state in z[t][0:nx_i] and the control in
+ *    z[t][nx_i:nx_i+nu_i].  Outputs beyond an instance's horizon or dims are
+ *    written as 0.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream and return after the
+ *    work is enqueued, except where stated.  Argument validation (null
+ *    pointers, dims, alignment) is synchronous; a failed validation enqueues
+ *    nothing.
+ *  - Per-instance outcomes (non-convergence, factorisation failure, NaN) are
+ *    reported in the status array, never as a call failure.
+ *  - A handle is not thread-safe; one host thread at a time.
+ *  - No exceptions cross this ABI.
+ */
+#ifndef TMPC_H
+#define TMPC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TMPC_OK = 0,
+    TMPC_ERR_INVALID_ARG = 1,   /* null pointer, bad dims, misaligned array     */
+    TMPC_ERR_CUDA = 2,          /* a CUDA runtime call failed                   */
+    TMPC_ERR_OOM = 3,           /* workspace allocation failed in tmpc_setup    */
+    TMPC_ERR_NOT_SETUP = 4,     /* backward without a matching solve, etc.      */
+    TMPC_ERR_UNSUPPORTED = 5    /* model/dims combination not compiled in       */
+} tmpc_status;
+
+/* per-instance status values written by tmpc_solve / tmpc_backward */
+enum {
+    TMPC_INST_OK = 0,         /* final SQP KKT residual (Eq. sqp_stop) <= eps_c   */
+    TMPC_INST_MAX_ITER = 1,   /* iteration caps reached before eps_c             */
+    TMPC_INST_NOT_PD = 2,     /* a pivot block of S was not positive definite    */
+    TMPC_INST_NAN = 3         /* a non-finite value appeared                     */
+};
+
+/* model ids (problem families; see the design doc for their equations) */
+enum {
+    TMPC_MODEL_DOUBLE_INTEGRATOR = 0, /* nx=4 nu=2 ng=4, ZOH.  dyn = [dt]                          */
+    TMPC_MODEL_LINEAR = 1,            /* layout nx, nu, ng=nu; x+ = A x + B u.  dyn = [A, B]      */
+    TMPC_MODEL_BICYCLE = 2,           /* nx=6 nu=2 ng=5, implicit midpoint.  dyn = [dt, L, ds, nt] */
+    TMPC_MODEL_QUADROTOR = 3          /* nx=6 nu=2 ng=2, RK4.  dyn = [dt, m, I, arm, g]            */
+};
+
+/* number of floats per instance in tmpc_solution.stats */
+#define TMPC_STATS 8
+/* stats[0] SQP iterations, [1] ADMM iterations (total), [2] r_prim and [3] r_dual of
+ * the last QP (Eq. admm:residuals), [4] final rho_bar, [5] factorisations of S,
+ * [6] KKT residual of Eq. (sqp_stop) at the returned point, [7] last line-search step. */
+
+typedef struct {
+    int32_t batch;   /* B >= 1                                                     */
+    int32_t N_max;   /* layout horizon; stage arrays hold N_max+1 stages           */
+    int32_t nx, nu;  /* layout state / control sizes                               */
+    int32_t ng;      /* layout inequality rows per stage                           */
+    int32_t n_dyn;   /* floats of dynamics parameters per instance                 */
+    int32_t n_track; /* centreline table intervals per instance (0 = no table)     */
+} tmpc_dims;
+
+typedef struct {
+    /* ADMM (Section III-B): sigma, initial rho_bar, rho_bar clip range, over-relaxation */
+    float sigma, rho0, rho_min, rho_max, alpha;
+    /* termination (Eq. admm:termination:slack), SQP stop (Eq. sqp_stop), active-set tolerance */
+    float eps_abs, eps_rel, eps_c, eps_g;
+    float ls_eta;        /* Armijo constant of Appendix D                             */
+    int32_t k_rho_iter;  /* rho_bar is re-evaluated every k_rho_iter ADMM iterations  */
+    float k_rho_ratio;   /* ... and accepted if it changes by more than this factor   */
+    int32_t max_sqp, max_admm;
+    int32_t n_ls;        /* line-search candidates alpha = 2^-k, k < n_ls (<= 16)     */
+    int32_t newton_steps;/* Newton steps per stage of the implicit initial rollout    */
+    int32_t early_exit;  /* 1: stop ADMM / SQP when converged; 0: fixed counts        */
+    int32_t check_every; /* ADMM termination test period when early_exit              */
+    /* backward: regularised-KKT refinement (see tmpc_backward) */
+    float bwd_rho, bwd_sigma;
+    int32_t bwd_iters;
+    int32_t threads;     /* CTA size per instance (0 = automatic)                     */
+    int32_t solver;      /* 0 automatic, 1 sequential block LDL', 2 block cyclic reduction */
+} tmpc_options;
+
+/* Problem parameters theta (the OCP of Appendix A with the cost of Eq. (cost)).
+ * All DEVICE pointers, layout as in the header comment; optional ones may be NULL
+ * (treated as zeros; gamma2 NULL = every row hard).
+ *   N [B], model [B]                           horizon and model id of each instance
+ *   Qd [B][Nmax+1][nx], Rd [B][Nmax+1][nu]     diagonal cost weights (row N: terminal)
+ *   Wd [B][nu]                                 control-rate weights (optional)
+ *   ref [B][Nmax+1][nx+nu]                     reference (x_ref, u_ref) (optional)
+ *   lin [B][Nmax+1][nx+nu]                     linear cost term (optional)
+ *   lo, hi [B][Nmax+1][ng]                     bounds of g_t; +-inf = no bound
+ *   gamma2, gamma1 [B][ng]                     L2 / L1 slack weights; gamma2 = +inf: hard row
+ *   dyn [B][n_dyn]                             model parameters
+ *   track [B][n_track+1][4]                    centreline table (x_c, y_c, psi_c, kappa) */
+typedef struct {
+    const int32_t* N;
+    const int32_t* model;
+    const float* Qd;
+    const float* Rd;
+    const float* Wd;
+    const float* ref;
+    const float* lin;
+    const float* lo;
+    const float* hi;
+    const float* gamma2;
+    const float* gamma1;
+    const float* dyn;
+    const float* track;
+} tmpc_params;
+
+/* Solution (z, xi, y) of Algorithm 1 and per-instance diagnostics; DEVICE pointers.
+ *   z [B][Nmax+1][nx+nu]   primal stage vectors
+ *   xi [B][Nmax+1][ng]     slacks (0 on hard rows)
+ *   y_eq [B][Nmax+1][nx]   multipliers of x_0 = x_init (row 0) and f_{t} = 0 (row t+1)
+ *   y_ineq [B][Nmax+1][ng] multipliers of the inequality rows (>0: upper side active)
+ *   status [B], stats [B][TMPC_STATS] (may be NULL) */
+typedef struct {
+    float* z;
+    float* xi;
+    float* y_eq;
+    float* y_ineq;
+    int32_t* status;
+    float* stats;
+} tmpc_solution;
+
+/* Gradients of a scalar loss with respect to the parameters (same layouts as the
+ * parameters; any pointer may be NULL to skip that gradient). */
+typedef struct {
+    float* x0;      /* [B][nx]   */
+    float* Qd;
+    float* Rd;
+    float* Wd;
+    float* ref;
+    float* lin;
+    float* lo;
+    float* hi;
+    float* gamma2;
+    float* gamma1;
+} tmpc_grads;
+
+typedef struct tmpc_handle tmpc_handle;
+
+/* Default options: sigma 1e-6, rho0 0.1, rho in [1e-6, 1e6], alpha 1.6,
+ * eps 1e-5, eps_g 1e-4, eta 0.4, k_rho 25 / ratio 5 (Section III-B), 1 SQP step,
+ * 200 ADMM iterations, 8 line-search candidates, 3 Newton steps. */
+void tmpc_default_options(tmpc_options* o);
+
+/* Create a solver for the given layout and options and the parameter arrays p.
+ * Allocates the whole workspace (stage blocks, factors of S, iterates) once;
+ * later calls never allocate.  Reads p->N and p->model back to the host once
+ * (synchronous) to order the work queue.  On failure *h is set to NULL.
+ * Errors: INVALID_ARG (null h/d/o/p or inconsistent dims), OOM, CUDA, UNSUPPORTED. */
+tmpc_status tmpc_setup(tmpc_handle** h, const tmpc_dims* d, const tmpc_options* o,
+                       const tmpc_params* p);
+
+/* Replace the parameter pointers (same layout, N and model values unchanged). */
+tmpc_status tmpc_update_params(tmpc_handle* h, const tmpc_params* p);
+
+/* Replace the options (same layout). */
+tmpc_status tmpc_set_options(tmpc_handle* h, const tmpc_options* o);
+
+/* Forward pass (Algorithm 1): solve every instance from x0 [B][nx] (DEVICE).
+ * If warm_start != 0, out->z, out->xi, out->y_eq and out->y_ineq are read as
+ * the initial primal-dual guess; otherwise the guess is the Newton rollout of
+ * the reference controls.  The handle keeps nothing the caller needs: the
+ * backward pass takes the solution arrays explicitly. */
+tmpc_status tmpc_solve(tmpc_handle* h, const float* x0, tmpc_solution* out,
+                       int32_t warm_start, void* stream);
+
+/* Backward pass (Algorithm 2) at the solution sol (DEVICE arrays as written by
+ * tmpc_solve for the same parameters and x0): given dL/dz [B][Nmax+1][nx+nu]
+ * and optionally dL/dxi [B][Nmax+1][ng] (NULL = 0), writes the requested
+ * gradients.  The active-set KKT system of Eq. (bwd:slack_reduced_system) is
+ * solved by iterative refinement preconditioned with the regularised
+ * block-tridiagonal matrix H + sigma_b I + rho_b (df'df + dgA'dgA) + gamma dgS'dgS,
+ * factored by the same block factorisation as the forward S (bwd_iters sweeps).
+ * The Hessian is the cost Hessian (the paper's Hessian approximation); it is
+ * exact for linear dynamics.  sol->status receives per-instance flags
+ * (NOT_PD / NAN) if non-NULL. */
+tmpc_status tmpc_backward(tmpc_handle* h, const float* x0, const tmpc_solution* sol,
+                          const float* dL_dz, const float* dL_dxi, tmpc_grads* g,
+                          void* stream);
+
+/* End-to-end forward pass from HOST memory: copies the parameter arrays of
+ * host_p and x0 (HOST pointers, pinned memory recommended) into device
+ * buffers owned by the handle, solves, copies z, xi, y_eq, y_ineq, status and
+ * stats back into the HOST arrays of host_out, and synchronises the stream
+ * before returning.  The handle's device parameter pointers are not changed. */
+tmpc_status tmpc_solve_host(tmpc_handle* h, const tmpc_params* host_p, const float* x0,
+                            tmpc_solution* host_out, void* stream);
+
+/* Free the handle and its workspace (synchronises its allocations). NULL is a no-op. */
+void tmpc_destroy(tmpc_handle* h);
+
+/* Static description of a status code. */
+const char* tmpc_status_string(tmpc_status s);
+
+/* Last CUDA error text seen by the library on this thread (for TMPC_ERR_CUDA). */
+const char* tmpc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TMPC_H */

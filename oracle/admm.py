@@ -135,6 +135,7 @@ def admm(qp, opts, x, zg, yf, yg, rho_bar, rho_schedule=None):
     rho_events = []
     converged = False
     r_prim = r_dual = math.inf
+    pn = dn = 0.0
     k = 0
     for k in range(1, opts.max_admm + 1):
         rho_f, rho_g = 1e3 * rho_bar, rho_bar
@@ -176,5 +177,5 @@ def admm(qp, opts, x, zg, yf, yg, rho_bar, rho_schedule=None):
                         refactors += 1
                         rho_events.append((k, rho_bar))
     return dict(x=x, zg=zg, xi=xi, yf=yf, yg=yg, rho_bar=rho_bar, iters=k,
-                r_prim=r_prim, r_dual=r_dual, refactors=refactors, converged=converged,
-                rho_events=rho_events)
+                r_prim=r_prim, r_dual=r_dual, prim_norm=pn, dual_norm=dn, refactors=refactors,
+                converged=converged, rho_events=rho_events)

@@ -229,18 +229,18 @@ def constraints(inst, z):
         G[:, 0, 6] = G[:, 1, 7] = 1.0
         return g, G
     if model == MODEL_BICYCLE:
-        # rows: accel, steer rate, speed, lateral error e(px, py, s)
+        # rows: accel, steer rate, speed, steering angle, lateral error e(px, py, s)
         tab, dsk = inst["track"], inst["dyn"][2]
         px, py, s = z[:, 0], z[:, 1], z[:, 5]
         xc, yc, psic, dxc, dyc, dpsic = track_eval(tab, dsk, s)
         sp, cp = np.sin(psic), np.cos(psic)
         e = -(px - xc) * sp + (py - yc) * cp
         de_ds = dxc * sp - dyc * cp - dpsic * ((px - xc) * cp + (py - yc) * sp)
-        g = np.stack([z[:, 6], z[:, 7], z[:, 3], e], axis=1)
-        G[:, 0, 6] = G[:, 1, 7] = G[:, 2, 3] = 1.0
-        G[:, 3, 0] = -sp
-        G[:, 3, 1] = cp
-        G[:, 3, 5] = de_ds
+        g = np.stack([z[:, 6], z[:, 7], z[:, 3], z[:, 4], e], axis=1)
+        G[:, 0, 6] = G[:, 1, 7] = G[:, 2, 3] = G[:, 3, 4] = 1.0
+        G[:, 4, 0] = -sp
+        G[:, 4, 1] = cp
+        G[:, 4, 5] = de_ds
         return g, G
     raise ValueError(model)
 

@@ -175,5 +175,6 @@ def solve(inst, opts, warm=None, replay=None, record=False):
             break
     kkt, parts = kkt_residual(inst, z, xi, yf, yg)
     stats = dict(sqp_iters=len(hist), admm_iters=admm_iters, r_prim=last["r_prim"],
-                 r_dual=last["r_dual"], rho_bar=rho_bar, refactors=refactors, kkt=kkt, **parts)
+                 r_dual=last["r_dual"], prim_norm=last["prim_norm"], dual_norm=last["dual_norm"],
+                 rho_bar=rho_bar, refactors=refactors, kkt=kkt, **parts)
     return dict(z=z, xi=xi, yf=yf, yg=yg, rho_bar=rho_bar, stats=stats, history=hist)

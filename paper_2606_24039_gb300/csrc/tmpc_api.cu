@@ -1,0 +1,585 @@
+// C-ABI implementation (include/tmpc.h): handle, workspace, validation, and the
+// fused persistent solve kernel (Algorithm 1 around Algorithm 3, one CTA per
+// instance, instances popped from a device work queue in longest-first order).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "../../include/tmpc.h"
+#include "tmpc_backward.cuh"
+#include "tmpc_solver.cuh"
+
+using namespace tmpc;
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+void set_err(const char* what, cudaError_t e) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define TMPC_CUDA(call)                                  \
+    do {                                                 \
+        cudaError_t _e = (call);                         \
+        if (_e != cudaSuccess) {                         \
+            set_err(#call, _e);                          \
+            return TMPC_ERR_CUDA;                        \
+        }                                                \
+    } while (0)
+
+__device__ __forceinline__ Smem carve_smem(void* raw, int n) {
+    Smem s;
+    char* p = reinterpret_cast<char*>(raw);
+    s.redd = reinterpret_cast<double*>(p);            p += 32 * 2 * sizeof(double);
+    s.lsacc = reinterpret_cast<double*>(p);           p += 2 * (kMaxLs + 1) * sizeof(double) + 16;
+    s.red = reinterpret_cast<float*>(p);              p += 32 * 8 * sizeof(float);
+    s.flags = reinterpret_cast<int*>(p);              p += 16 * sizeof(int);
+    s.A = reinterpret_cast<float*>(p);                p += n * n * sizeof(float);
+    s.Bm = reinterpret_cast<float*>(p);               p += n * n * sizeof(float);
+    s.Cm = reinterpret_cast<float*>(p);
+    return s;
+}
+
+size_t smem_bytes(int n) {
+    return 32 * 2 * sizeof(double) + 2 * (kMaxLs + 1) * sizeof(double) + 16 + 32 * 8 * sizeof(float) +
+           16 * sizeof(int) + 3 * (size_t)n * n * sizeof(float);
+}
+
+__device__ Ctx make_ctx(const KLayout& L, const KParams& p, float* ws, const WsOff& off, int i,
+                        const float* x0) {
+    Ctx c;
+    c.model = p.model[i];
+    const ModelDims md = model_dims(c.model, L.nx, L.nu, L.ng);
+    c.nx = md.nx; c.nu = md.nu; c.ng = md.ng; c.n = md.nx + md.nu;
+    c.N = p.N[i];
+    c.T = c.N + 1;
+    c.lnx = L.nx; c.lnu = L.nu; c.ln = L.n; c.lng = L.ng;
+    const long long Ts = L.Nmax + 1;
+    c.x0 = x0 + (long long)i * L.nx;
+    c.Qd = p.Qd + i * Ts * L.nx;
+    c.Rd = p.Rd + i * Ts * L.nu;
+    c.Wd = p.Wd ? p.Wd + (long long)i * L.nu : nullptr;
+    c.ref = p.ref ? p.ref + i * Ts * L.n : nullptr;
+    c.lin = p.lin ? p.lin + i * Ts * L.n : nullptr;
+    c.lo = p.lo + i * Ts * L.ng;
+    c.hi = p.hi + i * Ts * L.ng;
+    c.g2 = p.g2 ? p.g2 + (long long)i * L.ng : nullptr;
+    c.g1 = p.g1 ? p.g1 + (long long)i * L.ng : nullptr;
+    c.dyn = p.dyn + (long long)i * L.n_dyn;
+    c.track = p.track ? p.track + (long long)i * (L.n_track + 1) * 4 : nullptr;
+    if (c.model == MODEL_BICYCLE) {  // table intervals, clamped to the layout's table size
+        const float ntf = c.dyn[3];
+        int nt = (ntf == ntf) ? (int)fminf(fmaxf(ntf + 0.5f, 1.f), (float)L.n_track) : 1;
+        c.nt = nt < 1 ? 1 : nt;
+    } else {
+        c.nt = 0;
+    }
+    float* b = ws + (long long)i * off.stride;
+    c.Am = b + off.Am; c.Ap = b + off.Ap; c.cv = b + off.cv; c.fv = b + off.fv; c.Gm = b + off.Gm;
+    c.gv = b + off.gv; c.glo = b + off.glo; c.ghi = b + off.ghi; c.qv = b + off.qv;
+    c.Dinv = b + off.Dinv; c.Om = b + off.Om; c.x = b + off.x; c.xt = b + off.xt; c.eta = b + off.eta;
+    c.zg = b + off.zg; c.yg = b + off.yg; c.xi = b + off.xi; c.yf = b + off.yf; c.zb = b + off.zb;
+    c.xib = b + off.xib; c.yfb = b + off.yfb; c.ygb = b + off.ygb; c.gw = b + off.gw;
+    c.czb = b + off.czb; c.gzb = b + off.gzb; c.pf = b + off.pf; c.pg = b + off.pg;
+    c.amS = model_const_Am(c.model) ? 0 : c.nx * c.n;
+    c.apS = model_const_Ap(c.model) ? 0 : c.nx * c.n;
+    c.gS = model_const_G(c.model) ? 0 : c.ng * c.n;
+    return c;
+}
+
+__device__ void write_solution(const Ctx& c, const KLayout& L, const KSol& out, int i) {
+    const long long Ts = L.Nmax + 1;
+    float* z = out.z + i * Ts * L.n;
+    float* xi = out.xi + i * Ts * L.ng;
+    float* yf = out.yf + i * Ts * L.nx;
+    float* yg = out.yg + i * Ts * L.ng;
+    for (int e = threadIdx.x; e < Ts * L.n; e += blockDim.x) {
+        const int t = e / L.n, j = e % L.n;
+        z[e] = (t < c.T && j < c.n) ? c.zb[t * c.n + j] : 0.f;
+    }
+    for (int e = threadIdx.x; e < Ts * L.ng; e += blockDim.x) {
+        const int t = e / L.ng, r = e % L.ng;
+        const bool ok = t < c.T && r < c.ng;
+        xi[e] = ok ? c.xib[t * c.ng + r] : 0.f;
+        yg[e] = ok ? c.ygb[t * c.ng + r] : 0.f;
+    }
+    for (int e = threadIdx.x; e < Ts * L.nx; e += blockDim.x) {
+        const int t = e / L.nx, k = e % L.nx;
+        yf[e] = (t < c.T && k < c.nx) ? c.yfb[t * c.nx + k] : 0.f;
+    }
+}
+
+__device__ void solve_instance(const Ctx& c, const KOpts& o, const Smem& sm, const KLayout& L,
+                               const KSol& out, int inst, int warm) {
+    const int n = c.n, nx = c.nx, ng = c.ng, T = c.T;
+    if (threadIdx.x == 0) sm.flags[0] = 0;
+    if (warm) {
+        read_warm(c, L, out, inst);
+    } else {
+        rollout(c, o);
+        for (int e = threadIdx.x; e < T * ng; e += blockDim.x) { c.xib[e] = 0.f; c.ygb[e] = 0.f; }
+        for (int e = threadIdx.x; e < T * nx; e += blockDim.x) c.yfb[e] = 0.f;
+        __syncthreads();
+    }
+    float rho = o.rho0, rp = 0.f, rd = 0.f, alpha_last = 1.f;
+    int admm_total = 0, nfact = 0, sqp_done = 0;
+    for (int it = 0; it < o.max_sqp; ++it) {
+        linearize(c);
+        if (it > 0 && o.early_exit) {
+            const float kk = kkt(c, sm);
+            if (kk <= o.eps_c) break;
+        }
+        ++nfact;
+        if (!factor(c, sm, o.sigma, 1e3f * rho, rho, false) && threadIdx.x == 0) sm.flags[0] = 1;
+        // warm start of the QP from the current primal-dual point (x = zb, z_g = G zb),
+        // i.e. zero step, with the equality defect p_f = C x - c = -cv
+        for (int e = threadIdx.x; e < T * n; e += blockDim.x) c.x[e] = 0.f;
+        for (int e = threadIdx.x; e < T * nx; e += blockDim.x) {
+            c.yf[e] = c.yfb[e];
+            c.pf[e] = -c.cv[e];
+        }
+        for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
+            c.yg[e] = c.ygb[e];
+            c.zg[e] = 0.f;
+            c.xi[e] = 0.f;
+        }
+        __syncthreads();
+        int k = 0;
+        for (k = 1; k <= o.max_admm; ++k) {
+            admm_iter(c, o, rho);
+            const bool cc = o.early_exit && (k % o.check_every == 0);
+            const bool cr = (k % o.k_rho_iter == 0) && k < o.max_admm;
+            if (cc || cr || k == o.max_admm) {
+                const Res r = residuals(c, sm);
+                rp = r.r_prim;
+                rd = r.r_dual;
+                const bool conv = rp <= o.eps_abs + o.eps_rel * r.pn && rd <= o.eps_abs + o.eps_rel * r.dn;
+                if (cc && conv) break;
+                if (cr && rd > 0.f && !conv) {
+                    const float ratio = (rp / fmaxf(r.pn, 1e-30f)) / fmaxf(rd / fmaxf(r.dn, 1e-30f), 1e-30f);
+                    const float cand = fminf(fmaxf(rho * sqrtf(ratio), o.rho_min), o.rho_max);
+                    if (fmaxf(cand / rho, rho / cand) > o.k_rho_ratio) {
+                        // FP32 safeguard: a rho whose S cannot be factored is rejected
+                        ++nfact;
+                        if (factor(c, sm, o.sigma, 1e3f * cand, cand, false)) {
+                            rho = cand;
+                        } else {
+                            ++nfact;
+                            if (!factor(c, sm, o.sigma, 1e3f * rho, rho, false) && threadIdx.x == 0) sm.flags[0] = 1;
+                        }
+                    }
+                }
+            }
+        }
+        admm_total += (k > o.max_admm) ? o.max_admm : k;
+        // line search on the direction (x* - zb, xi* - xib)
+        float ys[1] = {0.f};
+        for (int e = threadIdx.x; e < T * nx; e += blockDim.x) ys[0] = fmaxf(ys[0], fin(c.yf[e]));
+        for (int e = threadIdx.x; e < T * ng; e += blockDim.x) ys[0] = fmaxf(ys[0], fin(c.yg[e]));
+        cta_max_k<1>(ys, sm.red);
+        const float a = linesearch(c, o, sm, ys[0]);
+        alpha_last = a;
+        for (int e = threadIdx.x; e < T * n; e += blockDim.x) c.zb[e] += a * c.x[e];
+        for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
+            c.xib[e] += a * (c.xi[e] - c.xib[e]);
+            c.ygb[e] += a * (c.yg[e] - c.ygb[e]);
+        }
+        for (int e = threadIdx.x; e < T * nx; e += blockDim.x) c.yfb[e] += a * (c.yf[e] - c.yfb[e]);
+        __syncthreads();
+        ++sqp_done;
+    }
+    linearize(c);
+    const float kk = kkt(c, sm);
+    float bad[1] = {0.f};
+    for (int e = threadIdx.x; e < T * n; e += blockDim.x) bad[0] = fmaxf(bad[0], fin(c.zb[e]));
+    cta_max_k<1>(bad, sm.red);
+    write_solution(c, L, out, inst);
+    if (threadIdx.x == 0) {
+        int st = TMPC_INST_OK;
+        if (!(bad[0] < kInf) || !(kk < kInf)) st = TMPC_INST_NAN;
+        else if (sm.flags[0]) st = TMPC_INST_NOT_PD;
+        else if (!(kk <= o.eps_c)) st = TMPC_INST_MAX_ITER;
+        if (out.status) out.status[inst] = st;
+        if (out.stats) {
+            float* s = out.stats + (long long)inst * TMPC_STATS;
+            s[0] = (float)sqp_done; s[1] = (float)admm_total; s[2] = rp; s[3] = rd;
+            s[4] = rho; s[5] = (float)nfact; s[6] = kk; s[7] = alpha_last;
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256, 2) solve_kernel(KLayout L, KOpts o, KParams p, KSol out, float* ws, WsOff off,
+                             const int* order, int* queue, const float* x0, int warm) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    const Smem sm = carve_smem(smem_raw, L.n);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int q = s_item;
+        __syncthreads();
+        if (q >= L.B) break;
+        const int i = order[q];
+        const Ctx c = make_ctx(L, p, ws, off, i, x0);
+        solve_instance(c, o, sm, L, out, i, warm);
+    }
+}
+
+__global__ void __launch_bounds__(256, 2) backward_kernel(KLayout L, KOpts o, KParams p, KSol sol, float* ws, WsOff off,
+                                const int* order, int* queue, const float* x0, const float* dLdz,
+                                const float* dLdxi, KGrads g) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    const Smem sm = carve_smem(smem_raw, L.n);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int q = s_item;
+        __syncthreads();
+        if (q >= L.B) break;
+        const int i = order[q];
+        const Ctx c = make_ctx(L, p, ws, off, i, x0);
+        backward_instance(c, o, sm, L, sol, i, dLdz, dLdxi, g);
+    }
+}
+
+KOpts to_kopts(const tmpc_options& o) {
+    KOpts k;
+    k.sigma = o.sigma; k.rho0 = o.rho0; k.rho_min = o.rho_min; k.rho_max = o.rho_max; k.alpha = o.alpha;
+    k.eps_abs = o.eps_abs; k.eps_rel = o.eps_rel; k.eps_c = o.eps_c; k.eps_g = o.eps_g; k.ls_eta = o.ls_eta;
+    k.k_rho_iter = o.k_rho_iter; k.k_rho_ratio = o.k_rho_ratio; k.max_sqp = o.max_sqp; k.max_admm = o.max_admm;
+    k.n_ls = o.n_ls; k.newton_steps = o.newton_steps; k.early_exit = o.early_exit;
+    k.check_every = o.check_every < 1 ? 1 : o.check_every;
+    k.bwd_rho = o.bwd_rho; k.bwd_sigma = o.bwd_sigma; k.bwd_iters = o.bwd_iters;
+    if (k.k_rho_iter < 1) k.k_rho_iter = 1 << 30;
+    return k;
+}
+
+KParams to_kparams(const tmpc_params& p) {
+    KParams k;
+    k.N = p.N; k.model = p.model; k.x0 = nullptr; k.Qd = p.Qd; k.Rd = p.Rd; k.Wd = p.Wd; k.ref = p.ref;
+    k.lin = p.lin; k.lo = p.lo; k.hi = p.hi; k.g2 = p.gamma2; k.g1 = p.gamma1; k.dyn = p.dyn;
+    k.track = p.track;
+    return k;
+}
+
+int align4(long long v) { return (int)((v + 3) & ~3LL); }
+
+}  // namespace
+
+struct tmpc_handle {
+    tmpc_dims d;
+    tmpc_options o;
+    tmpc_params p;
+    KLayout L;
+    WsOff off;
+    float* ws = nullptr;
+    int* order = nullptr;
+    int* queue = nullptr;
+    int nsm = 0;
+    int threads = 128;
+    size_t smem = 0;
+    int grid_solve = 1, grid_bwd = 1;
+    // staging for tmpc_solve_host
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    tmpc_params sp{};
+    float* s_x0 = nullptr;
+    tmpc_solution ss{};
+};
+
+extern "C" {
+
+void tmpc_default_options(tmpc_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->sigma = 1e-6f; o->rho0 = 0.1f; o->rho_min = 1e-6f; o->rho_max = 1e6f; o->alpha = 1.6f;
+    o->eps_abs = 1e-5f; o->eps_rel = 1e-5f; o->eps_c = 1e-5f; o->eps_g = 1e-4f; o->ls_eta = 0.4f;
+    o->k_rho_iter = 25; o->k_rho_ratio = 5.f; o->max_sqp = 1; o->max_admm = 200; o->n_ls = 8;
+    o->newton_steps = 3; o->early_exit = 0; o->check_every = 25;
+    o->bwd_rho = 1e3f; o->bwd_sigma = 1e-6f; o->bwd_iters = 12;
+    o->threads = 0; o->solver = 0;
+}
+
+const char* tmpc_status_string(tmpc_status s) {
+    switch (s) {
+        case TMPC_OK: return "ok";
+        case TMPC_ERR_INVALID_ARG: return "invalid argument";
+        case TMPC_ERR_CUDA: return "CUDA error";
+        case TMPC_ERR_OOM: return "out of device memory";
+        case TMPC_ERR_NOT_SETUP: return "not set up";
+        case TMPC_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* tmpc_last_error(void) { return g_last_error; }
+
+static tmpc_status check_options(const tmpc_options* o) {
+    if (!(o->sigma > 0.f) || !(o->rho0 > 0.f) || !(o->alpha > 0.f && o->alpha < 2.f)) return TMPC_ERR_INVALID_ARG;
+    if (o->max_sqp < 0 || o->max_admm < 1 || o->n_ls < 1 || o->n_ls > kMaxLs) return TMPC_ERR_INVALID_ARG;
+    if (o->newton_steps < 0 || o->bwd_iters < 1 || !(o->bwd_rho > 0.f)) return TMPC_ERR_INVALID_ARG;
+    if (o->threads < 0 || o->threads > 1024 || (o->threads % 32) != 0) return TMPC_ERR_INVALID_ARG;
+    return TMPC_OK;
+}
+
+static bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3u) == 0; }
+
+static tmpc_status check_params(const tmpc_dims& d, const tmpc_params* p) {
+    if (!p || !p->N || !p->model || !p->Qd || !p->Rd || !p->lo || !p->hi || !p->dyn) return TMPC_ERR_INVALID_ARG;
+    const void* ptrs[] = {p->N, p->model, p->Qd, p->Rd, p->Wd, p->ref, p->lin, p->lo, p->hi,
+                          p->gamma2, p->gamma1, p->dyn, p->track};
+    for (const void* q : ptrs)
+        if (q && !aligned4(q)) return TMPC_ERR_INVALID_ARG;
+    if (d.n_track > 0 && !p->track) return TMPC_ERR_INVALID_ARG;
+    return TMPC_OK;
+}
+
+tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options* o, const tmpc_params* p) {
+    if (!hp) return TMPC_ERR_INVALID_ARG;
+    *hp = nullptr;
+    if (!d || !o || !p) return TMPC_ERR_INVALID_ARG;
+    if (d->batch < 1 || d->N_max < 1 || d->nx < 1 || d->nu < 1 || d->ng < 1 || d->n_dyn < 1 ||
+        d->n_track < 0)
+        return TMPC_ERR_INVALID_ARG;
+    const int n = d->nx + d->nu;
+    if (n > 72 || d->nx > 64 || d->ng > 64) return TMPC_ERR_UNSUPPORTED;
+    if (check_options(o) != TMPC_OK || check_params(*d, p) != TMPC_OK) return TMPC_ERR_INVALID_ARG;
+
+    std::vector<int> Nh(d->batch), Mh(d->batch);
+    TMPC_CUDA(cudaMemcpy(Nh.data(), p->N, sizeof(int) * d->batch, cudaMemcpyDeviceToHost));
+    TMPC_CUDA(cudaMemcpy(Mh.data(), p->model, sizeof(int) * d->batch, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < d->batch; ++i) {
+        if (Nh[i] < 1 || Nh[i] > d->N_max) return TMPC_ERR_INVALID_ARG;
+        if (Mh[i] < 0 || Mh[i] > 3) return TMPC_ERR_INVALID_ARG;
+        const ModelDims md = model_dims(Mh[i], d->nx, d->nu, d->ng);
+        if (md.nx > d->nx || md.nu > d->nu || md.ng > d->ng) return TMPC_ERR_INVALID_ARG;
+        if (Mh[i] == MODEL_LINEAR && (d->n_dyn < d->nx * d->nx + d->nx * d->nu || d->ng > d->nu))
+            return TMPC_ERR_INVALID_ARG;
+        if (Mh[i] == MODEL_BICYCLE && (d->n_track < 1 || d->n_dyn < 4)) return TMPC_ERR_INVALID_ARG;
+        if (Mh[i] == MODEL_QUAD && d->n_dyn < 5) return TMPC_ERR_INVALID_ARG;
+    }
+
+    tmpc_handle* h = new (std::nothrow) tmpc_handle();
+    if (!h) return TMPC_ERR_OOM;
+    h->d = *d;
+    h->o = *o;
+    h->p = *p;
+    KLayout& L = h->L;
+    L.B = d->batch; L.Nmax = d->N_max; L.nx = d->nx; L.nu = d->nu; L.ng = d->ng; L.n = n;
+    L.n_dyn = d->n_dyn; L.n_track = d->n_track;
+    const long long T = d->N_max + 1, Nm = d->N_max;
+    const long long nxn = (long long)d->nx * n, nn = (long long)n * n;
+    long long cur = 0;
+    auto take = [&](long long cnt) { int at = align4(cur); cur = at + cnt; return at; };
+    WsOff& off = h->off;
+    off.Am = take(std::max(Nm, 1LL) * nxn);
+    off.Ap = take(std::max(Nm, 1LL) * nxn);
+    off.cv = take(T * d->nx);
+    off.fv = take(T * d->nx);
+    off.Gm = take(T * d->ng * n);
+    off.gv = take(T * d->ng);
+    off.glo = take(T * d->ng);
+    off.ghi = take(T * d->ng);
+    off.qv = take(T * n);
+    off.Dinv = take(T * nn);
+    off.Om = take(std::max(Nm, 1LL) * nn);
+    off.x = take(T * n);
+    off.xt = take(T * n);
+    off.eta = take(T * n);
+    off.zg = take(T * d->ng);
+    off.yg = take(T * d->ng);
+    off.xi = take(T * d->ng);
+    off.yf = take(T * d->nx);
+    off.zb = take(T * n);
+    off.xib = take(T * d->ng);
+    off.yfb = take(T * d->nx);
+    off.ygb = take(T * d->ng);
+    off.gw = take(T * d->ng);
+    off.czb = take(T * d->nx);
+    off.gzb = take(T * d->ng);
+    off.pf = take(T * d->nx);
+    off.pg = take(T * d->ng);
+    off.stride = align4(cur);
+
+    cudaError_t e = cudaMalloc(&h->ws, sizeof(float) * off.stride * d->batch);
+    if (e != cudaSuccess) { set_err("cudaMalloc(workspace)", e); delete h; return TMPC_ERR_OOM; }
+    e = cudaMalloc(&h->order, sizeof(int) * (d->batch + 2));
+    if (e != cudaSuccess) { set_err("cudaMalloc(order)", e); tmpc_destroy(h); return TMPC_ERR_OOM; }
+    h->queue = h->order + d->batch;
+    // longest-processing-time-first order of the work queue: (N+1) n^2 work estimate
+    std::vector<int> ord(d->batch);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+        const ModelDims ma = model_dims(Mh[a], d->nx, d->nu, d->ng), mb = model_dims(Mh[b], d->nx, d->nu, d->ng);
+        const long long wa = (long long)(Nh[a] + 1) * (ma.nx + ma.nu) * (ma.nx + ma.nu);
+        const long long wb = (long long)(Nh[b] + 1) * (mb.nx + mb.nu) * (mb.nx + mb.nu);
+        return wa > wb;
+    });
+    e = cudaMemcpy(h->order, ord.data(), sizeof(int) * d->batch, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { set_err("cudaMemcpy(order)", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
+
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
+    h->threads = o->threads > 0 ? o->threads : (n <= 16 ? 128 : 256);
+    h->smem = smem_bytes(n);
+    if (h->smem > 48 * 1024) {
+        cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
+        cudaFuncSetAttribute(backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
+    }
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel, h->threads, h->smem);
+    h->grid_solve = std::max(1, std::min(d->batch, std::max(per_sm, 1) * h->nsm));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backward_kernel, h->threads, h->smem);
+    h->grid_bwd = std::max(1, std::min(d->batch, std::max(per_sm, 1) * h->nsm));
+
+    // staging buffers of the host-memory entry point (allocated once here)
+    const long long B = d->batch;
+    const size_t sz[] = {
+        sizeof(int) * B, sizeof(int) * B,                                  // N, model
+        sizeof(float) * B * T * d->nx, sizeof(float) * B * T * d->nu,      // Qd, Rd
+        sizeof(float) * B * d->nu,                                          // Wd
+        sizeof(float) * B * T * n, sizeof(float) * B * T * n,               // ref, lin
+        sizeof(float) * B * T * d->ng, sizeof(float) * B * T * d->ng,       // lo, hi
+        sizeof(float) * B * d->ng, sizeof(float) * B * d->ng,               // gamma2, gamma1
+        sizeof(float) * B * d->n_dyn,                                       // dyn
+        sizeof(float) * B * (d->n_track + 1) * 4,                           // track
+        sizeof(float) * B * d->nx,                                          // x0
+        sizeof(float) * B * T * n, sizeof(float) * B * T * d->ng,           // z, xi
+        sizeof(float) * B * T * d->nx, sizeof(float) * B * T * d->ng,       // y_eq, y_ineq
+        sizeof(int) * B, sizeof(float) * B * TMPC_STATS};                   // status, stats
+    size_t tot = 0;
+    size_t offs[20];
+    for (int k = 0; k < 20; ++k) { offs[k] = tot; tot += (sz[k] + 255) & ~size_t(255); }
+    e = cudaMalloc(&h->stage, tot);
+    if (e != cudaSuccess) { set_err("cudaMalloc(staging)", e); tmpc_destroy(h); return TMPC_ERR_OOM; }
+    h->stage_bytes = tot;
+    char* sb = reinterpret_cast<char*>(h->stage);
+    h->sp.N = reinterpret_cast<int*>(sb + offs[0]);
+    h->sp.model = reinterpret_cast<int*>(sb + offs[1]);
+    h->sp.Qd = reinterpret_cast<float*>(sb + offs[2]);
+    h->sp.Rd = reinterpret_cast<float*>(sb + offs[3]);
+    h->sp.Wd = reinterpret_cast<float*>(sb + offs[4]);
+    h->sp.ref = reinterpret_cast<float*>(sb + offs[5]);
+    h->sp.lin = reinterpret_cast<float*>(sb + offs[6]);
+    h->sp.lo = reinterpret_cast<float*>(sb + offs[7]);
+    h->sp.hi = reinterpret_cast<float*>(sb + offs[8]);
+    h->sp.gamma2 = reinterpret_cast<float*>(sb + offs[9]);
+    h->sp.gamma1 = reinterpret_cast<float*>(sb + offs[10]);
+    h->sp.dyn = reinterpret_cast<float*>(sb + offs[11]);
+    h->sp.track = reinterpret_cast<float*>(sb + offs[12]);
+    h->s_x0 = reinterpret_cast<float*>(sb + offs[13]);
+    h->ss.z = reinterpret_cast<float*>(sb + offs[14]);
+    h->ss.xi = reinterpret_cast<float*>(sb + offs[15]);
+    h->ss.y_eq = reinterpret_cast<float*>(sb + offs[16]);
+    h->ss.y_ineq = reinterpret_cast<float*>(sb + offs[17]);
+    h->ss.status = reinterpret_cast<int*>(sb + offs[18]);
+    h->ss.stats = reinterpret_cast<float*>(sb + offs[19]);
+    *hp = h;
+    return TMPC_OK;
+}
+
+tmpc_status tmpc_update_params(tmpc_handle* h, const tmpc_params* p) {
+    if (!h) return TMPC_ERR_NOT_SETUP;
+    if (check_params(h->d, p) != TMPC_OK) return TMPC_ERR_INVALID_ARG;
+    h->p = *p;
+    return TMPC_OK;
+}
+
+tmpc_status tmpc_set_options(tmpc_handle* h, const tmpc_options* o) {
+    if (!h) return TMPC_ERR_NOT_SETUP;
+    if (!o || check_options(o) != TMPC_OK) return TMPC_ERR_INVALID_ARG;
+    if (o->threads != h->o.threads) return TMPC_ERR_INVALID_ARG;  // launch shape is fixed at setup
+    h->o = *o;
+    return TMPC_OK;
+}
+
+static tmpc_status launch_solve(tmpc_handle* h, const tmpc_params& p, const float* x0,
+                                const tmpc_solution& out, int warm, cudaStream_t s) {
+    KSol ks{out.z, out.xi, out.y_eq, out.y_ineq, out.status, out.stats};
+    TMPC_CUDA(cudaMemsetAsync(h->queue, 0, sizeof(int), s));
+    solve_kernel<<<h->grid_solve, h->threads, h->smem, s>>>(h->L, to_kopts(h->o), to_kparams(p), ks, h->ws,
+                                                            h->off, h->order, h->queue, x0, warm);
+    TMPC_CUDA(cudaGetLastError());
+    return TMPC_OK;
+}
+
+tmpc_status tmpc_solve(tmpc_handle* h, const float* x0, tmpc_solution* out, int32_t warm_start, void* stream) {
+    if (!h) return TMPC_ERR_NOT_SETUP;
+    if (!x0 || !out || !out->z || !out->xi || !out->y_eq || !out->y_ineq) return TMPC_ERR_INVALID_ARG;
+    if (!aligned4(x0) || !aligned4(out->z) || !aligned4(out->xi) || !aligned4(out->y_eq) || !aligned4(out->y_ineq))
+        return TMPC_ERR_INVALID_ARG;
+    return launch_solve(h, h->p, x0, *out, warm_start ? 1 : 0, reinterpret_cast<cudaStream_t>(stream));
+}
+
+tmpc_status tmpc_backward(tmpc_handle* h, const float* x0, const tmpc_solution* sol, const float* dL_dz,
+                          const float* dL_dxi, tmpc_grads* g, void* stream) {
+    if (!h) return TMPC_ERR_NOT_SETUP;
+    if (!x0 || !sol || !sol->z || !sol->xi || !sol->y_eq || !sol->y_ineq || !dL_dz || !g) return TMPC_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    KSol ks{sol->z, sol->xi, sol->y_eq, sol->y_ineq, sol->status, sol->stats};
+    KGrads kg{g->x0, g->Qd, g->Rd, g->Wd, g->ref, g->lin, g->lo, g->hi, g->gamma2, g->gamma1};
+    TMPC_CUDA(cudaMemsetAsync(h->queue, 0, sizeof(int), s));
+    backward_kernel<<<h->grid_bwd, h->threads, h->smem, s>>>(h->L, to_kopts(h->o), to_kparams(h->p), ks, h->ws,
+                                                             h->off, h->order, h->queue, x0, dL_dz, dL_dxi, kg);
+    TMPC_CUDA(cudaGetLastError());
+    return TMPC_OK;
+}
+
+tmpc_status tmpc_solve_host(tmpc_handle* h, const tmpc_params* hp, const float* x0, tmpc_solution* ho, void* stream) {
+    if (!h) return TMPC_ERR_NOT_SETUP;
+    if (!hp || !x0 || !ho || !ho->z || !ho->xi || !ho->y_eq || !ho->y_ineq) return TMPC_ERR_INVALID_ARG;
+    if (!hp->N || !hp->model || !hp->Qd || !hp->Rd || !hp->lo || !hp->hi || !hp->dyn) return TMPC_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const tmpc_dims& d = h->d;
+    const long long B = d.batch, T = d.N_max + 1, n = d.nx + d.nu;
+    auto h2d = [&](const void* src, const void* dst, size_t bytes) -> cudaError_t {
+        return cudaMemcpyAsync(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice, s);
+    };
+    tmpc_params dp = h->sp;
+    TMPC_CUDA(h2d(hp->N, dp.N, sizeof(int) * B));
+    TMPC_CUDA(h2d(hp->model, dp.model, sizeof(int) * B));
+    TMPC_CUDA(h2d(hp->Qd, dp.Qd, sizeof(float) * B * T * d.nx));
+    TMPC_CUDA(h2d(hp->Rd, dp.Rd, sizeof(float) * B * T * d.nu));
+    if (hp->Wd) TMPC_CUDA(h2d(hp->Wd, dp.Wd, sizeof(float) * B * d.nu)); else dp.Wd = nullptr;
+    if (hp->ref) TMPC_CUDA(h2d(hp->ref, dp.ref, sizeof(float) * B * T * n)); else dp.ref = nullptr;
+    if (hp->lin) TMPC_CUDA(h2d(hp->lin, dp.lin, sizeof(float) * B * T * n)); else dp.lin = nullptr;
+    TMPC_CUDA(h2d(hp->lo, dp.lo, sizeof(float) * B * T * d.ng));
+    TMPC_CUDA(h2d(hp->hi, dp.hi, sizeof(float) * B * T * d.ng));
+    if (hp->gamma2) TMPC_CUDA(h2d(hp->gamma2, dp.gamma2, sizeof(float) * B * d.ng)); else dp.gamma2 = nullptr;
+    if (hp->gamma1) TMPC_CUDA(h2d(hp->gamma1, dp.gamma1, sizeof(float) * B * d.ng)); else dp.gamma1 = nullptr;
+    TMPC_CUDA(h2d(hp->dyn, dp.dyn, sizeof(float) * B * d.n_dyn));
+    if (hp->track && d.n_track > 0) TMPC_CUDA(h2d(hp->track, dp.track, sizeof(float) * B * (d.n_track + 1) * 4));
+    else dp.track = nullptr;
+    TMPC_CUDA(h2d(x0, h->s_x0, sizeof(float) * B * d.nx));
+    tmpc_solution ds = h->ss;
+    tmpc_status st = launch_solve(h, dp, h->s_x0, ds, 0, s);
+    if (st != TMPC_OK) return st;
+    TMPC_CUDA(cudaMemcpyAsync(ho->z, ds.z, sizeof(float) * B * T * n, cudaMemcpyDeviceToHost, s));
+    TMPC_CUDA(cudaMemcpyAsync(ho->xi, ds.xi, sizeof(float) * B * T * d.ng, cudaMemcpyDeviceToHost, s));
+    TMPC_CUDA(cudaMemcpyAsync(ho->y_eq, ds.y_eq, sizeof(float) * B * T * d.nx, cudaMemcpyDeviceToHost, s));
+    TMPC_CUDA(cudaMemcpyAsync(ho->y_ineq, ds.y_ineq, sizeof(float) * B * T * d.ng, cudaMemcpyDeviceToHost, s));
+    if (ho->status) TMPC_CUDA(cudaMemcpyAsync(ho->status, ds.status, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
+    if (ho->stats)
+        TMPC_CUDA(cudaMemcpyAsync(ho->stats, ds.stats, sizeof(float) * B * TMPC_STATS, cudaMemcpyDeviceToHost, s));
+    TMPC_CUDA(cudaStreamSynchronize(s));
+    return TMPC_OK;
+}
+
+void tmpc_destroy(tmpc_handle* h) {
+    if (!h) return;
+    if (h->ws) cudaFree(h->ws);
+    if (h->order) cudaFree(h->order);
+    if (h->stage) cudaFree(h->stage);
+    delete h;
+}
+
+}  // extern "C"

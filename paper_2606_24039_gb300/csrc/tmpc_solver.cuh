@@ -1,0 +1,870 @@
+// Device side of the batched SQP / ADMM OCP solver: one CTA per instance,
+// CTA-cooperative stage operations, everything resident in the handle's
+// workspace (global memory, L1/L2-cached) with the n x n factorisation
+// scratch in shared memory.
+//
+// Paper map:
+//   linearize()      QP approximation at the SQP iterate (Section III-A, App. B)
+//   factor()         S = P + sigma I + rho_f C'C + G' W G and its block LDL'
+//                    factorisation (Theta_t, Phi_t of App. C), once per SQP
+//                    step and per accepted rho (Section III-E: factor reuse)
+//   admm_iter()      one iteration of Algorithm 3 (eta, S solve, relaxation,
+//                    projection / smoothed projection, dual update)
+//   residuals()      Eq. (admm:residuals) and the normalisers of
+//                    Eq. (admm:termination:slack); rho rule of Eq. (rho:update)
+//   linesearch()     Appendix D (merit, Armijo, candidates in parallel)
+//   kkt()            Eq. (sqp_stop)
+#pragma once
+#include <cuda_runtime.h>
+#include <float.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "tmpc_models.cuh"
+
+namespace tmpc {
+
+struct KOpts {
+    float sigma, rho0, rho_min, rho_max, alpha;
+    float eps_abs, eps_rel, eps_c, eps_g, ls_eta;
+    int k_rho_iter;
+    float k_rho_ratio;
+    int max_sqp, max_admm, n_ls, newton_steps, early_exit, check_every;
+    float bwd_rho, bwd_sigma;
+    int bwd_iters;
+};
+
+struct KLayout {
+    int B, Nmax, nx, nu, ng, n, n_dyn, n_track;
+};
+
+struct KParams {
+    const int* N;
+    const int* model;
+    const float* x0;
+    const float *Qd, *Rd, *Wd, *ref, *lin, *lo, *hi, *g2, *g1, *dyn, *track;
+};
+
+struct KSol {
+    float *z, *xi, *yf, *yg;
+    int* status;
+    float* stats;
+};
+
+// offsets (in floats) of the per-instance workspace arrays; slot = stride floats
+struct WsOff {
+    long long stride;
+    int Am, Ap, cv, fv, Gm, gv, glo, ghi, qv, Dinv, Om, x, xt, eta, zg, yg, xi, yf, zb, xib, yfb, ygb, gw, czb, gzb, pf, pg;
+};
+
+#define kInf __int_as_float(0x7f800000)
+constexpr int kMaxLs = 16;
+
+// shared-memory scratch of one CTA
+struct Smem {
+    float* A;      // n*n
+    float* Bm;     // n*n
+    float* Cm;     // n*n
+    float* red;    // 32*8 floats
+    double* redd;  // 32*2 doubles
+    double* lsacc; // 2*kMaxLs doubles
+    int* flags;    // 4 ints
+};
+
+struct Ctx {
+    int N, T, nx, nu, n, ng, model, nt;
+    int lnx, lnu, ln, lng;
+    const float *x0, *Qd, *Rd, *Wd, *ref, *lin, *lo, *hi, *g2, *g1, *dyn, *track;
+    float *Am, *Ap, *cv, *fv, *Gm, *gv, *glo, *ghi, *qv, *Dinv, *Om, *x, *xt, *eta, *zg, *yg, *xi, *yf;
+    float *zb, *xib, *yfb, *ygb, *gw, *czb, *gzb, *pf, *pg;
+    int amS, apS, gS;
+
+    __device__ __forceinline__ const float* Amt(int t) const { return Am + t * amS; }
+    __device__ __forceinline__ const float* Apt(int t) const { return Ap + t * apS; }
+    __device__ __forceinline__ const float* Gt(int t) const { return Gm + t * gS; }
+    __device__ __forceinline__ float Q(int t, int i) const { return Qd[t * lnx + i]; }
+    __device__ __forceinline__ float R(int t, int j) const { return Rd[t * lnu + j]; }
+    __device__ __forceinline__ float W(int j) const { return Wd ? Wd[j] : 0.f; }
+    __device__ __forceinline__ float refv(int t, int k) const { return ref ? ref[t * ln + k] : 0.f; }
+    __device__ __forceinline__ float linv(int t, int k) const { return lin ? lin[t * ln + k] : 0.f; }
+    __device__ __forceinline__ float lob(int t, int r) const { return lo[t * lng + r]; }
+    __device__ __forceinline__ float hib(int t, int r) const { return hi[t * lng + r]; }
+    __device__ __forceinline__ float gam2(int r) const { return g2 ? g2[r] : kInf; }
+    __device__ __forceinline__ float gam1(int r) const { return g1 ? g1[r] : 0.f; }
+    // diagonal of the cost Hessian block D_t (App. B: D_t = H^+_{t-1} + H^-_t)
+    __device__ __forceinline__ float Pdiag(int t, int j) const {
+        if (j < nx) return Q(t, j);
+        const int k = j - nx;
+        float v = R(t, k);
+        if (t < N) v += W(k);
+        if (t > 0) v += W(k);
+        return v;
+    }
+    // cost weight of the (x-x_ref)/(u-u_ref) term (no rate term)
+    __device__ __forceinline__ float Cw(int t, int j) const { return j < nx ? Q(t, j) : R(t, j - nx); }
+};
+
+// ---------------------------------------------------------------------------
+// CTA reductions (all threads get the result)
+// ---------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ void cta_max_k(float (&v)[K], float* red) {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] = fmaxf(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (l == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[k * 32 + w] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float r = red[k * 32];
+        for (int i = 1; i < nw; ++i) r = fmaxf(r, red[k * 32 + i]);
+        v[k] = r;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double cta_sum_d(double v, double* redd) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (l == 0) redd[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    for (int i = 0; i < nw; ++i) r += redd[i];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ float fin(float v) { return (v == v) ? fabsf(v) : kInf; }
+
+// ---------------------------------------------------------------------------
+// model evaluation per stage (one thread)
+// ---------------------------------------------------------------------------
+// f_t at (zt, zn) and optionally the Jacobian blocks Am, Ap (row-major nx x n).
+__device__ void stage_dyn(const Ctx& c, int t, const float* zt, const float* zn, float* f,
+                          float* Am, float* Ap) {
+    const int nx = c.nx, n = c.n;
+    switch (c.model) {
+        case MODEL_DI: {
+            const float dt = c.dyn[0];
+            f[0] = zt[0] + dt * zt[2] + 0.5f * dt * dt * zt[4] - zn[0];
+            f[1] = zt[1] + dt * zt[3] + 0.5f * dt * dt * zt[5] - zn[1];
+            f[2] = zt[2] + dt * zt[4] - zn[2];
+            f[3] = zt[3] + dt * zt[5] - zn[3];
+            break;
+        }
+        case MODEL_LINEAR: {
+            const float* A = c.dyn;
+            const float* B = c.dyn + nx * nx;
+            for (int k = 0; k < nx; ++k) {
+                float a = -zn[k];
+                for (int j = 0; j < nx; ++j) a += A[k * nx + j] * zt[j];
+                for (int j = 0; j < c.nu; ++j) a += B[k * c.nu + j] * zt[nx + j];
+                f[k] = a;
+            }
+            break;
+        }
+        case MODEL_QUAD: {
+            float phi[6], dPx[36], dPu[12];
+            quad_rk4(zt, zt + 6, c.dyn, phi, Am ? dPx : nullptr, Am ? dPu : nullptr);
+            for (int k = 0; k < 6; ++k) f[k] = phi[k] - zn[k];
+            if (Am) {
+                for (int k = 0; k < 6; ++k) {
+                    for (int j = 0; j < 6; ++j) Am[k * n + j] = dPx[k * 6 + j];
+                    for (int j = 0; j < 2; ++j) Am[k * n + 6 + j] = dPu[k * 2 + j];
+                }
+            }
+            break;
+        }
+        case MODEL_BICYCLE: {
+            const float dt = c.dyn[0];
+            float mid[6], fc[6], Jx[36], Ju[12];
+            for (int k = 0; k < 6; ++k) mid[k] = 0.5f * (zt[k] + zn[k]);
+            const bool jac = Am != nullptr;
+            bicycle_fc(mid, zt + 6, c.dyn[1], c.track, c.nt, c.dyn[2], fc, jac ? Jx : nullptr,
+                       jac ? Ju : nullptr);
+            for (int k = 0; k < 6; ++k) f[k] = zt[k] + dt * fc[k] - zn[k];
+            if (jac) {
+                for (int k = 0; k < 6; ++k) {
+                    for (int j = 0; j < 6; ++j) {
+                        const float h = 0.5f * dt * Jx[k * 6 + j];
+                        Am[k * n + j] = (k == j ? 1.f : 0.f) + h;
+                        Ap[k * n + j] = (k == j ? -1.f : 0.f) + h;
+                    }
+                    for (int j = 0; j < 2; ++j) {
+                        Am[k * n + 6 + j] = dt * Ju[k * 2 + j];
+                        Ap[k * n + 6 + j] = 0.f;
+                    }
+                }
+            }
+            break;
+        }
+    }
+}
+
+// g_t(z) and optionally G_t (row-major ng x n)
+__device__ void stage_con(const Ctx& c, const float* z, float* g, float* G) {
+    const int n = c.n, ng = c.ng, nx = c.nx;
+    if (G)
+        for (int i = 0; i < ng * n; ++i) G[i] = 0.f;
+    switch (c.model) {
+        case MODEL_DI:
+            g[0] = z[4]; g[1] = z[5]; g[2] = z[2]; g[3] = z[3];
+            if (G) { G[0 * n + 4] = 1.f; G[1 * n + 5] = 1.f; G[2 * n + 2] = 1.f; G[3 * n + 3] = 1.f; }
+            break;
+        case MODEL_LINEAR:
+            for (int r = 0; r < ng; ++r) {
+                g[r] = z[nx + r];
+                if (G) G[r * n + nx + r] = 1.f;
+            }
+            break;
+        case MODEL_QUAD:
+            g[0] = z[6]; g[1] = z[7];
+            if (G) { G[0 * n + 6] = 1.f; G[1 * n + 7] = 1.f; }
+            break;
+        case MODEL_BICYCLE: {  // accel, steer rate, speed, steering angle, lateral error
+            TrackPt tp = track_eval(c.track, c.nt, c.dyn[2], z[5]);
+            float sp, cp;
+            sincosf(tp.psic, &sp, &cp);
+            const float dx = z[0] - tp.xc, dy = z[1] - tp.yc;
+            g[0] = z[6]; g[1] = z[7]; g[2] = z[3]; g[3] = z[4];
+            g[4] = -dx * sp + dy * cp;
+            if (G) {
+                G[0 * n + 6] = 1.f; G[1 * n + 7] = 1.f; G[2 * n + 3] = 1.f; G[3 * n + 4] = 1.f;
+                G[4 * n + 0] = -sp;
+                G[4 * n + 1] = cp;
+                G[4 * n + 5] = tp.dxc * sp - tp.dyc * cp - tp.dpsic * (dx * cp + dy * sp);
+            }
+            break;
+        }
+    }
+}
+
+// small dense solve (Gaussian elimination, partial pivoting), M is m x m row-major, in place
+__device__ inline void small_solve(float* M, float* b, int m) {
+    for (int k = 0; k < m; ++k) {
+        int p = k;
+        float best = fabsf(M[k * m + k]);
+        for (int i = k + 1; i < m; ++i)
+            if (fabsf(M[i * m + k]) > best) { best = fabsf(M[i * m + k]); p = i; }
+        if (p != k) {
+            for (int j = 0; j < m; ++j) { float tmp = M[k * m + j]; M[k * m + j] = M[p * m + j]; M[p * m + j] = tmp; }
+            float tmp = b[k]; b[k] = b[p]; b[p] = tmp;
+        }
+        const float d = M[k * m + k];
+        for (int i = k + 1; i < m; ++i) {
+            const float l = M[i * m + k] / d;
+            for (int j = k; j < m; ++j) M[i * m + j] -= l * M[k * m + j];
+            b[i] -= l * b[k];
+        }
+    }
+    for (int i = m - 1; i >= 0; --i) {
+        float a = b[i];
+        for (int j = i + 1; j < m; ++j) a -= M[i * m + j] * b[j];
+        b[i] = a / M[i * m + i];
+    }
+}
+
+// y = P x  (cost Hessian, block-tridiagonal with diagonal blocks), stage t, entry j
+__device__ __forceinline__ float Px_entry(const Ctx& c, const float* x, int t, int j) {
+    float v = c.Pdiag(t, j) * x[t * c.n + j];
+    if (j >= c.nx) {
+        const float w = c.W(j - c.nx);
+        if (t > 0) v -= w * x[(t - 1) * c.n + j];
+        if (t < c.N) v -= w * x[(t + 1) * c.n + j];
+    }
+    return v;
+}
+
+// (C' v)_t entry j with v_r given by a functor of (row r, k)
+template <class V>
+__device__ __forceinline__ float Ct_entry(const Ctx& c, int t, int j, V v) {
+    float s = 0.f;
+    if (t == 0 && j < c.nx) s += v(0, j);
+    if (t < c.N) {
+        const float* Am = c.Amt(t);
+        for (int k = 0; k < c.nx; ++k) s += Am[k * c.n + j] * v(t + 1, k);
+    }
+    if (t > 0) {
+        const float* Ap = c.Apt(t - 1);
+        for (int k = 0; k < c.nx; ++k) s += Ap[k * c.n + j] * v(t, k);
+    }
+    return s;
+}
+
+// (C x)_r entry k
+__device__ __forceinline__ float Cx_entry(const Ctx& c, const float* x, int r, int k) {
+    if (r == 0) return x[k];
+    const int t = r - 1;
+    const float* Am = c.Amt(t);
+    const float* Ap = c.Apt(t);
+    const float* a = x + t * c.n;
+    const float* b = x + (t + 1) * c.n;
+    float s = 0.f;
+    for (int j = 0; j < c.n; ++j) s += Am[k * c.n + j] * a[j] + Ap[k * c.n + j] * b[j];
+    return s;
+}
+
+__device__ __forceinline__ float Gx_entry(const Ctx& c, const float* x, int t, int r) {
+    const float* G = c.Gt(t) + r * c.n;
+    const float* a = x + t * c.n;
+    float s = 0.f;
+    for (int j = 0; j < c.n; ++j) s += G[j] * a[j];
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// initial guess: x_0 = x_init, u_t = u_ref_t, x_{t+1} from f_t = 0 (Newton for
+// the implicit model, the explicit map otherwise)
+// ---------------------------------------------------------------------------
+__device__ void rollout(const Ctx& c, const KOpts& o) {
+    const int n = c.n, nx = c.nx, T = c.T;
+    for (int i = threadIdx.x; i < T * n; i += blockDim.x) {
+        const int t = i / n, j = i % n;
+        c.zb[i] = (j >= nx) ? c.refv(t, j) : (t == 0 ? c.x0[j] : 0.f);
+    }
+    __syncthreads();
+    if (c.model == MODEL_LINEAR) {
+        const float* A = c.dyn;
+        const float* B = c.dyn + nx * nx;
+        for (int t = 0; t < c.N; ++t) {
+            const float* z = c.zb + t * n;
+            for (int k = threadIdx.x; k < nx; k += blockDim.x) {
+                float a = 0.f;
+                for (int j = 0; j < nx; ++j) a += A[k * nx + j] * z[j];
+                for (int j = 0; j < c.nu; ++j) a += B[k * c.nu + j] * z[nx + j];
+                c.zb[(t + 1) * n + k] = a;
+            }
+            __syncthreads();
+        }
+        return;
+    }
+    if (threadIdx.x == 0) {
+        float f[6], Am[6 * 8], Ap[6 * 8], M[36], xn[6], zn[8];
+        for (int t = 0; t < c.N; ++t) {
+            const float* z = c.zb + t * n;
+            if (c.model == MODEL_QUAD) {
+                quad_rk4(z, z + 6, c.dyn, xn, nullptr, nullptr);
+            } else if (c.model == MODEL_DI) {
+                const float dt = c.dyn[0];
+                xn[0] = z[0] + dt * z[2] + 0.5f * dt * dt * z[4];
+                xn[1] = z[1] + dt * z[3] + 0.5f * dt * dt * z[5];
+                xn[2] = z[2] + dt * z[4];
+                xn[3] = z[3] + dt * z[5];
+            } else {  // bicycle: explicit Euler predictor + Newton on f_t(z_t, x_{t+1}) = 0
+                float fc[6];
+                bicycle_fc(z, z + 6, c.dyn[1], c.track, c.nt, c.dyn[2], fc, nullptr, nullptr);
+                for (int k = 0; k < 6; ++k) xn[k] = z[k] + c.dyn[0] * fc[k];
+                for (int it = 0; it < o.newton_steps; ++it) {
+                    for (int k = 0; k < 6; ++k) zn[k] = xn[k];
+                    zn[6] = c.zb[(t + 1) * n + 6];
+                    zn[7] = c.zb[(t + 1) * n + 7];
+                    stage_dyn(c, t, z, zn, f, Am, Ap);
+                    for (int k = 0; k < 6; ++k)
+                        for (int j = 0; j < 6; ++j) M[k * 6 + j] = Ap[k * n + j];
+                    small_solve(M, f, 6);
+                    for (int k = 0; k < 6; ++k) xn[k] -= f[k];
+                }
+            }
+            for (int k = 0; k < nx; ++k) c.zb[(t + 1) * n + k] = xn[k];
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// QP approximation at the SQP iterate zb (App. B), written in the coordinates
+// d = x - zb of the step (an affine change of variables that leaves every
+// ADMM iterate, residual and multiplier unchanged):
+//   Am, Ap, G                  Jacobian blocks at zb
+//   cv  = c - C zb             (x_init - zb_0; -f_t(zb))
+//   qv  = q + P zb             (the cost gradient at zb)
+//   glo, ghi = lo - g(zb), hi - g(zb)
+// and, for the absolute-coordinate normalisers of the termination test and
+// the rho rule, czb = C zb, gzb = G zb; fv = f(zb) and gv = g(zb) for the
+// merit / KKT evaluations.
+// ---------------------------------------------------------------------------
+__device__ void linearize(const Ctx& c) {
+    const int n = c.n, nx = c.nx, ng = c.ng, N = c.N, T = c.T;
+    const bool cA = model_const_Am(c.model), cP = model_const_Ap(c.model), cG = model_const_G(c.model);
+    // constant blocks
+    if (cA) {
+        if (c.model == MODEL_LINEAR) {
+            const float* A = c.dyn;
+            const float* B = c.dyn + nx * nx;
+            for (int i = threadIdx.x; i < nx * n; i += blockDim.x) {
+                const int k = i / n, j = i % n;
+                c.Am[i] = j < nx ? A[k * nx + j] : B[k * c.nu + (j - nx)];
+            }
+        } else if (threadIdx.x == 0) {  // double integrator, ZOH
+            const float dt = c.dyn[0];
+            for (int i = 0; i < nx * n; ++i) c.Am[i] = 0.f;
+            for (int k = 0; k < 4; ++k) c.Am[k * n + k] = 1.f;
+            c.Am[0 * n + 2] = dt; c.Am[1 * n + 3] = dt;
+            c.Am[0 * n + 4] = 0.5f * dt * dt; c.Am[1 * n + 5] = 0.5f * dt * dt;
+            c.Am[2 * n + 4] = dt; c.Am[3 * n + 5] = dt;
+        }
+    }
+    if (cP)
+        for (int i = threadIdx.x; i < nx * n; i += blockDim.x) {
+            const int k = i / n, j = i % n;
+            c.Ap[i] = (k == j) ? -1.f : 0.f;
+        }
+    if (cG && threadIdx.x == 0) {
+        float g[64];
+        stage_con(c, c.zb, g, c.Gm);
+    }
+    __syncthreads();  // constant A^-, A^+, G visible to every thread
+    // dynamics residual at zb (and the per-stage Jacobians of nonlinear models)
+    if (model_linear_dyn(c.model)) {
+        for (int i = threadIdx.x; i < N * nx; i += blockDim.x) {
+            const int t = i / nx, k = i % nx;
+            const float* zt = c.zb + t * n;
+            float a = -c.zb[(t + 1) * n + k];
+            if (c.model == MODEL_LINEAR) {
+                const float* A = c.dyn;
+                const float* B = c.dyn + nx * nx;
+                for (int j = 0; j < nx; ++j) a += A[k * nx + j] * zt[j];
+                for (int j = 0; j < c.nu; ++j) a += B[k * c.nu + j] * zt[nx + j];
+            } else {
+                const float dt = c.dyn[0];
+                const float v[4] = {zt[0] + dt * zt[2] + 0.5f * dt * dt * zt[4], zt[1] + dt * zt[3] + 0.5f * dt * dt * zt[5],
+                                    zt[2] + dt * zt[4], zt[3] + dt * zt[5]};
+                a += v[k];
+            }
+            c.fv[(t + 1) * nx + k] = a;
+        }
+    } else {
+        for (int t = threadIdx.x; t < N; t += blockDim.x) {
+            float Apq[6 * 8];
+            float f[8];
+            stage_dyn(c, t, c.zb + t * n, c.zb + (t + 1) * n, f, c.Am + t * c.amS,
+                      cP ? Apq : c.Ap + t * c.apS);
+            for (int k = 0; k < nx; ++k) c.fv[(t + 1) * nx + k] = f[k];
+        }
+    }
+    for (int k = threadIdx.x; k < nx; k += blockDim.x) c.fv[k] = c.zb[k] - c.x0[k];
+    // constraints at zb
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        float g[64];
+        stage_con(c, c.zb + t * n, g, cG ? nullptr : c.Gm + t * c.gS);
+        for (int r = 0; r < ng; ++r) {
+            c.gv[t * ng + r] = g[r];
+            c.glo[t * ng + r] = c.lob(t, r) - g[r];
+            c.ghi[t * ng + r] = c.hib(t, r) - g[r];
+        }
+    }
+    // cost gradient at zb
+    for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
+        const int t = e / n, j = e % n;
+        float gr = c.Cw(t, j) * (c.zb[e] - c.refv(t, j)) + c.linv(t, j);
+        if (j >= nx) {
+            const float w = c.W(j - nx);
+            if (t < N) gr += w * (c.zb[e] - c.zb[e + n]);
+            if (t > 0) gr -= w * (c.zb[e - n] - c.zb[e]);
+        }
+        c.qv[e] = gr;
+    }
+    __syncthreads();  // per-stage Jacobians and f visible
+    for (int e = threadIdx.x; e < T * nx; e += blockDim.x) {
+        c.czb[e] = Cx_entry(c, c.zb, e / nx, e % nx);
+        c.cv[e] = -c.fv[e];
+    }
+    for (int e = threadIdx.x; e < T * ng; e += blockDim.x) c.gzb[e] = Gx_entry(c, c.zb, e / ng, e % ng);
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// S = P + sigma I + rho_f C'C + G' diag(w) G (Theta_t, Phi_t of App. C) and its
+// block LDL' factorisation, sequential over stages:
+//   Delta_0 = Theta_0,  Om_t = Phi_t Delta_t^{-1},  Delta_{t+1} = Theta_{t+1} - Om_t Phi_t'
+// stored as Dinv_t = Delta_t^{-1} (n x n) and Om_t (n x n), row-major.
+// w = per-row weights gw (T x ng) if use_gw, else rho_g on every row.
+// Returns false if a pivot block was not positive definite (the factors are then
+// not usable; the failing pivot is replaced by 1 so that no inf/NaN is produced).
+// ---------------------------------------------------------------------------
+__device__ bool factor(const Ctx& c, const Smem& sm, float sigma, float rho_f, float rho_g,
+                       bool use_gw) {
+    if (threadIdx.x == 0) sm.flags[1] = 0;
+    const int n = c.n, nx = c.nx, ng = c.ng, N = c.N, nn = n * n;
+    float* A = sm.A;   // Delta_t -> Cholesky factor L -> Dinv
+    float* Li = sm.Bm; // L^{-1}
+    float* Ph = sm.Cm; // Phi_t
+    for (int t = 0; t <= N; ++t) {
+        const float* Amt = c.Amt(t);
+        const float* Apm = t > 0 ? c.Apt(t - 1) : nullptr;
+        const float* G = c.Gt(t);
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+            const int i = e / n, j = e % n;
+            float s = 0.f;
+            if (t < N)
+                for (int k = 0; k < nx; ++k) s += Amt[k * n + i] * Amt[k * n + j];
+            if (t > 0)
+                for (int k = 0; k < nx; ++k) s += Apm[k * n + i] * Apm[k * n + j];
+            if (t == 0 && i == j && i < nx) s += 1.f;  // A_init' A_init
+            float v = rho_f * s;
+            for (int r = 0; r < ng; ++r) {
+                const float wr = use_gw ? c.gw[t * ng + r] : rho_g;
+                v += wr * G[r * n + i] * G[r * n + j];
+            }
+            if (i == j) v += c.Pdiag(t, i) + sigma;
+            if (t > 0) {  // - Om_{t-1} Phi_{t-1}'
+                const float* Om = c.Om + (t - 1) * nn;
+                float d = 0.f;
+                for (int k = 0; k < n; ++k) d += Om[i * n + k] * Ph[j * n + k];
+                v -= d;
+            }
+            A[e] = v;
+        }
+        __syncthreads();
+        // Cholesky (right-looking), lower triangle of A
+        for (int k = 0; k < n; ++k) {
+            if (threadIdx.x == 0) {
+                float d = A[k * n + k];
+                if (!(d > 0.f)) { sm.flags[1] = 1; d = 1.f; }
+                A[k * n + k] = sqrtf(d);
+            }
+            __syncthreads();
+            const float lkk = A[k * n + k];
+            for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * n + k] /= lkk;
+            __syncthreads();
+            const int m = n - k - 1;
+            for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+                const int i = k + 1 + e / m, j = k + 1 + e % m;
+                if (j <= i) A[i * n + j] -= A[i * n + k] * A[j * n + k];
+            }
+            __syncthreads();
+        }
+        // L^{-1} column by column (thread per column, forward substitution)
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            for (int i = 0; i < j; ++i) Li[i * n + j] = 0.f;
+            Li[j * n + j] = 1.f / A[j * n + j];
+            for (int i = j + 1; i < n; ++i) {
+                float s = 0.f;
+                for (int k = j; k < i; ++k) s += A[i * n + k] * Li[k * n + j];
+                Li[i * n + j] = -s / A[i * n + i];
+            }
+        }
+        __syncthreads();
+        // Dinv = L^{-T} L^{-1}
+        float* Dinv = c.Dinv + t * nn;
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+            const int i = e / n, j = e % n;
+            const int k0 = i > j ? i : j;
+            float s = 0.f;
+            for (int k = k0; k < n; ++k) s += Li[k * n + i] * Li[k * n + j];
+            A[e] = s;
+            Dinv[e] = s;
+        }
+        __syncthreads();
+        if (t < N) {
+            // Phi_t = E_t + rho_f A^+_t' A^-_t   ((t+1, t) block of S)
+            const float* Apt = c.Apt(t);
+            for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+                const int i = e / n, j = e % n;
+                float s = 0.f;
+                for (int k = 0; k < nx; ++k) s += Apt[k * n + i] * Amt[k * n + j];
+                float v = rho_f * s;
+                if (i == j && i >= nx) v -= c.W(i - nx);
+                Ph[e] = v;
+            }
+            __syncthreads();
+            float* Om = c.Om + t * nn;
+            for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+                const int i = e / n, j = e % n;
+                float s = 0.f;
+                for (int k = 0; k < n; ++k) s += Ph[i * n + k] * A[k * n + j];
+                Om[e] = s;
+            }
+            __syncthreads();
+        }
+    }
+    const bool ok = sm.flags[1] == 0;
+    __syncthreads();
+    return ok;
+}
+
+// Solve S x = b with the block LDL' factors; b (T x n) is overwritten by the
+// forward sweep, the result goes to xo (T x n).
+__device__ void ldl_solve(const Ctx& c, float* b, float* xo) {
+    const int n = c.n, N = c.N, nn = n * n;
+    for (int t = 0; t < N; ++t) {
+        const float* Om = c.Om + t * nn;
+        const float* w = b + t * n;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            float s = 0.f;
+            for (int k = 0; k < n; ++k) s += Om[i * n + k] * w[k];
+            b[(t + 1) * n + i] -= s;
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < c.T * n; e += blockDim.x) {
+        const int t = e / n, i = e % n;
+        const float* D = c.Dinv + t * nn;
+        const float* w = b + t * n;
+        float s = 0.f;
+        for (int k = 0; k < n; ++k) s += D[i * n + k] * w[k];
+        xo[e] = s;
+    }
+    __syncthreads();
+    for (int t = N - 1; t >= 0; --t) {
+        const float* Om = c.Om + t * nn;
+        const float* xn = xo + (t + 1) * n;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            float s = 0.f;
+            for (int k = 0; k < n; ++k) s += Om[k * n + i] * xn[k];
+            xo[t * n + i] -= s;
+        }
+        __syncthreads();
+    }
+}
+
+// projection onto [lo, hi] (hard row) or the L1+L2 smoothed projection (soft row)
+__device__ __forceinline__ void project(float v, float lo, float hi, float rho_g, float g2,
+                                        float g1, float& z, float& xi) {
+    if (!(g2 < kInf)) {
+        z = fminf(fmaxf(v, lo), hi);
+        xi = 0.f;
+        return;
+    }
+    if (v > hi) {
+        const float s = fmaxf(0.f, (rho_g * (v - hi) - g1) / (rho_g + g2));
+        z = hi + s;
+        xi = -s;
+    } else if (v < lo) {
+        const float s = fmaxf(0.f, (rho_g * (lo - v) - g1) / (rho_g + g2));
+        z = lo - s;
+        xi = s;
+    } else {
+        z = v;
+        xi = 0.f;
+    }
+}
+
+// one ADMM iteration (Algorithm 3) in increment form.  With p_f = C x - c
+// (tracked, never recomputed from absolute values) and p_g = G x - z_g, the
+// primal system S xt = eta is solved for the increment dx = xt - x:
+//     S dx = eta - S x = -(P x + q) - C'(y_f + rho_f p_f) - G'(y_g + rho_g p_g),
+// then z~_f - c = p_f + C dx, z~_g = G x + G dx, and the relaxation, projection
+// and dual updates of Algorithm 3 follow.  In exact arithmetic this is the
+// paper's iteration; in FP32 the rho_f-scaled terms only ever multiply small,
+// accurately formed differences.
+__device__ void admm_iter(const Ctx& c, const KOpts& o, float rho_bar) {
+    const int n = c.n, nx = c.nx, ng = c.ng, T = c.T;
+    const float rho_f = 1e3f * rho_bar, rho_g = rho_bar, alpha = o.alpha;
+    for (int e = threadIdx.x; e < T * ng; e += blockDim.x) c.pg[e] = Gx_entry(c, c.x, e / ng, e % ng) - c.zg[e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
+        const int t = e / n, j = e % n;
+        float s = -(Px_entry(c, c.x, t, j) + c.qv[e]);
+        s -= Ct_entry(c, t, j, [&](int r, int k) { return c.yf[r * nx + k] + rho_f * c.pf[r * nx + k]; });
+        const float* G = c.Gt(t);
+        for (int r = 0; r < ng; ++r) s -= G[r * n + j] * (c.yg[t * ng + r] + rho_g * c.pg[t * ng + r]);
+        c.eta[e] = s;
+    }
+    __syncthreads();
+    ldl_solve(c, c.eta, c.xt);
+    for (int e = threadIdx.x; e < T * nx; e += blockDim.x) {
+        const float cd = Cx_entry(c, c.xt, e / nx, e % nx);
+        c.yf[e] += rho_f * alpha * (c.pf[e] + cd);
+        c.pf[e] += alpha * cd;
+    }
+    for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
+        const int t = e / ng, r = e % ng;
+        const float zh = c.zg[e] + alpha * (c.pg[e] + Gx_entry(c, c.xt, t, r));
+        const float v = zh + c.yg[e] / rho_g;
+        float zn, xn;
+        project(v, c.glo[e], c.ghi[e], rho_g, c.gam2(r), c.gam1(r), zn, xn);
+        c.yg[e] += rho_g * (zh - zn);
+        c.zg[e] = zn;
+        c.xi[e] = xn;
+    }
+    for (int e = threadIdx.x; e < T * n; e += blockDim.x) c.x[e] += alpha * c.xt[e];
+    __syncthreads();
+}
+
+// slack-row dual residual (second block of r_dual)
+__device__ __forceinline__ float slack_res(float xi, float y, float g2, float g1) {
+    if (xi != 0.f) return g2 * xi + (xi > 0.f ? g1 : -g1) + y;
+    return fmaxf(0.f, fabsf(y) - g1);
+}
+
+struct Res {
+    float r_prim, r_dual, pn, dn;
+};
+
+// residuals of Eq. (admm:residuals) and the normalisers of
+// Eq. (admm:termination:slack), the latter in absolute coordinates
+// (x_abs = zb + x, z_abs = z_g + G zb, c_abs = c + C zb, q_abs = q - P zb).
+__device__ Res residuals(const Ctx& c, const Smem& sm) {
+    const int n = c.n, nx = c.nx, ng = c.ng, T = c.T;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};  // r_prim, r_dual, primal norm, dual norm
+    for (int e = threadIdx.x; e < T * nx; e += blockDim.x) {
+        const float cabs = c.cv[e] + c.czb[e];
+        v[0] = fmaxf(v[0], fin(c.pf[e]));
+        v[2] = fmaxf(v[2], fmaxf(fin(c.pf[e] + cabs), fin(cabs)));
+    }
+    for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
+        const int t = e / ng, r = e % ng;
+        const float gx = Gx_entry(c, c.x, t, r);
+        v[0] = fmaxf(v[0], fin(gx - c.zg[e]));
+        v[2] = fmaxf(v[2], fmaxf(fin(gx + c.gzb[e]), fin(c.zg[e] + c.gzb[e])));
+        const float g2 = c.gam2(r);
+        if (g2 < kInf) {
+            v[1] = fmaxf(v[1], fin(slack_res(c.xi[e], c.yg[e], g2, c.gam1(r))));
+            v[3] = fmaxf(v[3], fmaxf(fin(g2 * c.xi[e]), fin(c.yg[e])));
+        }
+    }
+    for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
+        const int t = e / n, j = e % n;
+        const float px = Px_entry(c, c.x, t, j);
+        const float pzb = Px_entry(c, c.zb, t, j);
+        float aty = Ct_entry(c, t, j, [&](int r, int k) { return c.yf[r * nx + k]; });
+        const float* G = c.Gt(t);
+        for (int r = 0; r < ng; ++r) aty += G[r * n + j] * c.yg[t * ng + r];
+        v[1] = fmaxf(v[1], fin(px + c.qv[e] + aty));
+        v[3] = fmaxf(v[3], fmaxf(fmaxf(fin(px + pzb), fin(aty)), fin(c.qv[e] - pzb)));
+    }
+    cta_max_k<4>(v, sm.red);
+    return {v[0], v[1], v[2], v[3]};
+}
+
+// ---------------------------------------------------------------------------
+// merit contributions of stage t at the point za = zb + a dz, xia = xib + a dxi
+// (Appendix D): cost (incl. slack penalty) and constraint violation V.
+// ---------------------------------------------------------------------------
+__device__ void stage_merit(const Ctx& c, int t, float a, double& cost, double& viol) {
+    const int n = c.n, nx = c.nx, ng = c.ng;
+    float z[72], zn[72], f[64], g[64];
+    for (int j = 0; j < n; ++j) z[j] = c.zb[t * n + j] + a * c.x[t * n + j];
+    double cs = 0.0, vs = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const float d = z[j] - c.refv(t, j);
+        cs += 0.5 * (double)c.Cw(t, j) * d * d + (double)c.linv(t, j) * z[j];
+    }
+    if (t < c.N) {
+        for (int j = 0; j < n; ++j) zn[j] = c.zb[(t + 1) * n + j] + a * c.x[(t + 1) * n + j];
+        for (int k = 0; k < c.nu; ++k) {
+            const float d = z[nx + k] - zn[nx + k];
+            cs += 0.5 * (double)c.W(k) * d * d;
+        }
+        stage_dyn(c, t, z, zn, f, nullptr, nullptr);
+        for (int k = 0; k < nx; ++k) vs += fabs((double)f[k]);
+    }
+    if (t == 0)
+        for (int k = 0; k < nx; ++k) vs += fabs((double)z[k] - (double)c.x0[k]);
+    stage_con(c, z, g, nullptr);
+    for (int r = 0; r < ng; ++r) {
+        const float xi = c.xib[t * ng + r] + a * (c.xi[t * ng + r] - c.xib[t * ng + r]);
+        const float g2 = c.gam2(r);
+        if (g2 < kInf) cs += 0.5 * (double)g2 * xi * xi + (double)c.gam1(r) * fabs((double)xi);
+        const double gx = (double)g[r] + xi;
+        vs += fmax(gx - (double)c.hib(t, r), 0.0) + fmax((double)c.lob(t, r) - gx, 0.0);
+    }
+    cost += cs;
+    viol += vs;
+}
+
+// returns the chosen step (Appendix D)
+__device__ float linesearch(const Ctx& c, const KOpts& o, const Smem& sm, float ystar_inf) {
+    const int n = c.n, nx = c.nx, ng = c.ng, T = c.T;
+    const int K = o.n_ls < 1 ? 1 : (o.n_ls > kMaxLs ? kMaxLs : o.n_ls);
+    if (K == 1) return 1.f;
+    // directional derivative of the cost at zb along the step d = x (qv is the gradient at zb)
+    double gd = 0.0;
+    for (int e = threadIdx.x; e < T * n; e += blockDim.x) gd += (double)c.qv[e] * (double)c.x[e];
+    for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
+        const int r = e % ng;
+        const float g2 = c.gam2(r);
+        if (g2 < kInf) {
+            const float x0 = c.xib[e], dx = c.xi[e] - c.xib[e];
+            gd += (double)g2 * x0 * dx + (double)c.gam1(r) * (x0 != 0.f ? (x0 > 0.f ? dx : -dx) : fabsf(dx));
+        }
+    }
+    gd = cta_sum_d(gd, sm.redd);
+    // merit parts at a = 0 and at every candidate: thread-strided over (k, t)
+    for (int e = threadIdx.x; e < 2 * (K + 1); e += blockDim.x) sm.lsacc[e] = 0.0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < (K + 1) * T; e += blockDim.x) {
+        const int k = e / T, t = e % T;
+        const float a = k == 0 ? 0.f : ldexpf(1.f, -(k - 1));
+        double cs = 0.0, vs = 0.0;
+        stage_merit(c, t, a, cs, vs);
+        atomicAdd(&sm.lsacc[2 * k], cs);
+        atomicAdd(&sm.lsacc[2 * k + 1], vs);
+    }
+    __syncthreads();
+    const double l0 = sm.lsacc[0], V0 = sm.lsacc[1];
+    const double mu = fmax(gd / (0.5 * fmax(V0, (double)o.eps_c)), (double)ystar_inf + 1e-4);
+    const double phi0 = l0 + mu * V0;
+    const double D = gd - mu * V0;
+    float chosen = -1.f, best = 0.f;
+    double best_phi = INFINITY;
+    for (int k = 1; k <= K; ++k) {
+        const float a = ldexpf(1.f, -(k - 1));
+        const double ph = sm.lsacc[2 * k] + mu * sm.lsacc[2 * k + 1];
+        if (isfinite(ph) && ph <= phi0 + (double)o.ls_eta * a * D) { chosen = a; break; }
+    }
+    if (chosen < 0.f) {
+        for (int k = 1; k <= K; ++k) {
+            const float a = ldexpf(1.f, -(k - 1));
+            const double ph = sm.lsacc[2 * k] + mu * sm.lsacc[2 * k + 1];
+            if (isfinite(ph) && ph < best_phi) { best_phi = ph; best = a; }
+        }
+        chosen = best;
+    }
+    __syncthreads();
+    return chosen;
+}
+
+// KKT residual of Eq. (sqp_stop) at (zb, xib, yfb, ygb) using the current
+// linearisation (Am, Ap, G, fv, gv at zb)
+__device__ float kkt(const Ctx& c, const Smem& sm) {
+    const int n = c.n, nx = c.nx, ng = c.ng, T = c.T;
+    float v[1] = {0.f};
+    for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
+        const int t = e / n, j = e % n;
+        float gr = c.Cw(t, j) * (c.zb[e] - c.refv(t, j)) + c.linv(t, j);
+        if (j >= nx) {
+            const float w = c.W(j - nx);
+            if (t < c.N) gr += w * (c.zb[e] - c.zb[e + n]);
+            if (t > 0) gr -= w * (c.zb[e - n] - c.zb[e]);
+        }
+        gr += Ct_entry(c, t, j, [&](int r, int k) { return c.yfb[r * nx + k]; });
+        const float* G = c.Gt(t);
+        for (int r = 0; r < ng; ++r) gr += G[r * n + j] * c.ygb[t * ng + r];
+        v[0] = fmaxf(v[0], fin(gr));
+    }
+    for (int e = threadIdx.x; e < T * nx; e += blockDim.x) v[0] = fmaxf(v[0], fin(c.fv[e]));
+    for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
+        const int t = e / ng, r = e % ng;
+        const float g2 = c.gam2(r);
+        if (g2 < kInf) v[0] = fmaxf(v[0], fin(slack_res(c.xib[e], c.ygb[e], g2, c.gam1(r))));
+        const float gx = c.gv[e] + c.xib[e];
+        v[0] = fmaxf(v[0], fmaxf(gx - c.hib(t, r), c.lob(t, r) - gx));
+    }
+    cta_max_k<1>(v, sm.red);
+    return v[0];
+}
+
+// initial primal-dual point from a solution in the padded layout
+__device__ void read_warm(const Ctx& c, const KLayout& L, const KSol& out, int i) {
+    const long long Ts = L.Nmax + 1;
+    const float* z = out.z + i * Ts * L.n;
+    const float* xi = out.xi + i * Ts * L.ng;
+    const float* yf = out.yf + i * Ts * L.nx;
+    const float* yg = out.yg + i * Ts * L.ng;
+    for (int e = threadIdx.x; e < c.T * c.n; e += blockDim.x) c.zb[e] = z[(e / c.n) * L.n + e % c.n];
+    for (int e = threadIdx.x; e < c.T * c.ng; e += blockDim.x) {
+        c.xib[e] = xi[(e / c.ng) * L.ng + e % c.ng];
+        c.ygb[e] = yg[(e / c.ng) * L.ng + e % c.ng];
+    }
+    for (int e = threadIdx.x; e < c.T * c.nx; e += blockDim.x) c.yfb[e] = yf[(e / c.nx) * L.nx + e % c.nx];
+    __syncthreads();
+}
+
+}  // namespace tmpc

@@ -1,0 +1,197 @@
+"""Torch-facing binding of the C ABI (include/tmpc.h).
+
+PyTorch supplies device memory and streams only; every step of the solver
+(linearisation, factorisation, ADMM, line search, backward) runs in the CUDA
+library.  The same function names as the ABI are exposed on `Solver`.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _abi
+
+PARAM_KEYS = ("Qd", "Rd", "Wd", "ref", "lin", "lo", "hi", "gamma2", "gamma1", "dyn", "track")
+GRAD_KEYS = ("x0", "Qd", "Rd", "Wd", "ref", "lin", "lo", "hi", "gamma2", "gamma1")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def options_from(opts=None, **overrides) -> _abi.Options:
+    """ABI options from defaults, an object with matching attribute names, and overrides."""
+    o = _abi.default_options()
+    names = [f[0] for f in _abi.Options._fields_]
+    if opts is not None:
+        for k in names:
+            if hasattr(opts, k):
+                setattr(o, k, getattr(opts, k))
+    for k, v in overrides.items():
+        if k not in names:
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def tensors_from_batch(pb, device="cuda") -> dict:
+    """Device tensors (FP32 / int32, contiguous) of a problem batch object with
+    the attributes of the ABI parameter struct (N, model, x0, Qd, ...)."""
+    f = lambda a: None if a is None else torch.as_tensor(a, dtype=torch.float32).contiguous().to(device)
+    out = {k: f(getattr(pb, k)) for k in PARAM_KEYS}
+    out["x0"] = f(pb.x0)
+    out["N"] = torch.as_tensor(pb.N, dtype=torch.int32).contiguous().to(device)
+    out["model"] = torch.as_tensor(pb.model, dtype=torch.int32).contiguous().to(device)
+    return out
+
+
+class Solver:
+    """One C-ABI handle: workspace for a fixed layout (B, N_max, nx, nu, ng)."""
+
+    def __init__(self, dims: dict, params: dict, options: _abi.Options | None = None):
+        self.lib = _abi.load()
+        self.dims = _abi.Dims(dims["batch"], dims["N_max"], dims["nx"], dims["nu"], dims["ng"],
+                              dims["n_dyn"], dims.get("n_track", 0))
+        self.options = options if options is not None else _abi.default_options()
+        self._params = {}
+        self._pstruct = self._make_params(params)
+        self.handle = ctypes.c_void_p()
+        _abi.check(self.lib.tmpc_setup(ctypes.byref(self.handle), ctypes.byref(self.dims),
+                                       ctypes.byref(self.options), ctypes.byref(self._pstruct)),
+                   "tmpc_setup")
+
+    @classmethod
+    def from_batch(cls, pb, device="cuda", **overrides):
+        t = tensors_from_batch(pb, device)
+        dims = dict(batch=pb.B, N_max=pb.N_max, nx=pb.nx, nu=pb.nu, ng=pb.ng, n_dyn=pb.n_dyn,
+                    n_track=pb.n_track)
+        s = cls(dims, t, options_from(pb.opts, **overrides))
+        s.x0 = t["x0"]
+        return s
+
+    def _make_params(self, params):
+        keep = {}
+        for k in ("N", "model") + PARAM_KEYS:
+            v = params.get(k)
+            if v is not None:
+                if not v.is_contiguous():
+                    raise ValueError(f"parameter {k} must be contiguous")
+                keep[k] = v
+        self._params = keep
+        p = _abi.Params()
+        for k in ("N", "model") + PARAM_KEYS:
+            v = keep.get(k)
+            setattr(p, k, None if v is None else v.data_ptr())
+        return p
+
+    @property
+    def B(self):
+        return self.dims.batch
+
+    def _shapes(self):
+        d = self.dims
+        T = d.N_max + 1
+        n = d.nx + d.nu
+        return dict(z=(d.batch, T, n), xi=(d.batch, T, d.ng), y_eq=(d.batch, T, d.nx),
+                    y_ineq=(d.batch, T, d.ng))
+
+    def alloc_solution(self, device="cuda"):
+        sh = self._shapes()
+        out = {k: torch.zeros(v, dtype=torch.float32, device=device) for k, v in sh.items()}
+        out["status"] = torch.zeros(self.B, dtype=torch.int32, device=device)
+        out["stats"] = torch.zeros((self.B, _abi.TMPC_STATS), dtype=torch.float32, device=device)
+        return out
+
+    @staticmethod
+    def _sol_struct(sol):
+        return _abi.Solution(*[sol[k].data_ptr() if sol.get(k) is not None else None
+                               for k in ("z", "xi", "y_eq", "y_ineq", "status", "stats")])
+
+    def tmpc_update_params(self, params: dict):
+        merged = dict(self._params)
+        merged.update({k: v for k, v in params.items() if k in PARAM_KEYS})
+        self._pstruct = self._make_params(merged)
+        _abi.check(self.lib.tmpc_update_params(self.handle, ctypes.byref(self._pstruct)), "tmpc_update_params")
+
+    def tmpc_set_options(self, options: _abi.Options):
+        _abi.check(self.lib.tmpc_set_options(self.handle, ctypes.byref(options)), "tmpc_set_options")
+        self.options = options
+
+    def tmpc_solve(self, x0, sol=None, warm_start=False, stream=None):
+        if sol is None:
+            sol = self.alloc_solution(x0.device)
+        s = self._sol_struct(sol)
+        _abi.check(self.lib.tmpc_solve(self.handle, ctypes.c_void_p(x0.data_ptr()), ctypes.byref(s),
+                                       1 if warm_start else 0, _stream_ptr(stream)), "tmpc_solve")
+        return sol
+
+    def tmpc_backward(self, x0, sol, dL_dz, dL_dxi=None, grads=None, stream=None):
+        if grads is None:
+            grads = {k: torch.zeros_like(self._params[k] if k != "x0" else x0)
+                     for k in GRAD_KEYS if (k == "x0" or self._params.get(k) is not None)}
+        g = _abi.Grads(*[grads[k].data_ptr() if grads.get(k) is not None else None for k in GRAD_KEYS])
+        s = self._sol_struct(sol)
+        _abi.check(self.lib.tmpc_backward(self.handle, ctypes.c_void_p(x0.data_ptr()), ctypes.byref(s),
+                                          ctypes.c_void_p(dL_dz.contiguous().data_ptr()),
+                                          None if dL_dxi is None else ctypes.c_void_p(dL_dxi.contiguous().data_ptr()),
+                                          ctypes.byref(g), _stream_ptr(stream)), "tmpc_backward")
+        return grads
+
+    def tmpc_solve_host(self, host_params: dict, x0_host, out_host: dict, stream=None):
+        """End-to-end solve from pinned host tensors (copies inside the call)."""
+        p = _abi.Params()
+        for k in ("N", "model") + PARAM_KEYS:
+            v = host_params.get(k)
+            setattr(p, k, None if v is None else v.data_ptr())
+        s = self._sol_struct(out_host)
+        _abi.check(self.lib.tmpc_solve_host(self.handle, ctypes.byref(p), ctypes.c_void_p(x0_host.data_ptr()),
+                                            ctypes.byref(s), _stream_ptr(stream)), "tmpc_solve_host")
+        return out_host
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.tmpc_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class TmpcFunction(torch.autograd.Function):
+    """z, xi = OCP-solve(x0, Qd, Rd, ref, lo, hi) with the implicit-differentiation
+    backward of the library.  The solver handle carries the remaining parameters."""
+
+    @staticmethod
+    def forward(ctx, solver: Solver, x0, Qd, Rd, ref, lo, hi):
+        x0, Qd, Rd, ref, lo, hi = (t.detach().float().contiguous() for t in (x0, Qd, Rd, ref, lo, hi))
+        solver.tmpc_update_params(dict(Qd=Qd, Rd=Rd, ref=ref, lo=lo, hi=hi))
+        sol = solver.tmpc_solve(x0)
+        ctx.solver = solver
+        ctx.sol = sol
+        ctx.save_for_backward(x0, Qd, Rd, ref, lo, hi)
+        ctx.mark_non_differentiable(sol["status"])
+        return sol["z"], sol["xi"], sol["status"]
+
+    @staticmethod
+    def backward(ctx, dz, dxi, _dstatus):
+        x0, Qd, Rd, ref, lo, hi = ctx.saved_tensors
+        solver = ctx.solver
+        solver.tmpc_update_params(dict(Qd=Qd, Rd=Rd, ref=ref, lo=lo, hi=hi))
+        g = solver.tmpc_backward(x0, ctx.sol, dz.contiguous().float(),
+                                 None if dxi is None else dxi.contiguous().float())
+        return None, g["x0"], g["Qd"], g["Rd"], g["ref"], g["lo"], g["hi"]
+
+
+def solve_ocp(solver: Solver, x0, Qd, Rd, ref, lo, hi):
+    """Differentiable forward solve; returns (z, xi, status)."""
+    return TmpcFunction.apply(solver, x0, Qd, Rd, ref, lo, hi)

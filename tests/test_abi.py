@@ -1,0 +1,70 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads, exports
+every function declared in include/tmpc.h, and rejects bad arguments before
+touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2606_24039_gb300 import build, load
+    build.build()
+    return load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "tmpc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tmpc_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ["tmpc_setup", "tmpc_solve", "tmpc_backward", "tmpc_destroy", "tmpc_solve_host",
+              "tmpc_update_params", "tmpc_status_string"]:
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_setup_rejects_bad_arguments_without_a_gpu(lib):
+    from paper_2606_24039_gb300 import _abi
+    h = ctypes.c_void_p()
+    d = _abi.Dims(4, 10, 4, 2, 4, 1, 0)
+    o = _abi.default_options()
+    p = _abi.Params()
+    # null parameter pointers
+    assert lib.tmpc_setup(ctypes.byref(h), ctypes.byref(d), ctypes.byref(o), ctypes.byref(p)) == 1
+    assert h.value is None
+    # null handle pointer / dims
+    assert lib.tmpc_setup(None, ctypes.byref(d), ctypes.byref(o), ctypes.byref(p)) == 1
+    assert lib.tmpc_setup(ctypes.byref(h), None, ctypes.byref(o), ctypes.byref(p)) == 1
+    # dimensions beyond the compiled limits
+    d2 = _abi.Dims(4, 10, 70, 10, 4, 1, 0)
+    assert lib.tmpc_setup(ctypes.byref(h), ctypes.byref(d2), ctypes.byref(o), ctypes.byref(p)) == 5
+    # bad options
+    o2 = _abi.default_options()
+    o2.alpha = 2.5
+    assert lib.tmpc_setup(ctypes.byref(h), ctypes.byref(d), ctypes.byref(o2), ctypes.byref(p)) == 1
+    # calls on a null handle
+    assert lib.tmpc_solve(None, None, None, 0, None) == 4
+    assert lib.tmpc_backward(None, None, None, None, None, None, None) == 4
+    lib.tmpc_destroy(None)
+    assert lib.tmpc_status_string(0) == b"ok"
+
+
+def test_default_options_follow_the_paper(lib):
+    from paper_2606_24039_gb300 import _abi
+    o = _abi.default_options()
+    assert abs(o.sigma - 1e-6) < 1e-12 and abs(o.rho0 - 0.1) < 1e-7
+    assert o.k_rho_iter == 25 and abs(o.k_rho_ratio - 5.0) < 1e-7
+    assert abs(o.rho_min - 1e-6) < 1e-12 and abs(o.rho_max - 1e6) < 1
+    assert abs(o.ls_eta - 0.4) < 1e-7

@@ -55,7 +55,7 @@ MODEL_NAMES = {MODEL_DI: "double_integrator", MODEL_LINEAR: "linear",
                MODEL_BICYCLE: "bicycle", MODEL_QUAD: "planar_quadrotor"}
 
 # fixed (nx, nu, ng) of the nonlinear / fixed-size models
-MODEL_DIMS = {MODEL_DI: (4, 2, 4), MODEL_BICYCLE: (6, 2, 4), MODEL_QUAD: (6, 2, 2)}
+MODEL_DIMS = {MODEL_DI: (4, 2, 4), MODEL_BICYCLE: (6, 2, 5), MODEL_QUAD: (6, 2, 2)}
 
 INF = np.inf
 
@@ -88,7 +88,7 @@ class Options:
     newton_steps: int = 3
     early_exit: int = 0
     check_every: int = 25
-    bwd_rho: float = 1e4
+    bwd_rho: float = 1e3
     bwd_sigma: float = 1e-6
     bwd_iters: int = 12
 
@@ -277,19 +277,21 @@ def _fill_bicycle(rng, a, i, N, track_tab, dt=0.05, wheelbase=2.7, v0=None,
     v = rng.uniform(5.0, 15.0) if v0 is None else v0
     a["x0"][i, :nx] = np.array([xc, yc, psic, v, 0.0, 0.0])
     a["ref"][i, :N + 1, 3] = v                            # unused (zero weight) but recorded
-    # rows: accel, steer-rate, speed, lateral error e
+    # rows: accel, steer-rate, speed, steering angle, lateral error e
     a["lo"][i, :N + 1, 0] = -4.0
     a["hi"][i, :N + 1, 0] = 4.0
     a["lo"][i, :N + 1, 1] = -1.0
     a["hi"][i, :N + 1, 1] = 1.0
     a["lo"][i, 1:N + 1, 2] = 0.0
     a["hi"][i, 1:N + 1, 2] = 30.0
-    a["lo"][i, 1:N + 1, 3] = -4.0
-    a["hi"][i, 1:N + 1, 3] = 4.0
+    a["lo"][i, 1:N + 1, 3] = -0.6
+    a["hi"][i, 1:N + 1, 3] = 0.6
+    a["lo"][i, 1:N + 1, 4] = -4.0
+    a["hi"][i, 1:N + 1, 4] = 4.0
     a["gamma2"][i, :] = INF
     a["gamma1"][i, :] = 0.0
-    a["gamma2"][i, 3] = gamma2                            # track row is softened (L1 + L2)
-    a["gamma1"][i, 3] = gamma1
+    a["gamma2"][i, 4] = gamma2                            # track row is softened (L1 + L2)
+    a["gamma1"][i, 4] = gamma1
     nt = track_tab.shape[0] - 1
     a["dyn"][i, 0:4] = np.array([dt, wheelbase, TRACK_DS, nt])
     a["track"][i, :nt + 1] = track_tab
@@ -332,9 +334,9 @@ def racing(B=1024, N=50, seed=1002, max_sqp=10, max_admm=50, track_length=400.0)
     """Kinematic-bicycle racing (nx=6: x, y, psi, v, delta, s; nu=2: accel,
     steer-rate), implicit midpoint dt=0.05, N=50, random curvature-spline
     centrelines (curvature knots every 10 m in U[-0.2, 0.2]), box bounds on the
-    controls and speed, the lateral track error softened by L1+L2 slacks,
+    controls, speed and steering angle, the lateral track error softened by L1+L2 slacks,
     control-rate cost and a min-time (progress) terminal cost."""
-    nx, nu, ng = 6, 2, 4
+    nx, nu, ng = 6, 2, 5
     nt = int(round(track_length / TRACK_DS))
     a = _empty(B, nx, nu, ng, N, 4, nt)
     for i in range(B):
@@ -415,7 +417,7 @@ def uneven(B=4096, N_lo=10, N_hi=200, seed=1004, max_sqp=10, max_admm=50) -> Pro
     """Uneven batch: each instance draws its horizon from U{N_lo..N_hi} and its
     model from {double integrator, bicycle, planar quadrotor} with ratio 1:2:1."""
     rng = np.random.default_rng(seed)
-    nx, nu, ng = 6, 2, 4
+    nx, nu, ng = 6, 2, 5
     Ns = rng.integers(N_lo, N_hi + 1, size=B).astype(np.int32)
     models = rng.choice([MODEL_DI, MODEL_BICYCLE, MODEL_BICYCLE, MODEL_QUAD], size=B).astype(np.int32)
     N_max = int(Ns.max())
@@ -439,7 +441,7 @@ def long_horizon(B=8, N=8192, seed=1005, max_sqp=5, max_admm=100, dt=0.01,
                  track_length=2000.0) -> ProblemBatch:
     """Kinematic-bicycle racing as `racing`, with N=8192 knots at dt=0.01 on a
     closed random track of 2 km."""
-    nx, nu, ng = 6, 2, 4
+    nx, nu, ng = 6, 2, 5
     nt = int(round(track_length / TRACK_DS))
     a = _empty(B, nx, nu, ng, N, 4, nt)
     for i in range(B):
