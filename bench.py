@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-bwd", action="store_true", help="time the forward pass only")
+    ap.add_argument("--solver", type=int, default=0, help="0 auto, 1 generic sequential LDL', 2 shared-memory CR")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the host-memory end-to-end timing")
     return ap.parse_args()
 
@@ -71,7 +72,8 @@ def config_of(args, pb):
                         f"L1+L2 soft track row, rate cost), {pb.opts.max_sqp} SQP x {pb.opts.max_admm} ADMM",
             "batch": pb.B, "horizon": pb.N_max, "nx": pb.nx, "nu": pb.nu, "ng": pb.ng,
             "sqp_iters": pb.opts.max_sqp, "admm_iters": pb.opts.max_admm,
-            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{args.gpus}"}
+            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{args.gpus}",
+            "solver": {0: "auto", 1: "generic sequential block LDL'", 2: "shared-memory block cyclic reduction"}[args.solver]}
 
 
 # ----------------------------------------------------------------------------
@@ -217,17 +219,17 @@ def run_gpu(args):
     from paper_2606_24039_gb300 import Solver, build, tensors_from_batch
     build.build()
     pb = workload(args, rank)
-    s = Solver.from_batch(pb, device="cuda")
+    s = Solver.from_batch(pb, device="cuda", solver=args.solver)
     sol = s.alloc_solution("cuda")
     dLdz = torch.randn((pb.B, pb.N_max + 1, pb.n), device="cuda")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step():
-        s.tmpc_solve(s.x0, sol)
+        s.tmpc_solve(s.x0, sol, z_init=s.z_init)
 
     def step_fb():
-        s.tmpc_solve(s.x0, sol)
+        s.tmpc_solve(s.x0, sol, z_init=s.z_init)
         s.tmpc_backward(s.x0, sol, dLdz)
 
     for _ in range(args.warmup):
@@ -266,13 +268,13 @@ def run_gpu(args):
     h2d = sum(v.numel() * v.element_size() for v in hp.values() if v is not None)
     d2h = sum(v.numel() * v.element_size() for v in ho.values())
     for _ in range(0 if args.skip_e2e else max(1, args.warmup)):
-        s.tmpc_solve_host(hp, hp["x0"], ho)
+        s.tmpc_solve_host(hp, hp["x0"], ho, z_init_host=hp["z_init"])
     e2e_t = [float("nan")]
     for _ in range(0 if args.skip_e2e else args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        s.tmpc_solve_host(hp, hp["x0"], ho)
+        s.tmpc_solve_host(hp, hp["x0"], ho, z_init_host=hp["z_init"])
         e2e_t.append(time.perf_counter() - t)
     e2e_t = [v for v in e2e_t if v == v] or [float("nan")]
 

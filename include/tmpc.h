@@ -162,7 +162,9 @@ typedef struct tmpc_handle tmpc_handle;
 
 /* Default options: sigma 1e-6, rho0 0.1, rho in [1e-6, 1e6], alpha 1.6,
  * eps 1e-5, eps_g 1e-4, eta 0.4, k_rho 25 / ratio 5 (Section III-B), 1 SQP step,
- * 200 ADMM iterations, 8 line-search candidates, 3 Newton steps. */
+ * 200 ADMM iterations, 8 line-search candidates, 3 Newton steps; backward
+ * rho_b 1e4 (lowered tenfold, at most three times, if the FP32 factorisation
+ * fails), sigma_b 1e-6, 30 refinement sweeps. */
 void tmpc_default_options(tmpc_options* o);
 
 /* Create a solver for the given layout and options and the parameter arrays p.
@@ -205,9 +207,12 @@ tmpc_status tmpc_backward(tmpc_handle* h, const float* x0, const tmpc_solution* 
  * host_p and x0 (HOST pointers, pinned memory recommended) into device
  * buffers owned by the handle, solves, copies z, xi, y_eq, y_ineq, status and
  * stats back into the HOST arrays of host_out, and synchronises the stream
- * before returning.  The handle's device parameter pointers are not changed. */
+ * before returning.  z_init [B][Nmax+1][nx+nu] (HOST, may be NULL) is an
+ * initial primal guess (slacks and multipliers start at zero); NULL starts
+ * from the Newton rollout.  The handle's device parameter pointers are not
+ * changed. */
 tmpc_status tmpc_solve_host(tmpc_handle* h, const tmpc_params* host_p, const float* x0,
-                            tmpc_solution* host_out, void* stream);
+                            const float* z_init, tmpc_solution* host_out, void* stream);
 
 /* Free the handle and its workspace (synchronises its allocations). NULL is a no-op. */
 void tmpc_destroy(tmpc_handle* h);

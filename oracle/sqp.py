@@ -2,9 +2,10 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-  initial guess   x_0 = x_init, u_t = u_ref_t, each x_{t+1} found from
-                  f_t(z_t, z_{t+1}) = 0 by `newton_steps` Newton steps started
-                  from an explicit step (exact for explicit models);
+  initial guess   the instance's z_init if it carries one (zero slacks and
+                  multipliers), else x_0 = x_init, u_t = u_ref_t, each x_{t+1}
+                  found from f_t(z_t, z_{t+1}) = 0 by `newton_steps` Newton
+                  steps started from an explicit step (exact for explicit models);
   loop            convexify (oracle.qp) -> ADMM (oracle.admm, warm-started
                   from the current primal-dual point and the previous rho)
                   -> line search (Appendix D) -> convergence check (Eq. sqp_stop).
@@ -129,6 +130,10 @@ def solve(inst, opts, warm=None, replay=None, record=False):
     search steps / rho schedule (decision replay).  Returns dict(z, xi, yf, yg,
     rho_bar, stats, history)."""
     nx, ng, N = inst["nx"], inst["ng"], inst["N"]
+    if warm is None and inst.get("z_init") is not None:
+        # an instance that carries an initial primal guess starts from it (zero slacks / multipliers)
+        warm = dict(z=inst["z_init"], xi=np.zeros((N + 1, ng)), yf=np.zeros((N + 1, nx)),
+                    yg=np.zeros((N + 1, ng)))
     if warm is not None:
         z, xi = warm["z"].copy(), warm["xi"].copy()
         yf, yg = warm["yf"].copy(), warm["yg"].copy()

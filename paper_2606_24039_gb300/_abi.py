@@ -90,7 +90,7 @@ def load(path: str | None = None):
     lib.tmpc_solve.restype = ctypes.c_int
     lib.tmpc_backward.argtypes = [vp, vp, ctypes.POINTER(Solution), vp, vp, ctypes.POINTER(Grads), vp]
     lib.tmpc_backward.restype = ctypes.c_int
-    lib.tmpc_solve_host.argtypes = [vp, ctypes.POINTER(Params), vp, ctypes.POINTER(Solution), vp]
+    lib.tmpc_solve_host.argtypes = [vp, ctypes.POINTER(Params), vp, vp, ctypes.POINTER(Solution), vp]
     lib.tmpc_solve_host.restype = ctypes.c_int
     lib.tmpc_destroy.argtypes = [vp]
     lib.tmpc_destroy.restype = None

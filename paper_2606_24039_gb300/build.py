@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "lib")
 LIBNAME = "libtmpc.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["tmpc_api.cu"]
+SOURCES = ["tmpc_api.cu", "tmpc_fast.cu"]
 
 
 def nvcc_path() -> str:

@@ -12,6 +12,7 @@
 
 #include "../../include/tmpc.h"
 #include "tmpc_backward.cuh"
+#include "tmpc_fast_api.h"
 #include "tmpc_solver.cuh"
 
 using namespace tmpc;
@@ -37,7 +38,7 @@ __device__ __forceinline__ Smem carve_smem(void* raw, int n) {
     Smem s;
     char* p = reinterpret_cast<char*>(raw);
     s.redd = reinterpret_cast<double*>(p);            p += 32 * 2 * sizeof(double);
-    s.lsacc = reinterpret_cast<double*>(p);           p += 2 * (kMaxLs + 1) * sizeof(double) + 16;
+    s.lsacc = reinterpret_cast<double*>(p);           p += (2 * (kMaxLs + 1) + 2) * sizeof(double);
     s.red = reinterpret_cast<float*>(p);              p += 32 * 8 * sizeof(float);
     s.flags = reinterpret_cast<int*>(p);              p += 16 * sizeof(int);
     s.A = reinterpret_cast<float*>(p);                p += n * n * sizeof(float);
@@ -47,7 +48,7 @@ __device__ __forceinline__ Smem carve_smem(void* raw, int n) {
 }
 
 size_t smem_bytes(int n) {
-    return 32 * 2 * sizeof(double) + 2 * (kMaxLs + 1) * sizeof(double) + 16 + 32 * 8 * sizeof(float) +
+    return 32 * 2 * sizeof(double) + (2 * (kMaxLs + 1) + 2) * sizeof(double) + 32 * 8 * sizeof(float) +
            16 * sizeof(int) + 3 * (size_t)n * n * sizeof(float);
 }
 
@@ -216,7 +217,7 @@ __device__ void solve_instance(const Ctx& c, const KOpts& o, const Smem& sm, con
 }
 
 __global__ void __launch_bounds__(256, 2) solve_kernel(KLayout L, KOpts o, KParams p, KSol out, float* ws, WsOff off,
-                             const int* order, int* queue, const float* x0, int warm) {
+                             const int* order, int count, int* queue, const float* x0, int warm) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     const Smem sm = carve_smem(smem_raw, L.n);
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(256, 2) solve_kernel(KLayout L, KOpts o, KPara
         __syncthreads();
         const int q = s_item;
         __syncthreads();
-        if (q >= L.B) break;
+        if (q >= count) break;
         const int i = order[q];
         const Ctx c = make_ctx(L, p, ws, off, i, x0);
         solve_instance(c, o, sm, L, out, i, warm);
@@ -283,6 +284,15 @@ struct tmpc_handle {
     float* ws = nullptr;
     int* order = nullptr;
     int* queue = nullptr;
+    // work groups of the forward pass: g < 3 the shared-memory kernels of the
+    // double integrator / bicycle / quadrotor, g = 3 the generic kernel
+    struct Group {
+        int model = -1, offset = 0, count = 0, grid = 0, threads = 0;
+        size_t smem = 0;
+    } groups[4];
+    int n_groups = 0;
+    float* fws = nullptr;      // global arenas of the shared-memory path (instances that do not fit)
+    long long fstride = 0;
     int nsm = 0;
     int threads = 128;
     size_t smem = 0;
@@ -304,7 +314,7 @@ void tmpc_default_options(tmpc_options* o) {
     o->eps_abs = 1e-5f; o->eps_rel = 1e-5f; o->eps_c = 1e-5f; o->eps_g = 1e-4f; o->ls_eta = 0.4f;
     o->k_rho_iter = 25; o->k_rho_ratio = 5.f; o->max_sqp = 1; o->max_admm = 200; o->n_ls = 8;
     o->newton_steps = 3; o->early_exit = 0; o->check_every = 25;
-    o->bwd_rho = 1e3f; o->bwd_sigma = 1e-6f; o->bwd_iters = 12;
+    o->bwd_rho = 1e4f; o->bwd_sigma = 1e-6f; o->bwd_iters = 30;
     o->threads = 0; o->solver = 0;
 }
 
@@ -326,7 +336,8 @@ static tmpc_status check_options(const tmpc_options* o) {
     if (!(o->sigma > 0.f) || !(o->rho0 > 0.f) || !(o->alpha > 0.f && o->alpha < 2.f)) return TMPC_ERR_INVALID_ARG;
     if (o->max_sqp < 0 || o->max_admm < 1 || o->n_ls < 1 || o->n_ls > kMaxLs) return TMPC_ERR_INVALID_ARG;
     if (o->newton_steps < 0 || o->bwd_iters < 1 || !(o->bwd_rho > 0.f)) return TMPC_ERR_INVALID_ARG;
-    if (o->threads < 0 || o->threads > 1024 || (o->threads % 32) != 0) return TMPC_ERR_INVALID_ARG;
+    if (o->threads < 0 || o->threads > 256 || (o->threads % 32) != 0) return TMPC_ERR_INVALID_ARG;
+    if (o->solver < 0 || o->solver > 2) return TMPC_ERR_INVALID_ARG;
     return TMPC_OK;
 }
 
@@ -411,24 +422,69 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
 
     cudaError_t e = cudaMalloc(&h->ws, sizeof(float) * off.stride * d->batch);
     if (e != cudaSuccess) { set_err("cudaMalloc(workspace)", e); delete h; return TMPC_ERR_OOM; }
-    e = cudaMalloc(&h->order, sizeof(int) * (d->batch + 2));
+    e = cudaMalloc(&h->order, sizeof(int) * (2 * d->batch + 8));
     if (e != cudaSuccess) { set_err("cudaMalloc(order)", e); tmpc_destroy(h); return TMPC_ERR_OOM; }
-    h->queue = h->order + d->batch;
-    // longest-processing-time-first order of the work queue: (N+1) n^2 work estimate
-    std::vector<int> ord(d->batch);
-    std::iota(ord.begin(), ord.end(), 0);
-    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
-        const ModelDims ma = model_dims(Mh[a], d->nx, d->nu, d->ng), mb = model_dims(Mh[b], d->nx, d->nu, d->ng);
-        const long long wa = (long long)(Nh[a] + 1) * (ma.nx + ma.nu) * (ma.nx + ma.nu);
-        const long long wb = (long long)(Nh[b] + 1) * (mb.nx + mb.nu) * (mb.nx + mb.nu);
-        return wa > wb;
-    });
-    e = cudaMemcpy(h->order, ord.data(), sizeof(int) * d->batch, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) { set_err("cudaMemcpy(order)", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
-
+    h->queue = h->order + 2 * d->batch;   // 5 counters: 4 forward groups + backward
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
+    int max_optin = 0;
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // work estimate for longest-processing-time-first ordering: (N+1) n^2
+    auto work = [&](int i) {
+        const ModelDims m = model_dims(Mh[i], d->nx, d->nu, d->ng);
+        return (long long)(Nh[i] + 1) * (m.nx + m.nu) * (m.nx + m.nu);
+    };
+    auto by_work = [&](int a, int b) { return work(a) > work(b); };
+    // forward groups
+    std::vector<int> ord;
+    ord.reserve(2 * d->batch);
+    long long fmax = 0;
+    for (int g = 0; g < 4; ++g) {
+        std::vector<int> mem;
+        for (int i = 0; i < d->batch; ++i) {
+            const bool fastable = fast::supported(Mh[i]) && o->solver != 1;
+            const int gi = fastable ? (Mh[i] == MODEL_DI ? 0 : Mh[i] == MODEL_BICYCLE ? 1 : 2) : 3;
+            if (gi == g) mem.push_back(i);
+        }
+        if (mem.empty()) continue;
+        std::stable_sort(mem.begin(), mem.end(), by_work);
+        tmpc_handle::Group& G = h->groups[h->n_groups++];
+        G.offset = (int)ord.size();
+        G.count = (int)mem.size();
+        ord.insert(ord.end(), mem.begin(), mem.end());
+        if (g < 3) {
+            G.model = Mh[mem[0]];
+            G.threads = o->threads > 0 ? o->threads : 256;
+            int Tmax = 0;
+            for (int i : mem) Tmax = std::max(Tmax, Nh[i] + 1);
+            fmax = std::max(fmax, fast::arena_floats_host(G.model, Tmax));
+            // shared arena: the longest instance if it fits with 2 CTAs per SM, else a
+            // third of the opt-in limit (longer instances use their global arena)
+            const long long need = sizeof(float) * fast::arena_floats_host(G.model, Tmax);
+            const long long cap = std::max(48LL * 1024, (long long)max_optin / 2 - 8 * 1024);
+            G.smem = (size_t)std::min(need, need <= cap ? need : (long long)max_optin / 3);
+            int per = 0;
+            e = fast::prepare(G.model, G.smem, G.threads, &per);
+            if (e != cudaSuccess || per < 1) { set_err("fast::prepare", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
+            G.grid = std::max(1, std::min(G.count, per * h->nsm));
+        } else {
+            G.model = -1;
+        }
+    }
+    // backward: every instance, longest first
+    std::vector<int> bord(d->batch);
+    std::iota(bord.begin(), bord.end(), 0);
+    std::stable_sort(bord.begin(), bord.end(), by_work);
+    ord.insert(ord.end(), bord.begin(), bord.end());
+    e = cudaMemcpy(h->order, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { set_err("cudaMemcpy(order)", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
+    if (fmax > 0) {
+        h->fstride = (fmax + 31) & ~31LL;
+        e = cudaMalloc(&h->fws, sizeof(float) * h->fstride * d->batch);
+        if (e != cudaSuccess) { set_err("cudaMalloc(fast arenas)", e); tmpc_destroy(h); return TMPC_ERR_OOM; }
+    }
+
     h->threads = o->threads > 0 ? o->threads : (n <= 16 ? 128 : 256);
     h->smem = smem_bytes(n);
     if (h->smem > 48 * 1024) {
@@ -497,7 +553,7 @@ tmpc_status tmpc_update_params(tmpc_handle* h, const tmpc_params* p) {
 tmpc_status tmpc_set_options(tmpc_handle* h, const tmpc_options* o) {
     if (!h) return TMPC_ERR_NOT_SETUP;
     if (!o || check_options(o) != TMPC_OK) return TMPC_ERR_INVALID_ARG;
-    if (o->threads != h->o.threads) return TMPC_ERR_INVALID_ARG;  // launch shape is fixed at setup
+    if (o->threads != h->o.threads || o->solver != h->o.solver) return TMPC_ERR_INVALID_ARG;  // fixed at setup
     h->o = *o;
     return TMPC_OK;
 }
@@ -505,10 +561,20 @@ tmpc_status tmpc_set_options(tmpc_handle* h, const tmpc_options* o) {
 static tmpc_status launch_solve(tmpc_handle* h, const tmpc_params& p, const float* x0,
                                 const tmpc_solution& out, int warm, cudaStream_t s) {
     KSol ks{out.z, out.xi, out.y_eq, out.y_ineq, out.status, out.stats};
-    TMPC_CUDA(cudaMemsetAsync(h->queue, 0, sizeof(int), s));
-    solve_kernel<<<h->grid_solve, h->threads, h->smem, s>>>(h->L, to_kopts(h->o), to_kparams(p), ks, h->ws,
-                                                            h->off, h->order, h->queue, x0, warm);
-    TMPC_CUDA(cudaGetLastError());
+    TMPC_CUDA(cudaMemsetAsync(h->queue, 0, sizeof(int) * 5, s));
+    const KOpts ko = to_kopts(h->o);
+    const KParams kp = to_kparams(p);
+    for (int g = 0; g < h->n_groups; ++g) {
+        const tmpc_handle::Group& G = h->groups[g];
+        if (G.model >= 0) {
+            TMPC_CUDA(fast::launch(G.model, G.grid, G.threads, G.smem, s, h->L, ko, kp, ks, h->fws, h->fstride,
+                                   h->order + G.offset, G.count, h->queue + g, x0, warm));
+        } else {
+            solve_kernel<<<std::min(h->grid_solve, G.count), h->threads, h->smem, s>>>(
+                h->L, ko, kp, ks, h->ws, h->off, h->order + G.offset, G.count, h->queue + g, x0, warm);
+            TMPC_CUDA(cudaGetLastError());
+        }
+    }
     return TMPC_OK;
 }
 
@@ -527,14 +593,16 @@ tmpc_status tmpc_backward(tmpc_handle* h, const float* x0, const tmpc_solution* 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     KSol ks{sol->z, sol->xi, sol->y_eq, sol->y_ineq, sol->status, sol->stats};
     KGrads kg{g->x0, g->Qd, g->Rd, g->Wd, g->ref, g->lin, g->lo, g->hi, g->gamma2, g->gamma1};
-    TMPC_CUDA(cudaMemsetAsync(h->queue, 0, sizeof(int), s));
+    TMPC_CUDA(cudaMemsetAsync(h->queue + 4, 0, sizeof(int), s));
     backward_kernel<<<h->grid_bwd, h->threads, h->smem, s>>>(h->L, to_kopts(h->o), to_kparams(h->p), ks, h->ws,
-                                                             h->off, h->order, h->queue, x0, dL_dz, dL_dxi, kg);
+                                                             h->off, h->order + h->d.batch, h->queue + 4, x0,
+                                                             dL_dz, dL_dxi, kg);
     TMPC_CUDA(cudaGetLastError());
     return TMPC_OK;
 }
 
-tmpc_status tmpc_solve_host(tmpc_handle* h, const tmpc_params* hp, const float* x0, tmpc_solution* ho, void* stream) {
+tmpc_status tmpc_solve_host(tmpc_handle* h, const tmpc_params* hp, const float* x0, const float* z_init,
+                            tmpc_solution* ho, void* stream) {
     if (!h) return TMPC_ERR_NOT_SETUP;
     if (!hp || !x0 || !ho || !ho->z || !ho->xi || !ho->y_eq || !ho->y_ineq) return TMPC_ERR_INVALID_ARG;
     if (!hp->N || !hp->model || !hp->Qd || !hp->Rd || !hp->lo || !hp->hi || !hp->dyn) return TMPC_ERR_INVALID_ARG;
@@ -561,7 +629,13 @@ tmpc_status tmpc_solve_host(tmpc_handle* h, const tmpc_params* hp, const float* 
     else dp.track = nullptr;
     TMPC_CUDA(h2d(x0, h->s_x0, sizeof(float) * B * d.nx));
     tmpc_solution ds = h->ss;
-    tmpc_status st = launch_solve(h, dp, h->s_x0, ds, 0, s);
+    if (z_init) {
+        TMPC_CUDA(h2d(z_init, ds.z, sizeof(float) * B * T * n));
+        TMPC_CUDA(cudaMemsetAsync(ds.xi, 0, sizeof(float) * B * T * d.ng, s));
+        TMPC_CUDA(cudaMemsetAsync(ds.y_eq, 0, sizeof(float) * B * T * d.nx, s));
+        TMPC_CUDA(cudaMemsetAsync(ds.y_ineq, 0, sizeof(float) * B * T * d.ng, s));
+    }
+    tmpc_status st = launch_solve(h, dp, h->s_x0, ds, z_init ? 1 : 0, s);
     if (st != TMPC_OK) return st;
     TMPC_CUDA(cudaMemcpyAsync(ho->z, ds.z, sizeof(float) * B * T * n, cudaMemcpyDeviceToHost, s));
     TMPC_CUDA(cudaMemcpyAsync(ho->xi, ds.xi, sizeof(float) * B * T * d.ng, cudaMemcpyDeviceToHost, s));
@@ -579,6 +653,7 @@ void tmpc_destroy(tmpc_handle* h) {
     if (h->ws) cudaFree(h->ws);
     if (h->order) cudaFree(h->order);
     if (h->stage) cudaFree(h->stage);
+    if (h->fws) cudaFree(h->fws);
     delete h;
 }
 

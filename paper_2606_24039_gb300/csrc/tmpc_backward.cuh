@@ -41,7 +41,7 @@ __device__ __forceinline__ float active_code(float y, float val, float lo, float
     return (soft && fabsf(xi) > eg) ? 2.f * side : side;
 }
 
-__device__ void backward_instance(const Ctx& c, const KOpts& o, const Smem& sm, const KLayout& L,
+__device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Smem& sm, const KLayout& L,
                                   const KSol& sol, int inst, const float* dLdz_all,
                                   const float* dLdxi_all, const KGrads& g) {
     const int n = c.n, nx = c.nx, ng = c.ng, T = c.T, N = c.N;

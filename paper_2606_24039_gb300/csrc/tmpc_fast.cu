@@ -1,0 +1,911 @@
+// Shared-memory SQP / ADMM kernels for the small models (see tmpc_fast.cuh).
+#include <cuda_runtime.h>
+
+#include "../../include/tmpc.h"
+#include "tmpc_fast.cuh"
+#include "tmpc_fast_api.h"
+
+namespace tmpc {
+namespace fast {
+
+// ---------------------------------------------------------------------------
+// S blocks and their block cyclic reduction.  Block (stage) e of Dm / Um / Fa
+// starts at e * BS; entry (i, j) of a block is at bx(i, j).
+// ---------------------------------------------------------------------------
+// Theta_t (diagonal block t of S) into Dm, Phi_t' (block (t, t+1) of S) into Um
+template <int M>
+__device__ __forceinline__ void form_S(const Inst<M>& c, float sigma, float rho_f, float rho_g) {
+    constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG, NN = N * N, BS = Inst<M>::BS;
+    const int T = c.T;
+    for (int e = threadIdx.x; e < T * NN; e += blockDim.x) {
+        const int t = e / NN, ij = e % NN, i = ij / N, j = ij % N;
+        float s = 0.f;
+        if (t < c.Nh) {
+            const float* A = c.Amt(t);
+#pragma unroll
+            for (int k = 0; k < NX; ++k) s += A[k * N + i] * A[k * N + j];
+        }
+        if (t > 0 && i < NX && j < NX) {
+#pragma unroll
+            for (int k = 0; k < NX; ++k) s += c.Ap(t - 1, k, i) * c.Ap(t - 1, k, j);
+        }
+        if (t == 0 && i == j && i < NX) s += 1.f;
+        float v = rho_f * s;
+#pragma unroll
+        for (int r = 0; r < NG; ++r) v += rho_g * c.Gval(t, r, i) * c.Gval(t, r, j);
+        if (i == j) v += c.Pd[t * N + i] + sigma;
+        c.Dm[t * BS + Inst<M>::bx(i, j)] = v;
+        // U_t = S[t][t+1] = Phi_t' with Phi_t = E_t + rho_f A^+_t' A^-_t  (E_t = -W on the u block)
+        float u = 0.f;
+        if (t < c.Nh) {
+            const float* A = c.Amt(t);
+            float a = 0.f;
+            if (j < NX) {
+#pragma unroll
+                for (int k = 0; k < NX; ++k) a += A[k * N + i] * c.Ap(t, k, j);
+            }
+            u = rho_f * a;
+            if (i == j && i >= NX) u -= c.W(i - NX);
+        }
+        c.Um[t * BS + Inst<M>::bx(i, j)] = u;
+    }
+    __syncthreads();
+}
+
+// In-place inverse of the SPD N x N block at A (N <= 8) by a group of 8
+// consecutive lanes: lane i < N keeps row i of [A | I] (lanes N..7 carry zero
+// rows and write nothing); Gauss-Jordan elimination without pivoting (the
+// pivots of an SPD matrix are positive), pivot rows broadcast by shuffles of
+// width 8 inside the group.  Returns false in every lane if a pivot is <= 0.
+template <int N>
+__device__ __forceinline__ bool group_spd_inverse(float* A, int i, unsigned gmask) {
+    static_assert(N <= 8, "lane groups of 8");
+    float a[N], e[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        a[j] = (i < N) ? A[blk<N>(i, j)] : 0.f;
+        e[j] = (i == j) ? 1.f : 0.f;
+    }
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        float pa[N], pe[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            pa[j] = __shfl_sync(gmask, a[j], k, 8);
+            pe[j] = __shfl_sync(gmask, e[j], k, 8);
+        }
+        float p = pa[k];
+        if (!(p > 0.f)) { ok = false; p = 1.f; }
+        const float ip = 1.f / p;
+        if (i == k) {
+#pragma unroll
+            for (int j = 0; j < N; ++j) { a[j] = pa[j] * ip; e[j] = pe[j] * ip; }
+        } else {
+            const float f = a[k] * ip;
+#pragma unroll
+            for (int j = 0; j < N; ++j) { a[j] -= f * pa[j]; e[j] -= f * pe[j]; }
+        }
+    }
+    if (i < N)
+#pragma unroll
+        for (int j = 0; j < N; ++j) A[blk<N>(i, j)] = e[j];
+    return __all_sync(gmask, ok);
+}
+
+// Block cyclic reduction factorisation of S, in place:
+//   Dm[e] <- Dinv_e,  Fa[e] <- Fa_e = U_a Dinv_e,  Fb[e] <- Fb_e = U_e' Dinv_e
+// for every stage e eliminated at level s (U_a = S[e-s][e], U_e = S[e][e+s]);
+// the surviving diagonal blocks and couplings are updated in Dm / Um.  Work is
+// split in row tasks (one row of one block per thread).
+// Returns false if a pivot block was not positive definite.
+template <int M>
+__device__ __forceinline__ bool cr_factor(const Inst<M>& c, int* flag) {
+    constexpr int N = Inst<M>::N, BS = Inst<M>::BS;
+    const int T = c.T;
+    auto bx = [](int i, int j) { return Inst<M>::bx(i, j); };
+    if (threadIdx.x == 0) *flag = 0;
+    __syncthreads();
+    const int lane_in_group = threadIdx.x % 8, group = threadIdx.x / 8, ngroups = blockDim.x / 8;
+    const unsigned gmask = 0xFFu << ((threadIdx.x % 32) / 8 * 8);
+    for (int s = 1; s < T; s <<= 1) {
+        const int s2 = s << 1;
+        const int ne = (T - s + s2 - 1) / s2;   // eliminated: e = s + q s2 < T
+        const int nsv = (T + s2 - 1) / s2;      // surviving:  i = q s2 < T
+        for (int q = group; q < ne; q += ngroups)
+                if (!group_spd_inverse<N>(c.Dm + (s + q * s2) * BS, lane_in_group, gmask) && lane_in_group == 0)
+                    *flag = 1;
+        __syncthreads();
+        // row i of Fa_e = U_{e-s} Dinv_e and of Fb_e = U_e' Dinv_e (U_e = S[e][e+s], 0 if e is last)
+        for (int w = threadIdx.x; w < ne * N; w += blockDim.x) {
+            const int e = s + (w / N) * s2, i = w % N;
+            const float* Ua = c.Um + (e - s) * BS;
+            const float* Ue = c.Um + e * BS;
+            const float* D = c.Dm + e * BS;
+            const bool hasb = e + s < T;
+            float ra[N], rb[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) { ra[j] = 0.f; rb[j] = 0.f; }
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const float ua = Ua[bx(i, k)], ub = hasb ? Ue[bx(k, i)] : 0.f;
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    const float d = D[bx(k, j)];
+                    ra[j] += ua * d;
+                    rb[j] += ub * d;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                c.Fa[e * BS + bx(i, j)] = ra[j];
+                c.Fb[e * BS + bx(i, j)] = rb[j];
+            }
+        }
+        __syncthreads();
+        // row i of D_i0 -= Fa_{i0+s} U_i0' + Fb_{i0-s} U_{i0-s}
+        for (int w = threadIdx.x; w < nsv * N; w += blockDim.x) {
+            const int i0 = (w / N) * s2, i = w % N;
+            float row[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) row[j] = 0.f;
+            if (i0 + s < T) {
+                const float* F = c.Fa + (i0 + s) * BS;
+                const float* U = c.Um + i0 * BS;
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    const float f = F[bx(i, k)];
+#pragma unroll
+                    for (int j = 0; j < N; ++j) row[j] += f * U[bx(j, k)];
+                }
+            }
+            if (i0 >= s) {
+                const float* F = c.Fb + (i0 - s) * BS;
+                const float* U = c.Um + (i0 - s) * BS;
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    const float f = F[bx(i, k)];
+#pragma unroll
+                    for (int j = 0; j < N; ++j) row[j] += f * U[bx(k, j)];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < N; ++j) c.Dm[i0 * BS + bx(i, j)] -= row[j];
+        }
+        __syncthreads();
+        // row i of the coupling of surviving i0 to i0 + 2s:  U_i0 = -Fa_{i0+s} U_{i0+s}
+        for (int w = threadIdx.x; w < nsv * N; w += blockDim.x) {
+            const int i0 = (w / N) * s2, i = w % N;
+            float row[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) row[j] = 0.f;
+            if (i0 + s2 < T) {
+                const float* F = c.Fa + (i0 + s) * BS;
+                const float* U = c.Um + (i0 + s) * BS;
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    const float f = F[bx(i, k)];
+#pragma unroll
+                    for (int j = 0; j < N; ++j) row[j] -= f * U[bx(k, j)];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < N; ++j) c.Um[i0 * BS + bx(i, j)] = row[j];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 8 && !group_spd_inverse<N>(c.Dm, threadIdx.x, 0xFFu) && threadIdx.x == 0) *flag = 1;
+    __syncthreads();
+    const bool ok = *flag == 0;
+    __syncthreads();
+    return ok;
+}
+
+// row i of a factor block dotted with an N-vector v (32-byte aligned rows for N = 8)
+template <int N>
+__device__ __forceinline__ float rowdot(const float* blk_, int i, const float* v) {
+    if constexpr (N == 8) {
+        const float4 a0 = reinterpret_cast<const float4*>(blk_ + i * 8)[0];
+        const float4 a1 = reinterpret_cast<const float4*>(blk_ + i * 8)[1];
+        float4 v0 = reinterpret_cast<const float4*>(v)[0], v1 = reinterpret_cast<const float4*>(v)[1];
+        if (i & 4) { const float4 t = v0; v0 = v1; v1 = t; }  // swapped halves of rows 4..7
+        return (a0.x * v0.x + a0.y * v0.y) + (a0.z * v0.z + a0.w * v0.w) +
+               ((a1.x * v1.x + a1.y * v1.y) + (a1.z * v1.z + a1.w * v1.w));
+    } else {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < N; ++k) s += blk_[blk<N>(i, k)] * v[k];
+        return s;
+    }
+}
+// column i of a factor block dotted with v
+template <int N>
+__device__ __forceinline__ float coldot(const float* blk_, int i, const float* v) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) s += blk_[blk<N>(k, i)] * v[k];
+    return s;
+}
+
+// Solve S x = r with the cyclic-reduction factors; r is consumed, x -> xo.
+// One barrier per level on the way down (r_i -= Fa_{i+s} r_{i+s} + Fb_{i-s} r_{i-s})
+// and one on the way up (x_e = Dinv_e r_e - Fa_e' x_{e-s} - Fb_e' x_{e+s}).
+template <int M>
+__device__ __forceinline__ void cr_solve(const Inst<M>& c, float* r, float* xo) {
+    constexpr int N = Inst<M>::N, BS = Inst<M>::BS;
+    const int T = c.T;
+    int top = 1;
+    while (top < T) top <<= 1;
+    for (int s = 1; s < T; s <<= 1) {
+        const int s2 = s << 1;
+        const int nsv = (T + s2 - 1) / s2;
+        for (int w = threadIdx.x; w < nsv * N; w += blockDim.x) {
+            const int i0 = (w / N) * s2, i = w % N;
+            float a = 0.f;
+            if (i0 + s < T) a += rowdot<N>(c.Fa + (i0 + s) * BS, i, r + (i0 + s) * N);
+            if (i0 >= s) a += rowdot<N>(c.Fb + (i0 - s) * BS, i, r + (i0 - s) * N);
+            r[i0 * N + i] -= a;
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) xo[i] = rowdot<N>(c.Dm, i, r);
+    __syncthreads();
+    for (int s = top >> 1; s >= 1; s >>= 1) {
+        const int s2 = s << 1;
+        if (s >= T) continue;
+        const int ne = (T - s + s2 - 1) / s2;
+        for (int w = threadIdx.x; w < ne * N; w += blockDim.x) {
+            const int e = s + (w / N) * s2, i = w % N;
+            float a = rowdot<N>(c.Dm + e * BS, i, r + e * N) - coldot<N>(c.Fa + e * BS, i, xo + (e - s) * N);
+            if (e + s < T) a -= coldot<N>(c.Fb + e * BS, i, xo + (e + s) * N);
+            xo[e * N + i] = a;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// model evaluation (one thread per stage)
+// ---------------------------------------------------------------------------
+// f_t(z_t, z_{t+1}) and optionally the dense A^-_t (NX x N, row-major)
+template <int M>
+__device__ __forceinline__ void dyn_eval(const Inst<M>& c, const float* zt, const float* zn, float* f, float* Am) {
+    constexpr int N = Inst<M>::N;
+    if constexpr (M == MODEL_DI) {
+        const float dt = c.dyn[0];
+        f[0] = zt[0] + dt * zt[2] + 0.5f * dt * dt * zt[4] - zn[0];
+        f[1] = zt[1] + dt * zt[3] + 0.5f * dt * dt * zt[5] - zn[1];
+        f[2] = zt[2] + dt * zt[4] - zn[2];
+        f[3] = zt[3] + dt * zt[5] - zn[3];
+    } else if constexpr (M == MODEL_QUAD) {
+        float phi[6], dPx[36], dPu[12];
+        quad_rk4(zt, zt + 6, c.dyn, phi, Am ? dPx : nullptr, Am ? dPu : nullptr);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) f[k] = phi[k] - zn[k];
+        if (Am) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+#pragma unroll
+                for (int j = 0; j < 6; ++j) Am[k * N + j] = dPx[k * 6 + j];
+                Am[k * N + 6] = dPu[k * 2];
+                Am[k * N + 7] = dPu[k * 2 + 1];
+            }
+        }
+    } else {  // bicycle, implicit midpoint
+        const float dt = c.dyn[0];
+        float mid[6], fc[6], Jx[36], Ju[12];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) mid[k] = 0.5f * (zt[k] + zn[k]);
+        bicycle_fc(mid, zt + 6, c.dyn[1], c.track, c.nt, c.dyn[2], fc, Am ? Jx : nullptr, Am ? Ju : nullptr);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) f[k] = zt[k] + dt * fc[k] - zn[k];
+        if (Am) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+#pragma unroll
+                for (int j = 0; j < 6; ++j) Am[k * N + j] = (k == j ? 1.f : 0.f) + 0.5f * dt * Jx[k * 6 + j];
+                Am[k * N + 6] = dt * Ju[k * 2];
+                Am[k * N + 7] = dt * Ju[k * 2 + 1];
+            }
+        }
+    }
+}
+
+// g_t(z) and the dense row of G_t (if the model has one)
+template <int M>
+__device__ __forceinline__ void con_eval(const Inst<M>& c, const float* z, float* g, float* grow) {
+    using Tr = Traits<M>;
+#pragma unroll
+    for (int r = 0; r < Tr::NG; ++r)
+        if (Tr::sel(r) >= 0) g[r] = z[Tr::sel(r)];
+    if constexpr (Tr::DENSE_ROW >= 0) {  // lateral track error of the bicycle
+        TrackPt tp = track_eval(c.track, c.nt, c.dyn[2], z[5]);
+        float sp, cp;
+        sincosf(tp.psic, &sp, &cp);
+        const float dx = z[0] - tp.xc, dy = z[1] - tp.yc;
+        g[Tr::DENSE_ROW] = -dx * sp + dy * cp;
+        if (grow) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) grow[j] = 0.f;
+            grow[0] = -sp;
+            grow[1] = cp;
+            grow[5] = tp.dxc * sp - tp.dyc * cp - tp.dpsic * (dx * cp + dy * sp);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// initial guess (same as tmpc_solver.cuh rollout)
+// ---------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ void rollout(const Inst<M>& c, int newton_steps) {
+    constexpr int N = Inst<M>::N, NX = Inst<M>::NX;
+    for (int e = threadIdx.x; e < c.T * N; e += blockDim.x) {
+        const int t = e / N, j = e % N;
+        c.zb[e] = (j >= NX) ? c.refv(t, j) : (t == 0 ? c.x0[j] : 0.f);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int t = 0; t < c.Nh; ++t) {
+            const float* z = c.zb + t * N;
+            float xn[NX];
+            if constexpr (M == MODEL_QUAD) {
+                quad_rk4(z, z + 6, c.dyn, xn, nullptr, nullptr);
+            } else if constexpr (M == MODEL_DI) {
+                const float dt = c.dyn[0];
+                xn[0] = z[0] + dt * z[2] + 0.5f * dt * dt * z[4];
+                xn[1] = z[1] + dt * z[3] + 0.5f * dt * dt * z[5];
+                xn[2] = z[2] + dt * z[4];
+                xn[3] = z[3] + dt * z[5];
+            } else {
+                float fc[6], zn[8], f[6], Am[6 * 8], Mx[36];
+                bicycle_fc(z, z + 6, c.dyn[1], c.track, c.nt, c.dyn[2], fc, nullptr, nullptr);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) xn[k] = z[k] + c.dyn[0] * fc[k];
+                for (int it = 0; it < newton_steps; ++it) {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) zn[k] = xn[k];
+                    zn[6] = c.zb[(t + 1) * N + 6];
+                    zn[7] = c.zb[(t + 1) * N + 7];
+                    dyn_eval<M>(c, z, zn, f, Am);
+                    // d f / d x_{t+1} = A^+_x = A^-_x - 2 I
+#pragma unroll
+                    for (int k = 0; k < 6; ++k)
+#pragma unroll
+                        for (int j = 0; j < 6; ++j) Mx[k * 6 + j] = Am[k * N + j] - (k == j ? 2.f : 0.f);
+                    small_solve(Mx, f, 6);
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) xn[k] -= f[k];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NX; ++k) c.zb[(t + 1) * N + k] = xn[k];
+        }
+    }
+    __syncthreads();
+}
+
+// QP approximation at zb in step coordinates (see tmpc_solver.cuh linearize)
+template <int M>
+__device__ __forceinline__ void linearize(const Inst<M>& c) {
+    using Tr = Traits<M>;
+    constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
+    const int T = c.T;
+    if constexpr (Tr::LTI) {  // double integrator, ZOH
+        if (threadIdx.x == 0) {
+            const float dt = c.dyn[0];
+            for (int i = 0; i < NX * N; ++i) c.Am[i] = 0.f;
+            for (int k = 0; k < 4; ++k) c.Am[k * N + k] = 1.f;
+            c.Am[0 * N + 2] = dt; c.Am[1 * N + 3] = dt;
+            c.Am[0 * N + 4] = 0.5f * dt * dt; c.Am[1 * N + 5] = 0.5f * dt * dt;
+            c.Am[2 * N + 4] = dt; c.Am[3 * N + 5] = dt;
+        }
+    }
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        const float* z = c.zb + t * N;
+        if (t < c.Nh) {
+            float f[NX];
+            dyn_eval<M>(c, z, z + N, f, Tr::LTI ? nullptr : c.Am + t * Inst<M>::AMS);
+#pragma unroll
+            for (int k = 0; k < NX; ++k) c.cv[(t + 1) * NX + k] = -f[k];
+        }
+        if (t == 0)
+#pragma unroll
+            for (int k = 0; k < NX; ++k) c.cv[k] = c.x0[k] - z[k];
+        float g[NG];
+        con_eval<M>(c, z, g, Tr::DENSE_ROW >= 0 ? c.Grow + t * N : nullptr);
+#pragma unroll
+        for (int r = 0; r < NG; ++r) {
+            c.glo[t * NG + r] = c.lob(t, r) - g[r];
+            c.ghi[t * NG + r] = c.hib(t, r) - g[r];
+        }
+    }
+    for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
+        const int t = e / N, j = e % N;
+        float gr = c.Cw(t, j) * (c.zb[e] - c.refv(t, j)) + c.linv(t, j);
+        float pd = c.Cw(t, j);
+        if (j >= NX) {
+            const float w = c.W(j - NX);
+            if (t < c.Nh) { gr += w * (c.zb[e] - c.zb[e + N]); pd += w; }
+            if (t > 0) { gr -= w * (c.zb[e - N] - c.zb[e]); pd += w; }
+        }
+        c.qv[e] = gr;
+        c.Pd[e] = pd;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// one ADMM iteration in increment form (see tmpc_solver.cuh admm_iter)
+// ---------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ void admm_iter(const Inst<M>& c, float rho_bar, float alpha) {
+    using Tr = Traits<M>;
+    constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
+    const int T = c.T;
+    const float rho_f = 1e3f * rho_bar, rho_g = rho_bar, inv_rho_g = 1.f / rho_bar;
+    // per-row vectors: w_f = y_f + rho_f p_f,  p_g = G x - z_g,  w_g = y_g + rho_g p_g
+    for (int e = threadIdx.x; e < T * NX; e += blockDim.x) c.wf[e] = c.yf[e] + rho_f * c.pf[e];
+    for (int e = threadIdx.x; e < T * NG; e += blockDim.x) {
+        const float p = c.Gx(c.x, e / NG, e % NG) - c.zg[e];
+        c.pg[e] = p;
+        c.wg[e] = c.yg[e] + rho_g * p;
+    }
+    __syncthreads();
+    // r = -(P x + q) - C' w_f - G' w_g   (= eta - S x)
+    for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
+        const int t = e / N, j = e % N;
+        float s = -(c.Pv(c.x, t, j) + c.qv[e]);
+        s -= c.Ctv(t, j, [&](int row, int k) { return c.wf[row * NX + k]; });
+        const float* wg = c.wg + t * NG;
+#pragma unroll
+        for (int r = 0; r < NG; ++r) {
+            if (Tr::sel(r) >= 0) { if (Tr::sel(r) == j) s -= wg[r]; }
+            else s -= c.Grow[t * N + j] * wg[r];
+        }
+        c.r[e] = s;
+    }
+    __syncthreads();
+    cr_solve<M>(c, c.r, c.dx);
+    for (int e = threadIdx.x; e < T * NX; e += blockDim.x) {
+        const float cd = c.Cx(c.dx, e / NX, e % NX);
+        c.yf[e] += rho_f * alpha * (c.pf[e] + cd);
+        c.pf[e] += alpha * cd;
+    }
+    for (int e = threadIdx.x; e < T * NG; e += blockDim.x) {
+        const int t = e / NG, r = e % NG;
+        const float zh = c.zg[e] + alpha * (c.pg[e] + c.Gx(c.dx, t, r));
+        const float v = zh + c.yg[e] * inv_rho_g;
+        float zn, xn;
+        project(v, c.glo[e], c.ghi[e], rho_g, c.gam2(r), c.gam1(r), zn, xn);
+        c.yg[e] += rho_g * (zh - zn);
+        c.zg[e] = zn;
+        c.xi[e] = xn;
+    }
+    for (int e = threadIdx.x; e < T * N; e += blockDim.x) c.x[e] += alpha * c.dx[e];
+    __syncthreads();
+}
+
+// residuals and normalisers (see tmpc_solver.cuh residuals)
+template <int M>
+__device__ __forceinline__ Res residuals(const Inst<M>& c, float* red) {
+    constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
+    const int T = c.T;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int e = threadIdx.x; e < T * NX; e += blockDim.x) {
+        const float cabs = c.cv[e] + c.Cx(c.zb, e / NX, e % NX);
+        v[0] = fmaxf(v[0], fin(c.pf[e]));
+        v[2] = fmaxf(v[2], fmaxf(fin(c.pf[e] + cabs), fin(cabs)));
+    }
+    for (int e = threadIdx.x; e < T * NG; e += blockDim.x) {
+        const int t = e / NG, r = e % NG;
+        const float gx = c.Gx(c.x, t, r), gzb = c.Gx(c.zb, t, r);
+        v[0] = fmaxf(v[0], fin(gx - c.zg[e]));
+        v[2] = fmaxf(v[2], fmaxf(fin(gx + gzb), fin(c.zg[e] + gzb)));
+        const float g2 = c.gam2(r);
+        if (g2 < kInf) {
+            v[1] = fmaxf(v[1], fin(slack_res(c.xi[e], c.yg[e], g2, c.gam1(r))));
+            v[3] = fmaxf(v[3], fmaxf(fin(g2 * c.xi[e]), fin(c.yg[e])));
+        }
+    }
+    for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
+        const int t = e / N, j = e % N;
+        const float px = c.Pv(c.x, t, j), pzb = c.Pv(c.zb, t, j);
+        const float aty = c.Ctv(t, j, [&](int row, int k) { return c.yf[row * NX + k]; }) +
+                          c.Gtw(t, j, [&](int r) { return c.yg[t * NG + r]; });
+        v[1] = fmaxf(v[1], fin(px + c.qv[e] + aty));
+        v[3] = fmaxf(v[3], fmaxf(fmaxf(fin(px + pzb), fin(aty)), fin(c.qv[e] - pzb)));
+    }
+    cta_max_k<4>(v, red);
+    return {v[0], v[1], v[2], v[3]};
+}
+
+// merit contributions of stage t at zb + a x (Appendix D), in FP32: cost
+// (incl. slack penalty), constraint violation V, and the magnitude of the
+// numbers entering both (for the FP32 tie allowance of the Armijo test)
+template <int M>
+__device__ __forceinline__ void stage_merit(const Inst<M>& c, int t, float a, float& cost, float& viol, float& scale) {
+    constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NU = Inst<M>::NU, NG = Inst<M>::NG;
+    float z[N], zn[N], f[NX], g[NG];
+#pragma unroll
+    for (int j = 0; j < N; ++j) z[j] = c.zb[t * N + j] + a * c.x[t * N + j];
+    float cs = 0.f, vs = 0.f, sc = 0.f;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const float d = z[j] - c.refv(t, j);
+        const float q = 0.5f * c.Cw(t, j) * d * d, l = c.linv(t, j) * z[j];
+        cs += q + l;
+        sc += q + fabsf(l) + 2.f * fabsf(z[j]);
+    }
+    if (t < c.Nh) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) zn[j] = c.zb[(t + 1) * N + j] + a * c.x[(t + 1) * N + j];
+#pragma unroll
+        for (int k = 0; k < NU; ++k) {
+            const float d = z[NX + k] - zn[NX + k];
+            cs += 0.5f * c.W(k) * d * d;
+        }
+        dyn_eval<M>(c, z, zn, f, nullptr);
+#pragma unroll
+        for (int k = 0; k < NX; ++k) vs += fabsf(f[k]);
+    }
+    if (t == 0)
+#pragma unroll
+        for (int k = 0; k < NX; ++k) vs += fabsf(z[k] - c.x0[k]);
+    con_eval<M>(c, z, g, nullptr);
+#pragma unroll
+    for (int r = 0; r < NG; ++r) {
+        const float xi = c.xib[t * NG + r] + a * (c.xi[t * NG + r] - c.xib[t * NG + r]);
+        const float g2 = c.gam2(r);
+        if (g2 < kInf) cs += 0.5f * g2 * xi * xi + c.gam1(r) * fabsf(xi);
+        const float gx = g[r] + xi;
+        vs += fmaxf(gx - c.hib(t, r), 0.f) + fmaxf(c.lob(t, r) - gx, 0.f);
+    }
+    cost = cs;
+    viol = vs;
+    scale = sc + fabsf(cs);
+}
+
+struct Red {
+    float* red;
+    double* redd;
+    double* lsacc;
+    int* flags;
+};
+
+// Appendix D line search.  Stage values of every candidate are written in
+// FP32 to scratch (the factor arena is idle here: the next SQP step refactors),
+// then one thread per (candidate, quantity) sums its stages in FP64.
+template <int M>
+__device__ __forceinline__ float linesearch(const Inst<M>& c, const KOpts& o, const Red& rs, float ystar_inf) {
+    constexpr int N = Inst<M>::N, NG = Inst<M>::NG;
+    const int T = c.T;
+    const int K = o.n_ls < 1 ? 1 : (o.n_ls > kMaxLs ? kMaxLs : o.n_ls);
+    if (K == 1) return 1.f;
+    float* val = c.Fa;  // [(2k + q) T + t], q = 0 cost, 1 violation; scale at 2(K+1)T
+    double gd = 0.0;
+    for (int e = threadIdx.x; e < T * N; e += blockDim.x) gd += (double)(c.qv[e] * c.x[e]);
+    for (int e = threadIdx.x; e < T * NG; e += blockDim.x) {
+        const int r = e % NG;
+        const float g2 = c.gam2(r);
+        if (g2 < kInf) {
+            const float x0 = c.xib[e], dx = c.xi[e] - c.xib[e];
+            gd += (double)(g2 * x0 * dx + c.gam1(r) * (x0 != 0.f ? (x0 > 0.f ? dx : -dx) : fabsf(dx)));
+        }
+    }
+    gd = cta_sum_d(gd, rs.redd);
+    for (int e = threadIdx.x; e < (K + 1) * T; e += blockDim.x) {
+        const int k = e / T, t = e % T;
+        const float a = k == 0 ? 0.f : ldexpf(1.f, -(k - 1));
+        float cs, vs, sc;
+        stage_merit<M>(c, t, a, cs, vs, sc);
+        val[(2 * k) * T + t] = cs;
+        val[(2 * k + 1) * T + t] = vs;
+        if (k == 0) val[2 * (K + 1) * T + t] = sc;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * (K + 1) + 1; q += blockDim.x) {
+        double sum = 0.0;
+        for (int t = 0; t < T; ++t) sum += (double)val[q * T + t];
+        rs.lsacc[q] = sum;
+    }
+    __syncthreads();
+    const double l0 = rs.lsacc[0], V0 = rs.lsacc[1];
+    const double mu = fmax(gd / (0.5 * fmax(V0, (double)o.eps_c)), (double)ystar_inf + 1e-4);
+    const double phi0 = l0 + mu * V0;
+    const double D = gd - mu * V0;
+    // FP32 evaluation error of the merit: differences below it are ties, and a
+    // tie satisfies the Armijo test (4 units of FP32 rounding on the magnitude
+    // of every term that enters phi)
+    const double tau = 4.0 * 5.9604644775390625e-08 * rs.lsacc[2 * (K + 1)] * fmax(1.0, mu);
+    float chosen = -1.f, best = 0.f;
+    double best_phi = INFINITY;
+    for (int k = 1; k <= K; ++k) {
+        const float a = ldexpf(1.f, -(k - 1));
+        const double ph = rs.lsacc[2 * k] + mu * rs.lsacc[2 * k + 1];
+        if (isfinite(ph) && ph <= phi0 + (double)o.ls_eta * a * D + tau) { chosen = a; break; }
+    }
+    if (chosen < 0.f) {
+        for (int k = 1; k <= K; ++k) {
+            const float a = ldexpf(1.f, -(k - 1));
+            const double ph = rs.lsacc[2 * k] + mu * rs.lsacc[2 * k + 1];
+            if (isfinite(ph) && ph < best_phi) { best_phi = ph; best = a; }
+        }
+        chosen = best;
+    }
+    __syncthreads();
+    return chosen;
+}
+
+// KKT residual of Eq. (sqp_stop) at (zb, xib, yfb, ygb) with the current linearisation
+template <int M>
+__device__ __forceinline__ float kkt(const Inst<M>& c, float* red) {
+    constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
+    const int T = c.T;
+    float v[1] = {0.f};
+    for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
+        const int t = e / N, j = e % N;
+        const float gr = c.qv[e] + c.Ctv(t, j, [&](int row, int k) { return c.yfb[row * NX + k]; }) +
+                         c.Gtw(t, j, [&](int r) { return c.ygb[t * NG + r]; });
+        v[0] = fmaxf(v[0], fin(gr));
+    }
+    for (int e = threadIdx.x; e < T * NX; e += blockDim.x) v[0] = fmaxf(v[0], fin(c.cv[e]));
+    for (int e = threadIdx.x; e < T * NG; e += blockDim.x) {
+        const int r = e % NG;
+        const float g2 = c.gam2(r);
+        if (g2 < kInf) v[0] = fmaxf(v[0], fin(slack_res(c.xib[e], c.ygb[e], g2, c.gam1(r))));
+        // bound violation of g + xi:  g + xi - hi = xi - ghi,  lo - g - xi = glo - xi
+        v[0] = fmaxf(v[0], fmaxf(c.xib[e] - c.ghi[e], c.glo[e] - c.xib[e]));
+    }
+    cta_max_k<1>(v, red);
+    return v[0];
+}
+
+template <int M>
+__device__ __forceinline__ bool factor(const Inst<M>& c, const KOpts& o, float rho, int* flag) {
+    form_S<M>(c, o.sigma, 1e3f * rho, rho);
+    return cr_factor<M>(c, flag);
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1 for one instance
+// ---------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const Red& rs, const KLayout& L, const KSol& out,
+                               int inst, int warm) {
+    constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
+    const int T = c.T;
+    if (threadIdx.x == 0) rs.flags[0] = 0;
+    c.cache_params();
+    const long long Ts = L.Nmax + 1;
+    if (warm) {
+        const float* z = out.z + inst * Ts * L.n;
+        const float* xi = out.xi + inst * Ts * L.ng;
+        const float* yf = out.yf + inst * Ts * L.nx;
+        const float* yg = out.yg + inst * Ts * L.ng;
+        for (int e = threadIdx.x; e < T * N; e += blockDim.x) c.zb[e] = z[(e / N) * L.n + e % N];
+        for (int e = threadIdx.x; e < T * NG; e += blockDim.x) {
+            c.xib[e] = xi[(e / NG) * L.ng + e % NG];
+            c.ygb[e] = yg[(e / NG) * L.ng + e % NG];
+        }
+        for (int e = threadIdx.x; e < T * NX; e += blockDim.x) c.yfb[e] = yf[(e / NX) * L.nx + e % NX];
+        __syncthreads();
+    } else {
+        rollout<M>(c, o.newton_steps);
+        for (int e = threadIdx.x; e < T * NG; e += blockDim.x) { c.xib[e] = 0.f; c.ygb[e] = 0.f; }
+        for (int e = threadIdx.x; e < T * NX; e += blockDim.x) c.yfb[e] = 0.f;
+        __syncthreads();
+    }
+    float rho = o.rho0, rp = 0.f, rd = 0.f, alpha_last = 1.f;
+    int admm_total = 0, nfact = 0, sqp_done = 0;
+    for (int it = 0; it < o.max_sqp; ++it) {
+        linearize<M>(c);
+        if (it > 0 && o.early_exit) {
+            if (kkt<M>(c, rs.red) <= o.eps_c) break;
+        }
+        ++nfact;
+        if (!factor<M>(c, o, rho, rs.flags + 1) && threadIdx.x == 0) rs.flags[0] = 1;
+        for (int e = threadIdx.x; e < T * N; e += blockDim.x) c.x[e] = 0.f;
+        for (int e = threadIdx.x; e < T * NX; e += blockDim.x) { c.yf[e] = c.yfb[e]; c.pf[e] = -c.cv[e]; }
+        for (int e = threadIdx.x; e < T * NG; e += blockDim.x) { c.yg[e] = c.ygb[e]; c.zg[e] = 0.f; c.xi[e] = 0.f; }
+        __syncthreads();
+        int k = 0;
+        for (k = 1; k <= o.max_admm; ++k) {
+            admm_iter<M>(c, rho, o.alpha);
+            const bool cc = o.early_exit && (k % o.check_every == 0);
+            const bool cr = (k % o.k_rho_iter == 0) && k < o.max_admm;
+            if (cc || cr || k == o.max_admm) {
+                const Res r = residuals<M>(c, rs.red);
+                rp = r.r_prim;
+                rd = r.r_dual;
+                const bool conv = rp <= o.eps_abs + o.eps_rel * r.pn && rd <= o.eps_abs + o.eps_rel * r.dn;
+                if (cc && conv) break;
+                if (cr && rd > 0.f && !conv) {
+                    const float ratio = (rp / fmaxf(r.pn, 1e-30f)) / fmaxf(rd / fmaxf(r.dn, 1e-30f), 1e-30f);
+                    const float cand = fminf(fmaxf(rho * sqrtf(ratio), o.rho_min), o.rho_max);
+                    if (fmaxf(cand / rho, rho / cand) > o.k_rho_ratio) {
+                        ++nfact;
+                        if (factor<M>(c, o, cand, rs.flags + 1)) {
+                            rho = cand;
+                        } else {
+                            ++nfact;
+                            if (!factor<M>(c, o, rho, rs.flags + 1) && threadIdx.x == 0) rs.flags[0] = 1;
+                        }
+                    }
+                }
+            }
+        }
+        admm_total += (k > o.max_admm) ? o.max_admm : k;
+        float ys[1] = {0.f};
+        for (int e = threadIdx.x; e < T * NX; e += blockDim.x) ys[0] = fmaxf(ys[0], fin(c.yf[e]));
+        for (int e = threadIdx.x; e < T * NG; e += blockDim.x) ys[0] = fmaxf(ys[0], fin(c.yg[e]));
+        cta_max_k<1>(ys, rs.red);
+        const float a = linesearch<M>(c, o, rs, ys[0]);
+        alpha_last = a;
+        for (int e = threadIdx.x; e < T * N; e += blockDim.x) c.zb[e] += a * c.x[e];
+        for (int e = threadIdx.x; e < T * NG; e += blockDim.x) {
+            c.xib[e] += a * (c.xi[e] - c.xib[e]);
+            c.ygb[e] += a * (c.yg[e] - c.ygb[e]);
+        }
+        for (int e = threadIdx.x; e < T * NX; e += blockDim.x) c.yfb[e] += a * (c.yf[e] - c.yfb[e]);
+        __syncthreads();
+        ++sqp_done;
+    }
+    linearize<M>(c);
+    const float kk = kkt<M>(c, rs.red);
+    float bad[1] = {0.f};
+    for (int e = threadIdx.x; e < T * N; e += blockDim.x) bad[0] = fmaxf(bad[0], fin(c.zb[e]));
+    cta_max_k<1>(bad, rs.red);
+    // write the solution (padded layout, zeros beyond the horizon / model dims)
+    float* z = out.z + inst * Ts * L.n;
+    float* xo = out.xi + inst * Ts * L.ng;
+    float* yfo = out.yf + inst * Ts * L.nx;
+    float* ygo = out.yg + inst * Ts * L.ng;
+    for (int e = threadIdx.x; e < Ts * L.n; e += blockDim.x) {
+        const int t = e / L.n, j = e % L.n;
+        z[e] = (t < T && j < N) ? c.zb[t * N + j] : 0.f;
+    }
+    for (int e = threadIdx.x; e < Ts * L.ng; e += blockDim.x) {
+        const int t = e / L.ng, r = e % L.ng;
+        const bool ok = t < T && r < NG;
+        xo[e] = ok ? c.xib[t * NG + r] : 0.f;
+        ygo[e] = ok ? c.ygb[t * NG + r] : 0.f;
+    }
+    for (int e = threadIdx.x; e < Ts * L.nx; e += blockDim.x) {
+        const int t = e / L.nx, k = e % L.nx;
+        yfo[e] = (t < T && k < NX) ? c.yfb[t * NX + k] : 0.f;
+    }
+    if (threadIdx.x == 0) {
+        int st = TMPC_INST_OK;
+        if (!(bad[0] < kInf) || !(kk < kInf)) st = TMPC_INST_NAN;
+        else if (rs.flags[0]) st = TMPC_INST_NOT_PD;
+        else if (!(kk <= o.eps_c)) st = TMPC_INST_MAX_ITER;
+        if (out.status) out.status[inst] = st;
+        if (out.stats) {
+            float* s = out.stats + (long long)inst * TMPC_STATS;
+            s[0] = (float)sqp_done; s[1] = (float)admm_total; s[2] = rp; s[3] = rd;
+            s[4] = rho; s[5] = (float)nfact; s[6] = kk; s[7] = alpha_last;
+        }
+    }
+    __syncthreads();
+}
+
+// Persistent kernel over the instances listed in `order` (all of model M); an
+// instance whose arena does not fit `smem_floats` uses its global slot.
+template <int M>
+__global__ void __launch_bounds__(256, 2) solve_kernel(KLayout L, KOpts o, KParams p, KSol out, float* gws,
+                                                    long long gstride, const int* order, int count,
+                                                    int* queue, const float* x0, int warm,
+                                                    long long smem_floats) {
+    extern __shared__ __align__(16) float arena[];
+    __shared__ float red[32 * 8];
+    __shared__ double redd[64];
+    __shared__ double lsacc[2 * (kMaxLs + 1) + 2];
+    __shared__ int flags[4];
+    __shared__ int s_item;
+    const Red rs{red, redd, lsacc, flags};
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int q = s_item;
+        __syncthreads();
+        if (q >= count) break;
+        const int i = order[q];
+        Inst<M> c;
+        c.Nh = p.N[i];
+        c.T = c.Nh + 1;
+        c.lnx = L.nx; c.lnu = L.nu; c.ln = L.n; c.lng = L.ng;
+        const long long Ts = L.Nmax + 1;
+        c.x0 = x0 + (long long)i * L.nx;
+        c.Qd = p.Qd + i * Ts * L.nx;
+        c.Rd = p.Rd + i * Ts * L.nu;
+        c.Wd = p.Wd ? p.Wd + (long long)i * L.nu : nullptr;
+        c.ref = p.ref ? p.ref + i * Ts * L.n : nullptr;
+        c.lin = p.lin ? p.lin + i * Ts * L.n : nullptr;
+        c.lo = p.lo + i * Ts * L.ng;
+        c.hi = p.hi + i * Ts * L.ng;
+        c.g2 = p.g2 ? p.g2 + (long long)i * L.ng : nullptr;
+        c.g1 = p.g1 ? p.g1 + (long long)i * L.ng : nullptr;
+        c.dyn = p.dyn + (long long)i * L.n_dyn;
+        c.track = p.track ? p.track + (long long)i * (L.n_track + 1) * 4 : nullptr;
+        c.nt = 0;
+        if (M == MODEL_BICYCLE) {
+            const float ntf = c.dyn[3];
+            int nt = (ntf == ntf) ? (int)fminf(fmaxf(ntf + 0.5f, 1.f), (float)L.n_track) : 1;
+            c.nt = nt < 1 ? 1 : nt;
+        }
+        const long long need = arena_floats<M>(c.T);
+        c.carve(need <= smem_floats ? arena : gws + (long long)i * gstride);
+        solve_instance<M>(c, o, rs, L, out, i, warm);
+    }
+}
+
+template __global__ void solve_kernel<MODEL_DI>(KLayout, KOpts, KParams, KSol, float*, long long, const int*, int,
+                                                int*, const float*, int, long long);
+template __global__ void solve_kernel<MODEL_BICYCLE>(KLayout, KOpts, KParams, KSol, float*, long long, const int*,
+                                                     int, int*, const float*, int, long long);
+template __global__ void solve_kernel<MODEL_QUAD>(KLayout, KOpts, KParams, KSol, float*, long long, const int*,
+                                                  int, int*, const float*, int, long long);
+
+}  // namespace fast
+}  // namespace tmpc
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace tmpc {
+namespace fast {
+
+long long arena_floats_host(int model, int T) {
+    switch (model) {
+        case MODEL_DI: return arena_floats<MODEL_DI>(T);
+        case MODEL_BICYCLE: return arena_floats<MODEL_BICYCLE>(T);
+        case MODEL_QUAD: return arena_floats<MODEL_QUAD>(T);
+    }
+    return -1;
+}
+
+bool supported(int model) { return model == MODEL_DI || model == MODEL_BICYCLE || model == MODEL_QUAD; }
+
+static const void* kernel_of(int model) {
+    switch (model) {
+        case MODEL_DI: return (const void*)solve_kernel<MODEL_DI>;
+        case MODEL_BICYCLE: return (const void*)solve_kernel<MODEL_BICYCLE>;
+        case MODEL_QUAD: return (const void*)solve_kernel<MODEL_QUAD>;
+    }
+    return nullptr;
+}
+
+cudaError_t prepare(int model, size_t smem_bytes, int threads, int* blocks_per_sm) {
+    const void* k = kernel_of(model);
+    if (!k) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem_bytes);
+}
+
+cudaError_t launch(int model, int grid, int threads, size_t smem_bytes, cudaStream_t s, const KLayout& L,
+                   const KOpts& o, const KParams& p, const KSol& out, float* gws, long long gstride,
+                   const int* order, int count, int* queue, const float* x0, int warm) {
+    const long long sf = (long long)(smem_bytes / sizeof(float));
+    switch (model) {
+        case MODEL_DI:
+            solve_kernel<MODEL_DI><<<grid, threads, smem_bytes, s>>>(L, o, p, out, gws, gstride, order, count,
+                                                                       queue, x0, warm, sf);
+            break;
+        case MODEL_BICYCLE:
+            solve_kernel<MODEL_BICYCLE><<<grid, threads, smem_bytes, s>>>(L, o, p, out, gws, gstride, order,
+                                                                            count, queue, x0, warm, sf);
+            break;
+        case MODEL_QUAD:
+            solve_kernel<MODEL_QUAD><<<grid, threads, smem_bytes, s>>>(L, o, p, out, gws, gstride, order, count,
+                                                                         queue, x0, warm, sf);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fast
+}  // namespace tmpc

@@ -1,0 +1,269 @@
+// Shared-memory-resident SQP / ADMM path for the small models (double
+// integrator, kinematic bicycle, planar quadrotor): compile-time stage sizes,
+// one CTA per instance, every per-instance array in shared memory (or in the
+// handle's global workspace when an instance is too long to fit), and the
+// block-tridiagonal S = P + sigma I + rho_f C'C + rho_g G'G factored and solved
+// by block cyclic reduction.
+//
+// Block cyclic reduction = block LDL' of S after the odd-even permutation of
+// its stages: at level l the active stages are the multiples of s = 2^l; the
+// odd ones (e) are eliminated against their active neighbours a = e - s and
+// b = e + s,
+//     Dinv_e = D_e^{-1},  Fa_e = S_ae Dinv_e,  Fb_e = S_be Dinv_e,
+//     D_a -= Fa_e S_ea,   D_b -= Fb_e S_eb,    S_ab = -Fa_e S_eb,
+// and the solve is r_a -= Fa_e r_e, r_b -= Fb_e r_e on the way down,
+// x_e = Dinv_e r_e - Fa_e' x_a - Fb_e' x_b on the way up.  Its depth is
+// log2(N+1) levels instead of the 2(N+1) dependent stage steps of the
+// sequential factorisation, and it is the same factorisation (Cholesky of a
+// permuted SPD matrix), so it is as stable.
+//
+// The arithmetic of every phase is the one of tmpc_solver.cuh (same
+// step-coordinate ADMM with the tracked equality defect, same line search,
+// same KKT test); only the data placement and the S factorisation differ.
+#pragma once
+#include "tmpc_solver.cuh"
+
+namespace tmpc {
+namespace fast {
+
+// ---------------------------------------------------------------------------
+// model traits: compile-time sizes; inequality rows are either a selection of
+// one stage variable (sel[r] >= 0) or a dense row (sel[r] = -1, at most one)
+// ---------------------------------------------------------------------------
+template <int M> struct Traits;
+template <> struct Traits<MODEL_DI> {
+    static constexpr int NX = 4, NU = 2, NG = 4, IMPLICIT = 0, LTI = 1, DENSE_ROW = -1;
+    __device__ static constexpr int sel(int r) { return r == 0 ? 4 : r == 1 ? 5 : r == 2 ? 2 : 3; }
+};
+template <> struct Traits<MODEL_BICYCLE> {
+    static constexpr int NX = 6, NU = 2, NG = 5, IMPLICIT = 1, LTI = 0, DENSE_ROW = 4;
+    __device__ static constexpr int sel(int r) { return r == 0 ? 6 : r == 1 ? 7 : r == 2 ? 3 : r == 3 ? 4 : -1; }
+};
+template <> struct Traits<MODEL_QUAD> {
+    static constexpr int NX = 6, NU = 2, NG = 2, IMPLICIT = 0, LTI = 0, DENSE_ROW = -1;
+    __device__ static constexpr int sel(int r) { return r == 0 ? 6 : 7; }
+};
+
+// Per-instance arena: one list (name, floats) drives both the layout (carve)
+// and its size (arena_floats), so the two cannot disagree.
+//   factors of S:       Dm, Um, Fa, Fb           T x BS each (padded N x N blocks)
+//   stage vectors:      x, r, dx, qv, zb, Pd      T x N
+//   inequality rows:    zg, yg, xi, glo, ghi, xib, ygb, pg   T x NG
+//   equality rows:      yf, pf, cv, yfb           T x NX
+//   cached weights:     par                       32 (W, gamma2, gamma1)
+//   Jacobians:          Am (A^- per stage, padded stride AMS; one block if LTI), Grow (dense G row)
+#define TMPC_FAST_ARENA(X)                                                       \
+    X(Dm, (long long)T * BS) X(Um, (long long)T * BS) X(Fa, (long long)T * BS)   \
+    X(Fb, (long long)T * BS)                                                     \
+    X(x, T * N) X(r, T * N) X(dx, T * N) X(qv, T * N) X(zb, T * N) X(Pd, T * N) \
+    X(zg, T * NG) X(yg, T * NG) X(xi, T * NG) X(glo, T * NG) X(ghi, T * NG)      \
+    X(xib, T * NG) X(ygb, T * NG) X(pg, T * NG)                                  \
+    X(yf, T * NX) X(pf, T * NX) X(cv, T * NX) X(yfb, T * NX)                     \
+    X(par, 32)                                                                   \
+    X(Am, (Traits<M>::LTI ? (long long)AMS : (long long)T * AMS))                \
+    X(Grow, (Traits<M>::DENSE_ROW >= 0 ? (long long)T * N : 0LL))
+
+template <int M>
+__host__ __device__ constexpr long long arena_floats(int T) {
+    constexpr int NX = Traits<M>::NX, N = Traits<M>::NX + Traits<M>::NU, NG = Traits<M>::NG;
+    constexpr int BS = N * N + 4, AMS = NX * N + 8;
+    long long total = 0;
+#define TMPC_SIZE(name, cnt) total += (cnt);
+    TMPC_FAST_ARENA(TMPC_SIZE)
+#undef TMPC_SIZE
+    return total;
+}
+
+template <int M>
+struct Inst {
+    using Tr = Traits<M>;
+    static constexpr int NX = Tr::NX, NU = Tr::NU, N = NX + NU, NG = Tr::NG, NN = N * N;
+    static constexpr int AMS = NX * N + 8;
+    // factor blocks: stride NN + 4 floats (spreads the banks of neighbouring blocks) and,
+    // for N = 8, the two 4-float halves of rows 4..7 swapped (conflict-free 128-bit row loads)
+    static constexpr int BS = NN + 4;
+    __device__ static constexpr int bx(int i, int j) { return i * N + (N == 8 ? (j ^ (i & 4)) : j); }
+    int Nh, T, nt;
+    int lnx, lnu, ln, lng;
+    const float *x0, *Qd, *Rd, *Wd, *ref, *lin, *lo, *hi, *g2, *g1, *dyn, *track;
+    float *Dm, *Um, *Fa, *Fb;
+    float *x, *r, *dx, *qv, *zb, *Pd;
+    float *zg, *yg, *xi, *glo, *ghi, *xib, *ygb, *pg;
+    float *yf, *pf, *cv, *yfb;
+    float *wf, *wg;  // per-iteration row vectors, aliased on dx and xi (idle while they live)
+    float *Am, *Grow, *par;  // par: W[NU], gamma2[NG], gamma1[NG] cached in the arena
+
+    __device__ __forceinline__ void carve(float* p) {
+        const int T = this->T;
+#define TMPC_CARVE(name, cnt) name = p; p += (cnt);
+        TMPC_FAST_ARENA(TMPC_CARVE)
+#undef TMPC_CARVE
+        wf = dx;
+        wg = xi;
+    }
+    // copy the per-instance weights used in the inner loop into the arena
+    __device__ void cache_params() {
+        for (int k = threadIdx.x; k < NU + 2 * NG; k += blockDim.x) {
+            float v;
+            if (k < NU) v = Wd ? Wd[k] : 0.f;
+            else if (k < NU + NG) v = g2 ? g2[k - NU] : kInf;
+            else v = g1 ? g1[k - NU - NG] : 0.f;
+            par[k] = v;
+        }
+    }
+    __device__ __forceinline__ const float* Amt(int t) const { return Tr::LTI ? Am : Am + t * AMS; }
+    __device__ __forceinline__ float W(int k) const { return par[k]; }
+    __device__ __forceinline__ float refv(int t, int j) const { return ref ? ref[t * ln + j] : 0.f; }
+    __device__ __forceinline__ float linv(int t, int j) const { return lin ? lin[t * ln + j] : 0.f; }
+    __device__ __forceinline__ float Cw(int t, int j) const { return j < NX ? Qd[t * lnx + j] : Rd[t * lnu + j - NX]; }
+    __device__ __forceinline__ float gam2(int r) const { return par[NU + r]; }
+    __device__ __forceinline__ float gam1(int r) const { return par[NU + NG + r]; }
+    __device__ __forceinline__ float lob(int t, int r) const { return lo[t * lng + r]; }
+    __device__ __forceinline__ float hib(int t, int r) const { return hi[t * lng + r]; }
+
+    // A^+_t entry (k, j): implicit midpoint A^+ = [A^-_x - 2I, 0], explicit A^+ = [-I, 0]
+    __device__ __forceinline__ float Ap(int t, int k, int j) const {
+        if (j >= NX) return 0.f;
+        if (Tr::IMPLICIT) return Amt(t)[k * N + j] - (k == j ? 2.f : 0.f);
+        return k == j ? -1.f : 0.f;
+    }
+    // (G_t)_{r, j}
+    __device__ __forceinline__ float Gval(int t, int r, int j) const {
+        const int s = Tr::sel(r);
+        if (s >= 0) return j == s ? 1.f : 0.f;
+        return Grow[t * N + j];
+    }
+    // (G x)_t row r
+    __device__ __forceinline__ float Gx(const float* v, int t, int r) const {
+        const int s = Tr::sel(r);
+        if (s >= 0) return v[t * N + s];
+        const float* g = Grow + t * N;
+        float a = 0.f;
+#pragma unroll
+        for (int j = 0; j < N; ++j) a += g[j] * v[t * N + j];
+        return a;
+    }
+    // (G' w)_t entry j, w(r) functor
+    template <class F>
+    __device__ __forceinline__ float Gtw(int t, int j, F w) const {
+        float a = 0.f;
+#pragma unroll
+        for (int r = 0; r < NG; ++r) {
+            const int s = Tr::sel(r);
+            if (s >= 0) { if (s == j) a += w(r); }
+            else a += Grow[t * N + j] * w(r);
+        }
+        return a;
+    }
+    // (C v)_row entry k
+    __device__ __forceinline__ float Cx(const float* v, int row, int k) const {
+        if (row == 0) return v[k];
+        const int t = row - 1;
+        const float* A = Amt(t) + k * N;
+        const float* a = v + t * N;
+        const float* b = v + (t + 1) * N;
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < N; ++j) s += A[j] * a[j];
+        if (Tr::IMPLICIT) {
+#pragma unroll
+            for (int j = 0; j < NX; ++j) s += A[j] * b[j];
+            s -= 2.f * b[k];
+        } else {
+            s -= b[k];
+        }
+        return s;
+    }
+    // (C' v)_t entry j, v(row, k) functor
+    template <class F>
+    __device__ __forceinline__ float Ctv(int t, int j, F v) const {
+        float s = 0.f;
+        if (t == 0 && j < NX) s += v(0, j);
+        if (t < Nh) {
+            const float* A = Amt(t);
+#pragma unroll
+            for (int k = 0; k < NX; ++k) s += A[k * N + j] * v(t + 1, k);
+        }
+        if (t > 0 && j < NX) {
+            if (Tr::IMPLICIT) {
+                const float* A = Amt(t - 1);
+#pragma unroll
+                for (int k = 0; k < NX; ++k) s += A[k * N + j] * v(t, k);
+                s -= 2.f * v(t, j);
+            } else {
+                s -= v(t, j);
+            }
+        }
+        return s;
+    }
+    // (P v)_t entry j (cost Hessian: diagonal blocks Pd and the -W rate coupling)
+    __device__ __forceinline__ float Pv(const float* v, int t, int j) const {
+        float a = Pd[t * N + j] * v[t * N + j];
+        if (j >= NX) {
+            const float w = W(j - NX);
+            if (t > 0) a -= w * v[(t - 1) * N + j];
+            if (t < Nh) a -= w * v[(t + 1) * N + j];
+        }
+        return a;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// dense N x N SPD inverse by one thread (Cholesky, L^{-1}, L^{-T} L^{-1});
+// in place on a row-major block.  Returns false on a non-positive pivot.
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ constexpr int blk(int i, int j) { return i * N + (N == 8 ? (j ^ (i & 4)) : j); }
+
+template <int N>
+__device__ __forceinline__ bool spd_inverse(float* A) {
+    float L[N][N];
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < N; ++j) L[i][j] = (j <= i) ? A[blk<N>(i, j)] : 0.f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        float d = L[k][k];
+#pragma unroll
+        for (int p = 0; p < k; ++p) d -= L[k][p] * L[k][p];
+        if (!(d > 0.f)) { ok = false; d = 1.f; }
+        const float lk = sqrtf(d), il = 1.f / lk;
+        L[k][k] = lk;
+#pragma unroll
+        for (int i = k + 1; i < N; ++i) {
+            float s = L[i][k];
+#pragma unroll
+            for (int p = 0; p < k; ++p) s -= L[i][p] * L[k][p];
+            L[i][k] = s * il;
+        }
+    }
+    // column j of L^{-1} overwrites column j of L: entries (p, j), p < i, are already
+    // the inverse's, entries (i, p), p > j, and the diagonal (i, i), i > j, are still L's
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        L[j][j] = 1.f / L[j][j];
+#pragma unroll
+        for (int i = j + 1; i < N; ++i) {
+            float s = 0.f;
+#pragma unroll
+            for (int p = j; p < i; ++p) s += L[i][p] * L[p][j];
+            L[i][j] = -s / L[i][i];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            float s = 0.f;
+#pragma unroll
+            for (int p = i; p < N; ++p) s += L[p][i] * L[p][j];
+            A[blk<N>(i, j)] = s;
+            A[blk<N>(j, i)] = s;
+        }
+    return ok;
+}
+
+}  // namespace fast
+}  // namespace tmpc

@@ -1,0 +1,22 @@
+// Host interface of the shared-memory small-model kernels (tmpc_fast.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "tmpc_solver.cuh"
+
+namespace tmpc {
+namespace fast {
+
+// floats of per-instance storage needed by the shared-memory path for T stages
+long long arena_floats_host(int model, int T);
+// models handled by the shared-memory path
+bool supported(int model);
+// set the dynamic shared-memory limit of the model's kernel and query its occupancy
+cudaError_t prepare(int model, size_t smem_bytes, int threads, int* blocks_per_sm);
+// launch the persistent kernel over `count` instances listed in `order`
+cudaError_t launch(int model, int grid, int threads, size_t smem_bytes, cudaStream_t s, const KLayout& L,
+                   const KOpts& o, const KParams& p, const KSol& out, float* gws, long long gstride,
+                   const int* order, int count, int* queue, const float* x0, int warm);
+
+}  // namespace fast
+}  // namespace tmpc

@@ -145,7 +145,7 @@ __device__ __forceinline__ float fin(float v) { return (v == v) ? fabsf(v) : kIn
 // model evaluation per stage (one thread)
 // ---------------------------------------------------------------------------
 // f_t at (zt, zn) and optionally the Jacobian blocks Am, Ap (row-major nx x n).
-__device__ void stage_dyn(const Ctx& c, int t, const float* zt, const float* zn, float* f,
+__device__ inline void stage_dyn(const Ctx& c, int t, const float* zt, const float* zn, float* f,
                           float* Am, float* Ap) {
     const int nx = c.nx, n = c.n;
     switch (c.model) {
@@ -207,7 +207,7 @@ __device__ void stage_dyn(const Ctx& c, int t, const float* zt, const float* zn,
 }
 
 // g_t(z) and optionally G_t (row-major ng x n)
-__device__ void stage_con(const Ctx& c, const float* z, float* g, float* G) {
+__device__ inline void stage_con(const Ctx& c, const float* z, float* g, float* G) {
     const int n = c.n, ng = c.ng, nx = c.nx;
     if (G)
         for (int i = 0; i < ng * n; ++i) G[i] = 0.f;
@@ -321,7 +321,7 @@ __device__ __forceinline__ float Gx_entry(const Ctx& c, const float* x, int t, i
 // initial guess: x_0 = x_init, u_t = u_ref_t, x_{t+1} from f_t = 0 (Newton for
 // the implicit model, the explicit map otherwise)
 // ---------------------------------------------------------------------------
-__device__ void rollout(const Ctx& c, const KOpts& o) {
+__device__ inline void rollout(const Ctx& c, const KOpts& o) {
     const int n = c.n, nx = c.nx, T = c.T;
     for (int i = threadIdx.x; i < T * n; i += blockDim.x) {
         const int t = i / n, j = i % n;
@@ -388,7 +388,7 @@ __device__ void rollout(const Ctx& c, const KOpts& o) {
 // the rho rule, czb = C zb, gzb = G zb; fv = f(zb) and gv = g(zb) for the
 // merit / KKT evaluations.
 // ---------------------------------------------------------------------------
-__device__ void linearize(const Ctx& c) {
+__device__ inline void linearize(const Ctx& c) {
     const int n = c.n, nx = c.nx, ng = c.ng, N = c.N, T = c.T;
     const bool cA = model_const_Am(c.model), cP = model_const_Ap(c.model), cG = model_const_G(c.model);
     // constant blocks
@@ -487,7 +487,7 @@ __device__ void linearize(const Ctx& c) {
 // Returns false if a pivot block was not positive definite (the factors are then
 // not usable; the failing pivot is replaced by 1 so that no inf/NaN is produced).
 // ---------------------------------------------------------------------------
-__device__ bool factor(const Ctx& c, const Smem& sm, float sigma, float rho_f, float rho_g,
+__device__ inline bool factor(const Ctx& c, const Smem& sm, float sigma, float rho_f, float rho_g,
                        bool use_gw) {
     if (threadIdx.x == 0) sm.flags[1] = 0;
     const int n = c.n, nx = c.nx, ng = c.ng, N = c.N, nn = n * n;
@@ -590,7 +590,7 @@ __device__ bool factor(const Ctx& c, const Smem& sm, float sigma, float rho_f, f
 
 // Solve S x = b with the block LDL' factors; b (T x n) is overwritten by the
 // forward sweep, the result goes to xo (T x n).
-__device__ void ldl_solve(const Ctx& c, float* b, float* xo) {
+__device__ inline void ldl_solve(const Ctx& c, float* b, float* xo) {
     const int n = c.n, N = c.N, nn = n * n;
     for (int t = 0; t < N; ++t) {
         const float* Om = c.Om + t * nn;
@@ -653,7 +653,7 @@ __device__ __forceinline__ void project(float v, float lo, float hi, float rho_g
 // and dual updates of Algorithm 3 follow.  In exact arithmetic this is the
 // paper's iteration; in FP32 the rho_f-scaled terms only ever multiply small,
 // accurately formed differences.
-__device__ void admm_iter(const Ctx& c, const KOpts& o, float rho_bar) {
+__device__ inline void admm_iter(const Ctx& c, const KOpts& o, float rho_bar) {
     const int n = c.n, nx = c.nx, ng = c.ng, T = c.T;
     const float rho_f = 1e3f * rho_bar, rho_g = rho_bar, alpha = o.alpha;
     for (int e = threadIdx.x; e < T * ng; e += blockDim.x) c.pg[e] = Gx_entry(c, c.x, e / ng, e % ng) - c.zg[e];
@@ -700,7 +700,7 @@ struct Res {
 // residuals of Eq. (admm:residuals) and the normalisers of
 // Eq. (admm:termination:slack), the latter in absolute coordinates
 // (x_abs = zb + x, z_abs = z_g + G zb, c_abs = c + C zb, q_abs = q - P zb).
-__device__ Res residuals(const Ctx& c, const Smem& sm) {
+__device__ inline Res residuals(const Ctx& c, const Smem& sm) {
     const int n = c.n, nx = c.nx, ng = c.ng, T = c.T;
     float v[4] = {0.f, 0.f, 0.f, 0.f};  // r_prim, r_dual, primal norm, dual norm
     for (int e = threadIdx.x; e < T * nx; e += blockDim.x) {
@@ -737,7 +737,7 @@ __device__ Res residuals(const Ctx& c, const Smem& sm) {
 // merit contributions of stage t at the point za = zb + a dz, xia = xib + a dxi
 // (Appendix D): cost (incl. slack penalty) and constraint violation V.
 // ---------------------------------------------------------------------------
-__device__ void stage_merit(const Ctx& c, int t, float a, double& cost, double& viol) {
+__device__ inline void stage_merit(const Ctx& c, int t, float a, double& cost, double& viol, double& scale) {
     const int n = c.n, nx = c.nx, ng = c.ng;
     float z[72], zn[72], f[64], g[64];
     for (int j = 0; j < n; ++j) z[j] = c.zb[t * n + j] + a * c.x[t * n + j];
@@ -745,6 +745,7 @@ __device__ void stage_merit(const Ctx& c, int t, float a, double& cost, double& 
     for (int j = 0; j < n; ++j) {
         const float d = z[j] - c.refv(t, j);
         cs += 0.5 * (double)c.Cw(t, j) * d * d + (double)c.linv(t, j) * z[j];
+        scale += 0.5 * (double)c.Cw(t, j) * d * d + fabs((double)c.linv(t, j) * z[j]) + 2.0 * fabs((double)z[j]);
     }
     if (t < c.N) {
         for (int j = 0; j < n; ++j) zn[j] = c.zb[(t + 1) * n + j] + a * c.x[(t + 1) * n + j];
@@ -767,10 +768,11 @@ __device__ void stage_merit(const Ctx& c, int t, float a, double& cost, double& 
     }
     cost += cs;
     viol += vs;
+    scale += fabs(cs);
 }
 
 // returns the chosen step (Appendix D)
-__device__ float linesearch(const Ctx& c, const KOpts& o, const Smem& sm, float ystar_inf) {
+__device__ inline float linesearch(const Ctx& c, const KOpts& o, const Smem& sm, float ystar_inf) {
     const int n = c.n, nx = c.nx, ng = c.ng, T = c.T;
     const int K = o.n_ls < 1 ? 1 : (o.n_ls > kMaxLs ? kMaxLs : o.n_ls);
     if (K == 1) return 1.f;
@@ -787,13 +789,14 @@ __device__ float linesearch(const Ctx& c, const KOpts& o, const Smem& sm, float 
     }
     gd = cta_sum_d(gd, sm.redd);
     // merit parts at a = 0 and at every candidate: thread-strided over (k, t)
-    for (int e = threadIdx.x; e < 2 * (K + 1); e += blockDim.x) sm.lsacc[e] = 0.0;
+    for (int e = threadIdx.x; e < 2 * (K + 1) + 1; e += blockDim.x) sm.lsacc[e] = 0.0;
     __syncthreads();
     for (int e = threadIdx.x; e < (K + 1) * T; e += blockDim.x) {
         const int k = e / T, t = e % T;
         const float a = k == 0 ? 0.f : ldexpf(1.f, -(k - 1));
-        double cs = 0.0, vs = 0.0;
-        stage_merit(c, t, a, cs, vs);
+        double cs = 0.0, vs = 0.0, sc = 0.0;
+        stage_merit(c, t, a, cs, vs, sc);
+        if (k == 0) atomicAdd(&sm.lsacc[2 * (K + 1)], sc);
         atomicAdd(&sm.lsacc[2 * k], cs);
         atomicAdd(&sm.lsacc[2 * k + 1], vs);
     }
@@ -802,12 +805,16 @@ __device__ float linesearch(const Ctx& c, const KOpts& o, const Smem& sm, float 
     const double mu = fmax(gd / (0.5 * fmax(V0, (double)o.eps_c)), (double)ystar_inf + 1e-4);
     const double phi0 = l0 + mu * V0;
     const double D = gd - mu * V0;
+    // FP32 evaluation error of the merit: differences below it are ties, and a
+    // tie satisfies the Armijo test (4 units of FP32 rounding on the magnitude
+    // of every term that enters phi)
+    const double tau = 4.0 * 5.9604644775390625e-08 * sm.lsacc[2 * (K + 1)] * fmax(1.0, mu);
     float chosen = -1.f, best = 0.f;
     double best_phi = INFINITY;
     for (int k = 1; k <= K; ++k) {
         const float a = ldexpf(1.f, -(k - 1));
         const double ph = sm.lsacc[2 * k] + mu * sm.lsacc[2 * k + 1];
-        if (isfinite(ph) && ph <= phi0 + (double)o.ls_eta * a * D) { chosen = a; break; }
+        if (isfinite(ph) && ph <= phi0 + (double)o.ls_eta * a * D + tau) { chosen = a; break; }
     }
     if (chosen < 0.f) {
         for (int k = 1; k <= K; ++k) {
@@ -823,7 +830,7 @@ __device__ float linesearch(const Ctx& c, const KOpts& o, const Smem& sm, float 
 
 // KKT residual of Eq. (sqp_stop) at (zb, xib, yfb, ygb) using the current
 // linearisation (Am, Ap, G, fv, gv at zb)
-__device__ float kkt(const Ctx& c, const Smem& sm) {
+__device__ inline float kkt(const Ctx& c, const Smem& sm) {
     const int n = c.n, nx = c.nx, ng = c.ng, T = c.T;
     float v[1] = {0.f};
     for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
@@ -852,7 +859,7 @@ __device__ float kkt(const Ctx& c, const Smem& sm) {
 }
 
 // initial primal-dual point from a solution in the padded layout
-__device__ void read_warm(const Ctx& c, const KLayout& L, const KSol& out, int i) {
+__device__ inline void read_warm(const Ctx& c, const KLayout& L, const KSol& out, int i) {
     const long long Ts = L.Nmax + 1;
     const float* z = out.z + i * Ts * L.n;
     const float* xi = out.xi + i * Ts * L.ng;

@@ -47,6 +47,7 @@ def tensors_from_batch(pb, device="cuda") -> dict:
     f = lambda a: None if a is None else torch.as_tensor(a, dtype=torch.float32).contiguous().to(device)
     out = {k: f(getattr(pb, k)) for k in PARAM_KEYS}
     out["x0"] = f(pb.x0)
+    out["z_init"] = f(getattr(pb, "z_init", None))
     out["N"] = torch.as_tensor(pb.N, dtype=torch.int32).contiguous().to(device)
     out["model"] = torch.as_tensor(pb.model, dtype=torch.int32).contiguous().to(device)
     return out
@@ -74,6 +75,7 @@ class Solver:
                     n_track=pb.n_track)
         s = cls(dims, t, options_from(pb.opts, **overrides))
         s.x0 = t["x0"]
+        s.z_init = t["z_init"]
         return s
 
     def _make_params(self, params):
@@ -124,9 +126,18 @@ class Solver:
         _abi.check(self.lib.tmpc_set_options(self.handle, ctypes.byref(options)), "tmpc_set_options")
         self.options = options
 
-    def tmpc_solve(self, x0, sol=None, warm_start=False, stream=None):
+    def tmpc_solve(self, x0, sol=None, warm_start=False, stream=None, z_init=None):
+        """Forward solve.  warm_start reads sol as the initial primal-dual guess;
+        z_init (device tensor shaped like sol["z"]) is copied into sol["z"] as the
+        initial primal guess with zero slacks and multipliers."""
         if sol is None:
             sol = self.alloc_solution(x0.device)
+        if z_init is not None:
+            sol["z"].copy_(z_init)
+            sol["xi"].zero_()
+            sol["y_eq"].zero_()
+            sol["y_ineq"].zero_()
+            warm_start = True
         s = self._sol_struct(sol)
         _abi.check(self.lib.tmpc_solve(self.handle, ctypes.c_void_p(x0.data_ptr()), ctypes.byref(s),
                                        1 if warm_start else 0, _stream_ptr(stream)), "tmpc_solve")
@@ -144,15 +155,16 @@ class Solver:
                                           ctypes.byref(g), _stream_ptr(stream)), "tmpc_backward")
         return grads
 
-    def tmpc_solve_host(self, host_params: dict, x0_host, out_host: dict, stream=None):
+    def tmpc_solve_host(self, host_params: dict, x0_host, out_host: dict, stream=None, z_init_host=None):
         """End-to-end solve from pinned host tensors (copies inside the call)."""
         p = _abi.Params()
         for k in ("N", "model") + PARAM_KEYS:
             v = host_params.get(k)
             setattr(p, k, None if v is None else v.data_ptr())
         s = self._sol_struct(out_host)
+        zi = None if z_init_host is None else ctypes.c_void_p(z_init_host.data_ptr())
         _abi.check(self.lib.tmpc_solve_host(self.handle, ctypes.byref(p), ctypes.c_void_p(x0_host.data_ptr()),
-                                            ctypes.byref(s), _stream_ptr(stream)), "tmpc_solve_host")
+                                            zi, ctypes.byref(s), _stream_ptr(stream)), "tmpc_solve_host")
         return out_host
 
     def close(self):

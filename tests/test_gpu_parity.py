@@ -43,7 +43,7 @@ def _grad_rel(a, b, scale):
 def _run(pb, **over):
     from paper_2606_24039_gb300 import Solver
     s = Solver.from_batch(pb, device="cuda", **over)
-    sol = s.tmpc_solve(s.x0)
+    sol = s.tmpc_solve(s.x0, z_init=s.z_init)
     torch.cuda.synchronize()
     return s, {k: v.cpu().numpy() for k, v in sol.items()}, sol
 
@@ -108,21 +108,26 @@ def _compare(pb, sol, idx, allow_flips=0, opts=None, sensitivity=False):
     return errs
 
 
-def test_double_integrator_single_instance():
+SOLVERS = [pytest.param(1, id="generic_ldl"), pytest.param(2, id="smem_cr")]
+
+
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_double_integrator_single_instance(solver):
     pb = w.double_integrator(B=1, N=20, max_admm=200)
-    s, sol, _ = _run(pb)
+    s, sol, _ = _run(pb, solver=solver)
     errs = _compare(pb, sol, [0])
     assert sol["status"][0] in (0, 1)
     assert sol["stats"][0][1] == 200 and sol["stats"][0][0] == 1
 
 
-def test_double_integrator_batch_ragged_horizons():
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_double_integrator_batch_ragged_horizons(solver):
     pb = w.double_integrator(B=6, N=20, max_admm=200)
     pb.N[:] = [20, 1, 2, 7, 13, 19]     # ragged, including the degenerate N = 1
     for i in range(6):
         N = int(pb.N[i])
         pb.Qd[i, N, :] = 10 * pb.Qd[i, 0, :]
-    s, sol, _ = _run(pb)
+    s, sol, _ = _run(pb, solver=solver)
     _compare(pb, sol, range(6))
 
 
@@ -132,27 +137,42 @@ def test_tracking_full_dims_fixed_iterations():
     _compare(pb, sol, range(3))
 
 
-def test_racing_sqp_equal_iterations():
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_racing_sqp_equal_iterations(solver):
     pb = w.racing(B=8, N=50)
-    s, sol, _ = _run(pb)
+    s, sol, _ = _run(pb, solver=solver)
     _compare(pb, sol, range(8), sensitivity=True)
 
 
-def test_uneven_model_mix():
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_uneven_model_mix(solver):
     pb = w.uneven(B=12, N_lo=10, N_hi=40, seed=77, max_sqp=4, max_admm=50)
-    s, sol, _ = _run(pb)
+    s, sol, _ = _run(pb, solver=solver)
     _compare(pb, sol, range(12), sensitivity=True)
+
+
+def test_long_instances_fall_back_to_global_arenas():
+    """Instances whose shared-memory arena does not fit run the same kernel on
+    their global-memory arena: a batch mixing short and very long horizons."""
+    pb2 = w.racing(B=6, N=400, max_sqp=2, max_admm=40, track_length=800.0)
+    pb2.N[:] = [400, 25, 300, 30, 12, 399]
+    for i in range(6):
+        N = int(pb2.N[i])
+        pb2.lin[i, :, 5] = 0.0
+        pb2.lin[i, N, 5] = -1.0
+    s, sol, _ = _run(pb2, solver=2)
+    _compare(pb2, sol, range(6), sensitivity=True)
 
 
 def test_host_entry_point_matches_device_entry_point():
     pb = w.racing(B=4, N=30, max_sqp=3)
     from paper_2606_24039_gb300 import Solver, tensors_from_batch
     s = Solver.from_batch(pb, device="cuda")
-    dev = s.tmpc_solve(s.x0)
+    dev = s.tmpc_solve(s.x0, z_init=s.z_init)
     torch.cuda.synchronize()
     hp = {k: (v.cpu().pin_memory() if v is not None else None) for k, v in tensors_from_batch(pb, "cpu").items()}
     ho = {k: v.cpu().pin_memory() for k, v in s.alloc_solution("cpu").items()}
-    s.tmpc_solve_host(hp, hp["x0"], ho)
+    s.tmpc_solve_host(hp, hp["x0"], ho, z_init_host=hp["z_init"])
     for k in ("z", "xi", "y_eq", "y_ineq", "status", "stats"):
         assert torch.equal(ho[k], dev[k].cpu()), k
 

@@ -88,9 +88,9 @@ class Options:
     newton_steps: int = 3
     early_exit: int = 0
     check_every: int = 25
-    bwd_rho: float = 1e3
+    bwd_rho: float = 1e4
     bwd_sigma: float = 1e-6
-    bwd_iters: int = 12
+    bwd_iters: int = 30
 
 
 @dataclasses.dataclass
@@ -115,6 +115,7 @@ class ProblemBatch:
     track: np.ndarray | None
     opts: Options
     name: str = ""
+    z_init: np.ndarray | None = None   # [B][Nm+1][n] initial primal guess (warm start), or None
     extra: dict = dataclasses.field(default_factory=dict)
 
     @property
@@ -148,7 +149,8 @@ class ProblemBatch:
         if self.track is not None and int(self.model[i]) == MODEL_BICYCLE:
             nt = int(round(self.dyn[i, 3]))
             tr = self.track[i, :nt + 1].copy()
-        return dict(model=int(self.model[i]), N=Ni, nx=nx, nu=nu, ng=ng,
+        z0 = None if self.z_init is None else self.z_init[i, :T, :nx + nu].copy()
+        return dict(model=int(self.model[i]), N=Ni, nx=nx, nu=nu, ng=ng, z_init=z0,
                     x0=self.x0[i, :nx].copy(), Qd=self.Qd[i, :T, :nx].copy(),
                     Rd=self.Rd[i, :T, :nu].copy(), Wd=self.Wd[i, :nu].copy(),
                     ref=ref, lin=lin, lo=self.lo[i, :T, :ng].copy(),
@@ -163,7 +165,7 @@ class ProblemBatch:
             self, N=s(self.N), model=s(self.model), x0=s(self.x0), Qd=s(self.Qd),
             Rd=s(self.Rd), Wd=s(self.Wd), ref=s(self.ref), lin=s(self.lin), lo=s(self.lo),
             hi=s(self.hi), gamma2=s(self.gamma2), gamma1=s(self.gamma1), dyn=s(self.dyn),
-            track=s(self.track), extra=dict(self.extra))
+            track=s(self.track), z_init=s(self.z_init), extra=dict(self.extra))
 
 
 def _empty(B, nx, nu, ng, N_max, n_dyn, n_track):
@@ -247,6 +249,27 @@ def closed_track(rng, length=2000.0, harmonics=12, ds=TRACK_DS, kappa_max=0.2):
     raise RuntimeError("closed_track: could not draw a track within the curvature bound")
 
 
+def centreline_guess(tab, N, dt, v0, wheelbase, ds=TRACK_DS):
+    """Initial guess that follows the centreline at constant speed v0: stage t sits at
+    arc length s_t = v0 t dt on the centreline with the centreline heading, the
+    steering angle atan(wheelbase kappa(s_t)) and zero acceleration (geometry of
+    the table only, linear interpolation; not dynamically exact)."""
+    nt = tab.shape[0] - 1
+    L = nt * ds
+    s = v0 * dt * np.arange(N + 1)
+    sm = np.mod(s, L)
+    grid = np.arange(nt + 1) * ds
+    xc = np.interp(sm, grid, tab[:, 0])
+    yc = np.interp(sm, grid, tab[:, 1])
+    psi = np.interp(sm, grid, tab[:, 2]) + 2 * np.pi * np.floor(s / L)
+    kap = np.interp(sm, grid, tab[:, 3])
+    dl = np.arctan(wheelbase * kap)
+    z = np.zeros((N + 1, 8))
+    z[:, 0], z[:, 1], z[:, 2], z[:, 3], z[:, 4], z[:, 5] = xc, yc, psi, v0, dl, s
+    z[:-1, 7] = np.diff(dl) / dt
+    return z
+
+
 # ----------------------------------------------------------------------------
 # per-model instance fillers
 # ----------------------------------------------------------------------------
@@ -263,6 +286,8 @@ def _fill_di(rng, a, i, N, nx_l, nu_l, dt=0.05, x0=None):
     a["lo"][i, 1:N + 1, 2:4] = -2.0
     a["hi"][i, 1:N + 1, 2:4] = 2.0
     a["dyn"][i, 0] = dt
+    if "z_init" in a:
+        a["z_init"][i, :N + 1, :nx] = a["x0"][i, :nx]
 
 
 def _fill_bicycle(rng, a, i, N, track_tab, dt=0.05, wheelbase=2.7, v0=None,
@@ -295,6 +320,8 @@ def _fill_bicycle(rng, a, i, N, track_tab, dt=0.05, wheelbase=2.7, v0=None,
     nt = track_tab.shape[0] - 1
     a["dyn"][i, 0:4] = np.array([dt, wheelbase, TRACK_DS, nt])
     a["track"][i, :nt + 1] = track_tab
+    if "z_init" in a:
+        a["z_init"][i, :N + 1, :8] = centreline_guess(track_tab, N, dt, v, wheelbase)
 
 
 QUAD_MASS, QUAD_INERTIA, QUAD_ARM, GRAVITY = 1.0, 0.01, 0.1, 9.81
@@ -311,6 +338,9 @@ def _fill_quad(rng, a, i, N, dt=0.05):
     a["lo"][i, :N + 1, 0:2] = 0.0
     a["hi"][i, :N + 1, 0:2] = 10.0
     a["dyn"][i, 0:5] = np.array([dt, QUAD_MASS, QUAD_INERTIA, QUAD_ARM, GRAVITY])
+    if "z_init" in a:
+        a["z_init"][i, :N + 1, :nx] = a["x0"][i, :nx]
+        a["z_init"][i, :N + 1, nx:nx + nu] = hover
 
 
 # ----------------------------------------------------------------------------
@@ -339,6 +369,7 @@ def racing(B=1024, N=50, seed=1002, max_sqp=10, max_admm=50, track_length=400.0)
     nx, nu, ng = 6, 2, 5
     nt = int(round(track_length / TRACK_DS))
     a = _empty(B, nx, nu, ng, N, 4, nt)
+    a["z_init"] = np.zeros((B, N + 1, nx + nu))
     for i in range(B):
         r = np.random.default_rng([seed, i])
         tab = open_spline_track(r, length=track_length)
@@ -424,6 +455,7 @@ def uneven(B=4096, N_lo=10, N_hi=200, seed=1004, max_sqp=10, max_admm=50) -> Pro
     track_len = 400.0
     nt = int(round(track_len / TRACK_DS))
     a = _empty(B, nx, nu, ng, N_max, 5, nt)
+    a["z_init"] = np.zeros((B, N_max + 1, nx + nu))
     for i in range(B):
         r = np.random.default_rng([seed, i])
         if models[i] == MODEL_DI:
@@ -444,6 +476,7 @@ def long_horizon(B=8, N=8192, seed=1005, max_sqp=5, max_admm=100, dt=0.01,
     nx, nu, ng = 6, 2, 5
     nt = int(round(track_length / TRACK_DS))
     a = _empty(B, nx, nu, ng, N, 4, nt)
+    a["z_init"] = np.zeros((B, N + 1, nx + nu))
     for i in range(B):
         r = np.random.default_rng([seed, i])
         tab = closed_track(r, length=track_length)
