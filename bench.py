@@ -38,18 +38,20 @@ import numpy as np  # noqa: E402
 METRIC = "OCP solves/sec (fwd and fwd+bwd) at 1e-5 KKT residual; % of HBM/FP32 roofline"
 UNIT = "solves/s"
 
-# algorithmic FP32 work of the path, per stage (racing model, n = 8, nx = 6, ng = 4),
-# counted from the dense block operations of the method ("Roofline"):
-FLOP_ADMM_STAGE = 970.0     # one ADMM iteration (eta, S solve, A x~, relax/project/dual)
-FLOP_FACTOR_STAGE = 4600.0  # one block LDL' factorisation stage (Theta, Phi, Delta, inverse, Omega)
-FLOP_LIN_STAGE = 400.0      # one linearisation stage (Jacobians, shifted bounds)
+# algorithmic FP32 work of the path per stage, counted from the dense block
+# operations of the method's formulas for the bicycle model (n = 8, nx = 6,
+# ng = 5); an FMA counts 2.
+FLOP_ADMM_STAGE = 1140.0    # one ADMM iteration: eta, block LDL' solve, C x~, G x~, relax, project, duals
+FLOP_FACTOR_STAGE = 4800.0  # one factorisation: Theta_t, Phi_t, Schur update, pivot inverse, off-diagonal factor
+FLOP_LIN_STAGE = 400.0      # one linearisation: Jacobians, cost blocks, shifted bounds
+FLOP_MERIT_STAGE = 200.0    # one merit evaluation (dynamics residual, cost, violation) per line-search candidate
 SMS, FP32_LANES = 152, 128
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--batch", type=int, default=1024)
@@ -57,7 +59,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-bwd", action="store_true", help="time the forward pass only")
-    ap.add_argument("--solver", type=int, default=0, help="0 auto, 1 generic sequential LDL', 2 shared-memory CR")
+    ap.add_argument("--solver", type=int, default=0, help="0 auto, 1 generic sequential LDL', 2 shared-memory CR, 3 CR on global arenas")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the host-memory end-to-end timing")
     return ap.parse_args()
 
@@ -73,7 +75,8 @@ def config_of(args, pb):
             "batch": pb.B, "horizon": pb.N_max, "nx": pb.nx, "nu": pb.nu, "ng": pb.ng,
             "sqp_iters": pb.opts.max_sqp, "admm_iters": pb.opts.max_admm,
             "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{args.gpus}",
-            "solver": {0: "auto", 1: "generic sequential block LDL'", 2: "shared-memory block cyclic reduction"}[args.solver]}
+            "solver": {0: "auto", 1: "generic sequential block LDL'", 2: "shared-memory block cyclic reduction",
+                       3: "block cyclic reduction, global-memory arenas"}[args.solver]}
 
 
 # ----------------------------------------------------------------------------
@@ -155,8 +158,9 @@ class Clocks:
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
                  "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
                  "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                 "clocks_event_reasons.sw_power_cap,timestamp", "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(1.0)   # let the sampler start before the timed region
         except Exception:
             self.proc = None
         return self
@@ -170,11 +174,22 @@ class Clocks:
                 self.proc.kill()
             self.f.close()
 
-    def summary(self):
+    def summary(self, t0=None, t1=None):
         try:
             rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
         except Exception:
             return None
+        if t0 is not None:
+            import datetime
+            keep = []
+            for r in rows:
+                try:
+                    ts = datetime.datetime.strptime(r[-1].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except Exception:
+                    continue
+                if t0 <= ts <= t1:
+                    keep.append(r)
+            rows = keep or rows
         if not rows:
             return None
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
@@ -195,7 +210,50 @@ def algorithmic_flops(pb, stats):
     admm = stats[:, 1].astype(np.float64)
     fact = stats[:, 5].astype(np.float64)
     sqp = stats[:, 0].astype(np.float64)
-    return float(np.sum(T * (admm * FLOP_ADMM_STAGE + fact * FLOP_FACTOR_STAGE + (sqp + 1) * FLOP_LIN_STAGE)))
+    n_ls = float(pb.opts.n_ls)
+    return float(np.sum(T * (admm * FLOP_ADMM_STAGE + fact * FLOP_FACTOR_STAGE + (sqp + 1) * FLOP_LIN_STAGE
+                             + sqp * n_ls * FLOP_MERIT_STAGE)))
+
+
+FAST_MODELS = (0, 2, 3)   # models with a compile-time-sized shared-memory kernel
+
+
+def n_launch_groups(pb, solver):
+    """Solve kernels one forward call launches: one per fast-model group present,
+    plus one generic launch for every other model (all models when solver = 1)."""
+    models = set(int(m) for m in np.unique(pb.model))
+    if solver == 1:
+        return 1
+    fast = len(models & set(FAST_MODELS))
+    return fast + (1 if models - set(FAST_MODELS) else 0)
+
+
+KERNEL_SOURCES = ("tmpc_fast.cu", "tmpc_fast.cuh", "tmpc_fast_api.h", "tmpc_solver.cuh", "tmpc_models.cuh")
+
+
+def sources_digest():
+    """SHA-256 over the sources of the shared-memory solve kernel's translation unit."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2606_24039_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(f.encode())
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(pb):
+    """DRAM bytes (read + write) per launch of the solve kernel from the committed
+    ncu summary, scaled to this batch by instances; None when the kernel sources
+    changed since the counters were taken or no summary matches the workload."""
+    path = os.path.join(ROOT, "profiles", "solve_kernel_bicycle_racing_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    if rec.get("sources_sha256") != sources_digest() or rec.get("horizon") != pb.N_max:
+        return None
+    return rec["dram_bytes_per_launch"] * pb.B / rec["batch"]
 
 
 def run_gpu(args):
@@ -225,11 +283,24 @@ def run_gpu(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step():
-        s.tmpc_solve(s.x0, sol, z_init=s.z_init)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
 
-    def step_fb():
-        s.tmpc_solve(s.x0, sol, z_init=s.z_init)
+    def restart():
+        # every step starts from the same centreline guess (zero slacks and multipliers)
+        sol["z"].copy_(s.z_init)
+        for k in ("xi", "y_eq", "y_ineq"):
+            sol[k].zero_()
+
+    def step(kev=None):
+        restart()
+        if kev is not None:
+            kev[0].record(stream)
+        s.tmpc_solve(s.x0, sol, warm_start=True)
+        if kev is not None:
+            kev[1].record(stream)
+
+    def step_fb(kev=None):
+        step(kev)
         s.tmpc_backward(s.x0, sol, dLdz)
 
     for _ in range(args.warmup):
@@ -239,28 +310,32 @@ def run_gpu(args):
     torch.cuda.synchronize()
 
     def timed(fn):
-        times = []
+        times, ktimes = [], []
         for _ in range(args.steps):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             if world > 1:
                 dist.barrier()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
+            a, b, kev = ev(), ev(), (ev(), ev())
             a.record(stream)
-            fn()
+            fn(kev)
             b.record(stream)
             b.synchronize()
             times.append(a.elapsed_time(b))
-        return times
+            ktimes.append(kev[0].elapsed_time(kev[1]))
+        return times, ktimes
 
     with Clocks(local) as clk:
-        t_fwd = timed(step)
-        t_fb = timed(step_fb) if not args.skip_bwd else [float("nan")]
-    clocks = clk.summary()
+        t0 = time.time()
+        t_fwd, k_fwd = timed(step)
+        t_fb, _ = timed(step_fb) if not args.skip_bwd else ([float("nan")], None)
+        t1 = time.time()
+    clocks = clk.summary(t0, t1)
     stats = sol["stats"].cpu().numpy()
     status = sol["status"].cpu().numpy()
     kkt = stats[:, 6]
+    groups = n_launch_groups(pb, args.solver)
+    launches = args.steps * groups + (0 if args.skip_bwd else args.steps * (groups + 1))
 
     # end to end through the host-memory entry point
     hp = {k: (v.cpu().pin_memory() if v is not None else None) for k, v in tensors_from_batch(pb, "cpu").items()}
@@ -288,7 +363,8 @@ def run_gpu(args):
     total = pb.B * world
     value = total / (ms_f * 1e-3)
     flops = algorithmic_flops(pb, stats)
-    achieved = flops / (ms_f * 1e-3) / 1e12
+    ms_k = float(np.mean(k_fwd))          # the solve kernel(s) of one forward step, on the launching stream
+    achieved = flops / (ms_k * 1e-3) / 1e12
     peak_clock = 2070.0
     peak = SMS * FP32_LANES * 2 * peak_clock * 1e6 / 1e12
     if rank == 0:
@@ -300,9 +376,10 @@ def run_gpu(args):
             "clocks": clocks,
             "e2e": {"value": total / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": args.steps,
+            "gpu_launches": launches,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": measured_traffic(pb),
+                         "kernel": "fast::solve_kernel<MODEL_BICYCLE>", "kernel_ms": ms_k,
                          "peak_note": "FP32 FMA peak = 152 SM x 128 lanes x 2 flop x 2070 MHz (derived)"},
             "cpu_baseline": cpu_base,
             "quality": {"kkt_median": float(np.median(kkt)), "kkt_p90": float(np.percentile(kkt, 90)),

@@ -57,7 +57,7 @@ enum {
     TMPC_INST_NAN = 3         /* a non-finite value appeared                     */
 };
 
-/* model ids (problem families; see the design doc for their equations) */
+/* model ids (problem families; dynamics as in Appendix A of the paper, Remark A1) */
 enum {
     TMPC_MODEL_DOUBLE_INTEGRATOR = 0, /* nx=4 nu=2 ng=4, ZOH.  dyn = [dt]                          */
     TMPC_MODEL_LINEAR = 1,            /* layout nx, nu, ng=nu; x+ = A x + B u.  dyn = [A, B]      */
@@ -97,7 +97,9 @@ typedef struct {
     float bwd_rho, bwd_sigma;
     int32_t bwd_iters;
     int32_t threads;     /* CTA size per instance (0 = automatic)                     */
-    int32_t solver;      /* 0 automatic, 1 sequential block LDL', 2 block cyclic reduction */
+    int32_t solver;      /* 0 automatic, 1 sequential block LDL', 2 block cyclic reduction
+                          * (shared-memory arena per instance where it fits, else global),
+                          * 3 block cyclic reduction with every arena in global memory   */
 } tmpc_options;
 
 /* Problem parameters theta (the OCP of Appendix A with the cost of Eq. (cost)).

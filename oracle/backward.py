@@ -23,7 +23,7 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 3. The VJP of Eq. (loss_gradient): grad_theta L = -(dF/dtheta)' eta for
    theta = x_init, diagonal cost weights Q, R, W, references, linear cost
    term, active bounds, and the slack weights (gamma2, gamma1).
-Parity: pinned by tests/test_oracle_backward.py (central finite differences of
+Parity: pinned by tests/test_oracle_sqp_backward.py (central finite differences of
 the converged FP64 solution map, the gamma closed form, zero gradients of
 inactive bounds, and the LQ Riccati adjoint for dL/dx_init).
 """

@@ -16,8 +16,9 @@ The QP variable is the absolute stage vector (the constraints are written for
 the absolute point), so the linear term used by the QP is
 q_abs = q - P zbar: the model of the cost is
 l(zbar) + q'(z - zbar) + 1/2 (z - zbar)' P (z - zbar).
-Parity: pinned by tests/test_oracle_qp.py (dense S identity, Jacobians vs
-finite differences, q_abs of a quadratic cost equals its linear coefficient).
+Parity: pinned by tests/test_oracle_admm.py and tests/test_oracle_models.py
+(dense S identity, exact QP model of a quadratic cost, Jacobians vs
+finite differences).
 """
 from __future__ import annotations
 

@@ -127,7 +127,8 @@ def kkt_residual(inst, z, xi, yf, yg):
 def solve(inst, opts, warm=None, replay=None, record=False):
     """Algorithm 1 on one instance.  warm: optional dict(z, xi, yf, yg, rho_bar).
     replay: optional dict(alpha=[...], rho=[{k: rho}, ...]) that forces the line
-    search steps / rho schedule (decision replay).  Returns dict(z, xi, yf, yg,
+    search steps / rho schedule (decision replay); a missing "rho" key or a None
+    entry leaves that decision to the algorithm.  Returns dict(z, xi, yf, yg,
     rho_bar, stats, history)."""
     nx, ng, N = inst["nx"], inst["ng"], inst["N"]
     if warm is None and inst.get("z_init") is not None:
@@ -151,7 +152,7 @@ def solve(inst, opts, warm=None, replay=None, record=False):
         qp = qp_mod.build_qp(inst, z)
         x0 = z.reshape(-1)
         zg0 = qp["G"] @ x0
-        sched = None if replay is None else replay["rho"][it]
+        sched = None if replay is None or replay.get("rho") is None else replay["rho"][it]
         res = admm_mod.admm(qp, opts, x0, zg0, yf.reshape(-1), yg.reshape(-1), rho_bar,
                             rho_schedule=sched)
         rho_bar = res["rho_bar"]
@@ -162,9 +163,11 @@ def solve(inst, opts, warm=None, replay=None, record=False):
         yfs = res["yf"].reshape(N + 1, nx)
         ygs = res["yg"].reshape(N + 1, ng)
         ystar_inf = float(max(np.max(np.abs(yfs)), np.max(np.abs(ygs)) if ygs.size else 0.0))
-        if replay is not None:
-            a = replay["alpha"][it]
-            info = {}
+        forced = None
+        if replay is not None and replay.get("alpha") is not None and it < len(replay["alpha"]):
+            forced = replay["alpha"][it]
+        if forced is not None:
+            a, info = forced, {}
         else:
             a, info = linesearch(inst, opts, z, xi, zs - z, xis - xi, ystar_inf)
         z = z + a * (zs - z)

@@ -337,7 +337,7 @@ static tmpc_status check_options(const tmpc_options* o) {
     if (o->max_sqp < 0 || o->max_admm < 1 || o->n_ls < 1 || o->n_ls > kMaxLs) return TMPC_ERR_INVALID_ARG;
     if (o->newton_steps < 0 || o->bwd_iters < 1 || !(o->bwd_rho > 0.f)) return TMPC_ERR_INVALID_ARG;
     if (o->threads < 0 || o->threads > 256 || (o->threads % 32) != 0) return TMPC_ERR_INVALID_ARG;
-    if (o->solver < 0 || o->solver > 2) return TMPC_ERR_INVALID_ARG;
+    if (o->solver < 0 || o->solver > 3) return TMPC_ERR_INVALID_ARG;
     return TMPC_OK;
 }
 
@@ -464,6 +464,7 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
             const long long need = sizeof(float) * fast::arena_floats_host(G.model, Tmax);
             const long long cap = std::max(48LL * 1024, (long long)max_optin / 2 - 8 * 1024);
             G.smem = (size_t)std::min(need, need <= cap ? need : (long long)max_optin / 3);
+            if (o->solver == 3) G.smem = 0;   // every arena in global memory
             int per = 0;
             e = fast::prepare(G.model, G.smem, G.threads, &per);
             if (e != cudaSuccess || per < 1) { set_err("fast::prepare", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }

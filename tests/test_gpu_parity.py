@@ -73,6 +73,50 @@ def _sensitivity(pb, i, opts=None, trials=2, seed=0):
     return dev
 
 
+TIE_REL = 1e-4     # Armijo margins within this fraction of |phi(0)| count as ties
+
+
+def _near_tie_path(pb, i, zg, st, opts=None, bar=REL_TOL, budget=16):
+    """Decision replay for the line search of Appendix D.  The kernel takes the
+    Armijo test in FP32 on an FP32 step, so where the oracle's margin
+    phi(a) - phi(0) - eta a D of a candidate step lies within TIE_REL |phi(0)|
+    of zero the two may accept different steps.  Enumerates the step sequences
+    consistent with such ties (every other decision as the oracle takes it),
+    replays each in the oracle and accepts the instance when one of them lands
+    within `bar` of the kernel's solution with the kernel's last step."""
+    inst = pb.instance(i)
+    opts = opts or pb.opts
+    runs = [0]
+
+    def alts(info):
+        a = [2.0 ** (-k) for k in range(len(info["phis"]))]
+        band = TIE_REL * max(1.0, abs(info["phi0"]))
+        m = [p - (info["phi0"] + opts.ls_eta * ak * info["D"]) if np.isfinite(p) else np.inf
+             for ak, p in zip(a, info["phis"])]
+        out = []
+        for j in range(len(a)):
+            if m[j] <= band and all(m[k] >= -band for k in range(j)):
+                out.append(a[j])
+        return out
+
+    def dfs(prefix):
+        if runs[0] >= budget:
+            return False
+        runs[0] += 1
+        o = osqp.solve(inst, opts, replay=dict(alpha=list(prefix)), record=True)
+        hist = o["history"]
+        if len(prefix) >= len(hist):
+            return (_rel(zg, o["z"]) <= bar and hist[-1]["alpha"] == float(st[7])
+                    and st[0] == len(hist))
+        info = hist[len(prefix)]["ls"]
+        for a in alts(info):
+            if dfs(list(prefix) + [a]):
+                return True
+        return False
+
+    return dfs([])
+
+
 def _compare(pb, sol, idx, allow_flips=0, opts=None, sensitivity=False):
     """Strict mode: relative solution error <= 1e-4 and residuals within 1e-5
     (relative to the termination normalisers when they exceed 1).  Sensitivity
@@ -102,6 +146,8 @@ def _compare(pb, sol, idx, allow_flips=0, opts=None, sensitivity=False):
             slack = 10.0 * float(np.max(np.abs(zg - o["z"])))
         res_ok = abs(st[2] - os_["r_prim"]) <= RES_TOL * max(1.0, os_["prim_norm"]) + slack and \
                  abs(st[3] - os_["r_dual"]) <= RES_TOL * max(1.0, os_["dual_norm"]) + slack
+        if (e > bar or not res_ok) and sensitivity and _near_tie_path(pb, i, zg, st, opts, bar):
+            continue
         if e > bar or not res_ok:
             flips.append((i, e, bar, st[2], os_["r_prim"], st[3], os_["r_dual"], st[4], os_["rho_bar"]))
     assert len(flips) <= allow_flips, f"instances off the oracle: {flips}"
@@ -153,15 +199,45 @@ def test_uneven_model_mix(solver):
 
 def test_long_instances_fall_back_to_global_arenas():
     """Instances whose shared-memory arena does not fit run the same kernel on
-    their global-memory arena: a batch mixing short and very long horizons."""
-    pb2 = w.racing(B=6, N=400, max_sqp=2, max_admm=40, track_length=800.0)
-    pb2.N[:] = [400, 25, 300, 30, 12, 399]
+    a global-memory arena: a double-integrator batch mixing horizons of 600
+    stages (arena about 0.5 MB) with short ones, down to N = 1."""
+    pb = w.double_integrator(B=6, N=600, max_admm=200)
+    pb.N[:] = [600, 25, 400, 30, 1, 599]
     for i in range(6):
-        N = int(pb2.N[i])
-        pb2.lin[i, :, 5] = 0.0
-        pb2.lin[i, N, 5] = -1.0
-    s, sol, _ = _run(pb2, solver=2)
-    _compare(pb2, sol, range(6), sensitivity=True)
+        N = int(pb.N[i])
+        pb.Qd[i, N, :] = 10 * pb.Qd[i, 0, :]
+    s, sol, _ = _run(pb, solver=2)
+    _compare(pb, sol, range(6))
+
+
+def test_global_arenas_match_shared_arenas_bitwise():
+    """The cyclic-reduction kernel runs the same arithmetic whether an
+    instance's arena sits in shared or in global memory."""
+    pb = w.racing(B=8, N=40, max_sqp=3, max_admm=30)
+    pb.N[:] = [40, 7, 33, 1, 40, 20, 12, 39]
+    for i in range(8):
+        N = int(pb.N[i])
+        pb.lin[i, :, 5] = 0.0
+        pb.lin[i, N, 5] = -1.0
+    _, a, _ = _run(pb, solver=2)
+    _, b, _ = _run(pb, solver=3)
+    for k in ("z", "xi", "y_eq", "y_ineq", "status", "stats"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_long_racing_instances_one_sqp_step(solver):
+    """Racing instances of 300 to 400 stages (global-memory arenas on the
+    cyclic-reduction path) next to short ones: one SQP step of 100 ADMM
+    iterations and its line search."""
+    pb = w.racing(B=6, N=400, max_sqp=1, max_admm=100, track_length=800.0)
+    pb.N[:] = [400, 25, 300, 30, 12, 399]
+    for i in range(6):
+        N = int(pb.N[i])
+        pb.lin[i, :, 5] = 0.0
+        pb.lin[i, N, 5] = -1.0
+    s, sol, _ = _run(pb, solver=solver)
+    _compare(pb, sol, range(6), sensitivity=True)
 
 
 def test_host_entry_point_matches_device_entry_point():
