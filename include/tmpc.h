@@ -54,7 +54,9 @@ enum {
     TMPC_INST_OK = 0,         /* final SQP KKT residual (Eq. sqp_stop) <= eps_c   */
     TMPC_INST_MAX_ITER = 1,   /* iteration caps reached before eps_c             */
     TMPC_INST_NOT_PD = 2,     /* a pivot block of S was not positive definite    */
-    TMPC_INST_NAN = 3         /* a non-finite value appeared                     */
+    TMPC_INST_NAN = 3,        /* a non-finite value appeared                     */
+    TMPC_INST_INVALID = 4     /* tmpc_solve_static only: N or model of the instance
+                                 is out of range for the layout; not solved       */
 };
 
 /* model ids (problem families; dynamics as in Appendix A of the paper, Remark A1) */
@@ -215,6 +217,36 @@ tmpc_status tmpc_backward(tmpc_handle* h, const float* x0, const tmpc_solution* 
  * changed. */
 tmpc_status tmpc_solve_host(tmpc_handle* h, const tmpc_params* host_p, const float* x0,
                             const float* z_init, tmpc_solution* host_out, void* stream);
+
+/* Size of the device array that backs tmpc_solve_static (64 MiB per device). */
+#define TMPC_STATIC_SCRATCH_BYTES (64u << 20)
+
+/* Forward solve that allocates nothing.  The paper has no counterpart: it is an
+ * entry point for callers that may not allocate device memory when they solve,
+ * e.g. a control loop that must not block on the CUDA allocator or risk an
+ * out-of-memory failure once it runs, or code running while another component
+ * owns all device memory.  It computes what tmpc_setup + tmpc_solve compute with
+ * solver 1 (the generic kernel: Algorithm 1 around Algorithm 3), without a handle.
+ *
+ * d, o, p, x0, out: as for tmpc_setup / tmpc_solve (device pointers for p, x0
+ * and out; out->status is required, out->stats may be NULL).  o->solver must be
+ * 0 or 1.  Scratch: the instance order, the work-queue counter and one
+ * workspace per instance live in a file-scope device array of
+ * TMPC_STATIC_SCRATCH_BYTES.  A batch whose scratch does not fit is rejected
+ * with TMPC_ERR_INVALID_ARG before anything is enqueued; tmpc_last_error()
+ * then gives the bytes it needs (about 81 KB per racing instance of N = 50).
+ * Nothing in the scratch has to start at zero: the call's first kernel writes
+ * the order and the counter before the solve kernel reads them.
+ * Instance checks run on the device: an instance whose N or model does not fit
+ * the layout gets status TMPC_INST_INVALID and zero outputs.
+ * Set-up: the first call on a device (with that device current) looks up the
+ * address of the scratch array once; make that first call before any stream
+ * capture.  The scratch is shared by every caller on the device, so calls
+ * whose work can overlap (other streams, other host threads) race on it and
+ * corrupt each other's results: serialise them on one stream.  Instances run
+ * in no fixed order; each instance's result does not depend on it. */
+tmpc_status tmpc_solve_static(const tmpc_dims* d, const tmpc_options* o, const tmpc_params* p,
+                              const float* x0, tmpc_solution* out, int32_t warm_start, void* stream);
 
 /* Free the handle and its workspace (synchronises its allocations). NULL is a no-op. */
 void tmpc_destroy(tmpc_handle* h);

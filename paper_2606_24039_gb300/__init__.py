@@ -6,4 +6,5 @@ The compute path is the CUDA library behind the C ABI of include/tmpc.h
 (built by `build.build()`); this package only marshals arguments to it.
 """
 from ._abi import TmpcError, default_options, load  # noqa: F401
-from .solver import Solver, TmpcFunction, options_from, solve_ocp, tensors_from_batch  # noqa: F401
+from .solver import (Solver, TmpcFunction, options_from, solve_ocp, tensors_from_batch,  # noqa: F401
+                     tmpc_solve_static)

@@ -13,7 +13,8 @@ c_int_p = ctypes.POINTER(ctypes.c_int32)
 TMPC_STATS = 8
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
           4: "not set up", 5: "unsupported"}
-INST_STATUS = {0: "ok", 1: "max_iter", 2: "not_pd", 3: "nan"}
+INST_STATUS = {0: "ok", 1: "max_iter", 2: "not_pd", 3: "nan", 4: "invalid"}
+STATIC_SCRATCH_BYTES = 64 << 20
 
 
 class Dims(ctypes.Structure):
@@ -57,7 +58,7 @@ class Grads(ctypes.Structure):
 
 EXPORTS = ["tmpc_default_options", "tmpc_setup", "tmpc_update_params", "tmpc_set_options",
            "tmpc_solve", "tmpc_backward", "tmpc_solve_host", "tmpc_destroy",
-           "tmpc_status_string", "tmpc_last_error"]
+           "tmpc_status_string", "tmpc_last_error", "tmpc_solve_static"]
 
 _lib = None
 
@@ -92,6 +93,9 @@ def load(path: str | None = None):
     lib.tmpc_backward.restype = ctypes.c_int
     lib.tmpc_solve_host.argtypes = [vp, ctypes.POINTER(Params), vp, vp, ctypes.POINTER(Solution), vp]
     lib.tmpc_solve_host.restype = ctypes.c_int
+    lib.tmpc_solve_static.argtypes = [ctypes.POINTER(Dims), ctypes.POINTER(Options), ctypes.POINTER(Params), vp,
+                                      ctypes.POINTER(Solution), ctypes.c_int32, vp]
+    lib.tmpc_solve_static.restype = ctypes.c_int
     lib.tmpc_destroy.argtypes = [vp]
     lib.tmpc_destroy.restype = None
     lib.tmpc_status_string.argtypes = [ctypes.c_int]

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -656,6 +657,173 @@ void tmpc_destroy(tmpc_handle* h) {
     if (h->stage) cudaFree(h->stage);
     if (h->fws) cudaFree(h->fws);
     delete h;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// tmpc_solve_static: the generic solve kernel with its scratch (instance order,
+// work-queue counter, per-instance workspace) in a file-scope device array
+// instead of memory allocated by tmpc_setup.  Nothing here allocates.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_static_scratch[TMPC_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kStaticMaxDevices = 64;
+void* g_static_base[kStaticMaxDevices] = {};   // scratch address per device, looked up once
+std::mutex g_static_mu;
+
+// one-time set-up per device (the device must be current): address of the scratch array
+tmpc_status static_scratch_base(void** base) {
+    int dev = 0;
+    TMPC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kStaticMaxDevices) return TMPC_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_base[dev]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess || !ptr) {
+            set_err("cudaGetSymbolAddress(static scratch)", e);
+            return TMPC_ERR_CUDA;
+        }
+        g_static_base[dev] = ptr;
+    }
+    *base = g_static_base[dev];
+    return TMPC_OK;
+}
+
+// workspace offsets of one instance (same arrays as the workspace of tmpc_setup)
+long long static_ws_layout(const tmpc_dims& d, WsOff& off) {
+    const int n = d.nx + d.nu;
+    const long long T = d.N_max + 1, Nm = std::max(d.N_max, 1);
+    const long long nxn = (long long)d.nx * n, nn = (long long)n * n;
+    long long cur = 0;
+    auto take = [&](long long cnt) { const int at = align4(cur); cur = at + cnt; return at; };
+    off.Am = take(Nm * nxn);
+    off.Ap = take(Nm * nxn);
+    off.cv = take(T * d.nx);
+    off.fv = take(T * d.nx);
+    off.Gm = take(T * d.ng * n);
+    off.gv = take(T * d.ng);
+    off.glo = take(T * d.ng);
+    off.ghi = take(T * d.ng);
+    off.qv = take(T * n);
+    off.Dinv = take(T * nn);
+    off.Om = take(Nm * nn);
+    off.x = take(T * n);
+    off.xt = take(T * n);
+    off.eta = take(T * n);
+    off.zg = take(T * d.ng);
+    off.yg = take(T * d.ng);
+    off.xi = take(T * d.ng);
+    off.yf = take(T * d.nx);
+    off.zb = take(T * n);
+    off.xib = take(T * d.ng);
+    off.yfb = take(T * d.nx);
+    off.ygb = take(T * d.ng);
+    off.gw = take(T * d.ng);
+    off.czb = take(T * d.nx);
+    off.gzb = take(T * d.ng);
+    off.pf = take(T * d.nx);
+    off.pg = take(T * d.ng);
+    off.stride = align4(cur);
+    return off.stride;
+}
+
+// One CTA: checks every instance (the checks tmpc_setup makes on the host),
+// writes the valid ones to the tail of the order array and points the
+// work-queue counter at the first of them; an invalid instance gets
+// TMPC_INST_INVALID and zero outputs and is never solved.
+__global__ void static_prologue(KLayout L, const int* N, const int* model, int* order, int* queue, KSol out) {
+    __shared__ int s_valid;
+    if (threadIdx.x == 0) s_valid = 0;
+    __syncthreads();
+    const long long T = L.Nmax + 1;
+    for (int i = threadIdx.x; i < L.B; i += blockDim.x) {
+        const int Ni = N[i], m = model[i];
+        bool ok = Ni >= 1 && Ni <= L.Nmax && m >= 0 && m <= 3;
+        if (ok) {
+            const ModelDims md = model_dims(m, L.nx, L.nu, L.ng);
+            ok = md.nx <= L.nx && md.nu <= L.nu && md.ng <= L.ng;
+            if (m == MODEL_LINEAR) ok = ok && L.n_dyn >= L.nx * L.nx + L.nx * L.nu && L.ng <= L.nu;
+            if (m == MODEL_BICYCLE) ok = ok && L.n_track >= 1 && L.n_dyn >= 4;
+            if (m == MODEL_QUAD) ok = ok && L.n_dyn >= 5;
+        }
+        if (ok) {
+            const int slot = atomicAdd(&s_valid, 1);
+            order[L.B - 1 - slot] = i;
+        } else {
+            for (long long k = 0; k < T * L.n; ++k) out.z[i * T * L.n + k] = 0.f;
+            for (long long k = 0; k < T * L.ng; ++k) { out.xi[i * T * L.ng + k] = 0.f; out.yg[i * T * L.ng + k] = 0.f; }
+            for (long long k = 0; k < T * L.nx; ++k) out.yf[i * T * L.nx + k] = 0.f;
+            if (out.stats)
+                for (int k = 0; k < TMPC_STATS; ++k) out.stats[(long long)i * TMPC_STATS + k] = 0.f;
+            out.status[i] = TMPC_INST_INVALID;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *queue = L.B - s_valid;
+}
+
+}  // namespace
+
+extern "C" {
+
+tmpc_status tmpc_solve_static(const tmpc_dims* d, const tmpc_options* o, const tmpc_params* p, const float* x0,
+                              tmpc_solution* out, int32_t warm_start, void* stream) {
+    g_last_error[0] = '\0';
+    if (!d || !o || !p || !x0 || !out || !out->z || !out->xi || !out->y_eq || !out->y_ineq || !out->status)
+        return TMPC_ERR_INVALID_ARG;
+    if (d->batch < 1 || d->N_max < 1 || d->nx < 1 || d->nu < 1 || d->ng < 1 || d->n_dyn < 1 || d->n_track < 0)
+        return TMPC_ERR_INVALID_ARG;
+    const int n = d->nx + d->nu;
+    if (n > 72 || d->nx > 64 || d->ng > 64) return TMPC_ERR_UNSUPPORTED;
+    if (check_options(o) != TMPC_OK || check_params(*d, p) != TMPC_OK) return TMPC_ERR_INVALID_ARG;
+    if (o->solver != 0 && o->solver != 1) return TMPC_ERR_INVALID_ARG;
+    if (!aligned4(x0) || !aligned4(out->z) || !aligned4(out->xi) || !aligned4(out->y_eq) ||
+        !aligned4(out->y_ineq) || !aligned4(out->status) || (out->stats && !aligned4(out->stats)))
+        return TMPC_ERR_INVALID_ARG;
+
+    WsOff off;
+    const long long stride = static_ws_layout(*d, off);
+    const size_t head = ((sizeof(int) * ((size_t)d->batch + 1)) + 255) & ~size_t(255);  // order [B], counter
+    const size_t need = head + sizeof(float) * (size_t)stride * (size_t)d->batch;
+    if (need > (size_t)TMPC_STATIC_SCRATCH_BYTES) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "tmpc_solve_static: this batch needs %zu bytes of scratch (%lld per instance); "
+                 "the static scratch holds %zu bytes",
+                 need, (long long)(sizeof(float) * stride), (size_t)TMPC_STATIC_SCRATCH_BYTES);
+        return TMPC_ERR_INVALID_ARG;
+    }
+    void* base = nullptr;
+    const tmpc_status st = static_scratch_base(&base);
+    if (st != TMPC_OK) return st;
+    int* order = static_cast<int*>(base);
+    int* queue = order + d->batch;
+    float* ws = reinterpret_cast<float*>(static_cast<char*>(base) + head);
+
+    KLayout L;
+    L.B = d->batch; L.Nmax = d->N_max; L.nx = d->nx; L.nu = d->nu; L.ng = d->ng; L.n = n;
+    L.n_dyn = d->n_dyn; L.n_track = d->n_track;
+    const int threads = o->threads > 0 ? o->threads : (n <= 16 ? 128 : 256);
+    const size_t smem = smem_bytes(n);
+    if (smem > 48 * 1024)
+        TMPC_CUDA(cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, nsm = 1, per_sm = 1;
+    TMPC_CUDA(cudaGetDevice(&dev));
+    TMPC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    TMPC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel, threads, smem));
+    const int grid = std::max(1, std::min(d->batch, std::max(per_sm, 1) * nsm));
+
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const KSol ks{out->z, out->xi, out->y_eq, out->y_ineq, out->status, out->stats};
+    static_prologue<<<1, 256, 0, s>>>(L, p->N, p->model, order, queue, ks);
+    TMPC_CUDA(cudaGetLastError());
+    solve_kernel<<<grid, threads, smem, s>>>(L, to_kopts(*o), to_kparams(*p), ks, ws, off, order, d->batch,
+                                             queue, x0, warm_start ? 1 : 0);
+    TMPC_CUDA(cudaGetLastError());
+    return TMPC_OK;
 }
 
 }  // extern "C"

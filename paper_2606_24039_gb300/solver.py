@@ -179,6 +179,28 @@ class Solver:
             pass
 
 
+def tmpc_solve_static(dims: dict, params: dict, x0, sol: dict, options: _abi.Options | None = None,
+                      warm_start=False, stream=None):
+    """Forward solve through the no-allocation entry point (no handle; scratch in
+    the library's static device array).  `sol` must be preallocated (status
+    included); raises TmpcError when the batch does not fit the scratch."""
+    lib = _abi.load()
+    d = _abi.Dims(dims["batch"], dims["N_max"], dims["nx"], dims["nu"], dims["ng"], dims["n_dyn"],
+                  dims.get("n_track", 0))
+    o = options if options is not None else _abi.default_options()
+    p = _abi.Params()
+    for k in ("N", "model") + PARAM_KEYS:
+        v = params.get(k)
+        setattr(p, k, None if v is None else v.data_ptr())
+    s = Solver._sol_struct(sol)
+    code = lib.tmpc_solve_static(ctypes.byref(d), ctypes.byref(o), ctypes.byref(p), ctypes.c_void_p(x0.data_ptr()),
+                                 ctypes.byref(s), 1 if warm_start else 0, _stream_ptr(stream))
+    if code != 0:
+        raise _abi.TmpcError(f"tmpc_solve_static failed: {lib.tmpc_status_string(code).decode()}"
+                             f" ({lib.tmpc_last_error().decode()})")
+    return sol
+
+
 class TmpcFunction(torch.autograd.Function):
     """z, xi = OCP-solve(x0, Qd, Rd, ref, lo, hi) with the implicit-differentiation
     backward of the library.  The solver handle carries the remaining parameters."""

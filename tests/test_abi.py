@@ -68,3 +68,22 @@ def test_default_options_follow_the_paper(lib):
     assert o.k_rho_iter == 25 and abs(o.k_rho_ratio - 5.0) < 1e-7
     assert abs(o.rho_min - 1e-6) < 1e-12 and abs(o.rho_max - 1e6) < 1
     assert abs(o.ls_eta - 0.4) < 1e-7
+
+
+def test_static_entry_validates_before_touching_the_device(lib):
+    """tmpc_solve_static rejects null arguments and a batch whose scratch exceeds
+    the static array before any CUDA call (the pointers below are never read)."""
+    from paper_2606_24039_gb300 import _abi
+    d = _abi.Dims(4096, 30, 6, 2, 5, 4, 800)
+    o = _abi.default_options()
+    fake = 0x10000
+    p = _abi.Params(*([fake] * 13))
+    s = _abi.Solution(*([fake] * 6))
+    assert lib.tmpc_solve_static(None, ctypes.byref(o), ctypes.byref(p), fake, ctypes.byref(s), 0, None) == 1
+    assert lib.tmpc_solve_static(ctypes.byref(d), ctypes.byref(o), ctypes.byref(p), None, ctypes.byref(s), 0, None) == 1
+    o3 = _abi.default_options()
+    o3.solver = 2
+    assert lib.tmpc_solve_static(ctypes.byref(d), ctypes.byref(o3), ctypes.byref(p), fake, ctypes.byref(s), 0, None) == 1
+    assert lib.tmpc_solve_static(ctypes.byref(d), ctypes.byref(o), ctypes.byref(p), fake, ctypes.byref(s), 0, None) == 1
+    msg = lib.tmpc_last_error().decode()
+    assert "static scratch holds %d bytes" % _abi.STATIC_SCRATCH_BYTES in msg
