@@ -68,10 +68,13 @@ enum {
 };
 
 /* number of floats per instance in tmpc_solution.stats */
-#define TMPC_STATS 8
+#define TMPC_STATS 10
 /* stats[0] SQP iterations, [1] ADMM iterations (total), [2] r_prim and [3] r_dual of
  * the last QP (Eq. admm:residuals), [4] final rho_bar, [5] factorisations of S,
- * [6] KKT residual of Eq. (sqp_stop) at the returned point, [7] last line-search step. */
+ * [6] KKT residual of Eq. (sqp_stop) at the returned point, [7] last line-search step,
+ * [8], [9] line-search history of SQP iterations 0-5 and 6-11: the integer value
+ * holds 4 bits per iteration j at bit 4*(j mod 6), k for a step 2^-k (k >= 14 coded
+ * 14) and 15 for a zero step. */
 
 typedef struct {
     int32_t batch;   /* B >= 1                                                     */

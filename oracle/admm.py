@@ -114,11 +114,14 @@ def form_S(qp, sigma, rho_f, rho_g):
     return (qp["P"] + sigma * sp.identity(nz) + rho_f * (C.T @ C) + rho_g * (G.T @ G)).tocsr()
 
 
-def admm(qp, opts, x, zg, yf, yg, rho_bar, rho_schedule=None):
+def admm(qp, opts, x, zg, yf, yg, rho_bar, rho_schedule=None, perturb_S=None):
     """Run Algorithm 3 from the warm start (x, z_g, y_f, y_g) with rho_bar.
 
     rho_schedule: optional dict {iteration: rho_bar} that replaces the adaptive
     rule (used only to replay another solver's accepted rho values).
+    perturb_S: optional callable applied to S before each factorisation (used
+    only to measure how the fixed-count result responds to a backward error of
+    the factorisation, as a lower-precision solver incurs); None = exact S.
     Returns dict(x, zg, xi, yf, yg, rho_bar, iters, r_prim, r_dual, refactors,
     converged, rho_events)."""
     sigma, alpha = opts.sigma, opts.alpha
@@ -128,7 +131,8 @@ def admm(qp, opts, x, zg, yf, yg, rho_bar, rho_schedule=None):
     xi = np.zeros_like(zg)
 
     def factor(rb):
-        return _BandedSPD(form_S(qp, sigma, 1e3 * rb, rb))
+        S = form_S(qp, sigma, 1e3 * rb, rb)
+        return _BandedSPD(S if perturb_S is None else perturb_S(S))
 
     F = factor(rho_bar)
     refactors = 1

@@ -124,12 +124,14 @@ def kkt_residual(inst, z, xi, yf, yg):
     return max(stat, feas, viol), dict(stationarity=stat, dynamics=feas, bounds=viol)
 
 
-def solve(inst, opts, warm=None, replay=None, record=False):
+def solve(inst, opts, warm=None, replay=None, record=False, perturb_S=None):
     """Algorithm 1 on one instance.  warm: optional dict(z, xi, yf, yg, rho_bar).
     replay: optional dict(alpha=[...], rho=[{k: rho}, ...]) that forces the line
     search steps / rho schedule (decision replay); a missing "rho" key or a None
-    entry leaves that decision to the algorithm.  Returns dict(z, xi, yf, yg,
-    rho_bar, stats, history)."""
+    entry leaves that decision to the algorithm; with record, a forced step
+    still records the line-search quantities (merits, margins) along the
+    replayed path.  perturb_S: passed to the ADMM (backward-error analysis
+    only).  Returns dict(z, xi, yf, yg, rho_bar, stats, history)."""
     nx, ng, N = inst["nx"], inst["ng"], inst["N"]
     if warm is None and inst.get("z_init") is not None:
         # an instance that carries an initial primal guess starts from it (zero slacks / multipliers)
@@ -154,7 +156,7 @@ def solve(inst, opts, warm=None, replay=None, record=False):
         zg0 = qp["G"] @ x0
         sched = None if replay is None or replay.get("rho") is None else replay["rho"][it]
         res = admm_mod.admm(qp, opts, x0, zg0, yf.reshape(-1), yg.reshape(-1), rho_bar,
-                            rho_schedule=sched)
+                            rho_schedule=sched, perturb_S=perturb_S)
         rho_bar = res["rho_bar"]
         admm_iters += res["iters"]
         refactors += res["refactors"]
@@ -167,7 +169,8 @@ def solve(inst, opts, warm=None, replay=None, record=False):
         if replay is not None and replay.get("alpha") is not None and it < len(replay["alpha"]):
             forced = replay["alpha"][it]
         if forced is not None:
-            a, info = forced, {}
+            a = forced
+            info = linesearch(inst, opts, z, xi, zs - z, xis - xi, ystar_inf)[1] if record else {}
         else:
             a, info = linesearch(inst, opts, z, xi, zs - z, xis - xi, ystar_inf)
         z = z + a * (zs - z)

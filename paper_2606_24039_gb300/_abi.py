@@ -10,7 +10,7 @@ from . import build as _build
 c_float_p = ctypes.POINTER(ctypes.c_float)
 c_int_p = ctypes.POINTER(ctypes.c_int32)
 
-TMPC_STATS = 8
+TMPC_STATS = 10
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
           4: "not set up", 5: "unsupported"}
 INST_STATUS = {0: "ok", 1: "max_iter", 2: "not_pd", 3: "nan", 4: "invalid"}
@@ -104,6 +104,16 @@ def load(path: str | None = None):
     lib.tmpc_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
+
+
+def ls_history(stats_row, n_sqp):
+    """Line-search steps of the first min(n_sqp, 12) SQP iterations decoded from
+    stats[8:10] (2^-k per 4-bit code k, 0.0 for code 15)."""
+    out = []
+    for j in range(min(int(n_sqp), 12)):
+        code = (int(stats_row[8 + j // 6]) >> (4 * (j % 6))) & 15
+        out.append(0.0 if code == 15 else 2.0 ** (-code))
+    return out
 
 
 def check(code: int, what: str):

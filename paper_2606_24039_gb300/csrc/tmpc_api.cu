@@ -130,6 +130,7 @@ __device__ void solve_instance(const Ctx& c, const KOpts& o, const Smem& sm, con
         __syncthreads();
     }
     float rho = o.rho0, rp = 0.f, rd = 0.f, alpha_last = 1.f;
+    int ls_hist[2] = {0, 0};   // line-search step codes, 4 bits per SQP iteration
     int admm_total = 0, nfact = 0, sqp_done = 0;
     for (int it = 0; it < o.max_sqp; ++it) {
         linearize(c);
@@ -187,6 +188,7 @@ __device__ void solve_instance(const Ctx& c, const KOpts& o, const Smem& sm, con
         cta_max_k<1>(ys, sm.red);
         const float a = linesearch(c, o, sm, ys[0]);
         alpha_last = a;
+        if (it < 12) ls_hist[it / 6] |= ls_code(a) << (4 * (it % 6));
         for (int e = threadIdx.x; e < T * n; e += blockDim.x) c.zb[e] += a * c.x[e];
         for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
             c.xib[e] += a * (c.xi[e] - c.xib[e]);
@@ -212,6 +214,7 @@ __device__ void solve_instance(const Ctx& c, const KOpts& o, const Smem& sm, con
             float* s = out.stats + (long long)inst * TMPC_STATS;
             s[0] = (float)sqp_done; s[1] = (float)admm_total; s[2] = rp; s[3] = rd;
             s[4] = rho; s[5] = (float)nfact; s[6] = kk; s[7] = alpha_last;
+            s[8] = (float)ls_hist[0]; s[9] = (float)ls_hist[1];
         }
     }
     __syncthreads();

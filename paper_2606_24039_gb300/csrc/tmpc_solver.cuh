@@ -60,6 +60,17 @@ struct WsOff {
 #define kInf __int_as_float(0x7f800000)
 constexpr int kMaxLs = 16;
 
+// 4-bit code of a line-search step: k for alpha = 2^-k (k >= 14 coded 14), 15 for alpha = 0
+__device__ inline int ls_code(float a) {
+    if (!(a > 0.f)) return 15;
+    int k = 0;
+    while (k < 14 && a < 0.75f) {
+        a *= 2.f;
+        ++k;
+    }
+    return k;
+}
+
 // shared-memory scratch of one CTA
 struct Smem {
     float* A;      // n*n
