@@ -59,8 +59,10 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-bwd", action="store_true", help="time the forward pass only")
-    ap.add_argument("--solver", type=int, default=0, help="0 auto, 1 generic sequential LDL', 2 shared-memory CR, 3 CR on global arenas")
+    ap.add_argument("--solver", type=int, default=0, help="0 auto, 1 generic sequential LDL', 2 shared-memory CR, 3 CR on global arenas, "
+                    "4 warp-sequential LDL', 5 warp LDL' on global arenas")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the host-memory end-to-end timing")
+    ap.add_argument("--threads", type=int, default=0, help="threads per instance (0 = library default)")
     return ap.parse_args()
 
 
@@ -76,7 +78,9 @@ def config_of(args, pb):
             "sqp_iters": pb.opts.max_sqp, "admm_iters": pb.opts.max_admm,
             "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{args.gpus}",
             "solver": {0: "auto", 1: "generic sequential block LDL'", 2: "shared-memory block cyclic reduction",
-                       3: "block cyclic reduction, global-memory arenas"}[args.solver]}
+                       3: "block cyclic reduction, global-memory arenas",
+                       4: "shared-memory sequential block LDL' by one warp",
+                       5: "sequential block LDL' by one warp, global-memory arenas"}[args.solver]}
 
 
 # ----------------------------------------------------------------------------
@@ -277,7 +281,7 @@ def run_gpu(args):
     from paper_2606_24039_gb300 import Solver, build, tensors_from_batch
     build.build()
     pb = workload(args, rank)
-    s = Solver.from_batch(pb, device="cuda", solver=args.solver)
+    s = Solver.from_batch(pb, device="cuda", solver=args.solver, threads=args.threads)
     sol = s.alloc_solution("cuda")
     dLdz = torch.randn((pb.B, pb.N_max + 1, pb.n), device="cuda")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")

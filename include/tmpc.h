@@ -102,9 +102,13 @@ typedef struct {
     float bwd_rho, bwd_sigma;
     int32_t bwd_iters;
     int32_t threads;     /* CTA size per instance (0 = automatic)                     */
-    int32_t solver;      /* 0 automatic, 1 sequential block LDL', 2 block cyclic reduction
-                          * (shared-memory arena per instance where it fits, else global),
-                          * 3 block cyclic reduction with every arena in global memory   */
+    int32_t solver;      /* 0 automatic, 1 generic kernel (any model; sequential block LDL'
+                          * by the CTA, workspace in global memory), 2 block cyclic
+                          * reduction (shared-memory arena per instance where it fits, else
+                          * global), 3 as 2 with every arena in global memory, 4 sequential
+                          * block LDL' swept by one warp (shared-memory arena), 5 as 4 with
+                          * every arena in global memory.  2-5 apply to the double
+                          * integrator, bicycle and quadrotor; other models use 1.        */
 } tmpc_options;
 
 /* Problem parameters theta (the OCP of Appendix A with the cost of Eq. (cost)).

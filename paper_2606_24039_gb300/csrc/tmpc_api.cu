@@ -291,7 +291,7 @@ struct tmpc_handle {
     // work groups of the forward pass: g < 3 the shared-memory kernels of the
     // double integrator / bicycle / quadrotor, g = 3 the generic kernel
     struct Group {
-        int model = -1, offset = 0, count = 0, grid = 0, threads = 0;
+        int model = -1, offset = 0, count = 0, grid = 0, threads = 0, policy = 0;
         size_t smem = 0;
     } groups[4];
     int n_groups = 0;
@@ -341,7 +341,7 @@ static tmpc_status check_options(const tmpc_options* o) {
     if (o->max_sqp < 0 || o->max_admm < 1 || o->n_ls < 1 || o->n_ls > kMaxLs) return TMPC_ERR_INVALID_ARG;
     if (o->newton_steps < 0 || o->bwd_iters < 1 || !(o->bwd_rho > 0.f)) return TMPC_ERR_INVALID_ARG;
     if (o->threads < 0 || o->threads > 256 || (o->threads % 32) != 0) return TMPC_ERR_INVALID_ARG;
-    if (o->solver < 0 || o->solver > 3) return TMPC_ERR_INVALID_ARG;
+    if (o->solver < 0 || o->solver > 5) return TMPC_ERR_INVALID_ARG;
     return TMPC_OK;
 }
 
@@ -459,18 +459,20 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
         ord.insert(ord.end(), mem.begin(), mem.end());
         if (g < 3) {
             G.model = Mh[mem[0]];
-            G.threads = o->threads > 0 ? o->threads : 256;
+            // factorisation policy: solver 4 / 5 sequential LDL' by one warp, else cyclic reduction
+            G.policy = (o->solver == 4 || o->solver == 5) ? fast::kPolicyLDL : fast::kPolicyCR;
+            G.threads = o->threads > 0 ? o->threads : (G.policy == fast::kPolicyLDL ? 128 : 256);
             int Tmax = 0;
             for (int i : mem) Tmax = std::max(Tmax, Nh[i] + 1);
-            fmax = std::max(fmax, fast::arena_floats_host(G.model, Tmax));
+            fmax = std::max(fmax, fast::arena_floats_host(G.model, Tmax, G.policy));
             // shared arena: the longest instance if it fits with 2 CTAs per SM, else a
             // third of the opt-in limit (longer instances use their global arena)
-            const long long need = sizeof(float) * fast::arena_floats_host(G.model, Tmax);
+            const long long need = sizeof(float) * fast::arena_floats_host(G.model, Tmax, G.policy);
             const long long cap = std::max(48LL * 1024, (long long)max_optin / 2 - 8 * 1024);
             G.smem = (size_t)std::min(need, need <= cap ? need : (long long)max_optin / 3);
-            if (o->solver == 3) G.smem = 0;   // every arena in global memory
+            if (o->solver == 3 || o->solver == 5) G.smem = 0;   // every arena in global memory
             int per = 0;
-            e = fast::prepare(G.model, G.smem, G.threads, &per);
+            e = fast::prepare(G.model, G.policy, G.smem, G.threads, &per);
             if (e != cudaSuccess || per < 1) { set_err("fast::prepare", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
             G.grid = std::max(1, std::min(G.count, per * h->nsm));
         } else {
@@ -572,7 +574,7 @@ static tmpc_status launch_solve(tmpc_handle* h, const tmpc_params& p, const floa
     for (int g = 0; g < h->n_groups; ++g) {
         const tmpc_handle::Group& G = h->groups[g];
         if (G.model >= 0) {
-            TMPC_CUDA(fast::launch(G.model, G.grid, G.threads, G.smem, s, h->L, ko, kp, ks, h->fws, h->fstride,
+            TMPC_CUDA(fast::launch(G.model, G.policy, G.grid, G.threads, G.smem, s, h->L, ko, kp, ks, h->fws, h->fstride,
                                    h->order + G.offset, G.count, h->queue + g, x0, warm));
         } else {
             solve_kernel<<<std::min(h->grid_solve, G.count), h->threads, h->smem, s>>>(

@@ -12,41 +12,51 @@ namespace fast {
 // S blocks and their block cyclic reduction.  Block (stage) e of Dm / Um / Fa
 // starts at e * BS; entry (i, j) of a block is at bx(i, j).
 // ---------------------------------------------------------------------------
-// Theta_t (diagonal block t of S) into Dm, Phi_t' (block (t, t+1) of S) into Um
+// Entry (i, j) of Theta_t (diagonal block t of S) and of U_t = S[t][t+1] = Phi_t'
+// with Phi_t = E_t + rho_f A^+_t' A^-_t  (E_t = -W on the u block; U_t = 0 for t = N)
+template <int M>
+__device__ __forceinline__ void S_entries(const Inst<M>& c, int t, int i, int j, float sigma, float rho_f, float rho_g,
+                                          float& theta, float& u) {
+    constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
+    float s = 0.f;
+    if (t < c.Nh) {
+        const float* A = c.Amt(t);
+#pragma unroll
+        for (int k = 0; k < NX; ++k) s += A[k * N + i] * A[k * N + j];
+    }
+    if (t > 0 && i < NX && j < NX) {
+#pragma unroll
+        for (int k = 0; k < NX; ++k) s += c.Ap(t - 1, k, i) * c.Ap(t - 1, k, j);
+    }
+    if (t == 0 && i == j && i < NX) s += 1.f;
+    float v = rho_f * s;
+#pragma unroll
+    for (int r = 0; r < NG; ++r) v += rho_g * c.Gval(t, r, i) * c.Gval(t, r, j);
+    if (i == j) v += c.Pd[t * N + i] + sigma;
+    theta = v;
+    u = 0.f;
+    if (t < c.Nh) {
+        const float* A = c.Amt(t);
+        float a = 0.f;
+        if (j < NX) {
+#pragma unroll
+            for (int k = 0; k < NX; ++k) a += A[k * N + i] * c.Ap(t, k, j);
+        }
+        u = rho_f * a;
+        if (i == j && i >= NX) u -= c.W(i - NX);
+    }
+}
+
+// Theta_t into Dm, U_t into Um, every stage
 template <int M>
 __device__ __forceinline__ void form_S(const Inst<M>& c, float sigma, float rho_f, float rho_g) {
-    constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG, NN = N * N, BS = Inst<M>::BS;
+    constexpr int N = Inst<M>::N, NN = N * N, BS = Inst<M>::BS;
     const int T = c.T;
     for (int e = threadIdx.x; e < T * NN; e += blockDim.x) {
         const int t = e / NN, ij = e % NN, i = ij / N, j = ij % N;
-        float s = 0.f;
-        if (t < c.Nh) {
-            const float* A = c.Amt(t);
-#pragma unroll
-            for (int k = 0; k < NX; ++k) s += A[k * N + i] * A[k * N + j];
-        }
-        if (t > 0 && i < NX && j < NX) {
-#pragma unroll
-            for (int k = 0; k < NX; ++k) s += c.Ap(t - 1, k, i) * c.Ap(t - 1, k, j);
-        }
-        if (t == 0 && i == j && i < NX) s += 1.f;
-        float v = rho_f * s;
-#pragma unroll
-        for (int r = 0; r < NG; ++r) v += rho_g * c.Gval(t, r, i) * c.Gval(t, r, j);
-        if (i == j) v += c.Pd[t * N + i] + sigma;
-        c.Dm[t * BS + Inst<M>::bx(i, j)] = v;
-        // U_t = S[t][t+1] = Phi_t' with Phi_t = E_t + rho_f A^+_t' A^-_t  (E_t = -W on the u block)
-        float u = 0.f;
-        if (t < c.Nh) {
-            const float* A = c.Amt(t);
-            float a = 0.f;
-            if (j < NX) {
-#pragma unroll
-                for (int k = 0; k < NX; ++k) a += A[k * N + i] * c.Ap(t, k, j);
-            }
-            u = rho_f * a;
-            if (i == j && i >= NX) u -= c.W(i - NX);
-        }
+        float th, u;
+        S_entries<M>(c, t, i, j, sigma, rho_f, rho_g, th, u);
+        c.Dm[t * BS + Inst<M>::bx(i, j)] = th;
         c.Um[t * BS + Inst<M>::bx(i, j)] = u;
     }
     __syncthreads();
@@ -227,20 +237,116 @@ __device__ __forceinline__ float coldot(const float* blk_, int i, const float* v
     return s;
 }
 
+// Inverse of the reduced system left after L = top_level(T) levels of the
+// cyclic reduction (survivors b = q 2^L, q < top_blocks(T)): the remaining
+// levels of the factorisation are applied to the m = top_blocks(T) N unit
+// vectors.  Column col of Xt holds (M_R^-1) e_col with row q N + i for
+// survivor q, row i.  One task per (block, column) works in place.
+template <int M>
+__device__ __forceinline__ void top_inverse(const Inst<M>& c) {
+    constexpr int N = Inst<M>::N, BS = Inst<M>::BS;
+    const int T = c.T, L = top_level(T), S0 = 1 << L, TD = c.TD;
+    const int m = top_blocks(T) * N;
+    float* X = c.Xt;
+    for (int e = threadIdx.x; e < m * TD; e += blockDim.x) {
+        const int col = e / TD, row = e % TD;
+        X[e] = (row == col) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    int top = 1;
+    while (top < T) top <<= 1;
+    for (int s = S0; s < T; s <<= 1) {
+        const int s2 = s << 1, nsv = (T + s2 - 1) / s2;
+        for (int w = threadIdx.x; w < nsv * m; w += blockDim.x) {
+            const int col = w / nsv, i0 = (w % nsv) * s2;
+            float* x = X + col * TD;
+            float acc[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) acc[i] = 0.f;
+            if (i0 + s < T) {
+                const float* F = c.Fa + (i0 + s) * BS;
+                const float* v = x + ((i0 + s) >> L) * N;
+#pragma unroll
+                for (int i = 0; i < N; ++i)
+#pragma unroll
+                    for (int k = 0; k < N; ++k) acc[i] += F[Inst<M>::bx(i, k)] * v[k];
+            }
+            if (i0 >= s) {
+                const float* F = c.Fb + (i0 - s) * BS;
+                const float* v = x + ((i0 - s) >> L) * N;
+#pragma unroll
+                for (int i = 0; i < N; ++i)
+#pragma unroll
+                    for (int k = 0; k < N; ++k) acc[i] += F[Inst<M>::bx(i, k)] * v[k];
+            }
+            float* r0 = x + (i0 >> L) * N;
+#pragma unroll
+            for (int i = 0; i < N; ++i) r0[i] -= acc[i];
+        }
+        __syncthreads();
+    }
+    for (int col = threadIdx.x; col < m; col += blockDim.x) {
+        float* x = X + col * TD;
+        float v[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) v[k] = x[k];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            float a = 0.f;
+#pragma unroll
+            for (int k = 0; k < N; ++k) a += c.Dm[Inst<M>::bx(i, k)] * v[k];
+            x[i] = a;
+        }
+    }
+    __syncthreads();
+    for (int s = top >> 1; s >= S0; s >>= 1) {
+        if (s >= T) continue;
+        const int s2 = s << 1, ne = (T - s + s2 - 1) / s2;
+        for (int w = threadIdx.x; w < ne * m; w += blockDim.x) {
+            const int col = w / ne, e = s + (w % ne) * s2;
+            float* x = X + col * TD;
+            const float* D = c.Dm + e * BS;
+            const float* Fa = c.Fa + e * BS;
+            const float* Fb = c.Fb + e * BS;
+            const float* xa = x + ((e - s) >> L) * N;
+            const float* xb = x + ((e + s) >> L) * N;
+            const bool hasb = e + s < T;
+            float* re = x + (e >> L) * N;
+            float v[N], o[N];
+#pragma unroll
+            for (int k = 0; k < N; ++k) v[k] = re[k];
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                float a = 0.f;
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    a += D[Inst<M>::bx(i, k)] * v[k] - Fa[Inst<M>::bx(k, i)] * xa[k];
+                    if (hasb) a -= Fb[Inst<M>::bx(k, i)] * xb[k];
+                }
+                o[i] = a;
+            }
+#pragma unroll
+            for (int i = 0; i < N; ++i) re[i] = o[i];
+        }
+        __syncthreads();
+    }
+}
+
 // Solve S x = r with the cyclic-reduction factors; r is consumed, x -> xo.
-// One barrier per level on the way down (r_i -= Fa_{i+s} r_{i+s} + Fb_{i-s} r_{i-s})
-// and one on the way up (x_e = Dinv_e r_e - Fa_e' x_{e-s} - Fb_e' x_{e+s}).
+// Levels below top_level(T): one barrier per level on the way down
+// (r_i -= Fa_{i+s} r_{i+s} + Fb_{i-s} r_{i-s}) and one on the way up
+// (x_e = Dinv_e r_e - Fa_e' x_{e-s} - Fb_e' x_{e+s}); the survivors in between
+// are solved by the dense inverse of the reduced system (one barrier).
 template <int M>
 __device__ __forceinline__ void cr_solve(const Inst<M>& c, float* r, float* xo) {
     constexpr int N = Inst<M>::N, BS = Inst<M>::BS;
-    const int T = c.T;
-    int top = 1;
-    while (top < T) top <<= 1;
-    for (int s = 1; s < T; s <<= 1) {
-        const int s2 = s << 1;
-        const int nsv = (T + s2 - 1) / s2;
+    const int T = c.T, L = top_level(T), TD = c.TD;
+    const int m = top_blocks(T) * N;
+    for (int l = 0; l < L; ++l) {
+        const int s = 1 << l;
+        const int nsv = (T + 2 * s - 1) >> (l + 1);     // survivors i0 = q 2s < T
         for (int w = threadIdx.x; w < nsv * N; w += blockDim.x) {
-            const int i0 = (w / N) * s2, i = w % N;
+            const int i0 = (w / N) << (l + 1), i = w % N;
             float a = 0.f;
             if (i0 + s < T) a += rowdot<N>(c.Fa + (i0 + s) * BS, i, r + (i0 + s) * N);
             if (i0 >= s) a += rowdot<N>(c.Fb + (i0 - s) * BS, i, r + (i0 - s) * N);
@@ -248,20 +354,147 @@ __device__ __forceinline__ void cr_solve(const Inst<M>& c, float* r, float* xo) 
         }
         __syncthreads();
     }
-    for (int i = threadIdx.x; i < N; i += blockDim.x) xo[i] = rowdot<N>(c.Dm, i, r);
+    // survivors: x_R = M_R^-1 r_R (column col of Xt is M_R^-1 e_col); four lanes per
+    // row, lane part p summing the columns q N + k with k = p (mod 4), reduced by shuffles
+    {
+        const int nR = m / N, ntask = 4 * m, nround = (ntask + 31) & ~31;
+        for (int w = threadIdx.x; w < nround; w += blockDim.x) {   // whole warps together
+            const int row = w >> 2, part = w & 3;
+            float a = 0.f;
+            if (w < ntask) {
+                const float* Xr = c.Xt + row;
+                for (int q = 0; q < nR; ++q) {
+                    const float* rq = r + (q << L) * N;
+                    const float* Xq = Xr + q * N * TD;
+#pragma unroll
+                    for (int k = 0; k < N; k += 4)
+                        if (k + part < N) a += Xq[(k + part) * TD] * rq[k + part];
+                }
+            }
+            a += __shfl_xor_sync(0xFFFFFFFFu, a, 1);
+            a += __shfl_xor_sync(0xFFFFFFFFu, a, 2);
+            if (w < ntask && part == 0) xo[((row / N) << L) * N + row % N] = a;
+        }
+    }
     __syncthreads();
-    for (int s = top >> 1; s >= 1; s >>= 1) {
-        const int s2 = s << 1;
-        if (s >= T) continue;
-        const int ne = (T - s + s2 - 1) / s2;
+    for (int l = L - 1; l >= 0; --l) {
+        const int s = 1 << l;
+        const int ne = (T + s - 1) >> (l + 1);          // eliminated e = s + q 2s < T
         for (int w = threadIdx.x; w < ne * N; w += blockDim.x) {
-            const int e = s + (w / N) * s2, i = w % N;
+            const int e = s + ((w / N) << (l + 1)), i = w % N;
             float a = rowdot<N>(c.Dm + e * BS, i, r + e * N) - coldot<N>(c.Fa + e * BS, i, xo + (e - s) * N);
             if (e + s < T) a -= coldot<N>(c.Fb + e * BS, i, xo + (e + s) * N);
             xo[e * N + i] = a;
         }
         __syncthreads();
     }
+}
+
+// ---------------------------------------------------------------------------
+// kLDL: sequential block LDL' of S by warp 0.  Lane l holds entries
+// (i, j0), (i, j0 + 1) of an N x N block, i = l / 4, j0 = 2 (l % 4).
+//   D_0 = Theta_0;  L_t = U_{t-1}' D_{t-1}^-1,  D_t = Theta_t - L_t U_{t-1}
+// Dm[t] <- D_t^-1, Um[t] <- L_t (t >= 1); Theta_t and U_t are formed per step
+// (U_t kept in the two scratch blocks Wk for the next step).
+// ---------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ bool ldl_factor_warp(const Inst<M>& c, float sigma, float rho_f, float rho_g, int* flag) {
+    constexpr int N = Inst<M>::N, BS = Inst<M>::BS;
+    const int T = c.T;
+    if (threadIdx.x == 0) *flag = 0;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x, i = lane >> 2, j0 = (lane & 3) * 2, j1 = j0 + 1;
+        const bool v0 = i < N && j0 < N, v1 = i < N && j1 < N;
+        bool ok = true;
+        for (int t = 0; t < T; ++t) {
+            float th0 = 0.f, th1 = 0.f, u0 = 0.f, u1 = 0.f;
+            if (v0) S_entries<M>(c, t, i, j0, sigma, rho_f, rho_g, th0, u0);
+            if (v1) S_entries<M>(c, t, i, j1, sigma, rho_f, rho_g, th1, u1);
+            float* Un = c.Wk + (t & 1) * BS;           // U_t for the next step
+            if (t > 0) {
+                const float* Up = c.Wk + ((t - 1) & 1) * BS;   // U_{t-1}
+                const float* Dp = c.Dm + (t - 1) * BS;         // D_{t-1}^-1
+                float* Lt = c.Um + t * BS;
+                float l0 = 0.f, l1 = 0.f;
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    const float uki = (i < N) ? Up[Inst<M>::bx(k, i)] : 0.f;
+                    if (v0) l0 += uki * Dp[Inst<M>::bx(k, j0)];
+                    if (v1) l1 += uki * Dp[Inst<M>::bx(k, j1)];
+                }
+                if (v0) Lt[Inst<M>::bx(i, j0)] = l0;
+                if (v1) Lt[Inst<M>::bx(i, j1)] = l1;
+                __syncwarp();
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    const float lik = (i < N) ? Lt[Inst<M>::bx(i, k)] : 0.f;
+                    if (v0) th0 -= lik * Up[Inst<M>::bx(k, j0)];
+                    if (v1) th1 -= lik * Up[Inst<M>::bx(k, j1)];
+                }
+            }
+            float* Dt = c.Dm + t * BS;
+            if (v0) { Dt[Inst<M>::bx(i, j0)] = th0; Un[Inst<M>::bx(i, j0)] = u0; }
+            if (v1) { Dt[Inst<M>::bx(i, j1)] = th1; Un[Inst<M>::bx(i, j1)] = u1; }
+            __syncwarp();
+            if (lane < 8) ok = group_spd_inverse<N>(Dt, lane, 0xFFu) && ok;
+            __syncwarp();
+        }
+        if (lane == 0 && !ok) *flag = 1;
+    }
+    __syncthreads();
+    const bool res = *flag == 0;
+    __syncthreads();
+    return res;
+}
+
+// Solve S x = r in place with the kLDL factors (warp 0):
+//   y_0 = r_0, y_t = r_t - L_t y_{t-1};   x_{T-1} = D^-1 y,  x_t = D_t^-1 y_t - L_{t+1}' x_{t+1}
+// A lane holds y (or x) entries j0, j0 + 1 of the previous stage; row sums over
+// the 4 lanes of a row by xor-shuffles, redistributed from the row's lane 0.
+template <int M>
+__device__ __forceinline__ void ldl_solve_warp(const Inst<M>& c, float* r) {
+    constexpr int N = Inst<M>::N, BS = Inst<M>::BS;
+    const int T = c.T;
+    if (threadIdx.x < 32) {
+        const unsigned full = 0xFFFFFFFFu;
+        const int lane = threadIdx.x, i = lane >> 2, h = lane & 3, j0 = 2 * h, j1 = j0 + 1;
+        const bool vi = i < N, v0 = j0 < N, v1 = j1 < N;
+        float y0 = v0 ? r[j0] : 0.f, y1 = v1 ? r[j1] : 0.f;
+        for (int t = 1; t < T; ++t) {
+            const float* Lb = c.Um + t * BS;
+            const float rt = (vi && h == 0) ? r[t * N + i] : 0.f;
+            float p = 0.f;
+            if (vi && v0) p += Lb[Inst<M>::bx(i, j0)] * y0;
+            if (vi && v1) p += Lb[Inst<M>::bx(i, j1)] * y1;
+            p += __shfl_xor_sync(full, p, 1);
+            p += __shfl_xor_sync(full, p, 2);
+            const float yi = rt - p;
+            if (vi && h == 0) r[t * N + i] = yi;
+            y0 = __shfl_sync(full, yi, 4 * j0);
+            y1 = __shfl_sync(full, yi, 4 * j1);
+        }
+        float x0 = 0.f, x1 = 0.f;
+        for (int t = T - 1; t >= 0; --t) {
+            const float* D = c.Dm + t * BS;
+            const float* yt = r + t * N;
+            float p = 0.f;
+            if (vi && v0) p += D[Inst<M>::bx(i, j0)] * yt[j0];
+            if (vi && v1) p += D[Inst<M>::bx(i, j1)] * yt[j1];
+            if (t + 1 < T) {
+                const float* Ln = c.Um + (t + 1) * BS;
+                if (vi && v0) p -= Ln[Inst<M>::bx(j0, i)] * x0;
+                if (vi && v1) p -= Ln[Inst<M>::bx(j1, i)] * x1;
+            }
+            p += __shfl_xor_sync(full, p, 1);
+            p += __shfl_xor_sync(full, p, 2);
+            __syncwarp();
+            if (vi && h == 0) r[t * N + i] = p;
+            x0 = __shfl_sync(full, p, 4 * j0);
+            x1 = __shfl_sync(full, p, 4 * j1);
+        }
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -438,21 +671,30 @@ __device__ __forceinline__ void linearize(const Inst<M>& c) {
 // ---------------------------------------------------------------------------
 // one ADMM iteration in increment form (see tmpc_solver.cuh admm_iter)
 // ---------------------------------------------------------------------------
+// Row vectors of the right-hand side, w_f = y_f + rho_f p_f and
+// w_g = y_g + rho_g p_g, from the tracked defects p_f = C x - c and
+// p_g = G x - z_g (at the start of the ADMM loop and after a change of rho;
+// otherwise the fused update of admm_iter produces them).
 template <int M>
+__device__ __forceinline__ void admm_rowvec(const Inst<M>& c, float rho_bar) {
+    constexpr int NX = Inst<M>::NX, NG = Inst<M>::NG;
+    const int T = c.T;
+    const float rho_f = 1e3f * rho_bar, rho_g = rho_bar;
+    for (int e = threadIdx.x; e < T * NX; e += blockDim.x) c.wf[e] = c.yf[e] + rho_f * c.pf[e];
+    for (int e = threadIdx.x; e < T * NG; e += blockDim.x) c.wg[e] = c.yg[e] + rho_g * c.pg[e];
+    __syncthreads();
+}
+
+// r = -(P x + q) - C' w_f - G' w_g;  S dx = r;  then one fused pass over the
+// stage entries (t, j): x += alpha dx, equality row (t, j < NX) and
+// inequality row (t, j < NG) relaxed, projected and dual-updated, and the
+// next iteration's w_f, w_g.  G x is tracked through p_g like C x through p_f.
+template <int M, int P>
 __device__ __forceinline__ void admm_iter(const Inst<M>& c, float rho_bar, float alpha) {
     using Tr = Traits<M>;
     constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
     const int T = c.T;
     const float rho_f = 1e3f * rho_bar, rho_g = rho_bar, inv_rho_g = 1.f / rho_bar;
-    // per-row vectors: w_f = y_f + rho_f p_f,  p_g = G x - z_g,  w_g = y_g + rho_g p_g
-    for (int e = threadIdx.x; e < T * NX; e += blockDim.x) c.wf[e] = c.yf[e] + rho_f * c.pf[e];
-    for (int e = threadIdx.x; e < T * NG; e += blockDim.x) {
-        const float p = c.Gx(c.x, e / NG, e % NG) - c.zg[e];
-        c.pg[e] = p;
-        c.wg[e] = c.yg[e] + rho_g * p;
-    }
-    __syncthreads();
-    // r = -(P x + q) - C' w_f - G' w_g   (= eta - S x)
     for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
         const int t = e / N, j = e % N;
         float s = -(c.Pv(c.x, t, j) + c.qv[e]);
@@ -466,23 +708,36 @@ __device__ __forceinline__ void admm_iter(const Inst<M>& c, float rho_bar, float
         c.r[e] = s;
     }
     __syncthreads();
-    cr_solve<M>(c, c.r, c.dx);
-    for (int e = threadIdx.x; e < T * NX; e += blockDim.x) {
-        const float cd = c.Cx(c.dx, e / NX, e % NX);
-        c.yf[e] += rho_f * alpha * (c.pf[e] + cd);
-        c.pf[e] += alpha * cd;
+    if (P == kCR) cr_solve<M>(c, c.r, c.dx);
+    else ldl_solve_warp<M>(c, c.r);   // dx shares r
+    for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
+        const int t = e / N, j = e % N;
+        c.x[e] += alpha * c.dx[e];
+        if (j < NX) {
+            const int f = t * NX + j;
+            const float cd = c.Cx(c.dx, t, j);
+            const float yf = c.yf[f] + rho_f * alpha * (c.pf[f] + cd);
+            const float pf = c.pf[f] + alpha * cd;
+            c.yf[f] = yf;
+            c.pf[f] = pf;
+            c.wf[f] = yf + rho_f * pf;
+        }
+        if (j < NG) {
+            const int g = t * NG + j;
+            const float gd = c.Gx(c.dx, t, j);
+            const float zg = c.zg[g], pg = c.pg[g], yg0 = c.yg[g];
+            const float zh = zg + alpha * (pg + gd);
+            float zn, xn;
+            project(zh + yg0 * inv_rho_g, c.glo[g], c.ghi[g], rho_g, c.gam2(j), c.gam1(j), zn, xn);
+            const float yg = yg0 + rho_g * (zh - zn);
+            const float pgn = (pg + zg + alpha * gd) - zn;   // G x_new - z_g,new
+            c.yg[g] = yg;
+            c.zg[g] = zn;
+            c.xi[g] = xn;
+            c.pg[g] = pgn;
+            c.wg[g] = yg + rho_g * pgn;
+        }
     }
-    for (int e = threadIdx.x; e < T * NG; e += blockDim.x) {
-        const int t = e / NG, r = e % NG;
-        const float zh = c.zg[e] + alpha * (c.pg[e] + c.Gx(c.dx, t, r));
-        const float v = zh + c.yg[e] * inv_rho_g;
-        float zn, xn;
-        project(v, c.glo[e], c.ghi[e], rho_g, c.gam2(r), c.gam1(r), zn, xn);
-        c.yg[e] += rho_g * (zh - zn);
-        c.zg[e] = zn;
-        c.xi[e] = xn;
-    }
-    for (int e = threadIdx.x; e < T * N; e += blockDim.x) c.x[e] += alpha * c.dx[e];
     __syncthreads();
 }
 
@@ -576,13 +831,14 @@ struct Red {
 // Appendix D line search.  Stage values of every candidate are written in
 // FP32 to scratch (the factor arena is idle here: the next SQP step refactors),
 // then one thread per (candidate, quantity) sums its stages in FP64.
-template <int M>
+template <int M, int P>
 __device__ __forceinline__ float linesearch(const Inst<M>& c, const KOpts& o, const Red& rs, float ystar_inf) {
     constexpr int N = Inst<M>::N, NG = Inst<M>::NG;
     const int T = c.T;
     const int K = o.n_ls < 1 ? 1 : (o.n_ls > kMaxLs ? kMaxLs : o.n_ls);
     if (K == 1) return 1.f;
-    float* val = c.Fa;  // [(2k + q) T + t], q = 0 cost, 1 violation; scale at 2(K+1)T
+    // scratch [(2k + q) T + t], q = 0 cost, 1 violation; scale at 2(K+1)T (factors are dead here)
+    float* val = P == kCR ? c.Fa : c.Dm;
     double gd = 0.0;
     for (int e = threadIdx.x; e < T * N; e += blockDim.x) gd += (double)(c.qv[e] * c.x[e]);
     for (int e = threadIdx.x; e < T * NG; e += blockDim.x) {
@@ -661,16 +917,19 @@ __device__ __forceinline__ float kkt(const Inst<M>& c, float* red) {
     return v[0];
 }
 
-template <int M>
+template <int M, int P>
 __device__ __forceinline__ bool factor(const Inst<M>& c, const KOpts& o, float rho, int* flag) {
+    if (P == kLDL) return ldl_factor_warp<M>(c, o.sigma, 1e3f * rho, rho, flag);
     form_S<M>(c, o.sigma, 1e3f * rho, rho);
-    return cr_factor<M>(c, flag);
+    const bool ok = cr_factor<M>(c, flag);
+    top_inverse<M>(c);
+    return ok;
 }
 
 // ---------------------------------------------------------------------------
 // Algorithm 1 for one instance
 // ---------------------------------------------------------------------------
-template <int M>
+template <int M, int P>
 __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const Red& rs, const KLayout& L, const KSol& out,
                                int inst, int warm) {
     constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
@@ -705,14 +964,20 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
             if (kkt<M>(c, rs.red) <= o.eps_c) break;
         }
         ++nfact;
-        if (!factor<M>(c, o, rho, rs.flags + 1) && threadIdx.x == 0) rs.flags[0] = 1;
+        if (!factor<M, P>(c, o, rho, rs.flags + 1) && threadIdx.x == 0) rs.flags[0] = 1;
         for (int e = threadIdx.x; e < T * N; e += blockDim.x) c.x[e] = 0.f;
         for (int e = threadIdx.x; e < T * NX; e += blockDim.x) { c.yf[e] = c.yfb[e]; c.pf[e] = -c.cv[e]; }
-        for (int e = threadIdx.x; e < T * NG; e += blockDim.x) { c.yg[e] = c.ygb[e]; c.zg[e] = 0.f; c.xi[e] = 0.f; }
+        for (int e = threadIdx.x; e < T * NG; e += blockDim.x) {
+            c.yg[e] = c.ygb[e];
+            c.zg[e] = 0.f;
+            c.xi[e] = 0.f;
+            c.pg[e] = 0.f;   // G x - z_g at x = 0, z_g = 0
+        }
         __syncthreads();
+        admm_rowvec<M>(c, rho);
         int k = 0;
         for (k = 1; k <= o.max_admm; ++k) {
-            admm_iter<M>(c, rho, o.alpha);
+            admm_iter<M, P>(c, rho, o.alpha);
             const bool cc = o.early_exit && (k % o.check_every == 0);
             const bool cr = (k % o.k_rho_iter == 0) && k < o.max_admm;
             if (cc || cr || k == o.max_admm) {
@@ -726,11 +991,12 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
                     const float cand = fminf(fmaxf(rho * sqrtf(ratio), o.rho_min), o.rho_max);
                     if (fmaxf(cand / rho, rho / cand) > o.k_rho_ratio) {
                         ++nfact;
-                        if (factor<M>(c, o, cand, rs.flags + 1)) {
+                        if (factor<M, P>(c, o, cand, rs.flags + 1)) {
                             rho = cand;
+                            admm_rowvec<M>(c, rho);
                         } else {
                             ++nfact;
-                            if (!factor<M>(c, o, rho, rs.flags + 1) && threadIdx.x == 0) rs.flags[0] = 1;
+                            if (!factor<M, P>(c, o, rho, rs.flags + 1) && threadIdx.x == 0) rs.flags[0] = 1;
                         }
                     }
                 }
@@ -741,7 +1007,7 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
         for (int e = threadIdx.x; e < T * NX; e += blockDim.x) ys[0] = fmaxf(ys[0], fin(c.yf[e]));
         for (int e = threadIdx.x; e < T * NG; e += blockDim.x) ys[0] = fmaxf(ys[0], fin(c.yg[e]));
         cta_max_k<1>(ys, rs.red);
-        const float a = linesearch<M>(c, o, rs, ys[0]);
+        const float a = linesearch<M, P>(c, o, rs, ys[0]);
         alpha_last = a;
         if (it < 12) ls_hist[it / 6] |= ls_code(a) << (4 * (it % 6));
         for (int e = threadIdx.x; e < T * N; e += blockDim.x) c.zb[e] += a * c.x[e];
@@ -795,7 +1061,7 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
 
 // Persistent kernel over the instances listed in `order` (all of model M); an
 // instance whose arena does not fit `smem_floats` uses its global slot.
-template <int M>
+template <int M, int P>
 __global__ void __launch_bounds__(256, 2) solve_kernel(KLayout L, KOpts o, KParams p, KSol out, float* gws,
                                                     long long gstride, const int* order, int count,
                                                     int* queue, const float* x0, int warm,
@@ -837,18 +1103,22 @@ __global__ void __launch_bounds__(256, 2) solve_kernel(KLayout L, KOpts o, KPara
             int nt = (ntf == ntf) ? (int)fminf(fmaxf(ntf + 0.5f, 1.f), (float)L.n_track) : 1;
             c.nt = nt < 1 ? 1 : nt;
         }
-        const long long need = arena_floats<M>(c.T);
-        c.carve(need <= smem_floats ? arena : gws + (long long)i * gstride);
-        solve_instance<M>(c, o, rs, L, out, i, warm);
+        const long long need = arena_floats<M>(c.T, P);
+        c.carve(need <= smem_floats ? arena : gws + (long long)i * gstride, P);
+        solve_instance<M, P>(c, o, rs, L, out, i, warm);
     }
 }
 
-template __global__ void solve_kernel<MODEL_DI>(KLayout, KOpts, KParams, KSol, float*, long long, const int*, int,
-                                                int*, const float*, int, long long);
-template __global__ void solve_kernel<MODEL_BICYCLE>(KLayout, KOpts, KParams, KSol, float*, long long, const int*,
-                                                     int, int*, const float*, int, long long);
-template __global__ void solve_kernel<MODEL_QUAD>(KLayout, KOpts, KParams, KSol, float*, long long, const int*,
-                                                  int, int*, const float*, int, long long);
+#define TMPC_INSTANTIATE(M, P)                                                                           \
+    template __global__ void solve_kernel<M, P>(KLayout, KOpts, KParams, KSol, float*, long long, const int*, \
+                                                int, int*, const float*, int, long long);
+TMPC_INSTANTIATE(MODEL_DI, kCR)
+TMPC_INSTANTIATE(MODEL_BICYCLE, kCR)
+TMPC_INSTANTIATE(MODEL_QUAD, kCR)
+TMPC_INSTANTIATE(MODEL_DI, kLDL)
+TMPC_INSTANTIATE(MODEL_BICYCLE, kLDL)
+TMPC_INSTANTIATE(MODEL_QUAD, kLDL)
+#undef TMPC_INSTANTIATE
 
 }  // namespace fast
 }  // namespace tmpc
@@ -859,55 +1129,48 @@ template __global__ void solve_kernel<MODEL_QUAD>(KLayout, KOpts, KParams, KSol,
 namespace tmpc {
 namespace fast {
 
-long long arena_floats_host(int model, int T) {
+long long arena_floats_host(int model, int T, int policy) {
     switch (model) {
-        case MODEL_DI: return arena_floats<MODEL_DI>(T);
-        case MODEL_BICYCLE: return arena_floats<MODEL_BICYCLE>(T);
-        case MODEL_QUAD: return arena_floats<MODEL_QUAD>(T);
+        case MODEL_DI: return arena_floats<MODEL_DI>(T, policy);
+        case MODEL_BICYCLE: return arena_floats<MODEL_BICYCLE>(T, policy);
+        case MODEL_QUAD: return arena_floats<MODEL_QUAD>(T, policy);
     }
     return -1;
 }
 
 bool supported(int model) { return model == MODEL_DI || model == MODEL_BICYCLE || model == MODEL_QUAD; }
 
-static const void* kernel_of(int model) {
+template <int P>
+static const void* kernel_of_p(int model) {
     switch (model) {
-        case MODEL_DI: return (const void*)solve_kernel<MODEL_DI>;
-        case MODEL_BICYCLE: return (const void*)solve_kernel<MODEL_BICYCLE>;
-        case MODEL_QUAD: return (const void*)solve_kernel<MODEL_QUAD>;
+        case MODEL_DI: return (const void*)solve_kernel<MODEL_DI, P>;
+        case MODEL_BICYCLE: return (const void*)solve_kernel<MODEL_BICYCLE, P>;
+        case MODEL_QUAD: return (const void*)solve_kernel<MODEL_QUAD, P>;
     }
     return nullptr;
 }
 
-cudaError_t prepare(int model, size_t smem_bytes, int threads, int* blocks_per_sm) {
-    const void* k = kernel_of(model);
+static const void* kernel_of(int model, int policy) {
+    return policy == kLDL ? kernel_of_p<kLDL>(model) : kernel_of_p<kCR>(model);
+}
+
+cudaError_t prepare(int model, int policy, size_t smem_bytes, int threads, int* blocks_per_sm) {
+    const void* k = kernel_of(model, policy);
     if (!k) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem_bytes);
 }
 
-cudaError_t launch(int model, int grid, int threads, size_t smem_bytes, cudaStream_t s, const KLayout& L,
-                   const KOpts& o, const KParams& p, const KSol& out, float* gws, long long gstride,
-                   const int* order, int count, int* queue, const float* x0, int warm) {
+cudaError_t launch(int model, int policy, int grid, int threads, size_t smem_bytes, cudaStream_t s,
+                   const KLayout& L, const KOpts& o, const KParams& p, const KSol& out, float* gws,
+                   long long gstride, const int* order, int count, int* queue, const float* x0, int warm) {
     const long long sf = (long long)(smem_bytes / sizeof(float));
-    switch (model) {
-        case MODEL_DI:
-            solve_kernel<MODEL_DI><<<grid, threads, smem_bytes, s>>>(L, o, p, out, gws, gstride, order, count,
-                                                                       queue, x0, warm, sf);
-            break;
-        case MODEL_BICYCLE:
-            solve_kernel<MODEL_BICYCLE><<<grid, threads, smem_bytes, s>>>(L, o, p, out, gws, gstride, order,
-                                                                            count, queue, x0, warm, sf);
-            break;
-        case MODEL_QUAD:
-            solve_kernel<MODEL_QUAD><<<grid, threads, smem_bytes, s>>>(L, o, p, out, gws, gstride, order, count,
-                                                                         queue, x0, warm, sf);
-            break;
-        default:
-            return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    const void* k = kernel_of(model, policy);
+    if (!k) return cudaErrorInvalidValue;
+    void* args[] = {(void*)&L, (void*)&o, (void*)&p, (void*)&out, (void*)&gws, (void*)&gstride, (void*)&order,
+                    (void*)&count, (void*)&queue, (void*)&x0, (void*)&warm, (void*)&sf};
+    return cudaLaunchKernel(k, dim3(grid), dim3(threads), args, smem_bytes, s);
 }
 
 }  // namespace fast

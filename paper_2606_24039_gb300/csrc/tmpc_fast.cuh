@@ -26,6 +26,9 @@
 namespace tmpc {
 namespace fast {
 
+// 128-bit shared/global load of 4 consecutive floats (16-byte aligned address)
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
 // ---------------------------------------------------------------------------
 // model traits: compile-time sizes; inequality rows are either a selection of
 // one stage variable (sel[r] >= 0) or a dense row (sel[r] = -1, at most one)
@@ -44,29 +47,60 @@ template <> struct Traits<MODEL_QUAD> {
     __device__ static constexpr int sel(int r) { return r == 0 ? 6 : 7; }
 };
 
+// The cyclic reduction of S stops after top_level(T) levels, when at most
+// kTopBlocks blocks survive; the reduced system on those blocks (dimension
+// top_dim = survivors x N) is inverted once per factorisation and applied as a
+// dense matrix in every solve.
+constexpr int kTopBlocks = 8;
+__host__ __device__ constexpr int top_level(int T) {
+    int L = 0;
+    while (((T + (1 << L) - 1) >> L) > kTopBlocks) ++L;
+    return L;
+}
+__host__ __device__ constexpr int top_blocks(int T) { return (T + (1 << top_level(T)) - 1) >> top_level(T); }
+
+// Factorisation policies of S:
+//   kCR  block cyclic reduction by the whole CTA (depth 2 log2 T, all stages in
+//        parallel), top levels by the dense inverse of the reduced system
+//   kLDL sequential block LDL' (Riccati-like sweep over the stages) by one warp;
+//        half the factor storage, so more instances fit on an SM
+constexpr int kCR = 0, kLDL = 1;
+
 // Per-instance arena: one list (name, floats) drives both the layout (carve)
 // and its size (arena_floats), so the two cannot disagree.
-//   factors of S:       Dm, Um, Fa, Fb           T x BS each (padded N x N blocks)
-//   stage vectors:      x, r, dx, qv, zb, Pd      T x N
+//   factors of S:       Dm, Um                    T x BS each (padded N x N blocks)
+//                       kCR:  Dm = Dinv_e, Um = couplings, Fa, Fb (T x BS each),
+//                             Xt = inverse of the reduced system, top_dim^2
+//                             (top_dim = top_blocks(T) N, rounded to 4)
+//                       kLDL: Dm = Dinv_t, Um = L_t, Wk = 2 scratch blocks
+//   stage vectors:      x, r, dx, qv, zb, Pd      T x N   (kLDL: dx shares r)
 //   inequality rows:    zg, yg, xi, glo, ghi, xib, ygb, pg   T x NG
-//   equality rows:      yf, pf, cv, yfb           T x NX
+//   equality rows:      yf, pf, cv, yfb, wf       T x NX  (wg: T x NG)
 //   cached weights:     par                       32 (W, gamma2, gamma1)
 //   Jacobians:          Am (A^- per stage, padded stride AMS; one block if LTI), Grow (dense G row)
+// Every array up to Pd has a multiple of 4 floats (N = 8), so rows of Am, Grow
+// and the stage vectors start on 16-byte boundaries (128-bit loads).
 #define TMPC_FAST_ARENA(X)                                                       \
-    X(Dm, (long long)T * BS) X(Um, (long long)T * BS) X(Fa, (long long)T * BS)   \
-    X(Fb, (long long)T * BS)                                                     \
-    X(x, T * N) X(r, T * N) X(dx, T * N) X(qv, T * N) X(zb, T * N) X(Pd, T * N) \
+    X(Dm, (long long)T * BS) X(Um, (long long)T * BS)                            \
+    X(Fa, P == kCR ? (long long)T * BS : 0LL)                                     \
+    X(Fb, P == kCR ? (long long)T * BS : 0LL)                                     \
+    X(Xt, P == kCR ? (long long)TD * TD : 0LL)                                    \
+    X(Wk, P == kLDL ? 2LL * BS : 0LL)                                             \
+    X(Am, (Traits<M>::LTI ? (long long)AMS : (long long)T * AMS))                \
+    X(Grow, (Traits<M>::DENSE_ROW >= 0 ? (long long)T * N : 0LL))                \
+    X(x, T * N) X(r, T * N) X(dx, P == kCR ? T * N : 0) X(qv, T * N)             \
+    X(zb, T * N) X(Pd, T * N)                                                    \
     X(zg, T * NG) X(yg, T * NG) X(xi, T * NG) X(glo, T * NG) X(ghi, T * NG)      \
     X(xib, T * NG) X(ygb, T * NG) X(pg, T * NG)                                  \
     X(yf, T * NX) X(pf, T * NX) X(cv, T * NX) X(yfb, T * NX)                     \
-    X(par, 32)                                                                   \
-    X(Am, (Traits<M>::LTI ? (long long)AMS : (long long)T * AMS))                \
-    X(Grow, (Traits<M>::DENSE_ROW >= 0 ? (long long)T * N : 0LL))
+    X(wf, T * NX) X(wg, T * NG)                                                  \
+    X(par, 32)
 
 template <int M>
-__host__ __device__ constexpr long long arena_floats(int T) {
+__host__ __device__ constexpr long long arena_floats(int T, int P) {
     constexpr int NX = Traits<M>::NX, N = Traits<M>::NX + Traits<M>::NU, NG = Traits<M>::NG;
     constexpr int BS = N * N + 4, AMS = NX * N + 8;
+    const int TD = (top_blocks(T) * N + 3) & ~3;
     long long total = 0;
 #define TMPC_SIZE(name, cnt) total += (cnt);
     TMPC_FAST_ARENA(TMPC_SIZE)
@@ -86,20 +120,21 @@ struct Inst {
     int Nh, T, nt;
     int lnx, lnu, ln, lng;
     const float *x0, *Qd, *Rd, *Wd, *ref, *lin, *lo, *hi, *g2, *g1, *dyn, *track;
-    float *Dm, *Um, *Fa, *Fb;
+    float *Dm, *Um, *Fa, *Fb, *Xt, *Wk;
+    int TD;     // leading dimension of Xt
     float *x, *r, *dx, *qv, *zb, *Pd;
     float *zg, *yg, *xi, *glo, *ghi, *xib, *ygb, *pg;
     float *yf, *pf, *cv, *yfb;
-    float *wf, *wg;  // per-iteration row vectors, aliased on dx and xi (idle while they live)
+    float *wf, *wg;  // right-hand-side row vectors y_f + rho_f p_f, y_g + rho_g p_g
     float *Am, *Grow, *par;  // par: W[NU], gamma2[NG], gamma1[NG] cached in the arena
 
-    __device__ __forceinline__ void carve(float* p) {
+    __device__ __forceinline__ void carve(float* p, int P) {
         const int T = this->T;
+        TD = (top_blocks(T) * N + 3) & ~3;
 #define TMPC_CARVE(name, cnt) name = p; p += (cnt);
         TMPC_FAST_ARENA(TMPC_CARVE)
 #undef TMPC_CARVE
-        wf = dx;
-        wg = xi;
+        if (P == kLDL) dx = r;   // the sweep solves in place
     }
     // copy the per-instance weights used in the inner loop into the arena
     __device__ void cache_params() {
@@ -138,10 +173,16 @@ struct Inst {
         const int s = Tr::sel(r);
         if (s >= 0) return v[t * N + s];
         const float* g = Grow + t * N;
-        float a = 0.f;
+        if constexpr (N == 8) {
+            const float4 g0 = ld4(g), g1 = ld4(g + 4), v0 = ld4(v + t * N), v1 = ld4(v + t * N + 4);
+            return (g0.x * v0.x + g0.y * v0.y) + (g0.z * v0.z + g0.w * v0.w) +
+                   ((g1.x * v1.x + g1.y * v1.y) + (g1.z * v1.z + g1.w * v1.w));
+        } else {
+            float a = 0.f;
 #pragma unroll
-        for (int j = 0; j < N; ++j) a += g[j] * v[t * N + j];
-        return a;
+            for (int j = 0; j < N; ++j) a += g[j] * v[t * N + j];
+            return a;
+        }
     }
     // (G' w)_t entry j, w(r) functor
     template <class F>
@@ -162,6 +203,20 @@ struct Inst {
         const float* A = Amt(t) + k * N;
         const float* a = v + t * N;
         const float* b = v + (t + 1) * N;
+        if constexpr (N == 8) {
+            const float4 A0 = ld4(A), A1 = ld4(A + 4), a0 = ld4(a), a1 = ld4(a + 4);
+            float s = (A0.x * a0.x + A0.y * a0.y) + (A0.z * a0.z + A0.w * a0.w) +
+                      ((A1.x * a1.x + A1.y * a1.y) + (A1.z * a1.z + A1.w * a1.w));
+            if (Tr::IMPLICIT) {
+                static_assert(!Tr::IMPLICIT || NX == 6, "implicit model with NX = 6");
+                const float4 b0 = ld4(b), b1 = ld4(b + 4);
+                s += (A0.x * b0.x + A0.y * b0.y) + (A0.z * b0.z + A0.w * b0.w) + (A1.x * b1.x + A1.y * b1.y);
+                s -= 2.f * b[k];
+            } else {
+                s -= b[k];
+            }
+            return s;
+        }
         float s = 0.f;
 #pragma unroll
         for (int j = 0; j < N; ++j) s += A[j] * a[j];
@@ -209,61 +264,10 @@ struct Inst {
 };
 
 // ---------------------------------------------------------------------------
-// dense N x N SPD inverse by one thread (Cholesky, L^{-1}, L^{-T} L^{-1});
-// in place on a row-major block.  Returns false on a non-positive pivot.
+// entry (i, j) of a factor block (same swizzle as Inst::bx)
 // ---------------------------------------------------------------------------
 template <int N>
 __device__ __forceinline__ constexpr int blk(int i, int j) { return i * N + (N == 8 ? (j ^ (i & 4)) : j); }
-
-template <int N>
-__device__ __forceinline__ bool spd_inverse(float* A) {
-    float L[N][N];
-    bool ok = true;
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-#pragma unroll
-        for (int j = 0; j < N; ++j) L[i][j] = (j <= i) ? A[blk<N>(i, j)] : 0.f;
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        float d = L[k][k];
-#pragma unroll
-        for (int p = 0; p < k; ++p) d -= L[k][p] * L[k][p];
-        if (!(d > 0.f)) { ok = false; d = 1.f; }
-        const float lk = sqrtf(d), il = 1.f / lk;
-        L[k][k] = lk;
-#pragma unroll
-        for (int i = k + 1; i < N; ++i) {
-            float s = L[i][k];
-#pragma unroll
-            for (int p = 0; p < k; ++p) s -= L[i][p] * L[k][p];
-            L[i][k] = s * il;
-        }
-    }
-    // column j of L^{-1} overwrites column j of L: entries (p, j), p < i, are already
-    // the inverse's, entries (i, p), p > j, and the diagonal (i, i), i > j, are still L's
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-        L[j][j] = 1.f / L[j][j];
-#pragma unroll
-        for (int i = j + 1; i < N; ++i) {
-            float s = 0.f;
-#pragma unroll
-            for (int p = j; p < i; ++p) s += L[i][p] * L[p][j];
-            L[i][j] = -s / L[i][i];
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-#pragma unroll
-        for (int j = 0; j <= i; ++j) {
-            float s = 0.f;
-#pragma unroll
-            for (int p = i; p < N; ++p) s += L[p][i] * L[p][j];
-            A[blk<N>(i, j)] = s;
-            A[blk<N>(j, i)] = s;
-        }
-    return ok;
-}
 
 }  // namespace fast
 }  // namespace tmpc

@@ -7,14 +7,16 @@
 namespace tmpc {
 namespace fast {
 
+// factorisation policies of the shared-memory kernels
+constexpr int kPolicyCR = 0, kPolicyLDL = 1;
 // floats of per-instance storage needed by the shared-memory path for T stages
-long long arena_floats_host(int model, int T);
+long long arena_floats_host(int model, int T, int policy);
 // models handled by the shared-memory path
 bool supported(int model);
 // set the dynamic shared-memory limit of the model's kernel and query its occupancy
-cudaError_t prepare(int model, size_t smem_bytes, int threads, int* blocks_per_sm);
+cudaError_t prepare(int model, int policy, size_t smem_bytes, int threads, int* blocks_per_sm);
 // launch the persistent kernel over `count` instances listed in `order`
-cudaError_t launch(int model, int grid, int threads, size_t smem_bytes, cudaStream_t s, const KLayout& L,
+cudaError_t launch(int model, int policy, int grid, int threads, size_t smem_bytes, cudaStream_t s, const KLayout& L,
                    const KOpts& o, const KParams& p, const KSol& out, float* gws, long long gstride,
                    const int* order, int count, int* queue, const float* x0, int warm);
 

@@ -158,7 +158,7 @@ def _compare(pb, sol, idx, allow_flips=0, opts=None, sensitivity=False):
     return errs
 
 
-SOLVERS = [pytest.param(1, id="generic_ldl"), pytest.param(2, id="smem_cr")]
+SOLVERS = [pytest.param(1, id="generic_ldl"), pytest.param(2, id="smem_cr"), pytest.param(4, id="warp_ldl")]
 
 
 @pytest.mark.parametrize("solver", SOLVERS)
@@ -201,7 +201,8 @@ def test_uneven_model_mix(solver):
     _compare(pb, sol, range(12), sensitivity=True)
 
 
-def test_long_instances_fall_back_to_global_arenas():
+@pytest.mark.parametrize("solver", [pytest.param(2, id="smem_cr"), pytest.param(4, id="warp_ldl")])
+def test_long_instances_fall_back_to_global_arenas(solver):
     """Instances whose shared-memory arena does not fit run the same kernel on
     a global-memory arena: a double-integrator batch mixing horizons of 600
     stages (arena about 0.5 MB) with short ones, down to N = 1."""
@@ -210,21 +211,22 @@ def test_long_instances_fall_back_to_global_arenas():
     for i in range(6):
         N = int(pb.N[i])
         pb.Qd[i, N, :] = 10 * pb.Qd[i, 0, :]
-    s, sol, _ = _run(pb, solver=2)
+    s, sol, _ = _run(pb, solver=solver)
     _compare(pb, sol, range(6))
 
 
-def test_global_arenas_match_shared_arenas_bitwise():
-    """The cyclic-reduction kernel runs the same arithmetic whether an
-    instance's arena sits in shared or in global memory."""
+@pytest.mark.parametrize("shared,glob", [(2, 3), (4, 5)], ids=["smem_cr", "warp_ldl"])
+def test_global_arenas_match_shared_arenas_bitwise(shared, glob):
+    """The shared-memory kernels run the same arithmetic whether an instance's
+    arena sits in shared or in global memory."""
     pb = w.racing(B=8, N=40, max_sqp=3, max_admm=30)
     pb.N[:] = [40, 7, 33, 1, 40, 20, 12, 39]
     for i in range(8):
         N = int(pb.N[i])
         pb.lin[i, :, 5] = 0.0
         pb.lin[i, N, 5] = -1.0
-    _, a, _ = _run(pb, solver=2)
-    _, b, _ = _run(pb, solver=3)
+    _, a, _ = _run(pb, solver=shared)
+    _, b, _ = _run(pb, solver=glob)
     for k in ("z", "xi", "y_eq", "y_ineq", "status", "stats"):
         assert np.array_equal(a[k], b[k]), k
 
