@@ -38,13 +38,32 @@ import numpy as np  # noqa: E402
 METRIC = "OCP solves/sec (fwd and fwd+bwd) at 1e-5 KKT residual; % of HBM/FP32 roofline"
 UNIT = "solves/s"
 
-# algorithmic FP32 work of the path per stage, counted from the dense block
-# operations of the method's formulas for the bicycle model (n = 8, nx = 6,
-# ng = 5); an FMA counts 2.
-FLOP_ADMM_STAGE = 1140.0    # one ADMM iteration: eta, block LDL' solve, C x~, G x~, relax, project, duals
-FLOP_FACTOR_STAGE = 4800.0  # one factorisation: Theta_t, Phi_t, Schur update, pivot inverse, off-diagonal factor
-FLOP_LIN_STAGE = 400.0      # one linearisation: Jacobians, cost blocks, shifted bounds
-FLOP_MERIT_STAGE = 200.0    # one merit evaluation (dynamics residual, cost, violation) per line-search candidate
+# Algorithmic FP32 work of the path per stage, counted from the dense block
+# operations of the method's formulas for a model with n = nx + nu, nx, ng;
+# an FMA counts 2.  For the bicycle (8, 6, 5): 1056, 4992, 368 and 164.
+def flop_admm_stage(n, nx, ng):
+    # C'(.) and G'(.) of eta, block LDL' solve (6 n^2), C x~, G x~, relaxation, projection, duals
+    return 8 * nx * n + 4 * ng * n + 6 * n * n + 3 * n + 9 * nx + 10 * ng
+
+
+def flop_factor_stage(n, nx, ng):
+    # rho_f (A+'A+ + A-'A-) and Phi_t (6 n^2 nx), rho_g G'G (2 n^2 ng), Schur update, pivot inverse, off-diagonal factor
+    return 6 * n * n * nx + 2 * n * n * ng + 4 * n ** 3
+
+
+def flop_lin_stage(n, nx, ng):
+    return 6 * nx * n + 10 * n           # Jacobian products, cost gradient, shifted bounds
+
+
+def flop_merit_stage(n, nx, ng):
+    return 2 * nx * n + 6 * n + 4 * ng   # dynamics residual, cost, violation per line-search candidate
+
+
+def bytes_admm_stage(n, nx, lti):
+    # factor blocks (D^-1, off-diagonal factor) and, for time-varying models, A^-, A^+ read per iteration
+    return 4 * (2 * n * n + (0 if lti else 2 * nx * n))
+
+
 SMS, FP32_LANES = 152, 128
 
 
@@ -54,9 +73,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--batch", type=int, default=1024)
-    ap.add_argument("--horizon", type=int, default=50)
-    ap.add_argument("--cpu-sample", type=int, default=128)
+    ap.add_argument("--workload", default="racing",
+                    choices=["racing", "double_integrator", "tracking", "uneven", "long_horizon"],
+                    help="racing (default): bicycle B=1024 N=50; double_integrator: B=1 N=20; "
+                         "tracking: linear nx=48 nu=20 N=32 B=512; uneven: B=4096 N in 10..200, "
+                         "three models; long_horizon: bicycle B=8 N=8192")
+    ap.add_argument("--batch", type=int, default=0, help="instances (0 = the workload's size)")
+    ap.add_argument("--horizon", type=int, default=0, help="horizon N (0 = the workload's; fixed-N workloads)")
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="oracle instances timed for cpu_baseline (0 = about 10-30 CPU-seconds of the workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-bwd", action="store_true", help="time the forward pass only")
     ap.add_argument("--solver", type=int, default=0, help="0 auto, 1 generic sequential LDL', 2 shared-memory CR, 3 CR on global arenas, "
@@ -66,14 +91,36 @@ def parse():
     return ap.parse_args()
 
 
-def workload(args, rank=0):
+CPU_SAMPLE = {"racing": 128, "double_integrator": 512, "tracking": 96, "uneven": 192, "long_horizon": 16}
+
+WORKLOADS = {
+    # name: (generator, default batch, default horizon, seed, description)
+    "racing": ("racing", 1024, 50, 1002, "kinematic-bicycle racing (implicit midpoint, L1+L2 soft track row, "
+                                         "rate cost, progress cost)"),
+    "double_integrator": ("double_integrator", 1, 20, 1001, "2-D double integrator, box bounds on u and v"),
+    "tracking": ("tracking", 512, 32, 1003, "linear tracking nx=48 nu=20, MLP cost weights, |u| <= 1"),
+    "uneven": ("uneven", 4096, 0, 1004, "uneven batch N in 10..200, double integrator / bicycle / quadrotor 1:2:1"),
+    "long_horizon": ("long_horizon", 8, 8192, 1005, "kinematic-bicycle racing, dt=0.01, closed 2 km track"),
+}
+
+
+def make_batch(name, B, N, seed):
     import workloads as w
-    return w.racing(B=args.batch, N=args.horizon, seed=1002 + 7919 * rank)
+    gen = getattr(w, WORKLOADS[name][0])
+    if name == "uneven":
+        return gen(B=B, seed=seed)
+    return gen(B=B, N=N, seed=seed)
+
+
+def workload(args, rank=0):
+    _, B0, N0, seed, _ = WORKLOADS[args.workload]
+    return make_batch(args.workload, args.batch or B0, args.horizon or N0, seed + 7919 * rank)
 
 
 def config_of(args, pb):
-    return {"workload": f"kinematic-bicycle racing B={pb.B} N={pb.N_max} (implicit midpoint, "
-                        f"L1+L2 soft track row, rate cost), {pb.opts.max_sqp} SQP x {pb.opts.max_admm} ADMM",
+    desc = WORKLOADS[args.workload][4]
+    Ns = f"N={pb.N_max}" if np.all(pb.N == pb.N_max) else f"N={int(pb.N.min())}..{int(pb.N.max())}"
+    return {"workload": f"{args.workload}: {desc}, B={pb.B} {Ns}, {pb.opts.max_sqp} SQP x {pb.opts.max_admm} ADMM",
             "batch": pb.B, "horizon": pb.N_max, "nx": pb.nx, "nu": pb.nu, "ng": pb.ng,
             "sqp_iters": pb.opts.max_sqp, "admm_iters": pb.opts.max_admm,
             "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{args.gpus}",
@@ -89,10 +136,9 @@ def config_of(args, pb):
 _WORKER_BATCH = None
 
 
-def _init_worker(B, N, seed):
+def _init_worker(name, B, N, seed):
     global _WORKER_BATCH
-    import workloads as w
-    _WORKER_BATCH = w.racing(B=B, N=N, seed=seed)
+    _WORKER_BATCH = make_batch(name, B, N, seed)
 
 
 def _oracle_one(i):
@@ -108,8 +154,14 @@ def oracle_rate(args, n_inst, cores):
     """Solve n_inst instances of the workload with the FP64 oracle on `cores`
     processes; returns (solves/s, wall seconds, summed CPU seconds).  Instance
     generation happens once per worker, before the timed map."""
+    # one single-threaded process per core: the BLAS/LAPACK calls of the oracle must not
+    # start their own thread pools (the spawned workers read these at numpy import)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        os.environ[k] = "1"
     ctx = mp.get_context("spawn")
-    with ctx.Pool(cores, initializer=_init_worker, initargs=(n_inst, args.horizon, 1002)) as pool:
+    _, B0, N0, seed, _ = WORKLOADS[args.workload]
+    with ctx.Pool(cores, initializer=_init_worker,
+                  initargs=(args.workload, min(n_inst, args.batch or B0), args.horizon or N0, seed)) as pool:
         pool.map(_oracle_one, range(cores), chunksize=1)   # imports, warm caches
         t = time.perf_counter()
         times = pool.map(_oracle_one, range(n_inst), chunksize=1)
@@ -122,7 +174,7 @@ def run_reference(args):
     if rank != 0:
         return
     cores = os.cpu_count() or 1
-    per_step = max(cores, min(args.cpu_sample, 4 * cores))
+    per_step = max(cores, min(args.cpu_sample or CPU_SAMPLE[args.workload], 4 * cores))
     for _ in range(max(args.warmup, 0) and 1):
         oracle_rate(args, cores, cores)
     vals, walls = [], []
@@ -208,15 +260,34 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def _model_dims(pb):
+    import workloads as w
+    dims = np.array([w.model_dims(int(m), pb.nx, pb.nu, pb.ng) for m in pb.model], dtype=np.float64)
+    return dims[:, 0] + dims[:, 1], dims[:, 0], dims[:, 2]
+
+
 def algorithmic_flops(pb, stats):
     """FP32 flops the method needs for the solves just run (counts from the stats)."""
+    n, nx, ng = _model_dims(pb)
     T = pb.N.astype(np.float64) + 1.0
     admm = stats[:, 1].astype(np.float64)
     fact = stats[:, 5].astype(np.float64)
     sqp = stats[:, 0].astype(np.float64)
-    n_ls = float(pb.opts.n_ls)
-    return float(np.sum(T * (admm * FLOP_ADMM_STAGE + fact * FLOP_FACTOR_STAGE + (sqp + 1) * FLOP_LIN_STAGE
-                             + sqp * n_ls * FLOP_MERIT_STAGE)))
+    n_ls = float(pb.opts.n_ls) if pb.opts.n_ls > 1 else 0.0
+    return float(np.sum(T * (admm * flop_admm_stage(n, nx, ng) + fact * flop_factor_stage(n, nx, ng)
+                             + (sqp + 1) * flop_lin_stage(n, nx, ng) + sqp * n_ls * flop_merit_stage(n, nx, ng))))
+
+
+def algorithmic_bytes(pb, stats):
+    """Bytes the ADMM iterations must stream when the factors live in HBM (the
+    generic kernel's workspace): factor blocks and time-varying Jacobians."""
+    import workloads as w
+    n, nx, ng = _model_dims(pb)
+    lti = np.isin(pb.model, (w.MODEL_DI, w.MODEL_LINEAR))
+    T = pb.N.astype(np.float64) + 1.0
+    admm = stats[:, 1].astype(np.float64)
+    per = np.where(lti, 4 * 2 * n * n, 4 * (2 * n * n + 2 * nx * n))
+    return float(np.sum(T * admm * per))
 
 
 FAST_MODELS = (0, 2, 3)   # models with a compile-time-sized shared-memory kernel
@@ -246,7 +317,24 @@ def sources_digest():
     return h.hexdigest()
 
 
-def measured_traffic(pb):
+def measured_peak(key, fallback):
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))[key])
+    except Exception:
+        return fallback
+
+
+def kernel_name(pb, solver):
+    import workloads as w
+    names = {w.MODEL_DI: "MODEL_DI", w.MODEL_BICYCLE: "MODEL_BICYCLE", w.MODEL_QUAD: "MODEL_QUAD"}
+    pol = "kLDL" if solver in (4, 5) else "kCR"
+    ks = []
+    for m in sorted(set(int(v) for v in np.unique(pb.model))):
+        ks.append(f"fast::solve_kernel<{names[m]}, {pol}>" if (m in names and solver != 1) else "solve_kernel (generic)")
+    return " + ".join(sorted(set(ks)))
+
+
+def measured_traffic(args, pb):
     """DRAM bytes (read + write) per launch of the solve kernel from the committed
     ncu summary, scaled to this batch by instances; None when the kernel sources
     changed since the counters were taken or no summary matches the workload."""
@@ -255,7 +343,8 @@ def measured_traffic(pb):
         rec = json.load(open(path))
     except Exception:
         return None
-    if rec.get("sources_sha256") != sources_digest() or rec.get("horizon") != pb.N_max:
+    if (rec.get("sources_sha256") != sources_digest() or rec.get("horizon") != pb.N_max
+            or rec.get("workload_name", "racing") != args.workload):
         return None
     return rec["dram_bytes_per_launch"] * pb.B / rec["batch"]
 
@@ -270,7 +359,7 @@ def run_gpu(args):
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        n = max(cores, args.cpu_sample)
+        n = max(cores, args.cpu_sample or CPU_SAMPLE[args.workload])
         v, wall, cpu_s = oracle_rate(args, n, cores)
         cpu_base = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                     "sample": f"{n} instances of the same workload (FP64 numpy/scipy oracle, one process per core, "
@@ -289,17 +378,20 @@ def run_gpu(args):
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
+    warm = s.z_init is not None
+
     def restart():
-        # every step starts from the same centreline guess (zero slacks and multipliers)
-        sol["z"].copy_(s.z_init)
-        for k in ("xi", "y_eq", "y_ineq"):
-            sol[k].zero_()
+        # every step starts from the same initial guess (zero slacks and multipliers)
+        if warm:
+            sol["z"].copy_(s.z_init)
+            for k in ("xi", "y_eq", "y_ineq"):
+                sol[k].zero_()
 
     def step(kev=None):
         restart()
         if kev is not None:
             kev[0].record(stream)
-        s.tmpc_solve(s.x0, sol, warm_start=True)
+        s.tmpc_solve(s.x0, sol, warm_start=warm)
         if kev is not None:
             kev[1].record(stream)
 
@@ -368,9 +460,22 @@ def run_gpu(args):
     value = total / (ms_f * 1e-3)
     flops = algorithmic_flops(pb, stats)
     ms_k = float(np.mean(k_fwd))          # the solve kernel(s) of one forward step, on the launching stream
-    achieved = flops / (ms_k * 1e-3) / 1e12
     peak_clock = 2070.0
-    peak = SMS * FP32_LANES * 2 * peak_clock * 1e6 / 1e12
+    fp32_peak = SMS * FP32_LANES * 2 * peak_clock * 1e6 / 1e12
+    if args.workload == "tracking":
+        # factors of 0.74 MB per instance do not fit on chip: streamed from HBM every ADMM iteration
+        achieved = algorithmic_bytes(pb, stats) / (ms_k * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": measured_peak("hbm_gbs", 6800.0), "unit": "GB/s",
+                "flops_tflops": flops / (ms_k * 1e-3) / 1e12,
+                "peak_note": "STREAM-style copy bandwidth of this GPU pool (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        achieved = flops / (ms_k * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "peak_note": "FP32 FMA peak = 152 SM x 128 lanes x 2 flop x 2070 MHz (derived)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = measured_traffic(args, pb)
+    roof["kernel"] = kernel_name(pb, args.solver)
+    roof["kernel_ms"] = ms_k
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -381,10 +486,7 @@ def run_gpu(args):
             "e2e": {"value": total / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": launches,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": measured_traffic(pb),
-                         "kernel": "fast::solve_kernel<MODEL_BICYCLE>", "kernel_ms": ms_k,
-                         "peak_note": "FP32 FMA peak = 152 SM x 128 lanes x 2 flop x 2070 MHz (derived)"},
+            "roofline": roof,
             "cpu_baseline": cpu_base,
             "quality": {"kkt_median": float(np.median(kkt)), "kkt_p90": float(np.percentile(kkt, 90)),
                         "frac_kkt_le_1e-5": float(np.mean(kkt <= 1e-5)),
