@@ -55,8 +55,10 @@ enum {
     TMPC_INST_MAX_ITER = 1,   /* iteration caps reached before eps_c             */
     TMPC_INST_NOT_PD = 2,     /* a pivot block of S was not positive definite    */
     TMPC_INST_NAN = 3,        /* a non-finite value appeared                     */
-    TMPC_INST_INVALID = 4     /* tmpc_solve_static only: N or model of the instance
+    TMPC_INST_INVALID = 4,    /* tmpc_solve_static only: N or model of the instance
                                  is out of range for the layout; not solved       */
+    TMPC_INST_TIMEOUT = 5     /* a bounded wait for an asynchronous shared-memory copy
+                                 gave up; the result of the instance is not valid  */
 };
 
 /* model ids (problem families; dynamics as in Appendix A of the paper, Remark A1) */

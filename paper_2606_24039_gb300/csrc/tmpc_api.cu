@@ -35,26 +35,53 @@ void set_err(const char* what, cudaError_t e) {
         }                                                \
     } while (0)
 
-__device__ __forceinline__ Smem carve_smem(void* raw, int n) {
+// Shared memory of the generic kernels:
+//   reduction scratch, mbarriers, flags
+//   A, Bm       n^2 each: factorisation scratch (Delta / L^-1) and the two buffers
+//               of the block stream of ldl_solve
+//   red         8 x 96 floats: per-warp partial sums of ldl_solve
+//   with L.vs:  the ADMM vectors (vs_floats), eta and xt first and together at
+//               least n^2 floats, which the factorisation borrows as its third
+//               scratch Cm (eta and xt are dead whenever S is factored)
+//   else:       Cm, n^2 floats
+__host__ __device__ inline long long vs_floats(const KLayout& L) {
+    const long long T = L.Nmax + 1, n = L.n;
+    const long long et = T * n > n * n - T * n ? T * n : n * n - T * n;
+    return T * n + et + 2 * T * n + 2 * T * L.nx + 6 * T * L.ng;
+}
+
+__device__ __forceinline__ Smem carve_smem(void* raw, const KLayout& L) {
+    const int n = L.n;
     Smem s;
     char* p = reinterpret_cast<char*>(raw);
     s.redd = reinterpret_cast<double*>(p);            p += 32 * 2 * sizeof(double);
     s.lsacc = reinterpret_cast<double*>(p);           p += (2 * (kMaxLs + 1) + 2) * sizeof(double);
+    s.mbar = reinterpret_cast<unsigned long long*>(p); p += 2 * sizeof(unsigned long long);
     s.red = reinterpret_cast<float*>(p);              p += 32 * 8 * sizeof(float);
     s.flags = reinterpret_cast<int*>(p);              p += 16 * sizeof(int);
     s.A = reinterpret_cast<float*>(p);                p += n * n * sizeof(float);
     s.Bm = reinterpret_cast<float*>(p);               p += n * n * sizeof(float);
-    s.Cm = reinterpret_cast<float*>(p);
+    s.red8 = reinterpret_cast<float*>(p);             p += 8 * 96 * sizeof(float);
+    if (L.vs) {
+        s.vs = reinterpret_cast<float*>(p);
+        s.Cm = s.vs;
+    } else {
+        s.vs = nullptr;
+        s.Cm = reinterpret_cast<float*>(p);
+    }
     return s;
 }
 
-size_t smem_bytes(int n) {
-    return 32 * 2 * sizeof(double) + (2 * (kMaxLs + 1) + 2) * sizeof(double) + 32 * 8 * sizeof(float) +
-           16 * sizeof(int) + 3 * (size_t)n * n * sizeof(float);
+size_t smem_bytes(const KLayout& L) {
+    const size_t n = L.n;
+    const size_t fixed = 32 * 2 * sizeof(double) + (2 * (kMaxLs + 1) + 2) * sizeof(double) +
+                         2 * sizeof(unsigned long long) + 32 * 8 * sizeof(float) + 16 * sizeof(int) +
+                         2 * n * n * sizeof(float) + 8 * 96 * sizeof(float);
+    return fixed + (L.vs ? (size_t)vs_floats(L) * sizeof(float) : n * n * sizeof(float));
 }
 
 __device__ Ctx make_ctx(const KLayout& L, const KParams& p, float* ws, const WsOff& off, int i,
-                        const float* x0) {
+                        const float* x0, float* vs) {
     Ctx c;
     c.model = p.model[i];
     const ModelDims md = model_dims(c.model, L.nx, L.nu, L.ng);
@@ -89,6 +116,23 @@ __device__ Ctx make_ctx(const KLayout& L, const KParams& p, float* ws, const WsO
     c.zg = b + off.zg; c.yg = b + off.yg; c.xi = b + off.xi; c.yf = b + off.yf; c.zb = b + off.zb;
     c.xib = b + off.xib; c.yfb = b + off.yfb; c.ygb = b + off.ygb; c.gw = b + off.gw;
     c.czb = b + off.czb; c.gzb = b + off.gzb; c.pf = b + off.pf; c.pg = b + off.pg;
+    if (vs) {   // the ADMM vectors in shared memory (layout of vs_floats)
+        const long long T = L.Nmax + 1, n = L.n;
+        const long long et = T * n > n * n - T * n ? T * n : n * n - T * n;
+        float* q = vs;
+        c.eta = q; q += T * n;
+        c.xt = q;  q += et;
+        c.x = q;   q += T * n;
+        c.qv = q;  q += T * n;
+        c.yf = q;  q += T * L.nx;
+        c.pf = q;  q += T * L.nx;
+        c.zg = q;  q += T * L.ng;
+        c.yg = q;  q += T * L.ng;
+        c.xi = q;  q += T * L.ng;
+        c.glo = q; q += T * L.ng;
+        c.ghi = q; q += T * L.ng;
+        c.pg = q;
+    }
     c.amS = model_const_Am(c.model) ? 0 : c.nx * c.n;
     c.apS = model_const_Ap(c.model) ? 0 : c.nx * c.n;
     c.gS = model_const_G(c.model) ? 0 : c.ng * c.n;
@@ -120,7 +164,7 @@ __device__ void write_solution(const Ctx& c, const KLayout& L, const KSol& out, 
 __device__ void solve_instance(const Ctx& c, const KOpts& o, const Smem& sm, const KLayout& L,
                                const KSol& out, int inst, int warm) {
     const int n = c.n, nx = c.nx, ng = c.ng, T = c.T;
-    if (threadIdx.x == 0) sm.flags[0] = 0;
+    if (threadIdx.x == 0) { sm.flags[0] = 0; sm.flags[14] = 0; }
     if (warm) {
         read_warm(c, L, out, inst);
     } else {
@@ -155,7 +199,7 @@ __device__ void solve_instance(const Ctx& c, const KOpts& o, const Smem& sm, con
         __syncthreads();
         int k = 0;
         for (k = 1; k <= o.max_admm; ++k) {
-            admm_iter(c, o, rho);
+            admm_iter(c, o, rho, sm);
             const bool cc = o.early_exit && (k % o.check_every == 0);
             const bool cr = (k % o.k_rho_iter == 0) && k < o.max_admm;
             if (cc || cr || k == o.max_admm) {
@@ -207,6 +251,7 @@ __device__ void solve_instance(const Ctx& c, const KOpts& o, const Smem& sm, con
     if (threadIdx.x == 0) {
         int st = TMPC_INST_OK;
         if (!(bad[0] < kInf) || !(kk < kInf)) st = TMPC_INST_NAN;
+        else if (sm.flags[14]) st = TMPC_INST_TIMEOUT;
         else if (sm.flags[0]) st = TMPC_INST_NOT_PD;
         else if (!(kk <= o.eps_c)) st = TMPC_INST_MAX_ITER;
         if (out.status) out.status[inst] = st;
@@ -224,7 +269,8 @@ __global__ void __launch_bounds__(256, 2) solve_kernel(KLayout L, KOpts o, KPara
                              const int* order, int count, int* queue, const float* x0, int warm) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
-    const Smem sm = carve_smem(smem_raw, L.n);
+    const Smem sm = carve_smem(smem_raw, L);
+    block_stream_init(sm.mbar, sm.flags + 12);
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
         __syncthreads();
@@ -232,7 +278,7 @@ __global__ void __launch_bounds__(256, 2) solve_kernel(KLayout L, KOpts o, KPara
         __syncthreads();
         if (q >= count) break;
         const int i = order[q];
-        const Ctx c = make_ctx(L, p, ws, off, i, x0);
+        const Ctx c = make_ctx(L, p, ws, off, i, x0, sm.vs);
         solve_instance(c, o, sm, L, out, i, warm);
     }
 }
@@ -242,7 +288,8 @@ __global__ void __launch_bounds__(256, 2) backward_kernel(KLayout L, KOpts o, KP
                                 const float* dLdxi, KGrads g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
-    const Smem sm = carve_smem(smem_raw, L.n);
+    const Smem sm = carve_smem(smem_raw, L);
+    block_stream_init(sm.mbar, sm.flags + 12);
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
         __syncthreads();
@@ -250,7 +297,7 @@ __global__ void __launch_bounds__(256, 2) backward_kernel(KLayout L, KOpts o, KP
         __syncthreads();
         if (q >= L.B) break;
         const int i = order[q];
-        const Ctx c = make_ctx(L, p, ws, off, i, x0);
+        const Ctx c = make_ctx(L, p, ws, off, i, x0, sm.vs);
         backward_instance(c, o, sm, L, sol, i, dLdz, dLdxi, g);
     }
 }
@@ -308,6 +355,18 @@ struct tmpc_handle {
     float* s_x0 = nullptr;
     tmpc_solution ss{};
 };
+
+// 1 if the generic kernels keep two CTAs per SM with the ADMM vectors in shared memory
+int choose_vs(KLayout L, int threads, int max_optin) {
+    L.vs = 1;
+    const size_t bytes = smem_bytes(L);
+    if ((long long)bytes > max_optin) return 0;
+    if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+        return 0;
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel, threads, bytes) != cudaSuccess) return 0;
+    return per >= 2 ? 1 : 0;
+}
 
 extern "C" {
 
@@ -493,7 +552,9 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
     }
 
     h->threads = o->threads > 0 ? o->threads : (n <= 16 ? 128 : 256);
-    h->smem = smem_bytes(n);
+    // ADMM vectors in shared memory when two CTAs per SM still fit
+    h->L.vs = choose_vs(h->L, h->threads, max_optin);
+    h->smem = smem_bytes(h->L);
     if (h->smem > 48 * 1024) {
         cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
         cudaFuncSetAttribute(backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
@@ -812,7 +873,15 @@ tmpc_status tmpc_solve_static(const tmpc_dims* d, const tmpc_options* o, const t
     L.B = d->batch; L.Nmax = d->N_max; L.nx = d->nx; L.nu = d->nu; L.ng = d->ng; L.n = n;
     L.n_dyn = d->n_dyn; L.n_track = d->n_track;
     const int threads = o->threads > 0 ? o->threads : (n <= 16 ? 128 : 256);
-    const size_t smem = smem_bytes(n);
+    int max_optin = 0;
+    {
+        int dv = 0;
+        TMPC_CUDA(cudaGetDevice(&dv));
+        TMPC_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dv));
+    }
+    const int threads_static = o->threads > 0 ? o->threads : (n <= 16 ? 128 : 256);
+    L.vs = choose_vs(L, threads_static, max_optin);
+    const size_t smem = smem_bytes(L);
     if (smem > 48 * 1024)
         TMPC_CUDA(cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, nsm = 1, per_sm = 1;

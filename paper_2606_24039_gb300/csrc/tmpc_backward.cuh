@@ -49,7 +49,7 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
     const float* dLdz = dLdz_all + inst * Ts * L.n;
     const float* dLdxi = dLdxi_all ? dLdxi_all + inst * Ts * L.ng : nullptr;
     float rb = o.bwd_rho;
-    if (threadIdx.x == 0) sm.flags[0] = 0;
+    if (threadIdx.x == 0) { sm.flags[0] = 0; sm.flags[14] = 0; }
     read_warm(c, L, sol, inst);  // zb, xib, yfb, ygb <- solution
     linearize(c);                // Jacobians and g at the solution
     float* code = c.zg;   // active codes
@@ -123,7 +123,7 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
             c.eta[e] += rb * s;
         }
         __syncthreads();
-        ldl_solve(c, c.eta, c.xt);  // dx
+        ldl_solve(c, c.eta, c.xt, sm.red8, sm.A, sm.Bm, sm.mbar, sm.flags + 12);  // dx
         for (int e = threadIdx.x; e < T * nx; e += blockDim.x)
             lam[e] += rb * (Cx_entry(c, c.xt, e / nx, e % nx) - r2[e]);
         for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
@@ -207,6 +207,7 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
             }
         }
     if (threadIdx.x == 0 && sol.status && sm.flags[0]) sol.status[inst] = 2;  // not positive definite
+    if (threadIdx.x == 0 && sol.status && sm.flags[14]) sol.status[inst] = TMPC_INST_TIMEOUT;
     __syncthreads();
 }
 

@@ -36,6 +36,7 @@ struct KOpts {
 
 struct KLayout {
     int B, Nmax, nx, nu, ng, n, n_dyn, n_track;
+    int vs;   // generic kernel: 1 if the ADMM vectors live in shared memory (see carve_smem)
 };
 
 struct KParams {
@@ -77,9 +78,12 @@ struct Smem {
     float* Bm;     // n*n
     float* Cm;     // n*n
     float* red;    // 32*8 floats
+    float* red8;   // 8*96 floats (ldl_solve partial sums)
     double* redd;  // 32*2 doubles
     double* lsacc; // 2*kMaxLs doubles
     int* flags;    // 4 ints
+    unsigned long long* mbar;  // 2 mbarriers of the bulk-copy pipeline (ldl_solve)
+    float* vs;     // ADMM vectors of the current instance (nullptr: in the global workspace)
 };
 
 struct Ctx {
@@ -298,11 +302,17 @@ __device__ __forceinline__ float Ct_entry(const Ctx& c, int t, int j, V v) {
     if (t == 0 && j < c.nx) s += v(0, j);
     if (t < c.N) {
         const float* Am = c.Amt(t);
-        for (int k = 0; k < c.nx; ++k) s += Am[k * c.n + j] * v(t + 1, k);
+        float s1 = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < c.nx; ++k) s1 += Am[k * c.n + j] * v(t + 1, k);
+        s += s1;
     }
     if (t > 0) {
         const float* Ap = c.Apt(t - 1);
-        for (int k = 0; k < c.nx; ++k) s += Ap[k * c.n + j] * v(t, k);
+        float s2 = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < c.nx; ++k) s2 += Ap[k * c.n + j] * v(t, k);
+        s += s2;
     }
     return s;
 }
@@ -315,15 +325,20 @@ __device__ __forceinline__ float Cx_entry(const Ctx& c, const float* x, int r, i
     const float* Ap = c.Apt(t);
     const float* a = x + t * c.n;
     const float* b = x + (t + 1) * c.n;
-    float s = 0.f;
-    for (int j = 0; j < c.n; ++j) s += Am[k * c.n + j] * a[j] + Ap[k * c.n + j] * b[j];
-    return s;
+    float s = 0.f, s2 = 0.f;
+#pragma unroll 8
+    for (int j = 0; j < c.n; ++j) {
+        s += Am[k * c.n + j] * a[j];
+        s2 += Ap[k * c.n + j] * b[j];
+    }
+    return s + s2;
 }
 
 __device__ __forceinline__ float Gx_entry(const Ctx& c, const float* x, int t, int r) {
     const float* G = c.Gt(t) + r * c.n;
     const float* a = x + t * c.n;
     float s = 0.f;
+#pragma unroll 8
     for (int j = 0; j < c.n; ++j) s += G[j] * a[j];
     return s;
 }
@@ -601,8 +616,190 @@ __device__ inline bool factor(const Ctx& c, const Smem& sm, float sigma, float r
 
 // Solve S x = b with the block LDL' factors; b (T x n) is overwritten by the
 // forward sweep, the result goes to xo (T x n).
-__device__ inline void ldl_solve(const Ctx& c, float* b, float* xo) {
+//   forward   b_{t+1} -= Om_t b_t
+//   diagonal  x_t = Dinv_t b_t
+//   backward  x_t -= Om_t' x_{t+1}
+// For n >= 32 (the factors stream from global memory) every block is read
+// row-contiguously by whole warps: forward and diagonal rows are dotted by one
+// warp each (lanes over the columns, shuffle sum); the backward sweep lets warp
+// w accumulate the rows k = w (mod warps) of Om_t' x over its lanes' columns and
+// sums the per-warp partials through `red` (warps x 96 floats of shared memory).
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies global -> shared (cp.async.bulk, the TMA unit) with
+// completion counted on an mbarrier.  Addresses 16-byte aligned, size a
+// multiple of 16 bytes.  Waits are bounded: after kMbarSpin polls the wait
+// gives up and the caller falls back to reading global memory.
+// ---------------------------------------------------------------------------
+constexpr unsigned kMbarSpin = 1u << 24;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// thread issuing the copy: expect `bytes` on `bar`, then start the copy
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+// wait for phase `parity` of `bar` to complete; false if it did not within kMbarSpin polls
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    for (unsigned k = 0; k < kMbarSpin; ++k) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// once per CTA, before the first stream: both mbarriers and the stream state
+__device__ inline void block_stream_init(unsigned long long* mbar, int* state) {
+    if (threadIdx.x == 0) {
+        mbar_init(mbar, 1);
+        mbar_init(mbar + 1, 1);
+        fence_mbar_init();
+        state[0] = state[1] = state[2] = 0;
+    }
+    __syncthreads();
+}
+
+// Stream of equally sized blocks (one per step) into two shared buffers: the
+// block of step k + 1 is in flight while step k is consumed.  Every thread
+// calls get(k) in step order and sync() after using it.
+struct BlockStream {
+    float* buf[2];
+    unsigned long long* bar;
+    unsigned phase[2];
+    bool ok;
+    int* state;   // shared: [0], [1] phase bits of the two mbarriers, [2] set if a wait gave up
+    __device__ BlockStream(float* b0, float* b1, unsigned long long* bars, int* st) : bar(bars), ok(true), state(st) {
+        buf[0] = b0;
+        buf[1] = b1;
+        phase[0] = (unsigned)st[0];
+        phase[1] = (unsigned)st[1];
+    }
+    // after the last get / sync of a solve: store the phase bits for the next solve
+    __device__ void finish() {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            state[0] = (int)phase[0];
+            state[1] = (int)phase[1];
+            if (!ok) state[2] = 1;
+        }
+        __syncthreads();
+    }
+    // thread 0: start the copy of `src` into the buffer of step k
+    __device__ void issue(int k, const float* src, unsigned bytes) {
+        if (threadIdx.x == 0 && ok) {
+            fence_proxy_async();
+            bulk_load(buf[k & 1], src, bytes, bar + (k & 1));
+        }
+    }
+    // every thread: wait for the block of step k; returns the shared copy, or
+    // `fallback` (global memory) if the wait gave up
+    __device__ const float* get(int k, const float* fallback) {
+        if (!ok) return fallback;
+        const bool done = mbar_wait(bar + (k & 1), phase[k & 1]);
+        phase[k & 1] ^= 1u;
+        if (!__syncthreads_and(done)) {
+            ok = false;
+            return fallback;
+        }
+        return buf[k & 1];
+    }
+};
+
+// sbuf0/sbuf1 (n^2 floats each), mbar (2 mbarriers) and mstate (3 ints) enable
+// the shared-memory block stream; without them the blocks are read from global memory.
+__device__ inline void ldl_solve(const Ctx& c, float* b, float* xo, float* red, float* sbuf0 = nullptr,
+                                 float* sbuf1 = nullptr, unsigned long long* mbar = nullptr, int* mstate = nullptr) {
     const int n = c.n, N = c.N, nn = n * n;
+    if (n >= 32 && red) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        const bool k1 = lane + 32 < n, k2 = lane + 64 < n;   // n <= 72 < 96
+        // blocks of n^2 floats stream through two shared buffers (n even: whole 16-byte units)
+        const bool stream = sbuf0 && mstate && (n % 2 == 0);
+        const unsigned bytes = (unsigned)(nn * sizeof(float));
+        BlockStream bs(sbuf0, sbuf1, mbar, mstate);
+        int k = 0;   // step counter of the stream
+        if (stream) bs.issue(k, c.Om, bytes);
+        for (int t = 0; t < N; ++t, ++k) {
+            if (stream) bs.issue(k + 1, t + 1 < N ? c.Om + (t + 1) * nn : c.Dinv, bytes);
+            const float* Om = stream ? bs.get(k, c.Om + t * nn) : c.Om + t * nn;
+            const float* w = b + t * n;
+            const float w0 = w[lane], w1 = k1 ? w[lane + 32] : 0.f, w2 = k2 ? w[lane + 64] : 0.f;
+#pragma unroll 3
+            for (int i = warp; i < n; i += nw) {
+                const float* row = Om + i * n;
+                float s = row[lane] * w0;
+                if (k1) s += row[lane + 32] * w1;
+                if (k2) s += row[lane + 64] * w2;
+                s = warp_sum(s);
+                if (lane == 0) b[(t + 1) * n + i] -= s;
+            }
+            __syncthreads();
+        }
+        // diagonal: x_t = Dinv_t b_t (the block of step k is Dinv_t)
+        for (int t = 0; t < c.T; ++t, ++k) {
+            if (stream) bs.issue(k + 1, t + 1 < c.T ? c.Dinv + (t + 1) * nn : c.Om + (N - 1) * nn, bytes);
+            const float* D = stream ? bs.get(k, c.Dinv + t * nn) : c.Dinv + t * nn;
+            const float* w = b + t * n;
+            const float w0 = w[lane], w1 = k1 ? w[lane + 32] : 0.f, w2 = k2 ? w[lane + 64] : 0.f;
+#pragma unroll 3
+            for (int i = warp; i < n; i += nw) {
+                const float* row = D + i * n;
+                float s = row[lane] * w0;
+                if (k1) s += row[lane + 32] * w1;
+                if (k2) s += row[lane + 64] * w2;
+                s = warp_sum(s);
+                if (lane == 0) xo[t * n + i] = s;
+            }
+            __syncthreads();
+        }
+        for (int t = N - 1; t >= 0; --t, ++k) {
+            if (stream && t > 0) bs.issue(k + 1, c.Om + (t - 1) * nn, bytes);
+            const float* Om = stream ? bs.get(k, c.Om + t * nn) : c.Om + t * nn;
+            const float* xn = xo + (t + 1) * n;
+            float p0 = 0.f, p1 = 0.f, p2 = 0.f;
+#pragma unroll 3
+            for (int q = warp; q < n; q += nw) {
+                const float* row = Om + q * n;
+                const float xq = xn[q];
+                p0 += row[lane] * xq;
+                if (k1) p1 += row[lane + 32] * xq;
+                if (k2) p2 += row[lane + 64] * xq;
+            }
+            float* rw = red + warp * 96;
+            rw[lane] = p0;
+            rw[lane + 32] = p1;
+            rw[lane + 64] = p2;
+            __syncthreads();
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                float s = 0.f;
+                for (int q = 0; q < nw; ++q) s += red[q * 96 + i];
+                xo[t * n + i] -= s;
+            }
+            __syncthreads();
+        }
+        if (stream) bs.finish();
+        return;
+    }
     for (int t = 0; t < N; ++t) {
         const float* Om = c.Om + t * nn;
         const float* w = b + t * n;
@@ -664,7 +861,7 @@ __device__ __forceinline__ void project(float v, float lo, float hi, float rho_g
 // and dual updates of Algorithm 3 follow.  In exact arithmetic this is the
 // paper's iteration; in FP32 the rho_f-scaled terms only ever multiply small,
 // accurately formed differences.
-__device__ inline void admm_iter(const Ctx& c, const KOpts& o, float rho_bar) {
+__device__ inline void admm_iter(const Ctx& c, const KOpts& o, float rho_bar, const Smem& sm) {
     const int n = c.n, nx = c.nx, ng = c.ng, T = c.T;
     const float rho_f = 1e3f * rho_bar, rho_g = rho_bar, alpha = o.alpha;
     for (int e = threadIdx.x; e < T * ng; e += blockDim.x) c.pg[e] = Gx_entry(c, c.x, e / ng, e % ng) - c.zg[e];
@@ -678,7 +875,7 @@ __device__ inline void admm_iter(const Ctx& c, const KOpts& o, float rho_bar) {
         c.eta[e] = s;
     }
     __syncthreads();
-    ldl_solve(c, c.eta, c.xt);
+    ldl_solve(c, c.eta, c.xt, sm.red8, sm.A, sm.Bm, sm.mbar, sm.flags + 12);
     for (int e = threadIdx.x; e < T * nx; e += blockDim.x) {
         const float cd = Cx_entry(c, c.xt, e / nx, e % nx);
         c.yf[e] += rho_f * alpha * (c.pf[e] + cd);
@@ -734,10 +931,22 @@ __device__ inline Res residuals(const Ctx& c, const Smem& sm) {
         const int t = e / n, j = e % n;
         const float px = Px_entry(c, c.x, t, j);
         const float pzb = Px_entry(c, c.zb, t, j);
-        float aty = Ct_entry(c, t, j, [&](int r, int k) { return c.yf[r * nx + k]; });
+        // C'y_f + G'y_g accumulated in FP64: with up to 2 nx + ng terms, an FP32 sum
+        // would put a rounding floor near the termination tolerance under the residual
+        double atyd = 0.0;
+        if (t == 0 && j < nx) atyd += (double)c.yf[j];
+        if (t < c.N) {
+            const float* Am = c.Amt(t);
+            for (int k = 0; k < nx; ++k) atyd += (double)Am[k * n + j] * (double)c.yf[(t + 1) * nx + k];
+        }
+        if (t > 0) {
+            const float* Ap = c.Apt(t - 1);
+            for (int k = 0; k < nx; ++k) atyd += (double)Ap[k * n + j] * (double)c.yf[t * nx + k];
+        }
         const float* G = c.Gt(t);
-        for (int r = 0; r < ng; ++r) aty += G[r * n + j] * c.yg[t * ng + r];
-        v[1] = fmaxf(v[1], fin(px + c.qv[e] + aty));
+        for (int r = 0; r < ng; ++r) atyd += (double)G[r * n + j] * (double)c.yg[t * ng + r];
+        const float aty = (float)atyd;
+        v[1] = fmaxf(v[1], fin((float)((double)px + (double)c.qv[e] + atyd)));
         v[3] = fmaxf(v[3], fmaxf(fmaxf(fin(px + pzb), fin(aty)), fin(c.qv[e] - pzb)));
     }
     cta_max_k<4>(v, sm.red);
