@@ -452,10 +452,9 @@ def run_gpu(args):
     ms_f = float(np.mean(t_fwd))
     ms_fb = float(np.mean(t_fb))
     ms_e2e = 1e3 * float(np.mean(e2e_t))
-    if world > 1:
-        red = torch.tensor([ms_f, ms_fb, ms_e2e], device="cuda")
-        dist.all_reduce(red, op=dist.ReduceOp.MAX)
-        ms_f, ms_fb, ms_e2e = red.tolist()
+    if world > 1:   # the slowest rank sets the job time (no collective on the data path)
+        from paper_2606_24039_gb300.shard import max_over_ranks
+        ms_f, ms_fb, ms_e2e = (max_over_ranks(v, device="cuda") for v in (ms_f, ms_fb, ms_e2e))
     total = pb.B * world
     value = total / (ms_f * 1e-3)
     flops = algorithmic_flops(pb, stats)
