@@ -339,8 +339,10 @@ struct tmpc_handle {
     // double integrator / bicycle / quadrotor, g = 3 the generic kernel
     struct Group {
         int model = -1, offset = 0, count = 0, grid = 0, threads = 0, policy = 0;
+        int cluster = 0;   // > 0: CTAs per thread-block cluster (one cluster per instance)
         size_t smem = 0;
     } groups[4];
+    int* gflags = nullptr;     // team flags of cluster-launched instances (4 per instance)
     int n_groups = 0;
     float* fws = nullptr;      // global arenas of the shared-memory path (instances that do not fit)
     long long fstride = 0;
@@ -400,7 +402,7 @@ static tmpc_status check_options(const tmpc_options* o) {
     if (o->max_sqp < 0 || o->max_admm < 1 || o->n_ls < 1 || o->n_ls > kMaxLs) return TMPC_ERR_INVALID_ARG;
     if (o->newton_steps < 0 || o->bwd_iters < 1 || !(o->bwd_rho > 0.f)) return TMPC_ERR_INVALID_ARG;
     if (o->threads < 0 || o->threads > 256 || (o->threads % 32) != 0) return TMPC_ERR_INVALID_ARG;
-    if (o->solver < 0 || o->solver > 5) return TMPC_ERR_INVALID_ARG;
+    if (o->solver < 0 || o->solver > 6) return TMPC_ERR_INVALID_ARG;
     return TMPC_OK;
 }
 
@@ -530,10 +532,27 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
             const long long cap = std::max(48LL * 1024, (long long)max_optin / 2 - 8 * 1024);
             G.smem = (size_t)std::min(need, need <= cap ? need : (long long)max_optin / 3);
             if (o->solver == 3 || o->solver == 5) G.smem = 0;   // every arena in global memory
-            int per = 0;
-            e = fast::prepare(G.model, G.policy, G.smem, G.threads, &per);
-            if (e != cudaSuccess || per < 1) { set_err("fast::prepare", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
-            G.grid = std::max(1, std::min(G.count, per * h->nsm));
+            // few instances whose arenas do not fit: one thread-block cluster per instance
+            const bool few_long = o->solver == 0 && need > cap && (long long)G.count * 8 <= h->nsm;
+            if (o->solver == 6 || few_long) {
+                G.policy = fast::kPolicyCR;
+                G.threads = o->threads > 0 ? o->threads : 256;
+                for (int cl = 16; cl >= 2 && G.cluster == 0; cl >>= 1) {
+                    int mc = 0;
+                    if (fast::prepare_cluster(G.model, G.policy, cl, G.threads, &mc) == cudaSuccess && mc >= 1) {
+                        G.cluster = cl;
+                        G.grid = std::min(G.count, mc);   // clusters
+                    }
+                }
+                cudaGetLastError();   // clear a refused cluster size
+                if (G.cluster == 0 && o->solver == 6) { tmpc_destroy(h); return TMPC_ERR_UNSUPPORTED; }
+            }
+            if (G.cluster == 0) {
+                int per = 0;
+                e = fast::prepare(G.model, G.policy, G.smem, G.threads, &per);
+                if (e != cudaSuccess || per < 1) { set_err("fast::prepare", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
+                G.grid = std::max(1, std::min(G.count, per * h->nsm));
+            }
         } else {
             G.model = -1;
         }
@@ -545,6 +564,12 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
     ord.insert(ord.end(), bord.begin(), bord.end());
     e = cudaMemcpy(h->order, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { set_err("cudaMemcpy(order)", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
+    bool any_cluster = false;
+    for (int g = 0; g < h->n_groups; ++g) any_cluster = any_cluster || h->groups[g].cluster > 0;
+    if (any_cluster) {
+        e = cudaMalloc(&h->gflags, sizeof(int) * 4 * (size_t)d->batch);
+        if (e != cudaSuccess) { set_err("cudaMalloc(team flags)", e); tmpc_destroy(h); return TMPC_ERR_OOM; }
+    }
     if (fmax > 0) {
         h->fstride = (fmax + 31) & ~31LL;
         e = cudaMalloc(&h->fws, sizeof(float) * h->fstride * d->batch);
@@ -634,7 +659,10 @@ static tmpc_status launch_solve(tmpc_handle* h, const tmpc_params& p, const floa
     const KParams kp = to_kparams(p);
     for (int g = 0; g < h->n_groups; ++g) {
         const tmpc_handle::Group& G = h->groups[g];
-        if (G.model >= 0) {
+        if (G.model >= 0 && G.cluster > 0) {
+            TMPC_CUDA(fast::launch_cluster(G.model, G.policy, G.cluster, G.grid, G.threads, s, h->L, ko, kp, ks,
+                                           h->fws, h->fstride, h->order + G.offset, G.count, x0, warm, h->gflags));
+        } else if (G.model >= 0) {
             TMPC_CUDA(fast::launch(G.model, G.policy, G.grid, G.threads, G.smem, s, h->L, ko, kp, ks, h->fws, h->fstride,
                                    h->order + G.offset, G.count, h->queue + g, x0, warm));
         } else {
@@ -722,6 +750,7 @@ void tmpc_destroy(tmpc_handle* h) {
     if (h->order) cudaFree(h->order);
     if (h->stage) cudaFree(h->stage);
     if (h->fws) cudaFree(h->fws);
+    if (h->gflags) cudaFree(h->gflags);
     delete h;
 }
 

@@ -52,14 +52,14 @@ template <int M>
 __device__ __forceinline__ void form_S(const Inst<M>& c, float sigma, float rho_f, float rho_g) {
     constexpr int N = Inst<M>::N, NN = N * N, BS = Inst<M>::BS;
     const int T = c.T;
-    for (int e = threadIdx.x; e < T * NN; e += blockDim.x) {
+    for (int e = c.tid; e < T * NN; e += c.nth) {
         const int t = e / NN, ij = e % NN, i = ij / N, j = ij % N;
         float th, u;
         S_entries<M>(c, t, i, j, sigma, rho_f, rho_g, th, u);
         c.Dm[t * BS + Inst<M>::bx(i, j)] = th;
         c.Um[t * BS + Inst<M>::bx(i, j)] = u;
     }
-    __syncthreads();
+    c.sync();
 }
 
 // In-place inverse of the SPD N x N block at A (N <= 8) by a group of 8
@@ -114,10 +114,10 @@ __device__ __forceinline__ bool cr_factor(const Inst<M>& c, int* flag) {
     constexpr int N = Inst<M>::N, BS = Inst<M>::BS;
     const int T = c.T;
     auto bx = [](int i, int j) { return Inst<M>::bx(i, j); };
-    if (threadIdx.x == 0) *flag = 0;
-    __syncthreads();
-    const int lane_in_group = threadIdx.x % 8, group = threadIdx.x / 8, ngroups = blockDim.x / 8;
-    const unsigned gmask = 0xFFu << ((threadIdx.x % 32) / 8 * 8);
+    if (c.tid == 0) *flag = 0;
+    c.sync();
+    const int lane_in_group = c.tid % 8, group = c.tid / 8, ngroups = c.nth / 8;
+    const unsigned gmask = 0xFFu << ((c.tid % 32) / 8 * 8);
     for (int s = 1; s < T; s <<= 1) {
         const int s2 = s << 1;
         const int ne = (T - s + s2 - 1) / s2;   // eliminated: e = s + q s2 < T
@@ -125,9 +125,9 @@ __device__ __forceinline__ bool cr_factor(const Inst<M>& c, int* flag) {
         for (int q = group; q < ne; q += ngroups)
                 if (!group_spd_inverse<N>(c.Dm + (s + q * s2) * BS, lane_in_group, gmask) && lane_in_group == 0)
                     *flag = 1;
-        __syncthreads();
+        c.sync();
         // row i of Fa_e = U_{e-s} Dinv_e and of Fb_e = U_e' Dinv_e (U_e = S[e][e+s], 0 if e is last)
-        for (int w = threadIdx.x; w < ne * N; w += blockDim.x) {
+        for (int w = c.tid; w < ne * N; w += c.nth) {
             const int e = s + (w / N) * s2, i = w % N;
             const float* Ua = c.Um + (e - s) * BS;
             const float* Ue = c.Um + e * BS;
@@ -152,9 +152,9 @@ __device__ __forceinline__ bool cr_factor(const Inst<M>& c, int* flag) {
                 c.Fb[e * BS + bx(i, j)] = rb[j];
             }
         }
-        __syncthreads();
+        c.sync();
         // row i of D_i0 -= Fa_{i0+s} U_i0' + Fb_{i0-s} U_{i0-s}
-        for (int w = threadIdx.x; w < nsv * N; w += blockDim.x) {
+        for (int w = c.tid; w < nsv * N; w += c.nth) {
             const int i0 = (w / N) * s2, i = w % N;
             float row[N];
 #pragma unroll
@@ -182,9 +182,9 @@ __device__ __forceinline__ bool cr_factor(const Inst<M>& c, int* flag) {
 #pragma unroll
             for (int j = 0; j < N; ++j) c.Dm[i0 * BS + bx(i, j)] -= row[j];
         }
-        __syncthreads();
+        c.sync();
         // row i of the coupling of surviving i0 to i0 + 2s:  U_i0 = -Fa_{i0+s} U_{i0+s}
-        for (int w = threadIdx.x; w < nsv * N; w += blockDim.x) {
+        for (int w = c.tid; w < nsv * N; w += c.nth) {
             const int i0 = (w / N) * s2, i = w % N;
             float row[N];
 #pragma unroll
@@ -202,12 +202,12 @@ __device__ __forceinline__ bool cr_factor(const Inst<M>& c, int* flag) {
 #pragma unroll
             for (int j = 0; j < N; ++j) c.Um[i0 * BS + bx(i, j)] = row[j];
         }
-        __syncthreads();
+        c.sync();
     }
-    if (threadIdx.x < 8 && !group_spd_inverse<N>(c.Dm, threadIdx.x, 0xFFu) && threadIdx.x == 0) *flag = 1;
-    __syncthreads();
+    if (c.tid < 8 && !group_spd_inverse<N>(c.Dm, c.tid, 0xFFu) && c.tid == 0) *flag = 1;
+    c.sync();
     const bool ok = *flag == 0;
-    __syncthreads();
+    c.sync();
     return ok;
 }
 
@@ -248,16 +248,16 @@ __device__ __forceinline__ void top_inverse(const Inst<M>& c) {
     const int T = c.T, L = top_level(T), S0 = 1 << L, TD = c.TD;
     const int m = top_blocks(T) * N;
     float* X = c.Xt;
-    for (int e = threadIdx.x; e < m * TD; e += blockDim.x) {
+    for (int e = c.tid; e < m * TD; e += c.nth) {
         const int col = e / TD, row = e % TD;
         X[e] = (row == col) ? 1.f : 0.f;
     }
-    __syncthreads();
+    c.sync();
     int top = 1;
     while (top < T) top <<= 1;
     for (int s = S0; s < T; s <<= 1) {
         const int s2 = s << 1, nsv = (T + s2 - 1) / s2;
-        for (int w = threadIdx.x; w < nsv * m; w += blockDim.x) {
+        for (int w = c.tid; w < nsv * m; w += c.nth) {
             const int col = w / nsv, i0 = (w % nsv) * s2;
             float* x = X + col * TD;
             float acc[N];
@@ -283,9 +283,9 @@ __device__ __forceinline__ void top_inverse(const Inst<M>& c) {
 #pragma unroll
             for (int i = 0; i < N; ++i) r0[i] -= acc[i];
         }
-        __syncthreads();
+        c.sync();
     }
-    for (int col = threadIdx.x; col < m; col += blockDim.x) {
+    for (int col = c.tid; col < m; col += c.nth) {
         float* x = X + col * TD;
         float v[N];
 #pragma unroll
@@ -298,11 +298,11 @@ __device__ __forceinline__ void top_inverse(const Inst<M>& c) {
             x[i] = a;
         }
     }
-    __syncthreads();
+    c.sync();
     for (int s = top >> 1; s >= S0; s >>= 1) {
         if (s >= T) continue;
         const int s2 = s << 1, ne = (T - s + s2 - 1) / s2;
-        for (int w = threadIdx.x; w < ne * m; w += blockDim.x) {
+        for (int w = c.tid; w < ne * m; w += c.nth) {
             const int col = w / ne, e = s + (w % ne) * s2;
             float* x = X + col * TD;
             const float* D = c.Dm + e * BS;
@@ -328,7 +328,7 @@ __device__ __forceinline__ void top_inverse(const Inst<M>& c) {
 #pragma unroll
             for (int i = 0; i < N; ++i) re[i] = o[i];
         }
-        __syncthreads();
+        c.sync();
     }
 }
 
@@ -345,20 +345,20 @@ __device__ __forceinline__ void cr_solve(const Inst<M>& c, float* r, float* xo) 
     for (int l = 0; l < L; ++l) {
         const int s = 1 << l;
         const int nsv = (T + 2 * s - 1) >> (l + 1);     // survivors i0 = q 2s < T
-        for (int w = threadIdx.x; w < nsv * N; w += blockDim.x) {
+        for (int w = c.tid; w < nsv * N; w += c.nth) {
             const int i0 = (w / N) << (l + 1), i = w % N;
             float a = 0.f;
             if (i0 + s < T) a += rowdot<N>(c.Fa + (i0 + s) * BS, i, r + (i0 + s) * N);
             if (i0 >= s) a += rowdot<N>(c.Fb + (i0 - s) * BS, i, r + (i0 - s) * N);
             r[i0 * N + i] -= a;
         }
-        __syncthreads();
+        c.sync();
     }
     // survivors: x_R = M_R^-1 r_R (column col of Xt is M_R^-1 e_col); four lanes per
     // row, lane part p summing the columns q N + k with k = p (mod 4), reduced by shuffles
     {
         const int nR = m / N, ntask = 4 * m, nround = (ntask + 31) & ~31;
-        for (int w = threadIdx.x; w < nround; w += blockDim.x) {   // whole warps together
+        for (int w = c.tid; w < nround; w += c.nth) {   // whole warps together
             const int row = w >> 2, part = w & 3;
             float a = 0.f;
             if (w < ntask) {
@@ -376,17 +376,17 @@ __device__ __forceinline__ void cr_solve(const Inst<M>& c, float* r, float* xo) 
             if (w < ntask && part == 0) xo[((row / N) << L) * N + row % N] = a;
         }
     }
-    __syncthreads();
+    c.sync();
     for (int l = L - 1; l >= 0; --l) {
         const int s = 1 << l;
         const int ne = (T + s - 1) >> (l + 1);          // eliminated e = s + q 2s < T
-        for (int w = threadIdx.x; w < ne * N; w += blockDim.x) {
+        for (int w = c.tid; w < ne * N; w += c.nth) {
             const int e = s + ((w / N) << (l + 1)), i = w % N;
             float a = rowdot<N>(c.Dm + e * BS, i, r + e * N) - coldot<N>(c.Fa + e * BS, i, xo + (e - s) * N);
             if (e + s < T) a -= coldot<N>(c.Fb + e * BS, i, xo + (e + s) * N);
             xo[e * N + i] = a;
         }
-        __syncthreads();
+        c.sync();
     }
 }
 
@@ -401,10 +401,10 @@ template <int M>
 __device__ __forceinline__ bool ldl_factor_warp(const Inst<M>& c, float sigma, float rho_f, float rho_g, int* flag) {
     constexpr int N = Inst<M>::N, BS = Inst<M>::BS;
     const int T = c.T;
-    if (threadIdx.x == 0) *flag = 0;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x, i = lane >> 2, j0 = (lane & 3) * 2, j1 = j0 + 1;
+    if (c.tid == 0) *flag = 0;
+    c.sync();
+    if (c.tid < 32) {
+        const int lane = c.tid, i = lane >> 2, j0 = (lane & 3) * 2, j1 = j0 + 1;
         const bool v0 = i < N && j0 < N, v1 = i < N && j1 < N;
         bool ok = true;
         for (int t = 0; t < T; ++t) {
@@ -442,9 +442,9 @@ __device__ __forceinline__ bool ldl_factor_warp(const Inst<M>& c, float sigma, f
         }
         if (lane == 0 && !ok) *flag = 1;
     }
-    __syncthreads();
+    c.sync();
     const bool res = *flag == 0;
-    __syncthreads();
+    c.sync();
     return res;
 }
 
@@ -456,9 +456,9 @@ template <int M>
 __device__ __forceinline__ void ldl_solve_warp(const Inst<M>& c, float* r) {
     constexpr int N = Inst<M>::N, BS = Inst<M>::BS;
     const int T = c.T;
-    if (threadIdx.x < 32) {
+    if (c.tid < 32) {
         const unsigned full = 0xFFFFFFFFu;
-        const int lane = threadIdx.x, i = lane >> 2, h = lane & 3, j0 = 2 * h, j1 = j0 + 1;
+        const int lane = c.tid, i = lane >> 2, h = lane & 3, j0 = 2 * h, j1 = j0 + 1;
         const bool vi = i < N, v0 = j0 < N, v1 = j1 < N;
         float y0 = v0 ? r[j0] : 0.f, y1 = v1 ? r[j1] : 0.f;
         for (int t = 1; t < T; ++t) {
@@ -494,7 +494,7 @@ __device__ __forceinline__ void ldl_solve_warp(const Inst<M>& c, float* r) {
             x1 = __shfl_sync(full, p, 4 * j1);
         }
     }
-    __syncthreads();
+    c.sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -573,12 +573,12 @@ __device__ __forceinline__ void con_eval(const Inst<M>& c, const float* z, float
 template <int M>
 __device__ __forceinline__ void rollout(const Inst<M>& c, int newton_steps) {
     constexpr int N = Inst<M>::N, NX = Inst<M>::NX;
-    for (int e = threadIdx.x; e < c.T * N; e += blockDim.x) {
+    for (int e = c.tid; e < c.T * N; e += c.nth) {
         const int t = e / N, j = e % N;
         c.zb[e] = (j >= NX) ? c.refv(t, j) : (t == 0 ? c.x0[j] : 0.f);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    c.sync();
+    if (c.tid == 0) {
         for (int t = 0; t < c.Nh; ++t) {
             const float* z = c.zb + t * N;
             float xn[NX];
@@ -615,7 +615,7 @@ __device__ __forceinline__ void rollout(const Inst<M>& c, int newton_steps) {
             for (int k = 0; k < NX; ++k) c.zb[(t + 1) * N + k] = xn[k];
         }
     }
-    __syncthreads();
+    c.sync();
 }
 
 // QP approximation at zb in step coordinates (see tmpc_solver.cuh linearize)
@@ -625,7 +625,7 @@ __device__ __forceinline__ void linearize(const Inst<M>& c) {
     constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
     const int T = c.T;
     if constexpr (Tr::LTI) {  // double integrator, ZOH
-        if (threadIdx.x == 0) {
+        if (c.tid == 0) {
             const float dt = c.dyn[0];
             for (int i = 0; i < NX * N; ++i) c.Am[i] = 0.f;
             for (int k = 0; k < 4; ++k) c.Am[k * N + k] = 1.f;
@@ -634,7 +634,7 @@ __device__ __forceinline__ void linearize(const Inst<M>& c) {
             c.Am[2 * N + 4] = dt; c.Am[3 * N + 5] = dt;
         }
     }
-    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+    for (int t = c.tid; t < T; t += c.nth) {
         const float* z = c.zb + t * N;
         if (t < c.Nh) {
             float f[NX];
@@ -653,7 +653,7 @@ __device__ __forceinline__ void linearize(const Inst<M>& c) {
             c.ghi[t * NG + r] = c.hib(t, r) - g[r];
         }
     }
-    for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
+    for (int e = c.tid; e < T * N; e += c.nth) {
         const int t = e / N, j = e % N;
         float gr = c.Cw(t, j) * (c.zb[e] - c.refv(t, j)) + c.linv(t, j);
         float pd = c.Cw(t, j);
@@ -665,7 +665,7 @@ __device__ __forceinline__ void linearize(const Inst<M>& c) {
         c.qv[e] = gr;
         c.Pd[e] = pd;
     }
-    __syncthreads();
+    c.sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -680,9 +680,9 @@ __device__ __forceinline__ void admm_rowvec(const Inst<M>& c, float rho_bar) {
     constexpr int NX = Inst<M>::NX, NG = Inst<M>::NG;
     const int T = c.T;
     const float rho_f = 1e3f * rho_bar, rho_g = rho_bar;
-    for (int e = threadIdx.x; e < T * NX; e += blockDim.x) c.wf[e] = c.yf[e] + rho_f * c.pf[e];
-    for (int e = threadIdx.x; e < T * NG; e += blockDim.x) c.wg[e] = c.yg[e] + rho_g * c.pg[e];
-    __syncthreads();
+    for (int e = c.tid; e < T * NX; e += c.nth) c.wf[e] = c.yf[e] + rho_f * c.pf[e];
+    for (int e = c.tid; e < T * NG; e += c.nth) c.wg[e] = c.yg[e] + rho_g * c.pg[e];
+    c.sync();
 }
 
 // r = -(P x + q) - C' w_f - G' w_g;  S dx = r;  then one fused pass over the
@@ -695,7 +695,7 @@ __device__ __forceinline__ void admm_iter(const Inst<M>& c, float rho_bar, float
     constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
     const int T = c.T;
     const float rho_f = 1e3f * rho_bar, rho_g = rho_bar, inv_rho_g = 1.f / rho_bar;
-    for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
+    for (int e = c.tid; e < T * N; e += c.nth) {
         const int t = e / N, j = e % N;
         float s = -(c.Pv(c.x, t, j) + c.qv[e]);
         s -= c.Ctv(t, j, [&](int row, int k) { return c.wf[row * NX + k]; });
@@ -707,10 +707,10 @@ __device__ __forceinline__ void admm_iter(const Inst<M>& c, float rho_bar, float
         }
         c.r[e] = s;
     }
-    __syncthreads();
+    c.sync();
     if (P == kCR) cr_solve<M>(c, c.r, c.dx);
     else ldl_solve_warp<M>(c, c.r);   // dx shares r
-    for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
+    for (int e = c.tid; e < T * N; e += c.nth) {
         const int t = e / N, j = e % N;
         c.x[e] += alpha * c.dx[e];
         if (j < NX) {
@@ -738,7 +738,42 @@ __device__ __forceinline__ void admm_iter(const Inst<M>& c, float rho_bar, float
             c.wg[g] = yg + rho_g * pgn;
         }
     }
-    __syncthreads();
+    c.sync();
+}
+
+// ---------------------------------------------------------------------------
+// team reductions: the CTA reduction, then (cluster teams) one partial per CTA
+// through the global exchange area, the team barrier and a sum / max over CTAs
+// ---------------------------------------------------------------------------
+template <int M, int K>
+__device__ __forceinline__ void team_max_k(const Inst<M>& c, float (&v)[K], float* red) {
+    static_assert(K <= kXchDoubles, "exchange area");
+    cta_max_k<K>(v, red);
+    if (c.cl > 1) {
+        if (threadIdx.x == 0)
+            for (int k = 0; k < K; ++k) c.xch[c.rank * kXchDoubles + k] = (double)v[k];
+        c.sync();
+        for (int k = 0; k < K; ++k) {
+            float m = v[k];
+            for (int q = 0; q < c.cl; ++q) m = fmaxf(m, (float)c.xch[q * kXchDoubles + k]);
+            v[k] = m;
+        }
+        c.sync();
+    }
+}
+
+template <int M>
+__device__ __forceinline__ double team_sum_d(const Inst<M>& c, double v, double* redd) {
+    v = cta_sum_d(v, redd);
+    if (c.cl > 1) {
+        if (threadIdx.x == 0) c.xch[c.rank * kXchDoubles] = v;
+        c.sync();
+        double s = 0.0;
+        for (int q = 0; q < c.cl; ++q) s += c.xch[q * kXchDoubles];
+        v = s;
+        c.sync();
+    }
+    return v;
 }
 
 // residuals and normalisers (see tmpc_solver.cuh residuals)
@@ -747,12 +782,12 @@ __device__ __forceinline__ Res residuals(const Inst<M>& c, float* red) {
     constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
     const int T = c.T;
     float v[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int e = threadIdx.x; e < T * NX; e += blockDim.x) {
+    for (int e = c.tid; e < T * NX; e += c.nth) {
         const float cabs = c.cv[e] + c.Cx(c.zb, e / NX, e % NX);
         v[0] = fmaxf(v[0], fin(c.pf[e]));
         v[2] = fmaxf(v[2], fmaxf(fin(c.pf[e] + cabs), fin(cabs)));
     }
-    for (int e = threadIdx.x; e < T * NG; e += blockDim.x) {
+    for (int e = c.tid; e < T * NG; e += c.nth) {
         const int t = e / NG, r = e % NG;
         const float gx = c.Gx(c.x, t, r), gzb = c.Gx(c.zb, t, r);
         v[0] = fmaxf(v[0], fin(gx - c.zg[e]));
@@ -763,7 +798,7 @@ __device__ __forceinline__ Res residuals(const Inst<M>& c, float* red) {
             v[3] = fmaxf(v[3], fmaxf(fin(g2 * c.xi[e]), fin(c.yg[e])));
         }
     }
-    for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
+    for (int e = c.tid; e < T * N; e += c.nth) {
         const int t = e / N, j = e % N;
         const float px = c.Pv(c.x, t, j), pzb = c.Pv(c.zb, t, j);
         const float aty = c.Ctv(t, j, [&](int row, int k) { return c.yf[row * NX + k]; }) +
@@ -771,7 +806,7 @@ __device__ __forceinline__ Res residuals(const Inst<M>& c, float* red) {
         v[1] = fmaxf(v[1], fin(px + c.qv[e] + aty));
         v[3] = fmaxf(v[3], fmaxf(fmaxf(fin(px + pzb), fin(aty)), fin(c.qv[e] - pzb)));
     }
-    cta_max_k<4>(v, red);
+    team_max_k<M, 4>(c, v, red);
     return {v[0], v[1], v[2], v[3]};
 }
 
@@ -840,8 +875,8 @@ __device__ __forceinline__ float linesearch(const Inst<M>& c, const KOpts& o, co
     // scratch [(2k + q) T + t], q = 0 cost, 1 violation; scale at 2(K+1)T (factors are dead here)
     float* val = P == kCR ? c.Fa : c.Dm;
     double gd = 0.0;
-    for (int e = threadIdx.x; e < T * N; e += blockDim.x) gd += (double)(c.qv[e] * c.x[e]);
-    for (int e = threadIdx.x; e < T * NG; e += blockDim.x) {
+    for (int e = c.tid; e < T * N; e += c.nth) gd += (double)(c.qv[e] * c.x[e]);
+    for (int e = c.tid; e < T * NG; e += c.nth) {
         const int r = e % NG;
         const float g2 = c.gam2(r);
         if (g2 < kInf) {
@@ -849,8 +884,8 @@ __device__ __forceinline__ float linesearch(const Inst<M>& c, const KOpts& o, co
             gd += (double)(g2 * x0 * dx + c.gam1(r) * (x0 != 0.f ? (x0 > 0.f ? dx : -dx) : fabsf(dx)));
         }
     }
-    gd = cta_sum_d(gd, rs.redd);
-    for (int e = threadIdx.x; e < (K + 1) * T; e += blockDim.x) {
+    gd = team_sum_d<M>(c, gd, rs.redd);
+    for (int e = c.tid; e < (K + 1) * T; e += c.nth) {
         const int k = e / T, t = e % T;
         const float a = k == 0 ? 0.f : ldexpf(1.f, -(k - 1));
         float cs, vs, sc;
@@ -859,37 +894,39 @@ __device__ __forceinline__ float linesearch(const Inst<M>& c, const KOpts& o, co
         val[(2 * k + 1) * T + t] = vs;
         if (k == 0) val[2 * (K + 1) * T + t] = sc;
     }
-    __syncthreads();
-    for (int q = threadIdx.x; q < 2 * (K + 1) + 1; q += blockDim.x) {
+    c.sync();
+    // per-candidate sums (a cluster team publishes them through the exchange area)
+    double* acc = c.cl > 1 ? c.xch : rs.lsacc;
+    for (int q = c.tid; q < 2 * (K + 1) + 1; q += c.nth) {
         double sum = 0.0;
         for (int t = 0; t < T; ++t) sum += (double)val[q * T + t];
-        rs.lsacc[q] = sum;
+        acc[q] = sum;
     }
-    __syncthreads();
-    const double l0 = rs.lsacc[0], V0 = rs.lsacc[1];
+    c.sync();
+    const double l0 = acc[0], V0 = acc[1];
     const double mu = fmax(gd / (0.5 * fmax(V0, (double)o.eps_c)), (double)ystar_inf + 1e-4);
     const double phi0 = l0 + mu * V0;
     const double D = gd - mu * V0;
     // FP32 evaluation error of the merit: differences below it are ties, and a
     // tie satisfies the Armijo test (4 units of FP32 rounding on the magnitude
     // of every term that enters phi)
-    const double tau = 4.0 * 5.9604644775390625e-08 * rs.lsacc[2 * (K + 1)] * fmax(1.0, mu);
+    const double tau = 4.0 * 5.9604644775390625e-08 * acc[2 * (K + 1)] * fmax(1.0, mu);
     float chosen = -1.f, best = 0.f;
     double best_phi = INFINITY;
     for (int k = 1; k <= K; ++k) {
         const float a = ldexpf(1.f, -(k - 1));
-        const double ph = rs.lsacc[2 * k] + mu * rs.lsacc[2 * k + 1];
+        const double ph = acc[2 * k] + mu * acc[2 * k + 1];
         if (isfinite(ph) && ph <= phi0 + (double)o.ls_eta * a * D + tau) { chosen = a; break; }
     }
     if (chosen < 0.f) {
         for (int k = 1; k <= K; ++k) {
             const float a = ldexpf(1.f, -(k - 1));
-            const double ph = rs.lsacc[2 * k] + mu * rs.lsacc[2 * k + 1];
+            const double ph = acc[2 * k] + mu * acc[2 * k + 1];
             if (isfinite(ph) && ph < best_phi) { best_phi = ph; best = a; }
         }
         chosen = best;
     }
-    __syncthreads();
+    c.sync();
     return chosen;
 }
 
@@ -899,21 +936,21 @@ __device__ __forceinline__ float kkt(const Inst<M>& c, float* red) {
     constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
     const int T = c.T;
     float v[1] = {0.f};
-    for (int e = threadIdx.x; e < T * N; e += blockDim.x) {
+    for (int e = c.tid; e < T * N; e += c.nth) {
         const int t = e / N, j = e % N;
         const float gr = c.qv[e] + c.Ctv(t, j, [&](int row, int k) { return c.yfb[row * NX + k]; }) +
                          c.Gtw(t, j, [&](int r) { return c.ygb[t * NG + r]; });
         v[0] = fmaxf(v[0], fin(gr));
     }
-    for (int e = threadIdx.x; e < T * NX; e += blockDim.x) v[0] = fmaxf(v[0], fin(c.cv[e]));
-    for (int e = threadIdx.x; e < T * NG; e += blockDim.x) {
+    for (int e = c.tid; e < T * NX; e += c.nth) v[0] = fmaxf(v[0], fin(c.cv[e]));
+    for (int e = c.tid; e < T * NG; e += c.nth) {
         const int r = e % NG;
         const float g2 = c.gam2(r);
         if (g2 < kInf) v[0] = fmaxf(v[0], fin(slack_res(c.xib[e], c.ygb[e], g2, c.gam1(r))));
         // bound violation of g + xi:  g + xi - hi = xi - ghi,  lo - g - xi = glo - xi
         v[0] = fmaxf(v[0], fmaxf(c.xib[e] - c.ghi[e], c.glo[e] - c.xib[e]));
     }
-    cta_max_k<1>(v, red);
+    team_max_k<M, 1>(c, v, red);
     return v[0];
 }
 
@@ -934,7 +971,7 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
                                int inst, int warm) {
     constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
     const int T = c.T;
-    if (threadIdx.x == 0) rs.flags[0] = 0;
+    if (c.tid == 0) c.tflags[0] = 0;
     c.cache_params();
     const long long Ts = L.Nmax + 1;
     if (warm) {
@@ -942,18 +979,18 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
         const float* xi = out.xi + inst * Ts * L.ng;
         const float* yf = out.yf + inst * Ts * L.nx;
         const float* yg = out.yg + inst * Ts * L.ng;
-        for (int e = threadIdx.x; e < T * N; e += blockDim.x) c.zb[e] = z[(e / N) * L.n + e % N];
-        for (int e = threadIdx.x; e < T * NG; e += blockDim.x) {
+        for (int e = c.tid; e < T * N; e += c.nth) c.zb[e] = z[(e / N) * L.n + e % N];
+        for (int e = c.tid; e < T * NG; e += c.nth) {
             c.xib[e] = xi[(e / NG) * L.ng + e % NG];
             c.ygb[e] = yg[(e / NG) * L.ng + e % NG];
         }
-        for (int e = threadIdx.x; e < T * NX; e += blockDim.x) c.yfb[e] = yf[(e / NX) * L.nx + e % NX];
-        __syncthreads();
+        for (int e = c.tid; e < T * NX; e += c.nth) c.yfb[e] = yf[(e / NX) * L.nx + e % NX];
+        c.sync();
     } else {
         rollout<M>(c, o.newton_steps);
-        for (int e = threadIdx.x; e < T * NG; e += blockDim.x) { c.xib[e] = 0.f; c.ygb[e] = 0.f; }
-        for (int e = threadIdx.x; e < T * NX; e += blockDim.x) c.yfb[e] = 0.f;
-        __syncthreads();
+        for (int e = c.tid; e < T * NG; e += c.nth) { c.xib[e] = 0.f; c.ygb[e] = 0.f; }
+        for (int e = c.tid; e < T * NX; e += c.nth) c.yfb[e] = 0.f;
+        c.sync();
     }
     float rho = o.rho0, rp = 0.f, rd = 0.f, alpha_last = 1.f;
     int ls_hist[2] = {0, 0};   // line-search step codes, 4 bits per SQP iteration
@@ -964,16 +1001,16 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
             if (kkt<M>(c, rs.red) <= o.eps_c) break;
         }
         ++nfact;
-        if (!factor<M, P>(c, o, rho, rs.flags + 1) && threadIdx.x == 0) rs.flags[0] = 1;
-        for (int e = threadIdx.x; e < T * N; e += blockDim.x) c.x[e] = 0.f;
-        for (int e = threadIdx.x; e < T * NX; e += blockDim.x) { c.yf[e] = c.yfb[e]; c.pf[e] = -c.cv[e]; }
-        for (int e = threadIdx.x; e < T * NG; e += blockDim.x) {
+        if (!factor<M, P>(c, o, rho, c.tflags + 1) && c.tid == 0) c.tflags[0] = 1;
+        for (int e = c.tid; e < T * N; e += c.nth) c.x[e] = 0.f;
+        for (int e = c.tid; e < T * NX; e += c.nth) { c.yf[e] = c.yfb[e]; c.pf[e] = -c.cv[e]; }
+        for (int e = c.tid; e < T * NG; e += c.nth) {
             c.yg[e] = c.ygb[e];
             c.zg[e] = 0.f;
             c.xi[e] = 0.f;
             c.pg[e] = 0.f;   // G x - z_g at x = 0, z_g = 0
         }
-        __syncthreads();
+        c.sync();
         admm_rowvec<M>(c, rho);
         int k = 0;
         for (k = 1; k <= o.max_admm; ++k) {
@@ -991,12 +1028,12 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
                     const float cand = fminf(fmaxf(rho * sqrtf(ratio), o.rho_min), o.rho_max);
                     if (fmaxf(cand / rho, rho / cand) > o.k_rho_ratio) {
                         ++nfact;
-                        if (factor<M, P>(c, o, cand, rs.flags + 1)) {
+                        if (factor<M, P>(c, o, cand, c.tflags + 1)) {
                             rho = cand;
                             admm_rowvec<M>(c, rho);
                         } else {
                             ++nfact;
-                            if (!factor<M, P>(c, o, rho, rs.flags + 1) && threadIdx.x == 0) rs.flags[0] = 1;
+                            if (!factor<M, P>(c, o, rho, c.tflags + 1) && c.tid == 0) c.tflags[0] = 1;
                         }
                     }
                 }
@@ -1004,49 +1041,49 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
         }
         admm_total += (k > o.max_admm) ? o.max_admm : k;
         float ys[1] = {0.f};
-        for (int e = threadIdx.x; e < T * NX; e += blockDim.x) ys[0] = fmaxf(ys[0], fin(c.yf[e]));
-        for (int e = threadIdx.x; e < T * NG; e += blockDim.x) ys[0] = fmaxf(ys[0], fin(c.yg[e]));
-        cta_max_k<1>(ys, rs.red);
+        for (int e = c.tid; e < T * NX; e += c.nth) ys[0] = fmaxf(ys[0], fin(c.yf[e]));
+        for (int e = c.tid; e < T * NG; e += c.nth) ys[0] = fmaxf(ys[0], fin(c.yg[e]));
+        team_max_k<M, 1>(c, ys, rs.red);
         const float a = linesearch<M, P>(c, o, rs, ys[0]);
         alpha_last = a;
         if (it < 12) ls_hist[it / 6] |= ls_code(a) << (4 * (it % 6));
-        for (int e = threadIdx.x; e < T * N; e += blockDim.x) c.zb[e] += a * c.x[e];
-        for (int e = threadIdx.x; e < T * NG; e += blockDim.x) {
+        for (int e = c.tid; e < T * N; e += c.nth) c.zb[e] += a * c.x[e];
+        for (int e = c.tid; e < T * NG; e += c.nth) {
             c.xib[e] += a * (c.xi[e] - c.xib[e]);
             c.ygb[e] += a * (c.yg[e] - c.ygb[e]);
         }
-        for (int e = threadIdx.x; e < T * NX; e += blockDim.x) c.yfb[e] += a * (c.yf[e] - c.yfb[e]);
-        __syncthreads();
+        for (int e = c.tid; e < T * NX; e += c.nth) c.yfb[e] += a * (c.yf[e] - c.yfb[e]);
+        c.sync();
         ++sqp_done;
     }
     linearize<M>(c);
     const float kk = kkt<M>(c, rs.red);
     float bad[1] = {0.f};
-    for (int e = threadIdx.x; e < T * N; e += blockDim.x) bad[0] = fmaxf(bad[0], fin(c.zb[e]));
-    cta_max_k<1>(bad, rs.red);
+    for (int e = c.tid; e < T * N; e += c.nth) bad[0] = fmaxf(bad[0], fin(c.zb[e]));
+    team_max_k<M, 1>(c, bad, rs.red);
     // write the solution (padded layout, zeros beyond the horizon / model dims)
     float* z = out.z + inst * Ts * L.n;
     float* xo = out.xi + inst * Ts * L.ng;
     float* yfo = out.yf + inst * Ts * L.nx;
     float* ygo = out.yg + inst * Ts * L.ng;
-    for (int e = threadIdx.x; e < Ts * L.n; e += blockDim.x) {
+    for (int e = c.tid; e < Ts * L.n; e += c.nth) {
         const int t = e / L.n, j = e % L.n;
         z[e] = (t < T && j < N) ? c.zb[t * N + j] : 0.f;
     }
-    for (int e = threadIdx.x; e < Ts * L.ng; e += blockDim.x) {
+    for (int e = c.tid; e < Ts * L.ng; e += c.nth) {
         const int t = e / L.ng, r = e % L.ng;
         const bool ok = t < T && r < NG;
         xo[e] = ok ? c.xib[t * NG + r] : 0.f;
         ygo[e] = ok ? c.ygb[t * NG + r] : 0.f;
     }
-    for (int e = threadIdx.x; e < Ts * L.nx; e += blockDim.x) {
+    for (int e = c.tid; e < Ts * L.nx; e += c.nth) {
         const int t = e / L.nx, k = e % L.nx;
         yfo[e] = (t < T && k < NX) ? c.yfb[t * NX + k] : 0.f;
     }
-    if (threadIdx.x == 0) {
+    if (c.tid == 0) {
         int st = TMPC_INST_OK;
         if (!(bad[0] < kInf) || !(kk < kInf)) st = TMPC_INST_NAN;
-        else if (rs.flags[0]) st = TMPC_INST_NOT_PD;
+        else if (c.tflags[0]) st = TMPC_INST_NOT_PD;
         else if (!(kk <= o.eps_c)) st = TMPC_INST_MAX_ITER;
         if (out.status) out.status[inst] = st;
         if (out.stats) {
@@ -1056,11 +1093,39 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
             s[8] = (float)ls_hist[0]; s[9] = (float)ls_hist[1];
         }
     }
-    __syncthreads();
+    c.sync();
+}
+
+// instance i's parameter pointers and sizes
+template <int M>
+__device__ __forceinline__ void bind_instance(Inst<M>& c, const KLayout& L, const KParams& p, const float* x0, int i) {
+    c.Nh = p.N[i];
+    c.T = c.Nh + 1;
+    c.lnx = L.nx; c.lnu = L.nu; c.ln = L.n; c.lng = L.ng;
+    const long long Ts = L.Nmax + 1;
+    c.x0 = x0 + (long long)i * L.nx;
+    c.Qd = p.Qd + i * Ts * L.nx;
+    c.Rd = p.Rd + i * Ts * L.nu;
+    c.Wd = p.Wd ? p.Wd + (long long)i * L.nu : nullptr;
+    c.ref = p.ref ? p.ref + i * Ts * L.n : nullptr;
+    c.lin = p.lin ? p.lin + i * Ts * L.n : nullptr;
+    c.lo = p.lo + i * Ts * L.ng;
+    c.hi = p.hi + i * Ts * L.ng;
+    c.g2 = p.g2 ? p.g2 + (long long)i * L.ng : nullptr;
+    c.g1 = p.g1 ? p.g1 + (long long)i * L.ng : nullptr;
+    c.dyn = p.dyn + (long long)i * L.n_dyn;
+    c.track = p.track ? p.track + (long long)i * (L.n_track + 1) * 4 : nullptr;
+    c.nt = 0;
+    if (M == MODEL_BICYCLE) {
+        const float ntf = c.dyn[3];
+        int nt = (ntf == ntf) ? (int)fminf(fmaxf(ntf + 0.5f, 1.f), (float)L.n_track) : 1;
+        c.nt = nt < 1 ? 1 : nt;
+    }
 }
 
 // Persistent kernel over the instances listed in `order` (all of model M); an
-// instance whose arena does not fit `smem_floats` uses its global slot.
+// instance whose arena does not fit `smem_floats` uses its global slot.  The
+// team of an instance is the CTA.
 template <int M, int P>
 __global__ void __launch_bounds__(256, 2) solve_kernel(KLayout L, KOpts o, KParams p, KSol out, float* gws,
                                                     long long gstride, const int* order, int count,
@@ -1081,37 +1146,57 @@ __global__ void __launch_bounds__(256, 2) solve_kernel(KLayout L, KOpts o, KPara
         if (q >= count) break;
         const int i = order[q];
         Inst<M> c;
-        c.Nh = p.N[i];
-        c.T = c.Nh + 1;
-        c.lnx = L.nx; c.lnu = L.nu; c.ln = L.n; c.lng = L.ng;
-        const long long Ts = L.Nmax + 1;
-        c.x0 = x0 + (long long)i * L.nx;
-        c.Qd = p.Qd + i * Ts * L.nx;
-        c.Rd = p.Rd + i * Ts * L.nu;
-        c.Wd = p.Wd ? p.Wd + (long long)i * L.nu : nullptr;
-        c.ref = p.ref ? p.ref + i * Ts * L.n : nullptr;
-        c.lin = p.lin ? p.lin + i * Ts * L.n : nullptr;
-        c.lo = p.lo + i * Ts * L.ng;
-        c.hi = p.hi + i * Ts * L.ng;
-        c.g2 = p.g2 ? p.g2 + (long long)i * L.ng : nullptr;
-        c.g1 = p.g1 ? p.g1 + (long long)i * L.ng : nullptr;
-        c.dyn = p.dyn + (long long)i * L.n_dyn;
-        c.track = p.track ? p.track + (long long)i * (L.n_track + 1) * 4 : nullptr;
-        c.nt = 0;
-        if (M == MODEL_BICYCLE) {
-            const float ntf = c.dyn[3];
-            int nt = (ntf == ntf) ? (int)fminf(fmaxf(ntf + 0.5f, 1.f), (float)L.n_track) : 1;
-            c.nt = nt < 1 ? 1 : nt;
-        }
+        bind_instance<M>(c, L, p, x0, i);
+        c.tid = threadIdx.x;
+        c.nth = blockDim.x;
+        c.cl = 1;
+        c.rank = 0;
+        c.tflags = flags;
         const long long need = arena_floats<M>(c.T, P);
         c.carve(need <= smem_floats ? arena : gws + (long long)i * gstride, P);
         solve_instance<M, P>(c, o, rs, L, out, i, warm);
     }
 }
 
+// Cluster variant for long horizons on few instances: the team of an instance
+// is a thread-block cluster of `cl` CTAs (launched with that cluster size),
+// working on the instance's global-memory arena; cluster k takes the
+// instances order[k], order[k + clusters], ... so that every CTA of a cluster
+// follows the same control flow.  Team flags live in the instance's slot.
+template <int M, int P>
+__global__ void __launch_bounds__(256, 2) solve_kernel_cluster(KLayout L, KOpts o, KParams p, KSol out, float* gws,
+                                                            long long gstride, const int* order, int count,
+                                                            const float* x0, int warm, int* gflags) {
+    __shared__ float red[32 * 8];
+    __shared__ double redd[64];
+    __shared__ double lsacc[2 * (kMaxLs + 1) + 2];
+    __shared__ int flags[4];
+    const Red rs{red, redd, lsacc, flags};
+    unsigned rank, ncta, cid, ncl;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(ncta));
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cid));
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(ncl));
+    for (int q = (int)cid; q < count; q += (int)ncl) {
+        const int i = order[q];
+        Inst<M> c;
+        bind_instance<M>(c, L, p, x0, i);
+        c.tid = (int)rank * blockDim.x + threadIdx.x;
+        c.nth = (int)ncta * blockDim.x;
+        c.cl = (int)ncta;
+        c.rank = (int)rank;
+        c.tflags = gflags + 4LL * i;
+        c.carve(gws + (long long)i * gstride, P);
+        solve_instance<M, P>(c, o, rs, L, out, i, warm);
+        c.sync();   // the next instance reuses nothing of this one, but keep the CTAs in step
+    }
+}
+
 #define TMPC_INSTANTIATE(M, P)                                                                           \
     template __global__ void solve_kernel<M, P>(KLayout, KOpts, KParams, KSol, float*, long long, const int*, \
-                                                int, int*, const float*, int, long long);
+                                                int, int*, const float*, int, long long);                 \
+    template __global__ void solve_kernel_cluster<M, P>(KLayout, KOpts, KParams, KSol, float*, long long,     \
+                                                        const int*, int, const float*, int, int*);
 TMPC_INSTANTIATE(MODEL_DI, kCR)
 TMPC_INSTANTIATE(MODEL_BICYCLE, kCR)
 TMPC_INSTANTIATE(MODEL_QUAD, kCR)
@@ -1160,6 +1245,64 @@ cudaError_t prepare(int model, int policy, size_t smem_bytes, int threads, int* 
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem_bytes);
+}
+
+template <int P>
+static const void* cluster_kernel_of_p(int model) {
+    switch (model) {
+        case MODEL_DI: return (const void*)solve_kernel_cluster<MODEL_DI, P>;
+        case MODEL_BICYCLE: return (const void*)solve_kernel_cluster<MODEL_BICYCLE, P>;
+        case MODEL_QUAD: return (const void*)solve_kernel_cluster<MODEL_QUAD, P>;
+    }
+    return nullptr;
+}
+
+static const void* cluster_kernel_of(int model, int policy) {
+    return policy == kLDL ? cluster_kernel_of_p<kLDL>(model) : cluster_kernel_of_p<kCR>(model);
+}
+
+cudaError_t prepare_cluster(int model, int policy, int cl, int threads, int* max_clusters) {
+    const void* k = cluster_kernel_of(model, policy);
+    if (!k) return cudaErrorInvalidValue;
+    if (cl > 8) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cl);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(max_clusters, k, &cfg);
+}
+
+cudaError_t launch_cluster(int model, int policy, int cl, int nclusters, int threads, cudaStream_t s,
+                           const KLayout& L, const KOpts& o, const KParams& p, const KSol& out, float* gws,
+                           long long gstride, const int* order, int count, const float* x0, int warm,
+                           int* gflags) {
+    const void* k = cluster_kernel_of(model, policy);
+    if (!k) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cl * nclusters);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void* args[] = {(void*)&L, (void*)&o, (void*)&p, (void*)&out, (void*)&gws, (void*)&gstride, (void*)&order,
+                    (void*)&count, (void*)&x0, (void*)&warm, (void*)&gflags};
+    return cudaLaunchKernelExC(&cfg, k, args);
 }
 
 cudaError_t launch(int model, int policy, int grid, int threads, size_t smem_bytes, cudaStream_t s,

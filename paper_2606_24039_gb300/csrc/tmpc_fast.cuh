@@ -65,6 +65,8 @@ __host__ __device__ constexpr int top_blocks(int T) { return (T + (1 << top_leve
 //   kLDL sequential block LDL' (Riccati-like sweep over the stages) by one warp;
 //        half the factor storage, so more instances fit on an SM
 constexpr int kCR = 0, kLDL = 1;
+// largest team (CTAs of a cluster) and doubles exchanged per CTA in a team reduction
+constexpr int kTeamMax = 16, kXchDoubles = 40;
 
 // Per-instance arena: one list (name, floats) drives both the layout (carve)
 // and its size (arena_floats), so the two cannot disagree.
@@ -86,6 +88,7 @@ constexpr int kCR = 0, kLDL = 1;
     X(Fb, P == kCR ? (long long)T * BS : 0LL)                                     \
     X(Xt, P == kCR ? (long long)TD * TD : 0LL)                                    \
     X(Wk, P == kLDL ? 2LL * BS : 0LL)                                             \
+    X(Xc, 2LL * kTeamMax * kXchDoubles + 8)                                      \
     X(Am, (Traits<M>::LTI ? (long long)AMS : (long long)T * AMS))                \
     X(Grow, (Traits<M>::DENSE_ROW >= 0 ? (long long)T * N : 0LL))                \
     X(x, T * N) X(r, T * N) X(dx, P == kCR ? T * N : 0) X(qv, T * N)             \
@@ -119,8 +122,13 @@ struct Inst {
     __device__ static constexpr int bx(int i, int j) { return i * N + (N == 8 ? (j ^ (i & 4)) : j); }
     int Nh, T, nt;
     int lnx, lnu, ln, lng;
+    // the team of threads that works on the instance: one CTA (cl = 1) or the
+    // cl CTAs of a thread-block cluster; tid / nth index the whole team
+    int tid, nth, cl, rank;
+    int* tflags;    // team-visible flags (shared memory for one CTA, global for a cluster)
+    double* xch;    // exchange area of the team reductions (global, cluster teams only)
     const float *x0, *Qd, *Rd, *Wd, *ref, *lin, *lo, *hi, *g2, *g1, *dyn, *track;
-    float *Dm, *Um, *Fa, *Fb, *Xt, *Wk;
+    float *Dm, *Um, *Fa, *Fb, *Xt, *Wk, *Xc;
     int TD;     // leading dimension of Xt
     float *x, *r, *dx, *qv, *zb, *Pd;
     float *zg, *yg, *xi, *glo, *ghi, *xib, *ygb, *pg;
@@ -128,6 +136,15 @@ struct Inst {
     float *wf, *wg;  // right-hand-side row vectors y_f + rho_f p_f, y_g + rho_g p_g
     float *Am, *Grow, *par;  // par: W[NU], gamma2[NG], gamma1[NG] cached in the arena
 
+    // barrier of the team: the CTA barrier, or the cluster barrier with release /
+    // acquire ordering of the global-memory arena
+    __device__ __forceinline__ void sync() const {
+        if (cl > 1) {
+            asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+        } else {
+            __syncthreads();
+        }
+    }
     __device__ __forceinline__ void carve(float* p, int P) {
         const int T = this->T;
         TD = (top_blocks(T) * N + 3) & ~3;
@@ -135,10 +152,11 @@ struct Inst {
         TMPC_FAST_ARENA(TMPC_CARVE)
 #undef TMPC_CARVE
         if (P == kLDL) dx = r;   // the sweep solves in place
+        xch = reinterpret_cast<double*>(Xc);
     }
     // copy the per-instance weights used in the inner loop into the arena
     __device__ void cache_params() {
-        for (int k = threadIdx.x; k < NU + 2 * NG; k += blockDim.x) {
+        for (int k = tid; k < NU + 2 * NG; k += nth) {
             float v;
             if (k < NU) v = Wd ? Wd[k] : 0.f;
             else if (k < NU + NG) v = g2 ? g2[k - NU] : kInf;

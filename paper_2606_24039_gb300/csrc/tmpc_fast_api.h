@@ -20,5 +20,12 @@ cudaError_t launch(int model, int policy, int grid, int threads, size_t smem_byt
                    const KOpts& o, const KParams& p, const KSol& out, float* gws, long long gstride,
                    const int* order, int count, int* queue, const float* x0, int warm);
 
+// thread-block-cluster variant (one cluster of `cl` CTAs per instance, global arenas)
+cudaError_t prepare_cluster(int model, int policy, int cl, int threads, int* max_clusters);
+cudaError_t launch_cluster(int model, int policy, int cl, int nclusters, int threads, cudaStream_t s,
+                           const KLayout& L, const KOpts& o, const KParams& p, const KSol& out, float* gws,
+                           long long gstride, const int* order, int count, const float* x0, int warm,
+                           int* gflags);
+
 }  // namespace fast
 }  // namespace tmpc

@@ -259,7 +259,24 @@ def test_global_arenas_match_shared_arenas_bitwise(shared, glob):
         assert np.array_equal(a[k], b[k]), k
 
 
-@pytest.mark.parametrize("solver", SOLVERS)
+def test_cluster_team_matches_single_cta_bitwise_on_lq():
+    """One thread-block cluster per instance (solver 6) runs the cyclic
+    reduction of a single CTA with global arenas (solver 3) with the work of
+    every phase spread over the cluster: same arithmetic per entry, so equal
+    results on a problem without line search (maxima are order independent)."""
+    pb = w.double_integrator(B=3, N=900, max_admm=150)
+    pb.N[:] = [900, 517, 64]
+    for i in range(3):
+        N = int(pb.N[i])
+        pb.Qd[i, N, :] = 10 * pb.Qd[i, 0, :]
+    _, a, _ = _run(pb, solver=3)
+    _, b, _ = _run(pb, solver=6)
+    for k in ("z", "xi", "y_eq", "y_ineq", "status", "stats"):
+        assert np.array_equal(a[k], b[k]), k
+    _compare(pb, b, range(3))
+
+
+@pytest.mark.parametrize("solver", SOLVERS + [pytest.param(6, id="cluster_cr")])
 def test_long_racing_instances_one_sqp_step(solver):
     """Racing instances of 300 to 400 stages (global-memory arenas on the
     cyclic-reduction path) next to short ones: one SQP step whose QP is solved
