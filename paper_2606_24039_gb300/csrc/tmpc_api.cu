@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(256, 2) solve_kernel(KLayout L, KOpts o, KPara
 }
 
 __global__ void __launch_bounds__(256, 2) backward_kernel(KLayout L, KOpts o, KParams p, KSol sol, float* ws, WsOff off,
-                                const int* order, int* queue, const float* x0, const float* dLdz,
+                                const int* order, int count, int* queue, const float* x0, const float* dLdz,
                                 const float* dLdxi, KGrads g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(256, 2) backward_kernel(KLayout L, KOpts o, KP
         __syncthreads();
         const int q = s_item;
         __syncthreads();
-        if (q >= L.B) break;
+        if (q >= count) break;
         const int i = order[q];
         const Ctx c = make_ctx(L, p, ws, off, i, x0, sm.vs);
         backward_instance(c, o, sm, L, sol, i, dLdz, dLdxi, g);
@@ -340,8 +340,10 @@ struct tmpc_handle {
     struct Group {
         int model = -1, offset = 0, count = 0, grid = 0, threads = 0, policy = 0;
         int cluster = 0;   // > 0: CTAs per thread-block cluster (one cluster per instance)
+        int bgrid = 0;     // > 0: the group's backward runs on the shared-memory path with this grid
         size_t smem = 0;
     } groups[4];
+    int bwd_generic = 0;       // instances whose backward runs on the generic kernel
     int* gflags = nullptr;     // team flags of cluster-launched instances (4 per instance)
     int n_groups = 0;
     float* fws = nullptr;      // global arenas of the shared-memory path (instances that do not fit)
@@ -546,6 +548,7 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
                 }
                 cudaGetLastError();   // clear a refused cluster size
                 if (G.cluster == 0 && o->solver == 6) { tmpc_destroy(h); return TMPC_ERR_UNSUPPORTED; }
+                if (G.cluster > 0) fmax = std::max(fmax, fast::arena_floats_host(G.model, Tmax, G.policy, 1));
             }
             if (G.cluster == 0) {
                 int per = 0;
@@ -557,10 +560,25 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
             G.model = -1;
         }
     }
-    // backward: every instance, longest first
-    std::vector<int> bord(d->batch);
-    std::iota(bord.begin(), bord.end(), 0);
+    // backward: groups on the cyclic-reduction policy run the shared-memory
+    // backward over their forward order; every other instance (generic group,
+    // warp-LDL groups) the generic backward, longest first
+    std::vector<char> fastb(d->batch, 0);
+    for (int g = 0; g < h->n_groups; ++g) {
+        tmpc_handle::Group& G = h->groups[g];
+        if (G.model < 0 || G.policy != fast::kPolicyCR || o->solver == 1) continue;
+        int per = 0;
+        e = fast::prepare_backward(G.model, G.cluster, G.smem, G.threads, &per);
+        if (e != cudaSuccess || per < 1) { cudaGetLastError(); continue; }
+        G.bgrid = G.cluster > 0 ? G.grid : std::max(1, std::min(G.count, per * h->nsm));
+        for (int q = 0; q < G.count; ++q) fastb[ord[G.offset + q]] = 1;
+    }
+    std::vector<int> bord;
+    for (int i = 0; i < d->batch; ++i)
+        if (!fastb[i]) bord.push_back(i);
     std::stable_sort(bord.begin(), bord.end(), by_work);
+    h->bwd_generic = (int)bord.size();
+    bord.resize(d->batch, 0);
     ord.insert(ord.end(), bord.begin(), bord.end());
     e = cudaMemcpy(h->order, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { set_err("cudaMemcpy(order)", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
@@ -689,11 +707,21 @@ tmpc_status tmpc_backward(tmpc_handle* h, const float* x0, const tmpc_solution* 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     KSol ks{sol->z, sol->xi, sol->y_eq, sol->y_ineq, sol->status, sol->stats};
     KGrads kg{g->x0, g->Qd, g->Rd, g->Wd, g->ref, g->lin, g->lo, g->hi, g->gamma2, g->gamma1};
-    TMPC_CUDA(cudaMemsetAsync(h->queue + 4, 0, sizeof(int), s));
-    backward_kernel<<<h->grid_bwd, h->threads, h->smem, s>>>(h->L, to_kopts(h->o), to_kparams(h->p), ks, h->ws,
-                                                             h->off, h->order + h->d.batch, h->queue + 4, x0,
-                                                             dL_dz, dL_dxi, kg);
-    TMPC_CUDA(cudaGetLastError());
+    TMPC_CUDA(cudaMemsetAsync(h->queue, 0, sizeof(int) * 5, s));
+    const KOpts ko = to_kopts(h->o);
+    const KParams kp = to_kparams(h->p);
+    for (int gi = 0; gi < h->n_groups; ++gi) {
+        const tmpc_handle::Group& G = h->groups[gi];
+        if (G.bgrid <= 0) continue;
+        TMPC_CUDA(fast::launch_backward(G.model, G.cluster, G.bgrid, G.threads, G.smem, s, h->L, ko, kp, ks, h->fws,
+                                        h->fstride, h->order + G.offset, G.count, h->queue + gi, x0, h->gflags,
+                                        dL_dz, dL_dxi, kg));
+    }
+    if (h->bwd_generic > 0) {
+        backward_kernel<<<std::min(h->grid_bwd, h->bwd_generic), h->threads, h->smem, s>>>(
+            h->L, ko, kp, ks, h->ws, h->off, h->order + h->d.batch, h->bwd_generic, h->queue + 4, x0, dL_dz, dL_dxi, kg);
+        TMPC_CUDA(cudaGetLastError());
+    }
     return TMPC_OK;
 }
 

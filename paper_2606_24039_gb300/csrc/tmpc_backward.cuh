@@ -92,6 +92,11 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
         ok = factor(c, sm, o.bwd_sigma, rb, rb, true);
     }
     if (!ok && threadIdx.x == 0) sm.flags[0] = 1;
+    // divergence guard: the refinement contracts in exact arithmetic; if the
+    // steps grow (an FP32 factor of S_b too inaccurate for this rho_b), lower
+    // rho_b tenfold, refactor and restart (at most three times)
+    float d0 = 0.f, dprev = kInf;
+    int restarts = 0;
     for (int it = 0; it < o.bwd_iters; ++it) {
         for (int e = threadIdx.x; e < T * ng; e += blockDim.x) gz[e] = Gx_entry(c, ex, e / ng, e % ng);
         __syncthreads();
@@ -131,7 +136,31 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
             if (cd != 0.f && fabsf(cd) < 1.5f) mu[e] += rb * (Gx_entry(c, c.xt, e / ng, e % ng) - r3[e]);
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < T * n; e += blockDim.x) ex[e] += c.xt[e];
+        float dm[1] = {0.f};
+        for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
+            ex[e] += c.xt[e];
+            dm[0] = fmaxf(dm[0], fin(c.xt[e]));
+        }
+        cta_max_k<1>(dm, sm.red);
+        if (it == 0) d0 = dm[0];
+        const bool diverging = !(dm[0] < kInf) || (it >= 2 && dm[0] > 2.f * dprev && dm[0] > 1e-4f * d0);
+        if (diverging && restarts < 3) {
+            ++restarts;
+            rb *= 0.1f;
+            for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
+                if (code[e] != 0.f && fabsf(code[e]) < 1.5f) c.gw[e] = rb;
+                mu[e] = 0.f;
+            }
+            for (int e = threadIdx.x; e < T * nx; e += blockDim.x) lam[e] = 0.f;
+            for (int e = threadIdx.x; e < T * n; e += blockDim.x) ex[e] = 0.f;
+            __syncthreads();
+            if (!factor(c, sm, o.bwd_sigma, rb, rb, true) && threadIdx.x == 0) sm.flags[0] = 1;
+            d0 = 0.f;
+            dprev = kInf;
+            it = -1;
+            continue;
+        }
+        dprev = dm[0];
         __syncthreads();
     }
     for (int e = threadIdx.x; e < T * ng; e += blockDim.x) gz[e] = Gx_entry(c, ex, e / ng, e % ng);

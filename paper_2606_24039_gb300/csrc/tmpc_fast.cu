@@ -4,6 +4,7 @@
 #include "../../include/tmpc.h"
 #include "tmpc_fast.cuh"
 #include "tmpc_fast_api.h"
+#include "tmpc_backward.cuh"
 
 namespace tmpc {
 namespace fast {
@@ -16,7 +17,7 @@ namespace fast {
 // with Phi_t = E_t + rho_f A^+_t' A^-_t  (E_t = -W on the u block; U_t = 0 for t = N)
 template <int M>
 __device__ __forceinline__ void S_entries(const Inst<M>& c, int t, int i, int j, float sigma, float rho_f, float rho_g,
-                                          float& theta, float& u) {
+                                          float& theta, float& u, const float* gw = nullptr) {
     constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
     float s = 0.f;
     if (t < c.Nh) {
@@ -31,7 +32,7 @@ __device__ __forceinline__ void S_entries(const Inst<M>& c, int t, int i, int j,
     if (t == 0 && i == j && i < NX) s += 1.f;
     float v = rho_f * s;
 #pragma unroll
-    for (int r = 0; r < NG; ++r) v += rho_g * c.Gval(t, r, i) * c.Gval(t, r, j);
+    for (int r = 0; r < NG; ++r) v += (gw ? gw[t * NG + r] : rho_g) * c.Gval(t, r, i) * c.Gval(t, r, j);
     if (i == j) v += c.Pd[t * N + i] + sigma;
     theta = v;
     u = 0.f;
@@ -49,13 +50,14 @@ __device__ __forceinline__ void S_entries(const Inst<M>& c, int t, int i, int j,
 
 // Theta_t into Dm, U_t into Um, every stage
 template <int M>
-__device__ __forceinline__ void form_S(const Inst<M>& c, float sigma, float rho_f, float rho_g) {
+__device__ __forceinline__ void form_S(const Inst<M>& c, float sigma, float rho_f, float rho_g,
+                                       const float* gw = nullptr) {
     constexpr int N = Inst<M>::N, NN = N * N, BS = Inst<M>::BS;
     const int T = c.T;
     for (int e = c.tid; e < T * NN; e += c.nth) {
         const int t = e / NN, ij = e % NN, i = ij / N, j = ij % N;
         float th, u;
-        S_entries<M>(c, t, i, j, sigma, rho_f, rho_g, th, u);
+        S_entries<M>(c, t, i, j, sigma, rho_f, rho_g, th, u, gw);
         c.Dm[t * BS + Inst<M>::bx(i, j)] = th;
         c.Um[t * BS + Inst<M>::bx(i, j)] = u;
     }
@@ -1096,6 +1098,232 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
     c.sync();
 }
 
+// ---------------------------------------------------------------------------
+// Algorithm 2 for one instance (same method as tmpc_backward.cuh, here on the
+// team and arena of the shared-memory kernels; S_b is factored by the cyclic
+// reduction of the forward).  Arena reuse: code -> zg, w -> wg, rhs -> qv,
+// eta_x -> x, eta_f -> yf, eta_H -> yg, G eta_x -> xi, r2 -> pf, r3 -> pg.
+// ---------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ void backward_instance_team(Inst<M>& c, const KOpts& o, const Red& rs, const KLayout& L,
+                                                       const KSol& sol, int inst, const float* dLdz_all,
+                                                       const float* dLdxi_all, const KGrads& g) {
+    using Tr = Traits<M>;
+    constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NU = Inst<M>::NU, NG = Inst<M>::NG;
+    const int T = c.T;
+    const long long Ts = L.Nmax + 1;
+    const float* dLdz = dLdz_all + inst * Ts * L.n;
+    const float* dLdxi = dLdxi_all ? dLdxi_all + inst * Ts * L.ng : nullptr;
+    float rb = o.bwd_rho;
+    if (c.tid == 0) c.tflags[0] = 0;
+    c.cache_params();
+    // the solution is the point of the linearisation
+    {
+        const float* z = sol.z + inst * Ts * L.n;
+        const float* xi = sol.xi + inst * Ts * L.ng;
+        const float* yf = sol.yf + inst * Ts * L.nx;
+        const float* yg = sol.yg + inst * Ts * L.ng;
+        for (int e = c.tid; e < T * N; e += c.nth) c.zb[e] = z[(e / N) * L.n + e % N];
+        for (int e = c.tid; e < T * NG; e += c.nth) {
+            c.xib[e] = xi[(e / NG) * L.ng + e % NG];
+            c.ygb[e] = yg[(e / NG) * L.ng + e % NG];
+        }
+        for (int e = c.tid; e < T * NX; e += c.nth) c.yfb[e] = yf[(e / NX) * L.nx + e % NX];
+        c.sync();
+    }
+    linearize<M>(c);
+    float* code = c.zg;
+    float* gw = c.wg;
+    float* bx = c.qv;
+    float* ex = c.x;
+    float* lam = c.yf;
+    float* mu = c.yg;
+    float* gz = c.xi;
+    float* r2 = c.pf;
+    float* r3 = c.pg;
+    for (int e = c.tid; e < T * NG; e += c.nth) {
+        const int t = e / NG, r = e % NG;
+        // g + xi - lo = xi - glo and hi - g - xi = ghi - xi in the shifted bounds of the linearisation
+        const float lo = c.lob(t, r), hi = c.hib(t, r), y = c.ygb[e], xv = c.xib[e], eg = o.eps_g;
+        const float dlo = xv - c.glo[e], dhi = c.ghi[e] - xv;
+        const bool lower = (lo > -kInf) && ((y < -eg) || (fabsf(y) < eg && dlo <= eg * fmaxf(1.f, fabsf(lo))));
+        const bool upper = !lower && (hi < kInf) && ((y > eg) || (fabsf(y) < eg && dhi <= eg * fmaxf(1.f, fabsf(hi))));
+        float cd = 0.f;
+        if (lower || upper) {
+            const float side = upper ? 1.f : -1.f;
+            cd = (c.gam2(r) < kInf && fabsf(xv) > eg) ? 2.f * side : side;
+        }
+        code[e] = cd;
+        gw[e] = (cd == 0.f) ? 0.f : (fabsf(cd) > 1.5f ? c.gam2(r) : rb);
+        mu[e] = 0.f;
+    }
+    for (int e = c.tid; e < T * NX; e += c.nth) lam[e] = 0.f;
+    c.sync();
+    for (int e = c.tid; e < T * N; e += c.nth) {
+        const int t = e / N, j = e % N;
+        float b = dLdz[t * L.n + j];
+        if (dLdxi)
+#pragma unroll
+            for (int r = 0; r < NG; ++r)
+                if (fabsf(code[t * NG + r]) > 1.5f) b -= c.Gval(t, r, j) * dLdxi[t * L.ng + r];
+        bx[e] = b;
+        ex[e] = 0.f;
+    }
+    c.sync();
+    // S_b = H + sigma_b I + rho_b C'C + G' diag(w) G; FP32 safeguard: lower rho_b up to three times
+    form_S<M>(c, o.bwd_sigma, rb, rb, gw);
+    bool ok = cr_factor<M>(c, c.tflags + 1);
+    for (int tries = 0; !ok && tries < 3; ++tries) {
+        rb *= 0.1f;
+        for (int e = c.tid; e < T * NG; e += c.nth)
+            if (code[e] != 0.f && fabsf(code[e]) < 1.5f) gw[e] = rb;
+        c.sync();
+        form_S<M>(c, o.bwd_sigma, rb, rb, gw);
+        ok = cr_factor<M>(c, c.tflags + 1);
+    }
+    if (!ok && c.tid == 0) c.tflags[0] = 1;
+    top_inverse<M>(c);
+    // divergence guard (see tmpc_backward.cuh): growing steps lower rho_b and restart
+    float d0 = 0.f, dprev = kInf;
+    int restarts = 0;
+    for (int it = 0; it < o.bwd_iters; ++it) {
+        for (int e = c.tid; e < T * NG; e += c.nth) gz[e] = c.Gx(ex, e / NG, e % NG);
+        c.sync();
+        for (int e = c.tid; e < T * N; e += c.nth) {
+            const int t = e / N, j = e % N;
+            float sv = bx[e] - c.Pv(ex, t, j);
+            sv -= c.Ctv(t, j, [&](int row, int k) { return lam[row * NX + k]; });
+#pragma unroll
+            for (int r = 0; r < NG; ++r) {
+                const float cd = code[t * NG + r];
+                if (fabsf(cd) > 1.5f) sv -= c.gam2(r) * c.Gval(t, r, j) * gz[t * NG + r];
+                else if (cd != 0.f) sv -= c.Gval(t, r, j) * mu[t * NG + r];
+            }
+            c.r[e] = sv;
+        }
+        for (int e = c.tid; e < T * NX; e += c.nth) r2[e] = -c.Cx(ex, e / NX, e % NX);
+        for (int e = c.tid; e < T * NG; e += c.nth) {
+            const float cd = code[e];
+            r3[e] = (cd != 0.f && fabsf(cd) < 1.5f) ? -gz[e] : 0.f;
+        }
+        c.sync();
+        for (int e = c.tid; e < T * N; e += c.nth) {
+            const int t = e / N, j = e % N;
+            float sv = c.Ctv(t, j, [&](int row, int k) { return r2[row * NX + k]; });
+            sv += c.Gtw(t, j, [&](int r) { return r3[t * NG + r]; });
+            c.r[e] += rb * sv;
+        }
+        c.sync();
+        cr_solve<M>(c, c.r, c.dx);
+        for (int e = c.tid; e < T * NX; e += c.nth) lam[e] += rb * (c.Cx(c.dx, e / NX, e % NX) - r2[e]);
+        for (int e = c.tid; e < T * NG; e += c.nth) {
+            const float cd = code[e];
+            if (cd != 0.f && fabsf(cd) < 1.5f) mu[e] += rb * (c.Gx(c.dx, e / NG, e % NG) - r3[e]);
+        }
+        c.sync();
+        float dm[1] = {0.f};
+        for (int e = c.tid; e < T * N; e += c.nth) {
+            ex[e] += c.dx[e];
+            dm[0] = fmaxf(dm[0], fin(c.dx[e]));
+        }
+        team_max_k<M, 1>(c, dm, rs.red);
+        if (it == 0) d0 = dm[0];
+        const bool diverging = !(dm[0] < kInf) || (it >= 2 && dm[0] > 2.f * dprev && dm[0] > 1e-4f * d0);
+        if (diverging && restarts < 3) {
+            ++restarts;
+            rb *= 0.1f;
+            for (int e = c.tid; e < T * NG; e += c.nth) {
+                if (code[e] != 0.f && fabsf(code[e]) < 1.5f) gw[e] = rb;
+                mu[e] = 0.f;
+            }
+            for (int e = c.tid; e < T * NX; e += c.nth) lam[e] = 0.f;
+            for (int e = c.tid; e < T * N; e += c.nth) ex[e] = 0.f;
+            c.sync();
+            form_S<M>(c, o.bwd_sigma, rb, rb, gw);
+            if (!cr_factor<M>(c, c.tflags + 1) && c.tid == 0) c.tflags[0] = 1;
+            top_inverse<M>(c);
+            d0 = 0.f;
+            dprev = kInf;
+            it = -1;
+            continue;
+        }
+        dprev = dm[0];
+        c.sync();
+    }
+    for (int e = c.tid; e < T * NG; e += c.nth) gz[e] = c.Gx(ex, e / NG, e % NG);
+    c.sync();
+    // ---- vector-Jacobian product (Eq. loss_gradient) ----
+    const long long b = inst;
+    if (g.x0)
+        for (int k = c.tid; k < L.nx; k += c.nth) g.x0[b * L.nx + k] = k < NX ? lam[k] : 0.f;
+    for (int e = c.tid; e < Ts * L.n; e += c.nth) {
+        const int t = e / L.n, j = e % L.n;
+        const bool okk = t < T && j < N;
+        const float et = okk ? ex[t * N + j] : 0.f;
+        if (g.ref) g.ref[b * Ts * L.n + e] = okk ? c.Cw(t, j) * et : 0.f;
+        if (g.lin) g.lin[b * Ts * L.n + e] = -et;
+    }
+    for (int e = c.tid; e < Ts * L.nx; e += c.nth) {
+        const int t = e / L.nx, i = e % L.nx;
+        const bool okk = t < T && i < NX;
+        if (g.Qd) g.Qd[b * Ts * L.nx + e] = okk ? -ex[t * N + i] * (c.zb[t * N + i] - c.refv(t, i)) : 0.f;
+    }
+    for (int e = c.tid; e < Ts * L.nu; e += c.nth) {
+        const int t = e / L.nu, k = e % L.nu;
+        const bool okk = t < T && k < NU;
+        const int j = NX + k;
+        if (g.Rd) g.Rd[b * Ts * L.nu + e] = okk ? -ex[t * N + j] * (c.zb[t * N + j] - c.refv(t, j)) : 0.f;
+    }
+    for (int e = c.tid; e < Ts * L.ng; e += c.nth) {
+        const int t = e / L.ng, r = e % L.ng;
+        float glo = 0.f, ghi = 0.f;
+        if (t < T && r < NG) {
+            const int q = t * NG + r;
+            const float cd = code[q];
+            float eA = 0.f;
+            if (fabsf(cd) > 1.5f) eA = (dLdxi ? dLdxi[t * L.ng + r] : 0.f) + c.gam2(r) * gz[q];
+            else if (cd != 0.f) eA = mu[q];
+            if (cd > 0.f) ghi = eA;
+            if (cd < 0.f) glo = eA;
+        }
+        if (g.lo) g.lo[b * Ts * L.ng + e] = glo;
+        if (g.hi) g.hi[b * Ts * L.ng + e] = ghi;
+    }
+    if (g.Wd)
+        for (int k = 0; k < L.nu; ++k) {
+            double sw = 0.0;
+            if (k < NU)
+                for (int t = c.tid; t < c.Nh; t += c.nth) {
+                    const int j = NX + k;
+                    sw += (double)(ex[t * N + j] - ex[(t + 1) * N + j]) * (c.zb[t * N + j] - c.zb[(t + 1) * N + j]);
+                }
+            sw = team_sum_d<M>(c, sw, rs.redd);
+            if (c.tid == 0) g.Wd[b * L.nu + k] = (float)(-sw);
+        }
+    if (g.g2 || g.g1)
+        for (int r = 0; r < L.ng; ++r) {
+            double s2 = 0.0, s1 = 0.0;
+            if (r < NG)
+                for (int t = c.tid; t < T; t += c.nth) {
+                    const int q = t * NG + r;
+                    if (fabsf(code[q]) > 1.5f) {
+                        const float exi = -gz[q];
+                        const float xv = c.xib[q];
+                        s2 += (double)xv * exi;
+                        s1 += (double)(xv > 0.f ? 1.f : (xv < 0.f ? -1.f : 0.f)) * exi;
+                    }
+                }
+            s2 = team_sum_d<M>(c, s2, rs.redd);
+            s1 = team_sum_d<M>(c, s1, rs.redd);
+            if (c.tid == 0) {
+                if (g.g2) g.g2[b * L.ng + r] = (float)(-s2);
+                if (g.g1) g.g1[b * L.ng + r] = (float)(-s1);
+            }
+        }
+    if (c.tid == 0 && sol.status && c.tflags[0]) sol.status[inst] = TMPC_INST_NOT_PD;
+    c.sync();
+}
+
 // instance i's parameter pointers and sizes
 template <int M>
 __device__ __forceinline__ void bind_instance(Inst<M>& c, const KLayout& L, const KParams& p, const float* x0, int i) {
@@ -1186,9 +1414,73 @@ __global__ void __launch_bounds__(256, 2) solve_kernel_cluster(KLayout L, KOpts 
         c.cl = (int)ncta;
         c.rank = (int)rank;
         c.tflags = gflags + 4LL * i;
-        c.carve(gws + (long long)i * gstride, P);
+        c.carve(gws + (long long)i * gstride, P, 1);
         solve_instance<M, P>(c, o, rs, L, out, i, warm);
         c.sync();   // the next instance reuses nothing of this one, but keep the CTAs in step
+    }
+}
+
+// Backward kernels (Algorithm 2) of the shared-memory path: persistent CTA
+// teams over a work queue, and one thread-block cluster per instance.
+template <int M>
+__global__ void __launch_bounds__(256, 2) backward_kernel(KLayout L, KOpts o, KParams p, KSol sol, float* gws,
+                                                       long long gstride, const int* order, int count,
+                                                       int* queue, const float* x0, long long smem_floats,
+                                                       const float* dLdz, const float* dLdxi, KGrads g) {
+    extern __shared__ __align__(16) float arena[];
+    __shared__ float red[32 * 8];
+    __shared__ double redd[64];
+    __shared__ double lsacc[2 * (kMaxLs + 1) + 2];
+    __shared__ int flags[4];
+    __shared__ int s_item;
+    const Red rs{red, redd, lsacc, flags};
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int q = s_item;
+        __syncthreads();
+        if (q >= count) break;
+        const int i = order[q];
+        Inst<M> c;
+        bind_instance<M>(c, L, p, x0, i);
+        c.tid = threadIdx.x;
+        c.nth = blockDim.x;
+        c.cl = 1;
+        c.rank = 0;
+        c.tflags = flags;
+        const long long need = arena_floats<M>(c.T, kCR);
+        c.carve(need <= smem_floats ? arena : gws + (long long)i * gstride, kCR);
+        backward_instance_team<M>(c, o, rs, L, sol, i, dLdz, dLdxi, g);
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(256, 2) backward_kernel_cluster(KLayout L, KOpts o, KParams p, KSol sol, float* gws,
+                                                               long long gstride, const int* order, int count,
+                                                               const float* x0, int* gflags, const float* dLdz,
+                                                               const float* dLdxi, KGrads g) {
+    __shared__ float red[32 * 8];
+    __shared__ double redd[64];
+    __shared__ double lsacc[2 * (kMaxLs + 1) + 2];
+    __shared__ int flags[4];
+    const Red rs{red, redd, lsacc, flags};
+    unsigned rank, ncta, cid, ncl;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(ncta));
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cid));
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(ncl));
+    for (int q = (int)cid; q < count; q += (int)ncl) {
+        const int i = order[q];
+        Inst<M> c;
+        bind_instance<M>(c, L, p, x0, i);
+        c.tid = (int)rank * blockDim.x + threadIdx.x;
+        c.nth = (int)ncta * blockDim.x;
+        c.cl = (int)ncta;
+        c.rank = (int)rank;
+        c.tflags = gflags + 4LL * i;
+        c.carve(gws + (long long)i * gstride, kCR, 1);
+        backward_instance_team<M>(c, o, rs, L, sol, i, dLdz, dLdxi, g);
+        c.sync();
     }
 }
 
@@ -1200,6 +1492,22 @@ __global__ void __launch_bounds__(256, 2) solve_kernel_cluster(KLayout L, KOpts 
 TMPC_INSTANTIATE(MODEL_DI, kCR)
 TMPC_INSTANTIATE(MODEL_BICYCLE, kCR)
 TMPC_INSTANTIATE(MODEL_QUAD, kCR)
+template __global__ void backward_kernel<MODEL_DI>(KLayout, KOpts, KParams, KSol, float*, long long, const int*, int,
+                                                   int*, const float*, long long, const float*, const float*, KGrads);
+template __global__ void backward_kernel<MODEL_BICYCLE>(KLayout, KOpts, KParams, KSol, float*, long long, const int*,
+                                                        int, int*, const float*, long long, const float*,
+                                                        const float*, KGrads);
+template __global__ void backward_kernel<MODEL_QUAD>(KLayout, KOpts, KParams, KSol, float*, long long, const int*, int,
+                                                     int*, const float*, long long, const float*, const float*, KGrads);
+template __global__ void backward_kernel_cluster<MODEL_DI>(KLayout, KOpts, KParams, KSol, float*, long long,
+                                                           const int*, int, const float*, int*, const float*,
+                                                           const float*, KGrads);
+template __global__ void backward_kernel_cluster<MODEL_BICYCLE>(KLayout, KOpts, KParams, KSol, float*, long long,
+                                                                const int*, int, const float*, int*, const float*,
+                                                                const float*, KGrads);
+template __global__ void backward_kernel_cluster<MODEL_QUAD>(KLayout, KOpts, KParams, KSol, float*, long long,
+                                                             const int*, int, const float*, int*, const float*,
+                                                             const float*, KGrads);
 TMPC_INSTANTIATE(MODEL_DI, kLDL)
 TMPC_INSTANTIATE(MODEL_BICYCLE, kLDL)
 TMPC_INSTANTIATE(MODEL_QUAD, kLDL)
@@ -1214,11 +1522,12 @@ TMPC_INSTANTIATE(MODEL_QUAD, kLDL)
 namespace tmpc {
 namespace fast {
 
-long long arena_floats_host(int model, int T, int policy) {
+long long arena_floats_host(int model, int T, int policy, int cluster) {
+    const int cl = cluster ? 1 : 0;
     switch (model) {
-        case MODEL_DI: return arena_floats<MODEL_DI>(T, policy);
-        case MODEL_BICYCLE: return arena_floats<MODEL_BICYCLE>(T, policy);
-        case MODEL_QUAD: return arena_floats<MODEL_QUAD>(T, policy);
+        case MODEL_DI: return arena_floats<MODEL_DI>(T, policy, cl);
+        case MODEL_BICYCLE: return arena_floats<MODEL_BICYCLE>(T, policy, cl);
+        case MODEL_QUAD: return arena_floats<MODEL_QUAD>(T, policy, cl);
     }
     return -1;
 }
@@ -1303,6 +1612,61 @@ cudaError_t launch_cluster(int model, int policy, int cl, int nclusters, int thr
     void* args[] = {(void*)&L, (void*)&o, (void*)&p, (void*)&out, (void*)&gws, (void*)&gstride, (void*)&order,
                     (void*)&count, (void*)&x0, (void*)&warm, (void*)&gflags};
     return cudaLaunchKernelExC(&cfg, k, args);
+}
+
+static const void* bwd_kernel_of(int model, bool cluster) {
+    switch (model) {
+        case MODEL_DI: return cluster ? (const void*)backward_kernel_cluster<MODEL_DI> : (const void*)backward_kernel<MODEL_DI>;
+        case MODEL_BICYCLE:
+            return cluster ? (const void*)backward_kernel_cluster<MODEL_BICYCLE> : (const void*)backward_kernel<MODEL_BICYCLE>;
+        case MODEL_QUAD: return cluster ? (const void*)backward_kernel_cluster<MODEL_QUAD> : (const void*)backward_kernel<MODEL_QUAD>;
+    }
+    return nullptr;
+}
+
+cudaError_t prepare_backward(int model, int cl, size_t smem_bytes, int threads, int* per) {
+    const void* k = bwd_kernel_of(model, cl > 0);
+    if (!k) return cudaErrorInvalidValue;
+    if (cl > 0) {
+        if (cl > 8) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+        }
+        *per = 1;
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k, threads, smem_bytes);
+}
+
+cudaError_t launch_backward(int model, int cl, int grid, int threads, size_t smem_bytes, cudaStream_t s,
+                            const KLayout& L, const KOpts& o, const KParams& p, const KSol& sol, float* gws,
+                            long long gstride, const int* order, int count, int* queue, const float* x0,
+                            int* gflags, const float* dLdz, const float* dLdxi, const KGrads& g) {
+    const void* k = bwd_kernel_of(model, cl > 0);
+    if (!k) return cudaErrorInvalidValue;
+    if (cl > 0) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(cl * grid);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        void* args[] = {(void*)&L, (void*)&o, (void*)&p, (void*)&sol, (void*)&gws, (void*)&gstride, (void*)&order,
+                        (void*)&count, (void*)&x0, (void*)&gflags, (void*)&dLdz, (void*)&dLdxi, (void*)&g};
+        return cudaLaunchKernelExC(&cfg, k, args);
+    }
+    const long long sf = (long long)(smem_bytes / sizeof(float));
+    void* args[] = {(void*)&L, (void*)&o, (void*)&p, (void*)&sol, (void*)&gws, (void*)&gstride, (void*)&order,
+                    (void*)&count, (void*)&queue, (void*)&x0, (void*)&sf, (void*)&dLdz, (void*)&dLdxi, (void*)&g};
+    return cudaLaunchKernel(k, dim3(grid), dim3(threads), args, smem_bytes, s);
 }
 
 cudaError_t launch(int model, int policy, int grid, int threads, size_t smem_bytes, cudaStream_t s,

@@ -88,7 +88,7 @@ constexpr int kTeamMax = 16, kXchDoubles = 40;
     X(Fb, P == kCR ? (long long)T * BS : 0LL)                                     \
     X(Xt, P == kCR ? (long long)TD * TD : 0LL)                                    \
     X(Wk, P == kLDL ? 2LL * BS : 0LL)                                             \
-    X(Xc, 2LL * kTeamMax * kXchDoubles + 8)                                      \
+    X(Xc, CL ? 2LL * kTeamMax * kXchDoubles + 8 : 0LL)                          \
     X(Am, (Traits<M>::LTI ? (long long)AMS : (long long)T * AMS))                \
     X(Grow, (Traits<M>::DENSE_ROW >= 0 ? (long long)T * N : 0LL))                \
     X(x, T * N) X(r, T * N) X(dx, P == kCR ? T * N : 0) X(qv, T * N)             \
@@ -99,8 +99,9 @@ constexpr int kTeamMax = 16, kXchDoubles = 40;
     X(wf, T * NX) X(wg, T * NG)                                                  \
     X(par, 32)
 
+// CL: the arena of a cluster team (with the exchange area of its reductions)
 template <int M>
-__host__ __device__ constexpr long long arena_floats(int T, int P) {
+__host__ __device__ constexpr long long arena_floats(int T, int P, int CL = 0) {
     constexpr int NX = Traits<M>::NX, N = Traits<M>::NX + Traits<M>::NU, NG = Traits<M>::NG;
     constexpr int BS = N * N + 4, AMS = NX * N + 8;
     const int TD = (top_blocks(T) * N + 3) & ~3;
@@ -145,14 +146,14 @@ struct Inst {
             __syncthreads();
         }
     }
-    __device__ __forceinline__ void carve(float* p, int P) {
+    __device__ __forceinline__ void carve(float* p, int P, int CL = 0) {
         const int T = this->T;
         TD = (top_blocks(T) * N + 3) & ~3;
 #define TMPC_CARVE(name, cnt) name = p; p += (cnt);
         TMPC_FAST_ARENA(TMPC_CARVE)
 #undef TMPC_CARVE
         if (P == kLDL) dx = r;   // the sweep solves in place
-        xch = reinterpret_cast<double*>(Xc);
+        xch = CL ? reinterpret_cast<double*>(Xc) : nullptr;
     }
     // copy the per-instance weights used in the inner loop into the arena
     __device__ void cache_params() {

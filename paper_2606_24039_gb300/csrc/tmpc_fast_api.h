@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "tmpc_backward.cuh"
 #include "tmpc_solver.cuh"
 
 namespace tmpc {
@@ -10,7 +11,8 @@ namespace fast {
 // factorisation policies of the shared-memory kernels
 constexpr int kPolicyCR = 0, kPolicyLDL = 1;
 // floats of per-instance storage needed by the shared-memory path for T stages
-long long arena_floats_host(int model, int T, int policy);
+// (cluster != 0: the arena of a cluster team, with its exchange area)
+long long arena_floats_host(int model, int T, int policy, int cluster = 0);
 // models handled by the shared-memory path
 bool supported(int model);
 // set the dynamic shared-memory limit of the model's kernel and query its occupancy
@@ -26,6 +28,14 @@ cudaError_t launch_cluster(int model, int policy, int cl, int nclusters, int thr
                            const KLayout& L, const KOpts& o, const KParams& p, const KSol& out, float* gws,
                            long long gstride, const int* order, int count, const float* x0, int warm,
                            int* gflags);
+
+// backward kernels (Algorithm 2) of the shared-memory path, cyclic-reduction policy;
+// cl > 0: one cluster of cl CTAs per instance (grid = clusters)
+cudaError_t prepare_backward(int model, int cl, size_t smem_bytes, int threads, int* per);
+cudaError_t launch_backward(int model, int cl, int grid, int threads, size_t smem_bytes, cudaStream_t s,
+                            const KLayout& L, const KOpts& o, const KParams& p, const KSol& sol, float* gws,
+                            long long gstride, const int* order, int count, int* queue, const float* x0,
+                            int* gflags, const float* dLdz, const float* dLdxi, const KGrads& g);
 
 }  // namespace fast
 }  // namespace tmpc

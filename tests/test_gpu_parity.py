@@ -373,7 +373,8 @@ def test_backward_matches_oracle_on_oracle_solution(nx, nu):
     assert nact > 0
 
 
-def test_backward_soft_rows_match_oracle():
+@pytest.mark.parametrize("solver", [pytest.param(1, id="generic"), pytest.param(0, id="smem_cr")])
+def test_backward_soft_rows_match_oracle(solver):
     """L1+L2-softened rows: slack-active rows use the reduced system of
     Eq. (bwd:slack_reduced_system) and the gamma gradients of Appendix E.
     Initial states chosen so that the active-set KKT matrix is nonsingular."""
@@ -384,7 +385,7 @@ def test_backward_soft_rows_match_oracle():
     pb.Wd[:] = np.array([0.2, 0.1])
     opts = dataclasses.replace(pb.opts, early_exit=1, eps_abs=1e-11, eps_rel=1e-11)
     from paper_2606_24039_gb300 import Solver
-    s = Solver.from_batch(pb, device="cuda")
+    s = Solver.from_batch(pb, device="cuda", solver=solver)
     sol_np = {}
     refs = [osqp.solve(pb.instance(i), opts) for i in range(pb.B)]
     for k, kk in (("z", "z"), ("xi", "xi"), ("y_eq", "yf"), ("y_ineq", "yg")):
@@ -407,3 +408,32 @@ def test_backward_soft_rows_match_oracle():
         for k in keys:
             rel = _grad_rel(g[k][i].cpu().numpy().reshape(-1), gr[k].reshape(-1), 10.0 * scale)
             assert rel < GRAD_TOL, (i, k, rel)
+
+
+@pytest.mark.parametrize("solver", [pytest.param(1, id="generic"), pytest.param(0, id="smem_cr"),
+                                    pytest.param(6, id="cluster_cr")])
+def test_backward_racing_on_oracle_point(solver):
+    """Backward of the bicycle model (implicit midpoint Jacobians, the soft
+    track row, rate cost) at the oracle's SQP point: the linear algebra of
+    Algorithm 2 compared at the same point, on the shared-memory, cluster and
+    generic kernels."""
+    pb = w.racing(B=3, N=30, max_sqp=3, max_admm=200)
+    from paper_2606_24039_gb300 import Solver
+    s = Solver.from_batch(pb, device="cuda", solver=solver)
+    refs = [osqp.solve(pb.instance(i), pb.opts) for i in range(pb.B)]
+    sol = {}
+    for k, kk in (("z", "z"), ("xi", "xi"), ("y_eq", "yf"), ("y_ineq", "yg")):
+        sol[k] = torch.tensor(np.stack([r[kk] for r in refs]), dtype=torch.float32, device="cuda")
+    sol["status"] = torch.zeros(pb.B, dtype=torch.int32, device="cuda")
+    rng = np.random.default_rng(11)
+    dLdz = rng.normal(size=(pb.B, pb.N_max + 1, pb.n))
+    g = s.tmpc_backward(s.x0, sol, torch.tensor(dLdz, dtype=torch.float32, device="cuda"))
+    torch.cuda.synchronize()
+    keys = ("x0", "Qd", "Rd", "Wd", "ref", "lin", "lo", "hi", "gamma2", "gamma1")
+    for i in range(pb.B):
+        gr, info = obwd.backward(pb.instance(i), refs[i], dLdz[i], eps_g=pb.opts.eps_g)
+        if info["singular"]:
+            continue
+        a = np.concatenate([g[k][i].cpu().numpy().reshape(-1) for k in keys])
+        b = np.concatenate([gr[k].reshape(-1) for k in keys])
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < GRAD_TOL, (i, np.linalg.norm(a - b) / np.linalg.norm(b))
