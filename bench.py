@@ -88,6 +88,8 @@ def parse():
                     "4 warp-sequential LDL', 5 warp LDL' on global arenas")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the host-memory end-to-end timing")
     ap.add_argument("--threads", type=int, default=0, help="threads per instance (0 = library default)")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the plain per-phase form (one launch per phase, eager and as a CUDA graph)")
     return ap.parse_args()
 
 
@@ -433,6 +435,57 @@ def run_gpu(args):
     groups = n_launch_groups(pb, args.solver)
     launches = args.steps * groups + (0 if args.skip_bwd else args.steps * (groups + 1))
 
+    # the plain per-phase form of the same solve: one launch per phase, eager and
+    # captured as a CUDA graph (the baseline the persistent kernel is compared with)
+    plain = None
+    if not args.no_plain and args.workload in ("racing", "double_integrator", "uneven") and args.solver in (0, 2):
+        sp = Solver.from_batch(pb, device="cuda", solver=7, threads=args.threads)
+        solp = sp.alloc_solution("cuda")
+        side = torch.cuda.Stream()
+
+        def pstep():
+            if warm:
+                solp["z"].copy_(sp.z_init)
+                for k in ("xi", "y_eq", "y_ineq"):
+                    solp[k].zero_()
+            sp.tmpc_solve(sp.x0, solp, warm_start=warm)
+
+        for _ in range(2):
+            pstep()
+        torch.cuda.synchronize()
+        n_plain = max(2, min(args.steps, 5))
+
+        def time_fn(fn):
+            ts = []
+            for _ in range(n_plain):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                a, b = ev(), ev()
+                a.record(stream)
+                fn()
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            return float(np.mean(ts))
+
+        eager_ms = time_fn(pstep)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            pstep()
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=side):
+                pstep()
+        torch.cuda.synchronize()
+        graph_ms = time_fn(g.replay)
+        kp = solp["stats"][:, 6].cpu().numpy()
+        groups_p = n_launch_groups(pb, 2)
+        plain = {"eager_ms": eager_ms, "graph_ms": graph_ms, "persistent_ms": float(np.mean(t_fwd)),
+                 "launches_per_step": groups_p * (2 + pb.opts.max_sqp * (2 + pb.opts.max_admm)),
+                 "kkt_median": float(np.median(kp)), "kkt_median_persistent": float(np.median(kkt)),
+                 "speedup_vs_eager": eager_ms / float(np.mean(t_fwd)), "speedup_vs_graph": graph_ms / float(np.mean(t_fwd))}
+        del g
+        sp.close()
+
     # end to end through the host-memory entry point
     hp = {k: (v.cpu().pin_memory() if v is not None else None) for k, v in tensors_from_batch(pb, "cpu").items()}
     ho = {k: v.cpu().pin_memory() for k, v in s.alloc_solution("cpu").items()}
@@ -487,6 +540,7 @@ def run_gpu(args):
             "gpu_launches": launches,
             "roofline": roof,
             "cpu_baseline": cpu_base,
+            "plain_form": plain,
             "quality": {"kkt_median": float(np.median(kkt)), "kkt_p90": float(np.percentile(kkt, 90)),
                         "frac_kkt_le_1e-5": float(np.mean(kkt <= 1e-5)),
                         "status_counts": {str(k): int(v) for k, v in zip(*np.unique(status, return_counts=True))},

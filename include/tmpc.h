@@ -109,8 +109,12 @@ typedef struct {
                           * reduction (shared-memory arena per instance where it fits, else
                           * global), 3 as 2 with every arena in global memory, 4 sequential
                           * block LDL' swept by one warp (shared-memory arena), 5 as 4 with
-                          * every arena in global memory.  2-5 apply to the double
-                          * integrator, bicycle and quadrotor; other models use 1.        */
+                          * every arena in global memory, 6 block cyclic reduction by one
+                          * thread-block cluster per instance (long horizons, few
+                          * instances), 7 the plain per-phase form (one launch per ADMM
+                          * iteration and phase, state in global memory, fixed counts: a
+                          * measurement baseline).  2-7 apply to the double integrator,
+                          * bicycle and quadrotor; other models use 1.                    */
 } tmpc_options;
 
 /* Problem parameters theta (the OCP of Appendix A with the cost of Eq. (cost)).

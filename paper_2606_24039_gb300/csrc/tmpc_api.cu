@@ -341,10 +341,12 @@ struct tmpc_handle {
         int model = -1, offset = 0, count = 0, grid = 0, threads = 0, policy = 0;
         int cluster = 0;   // > 0: CTAs per thread-block cluster (one cluster per instance)
         int bgrid = 0;     // > 0: the group's backward runs on the shared-memory path with this grid
+        int plain = 0;     // 1: plain per-phase form (one launch per phase, solver 7)
         size_t smem = 0;
     } groups[4];
     int bwd_generic = 0;       // instances whose backward runs on the generic kernel
     int* gflags = nullptr;     // team flags of cluster-launched instances (4 per instance)
+    fast::PlainState* pstate = nullptr;   // per-instance state of the plain per-phase form
     int n_groups = 0;
     float* fws = nullptr;      // global arenas of the shared-memory path (instances that do not fit)
     long long fstride = 0;
@@ -404,7 +406,7 @@ static tmpc_status check_options(const tmpc_options* o) {
     if (o->max_sqp < 0 || o->max_admm < 1 || o->n_ls < 1 || o->n_ls > kMaxLs) return TMPC_ERR_INVALID_ARG;
     if (o->newton_steps < 0 || o->bwd_iters < 1 || !(o->bwd_rho > 0.f)) return TMPC_ERR_INVALID_ARG;
     if (o->threads < 0 || o->threads > 256 || (o->threads % 32) != 0) return TMPC_ERR_INVALID_ARG;
-    if (o->solver < 0 || o->solver > 6) return TMPC_ERR_INVALID_ARG;
+    if (o->solver < 0 || o->solver > 7) return TMPC_ERR_INVALID_ARG;
     return TMPC_OK;
 }
 
@@ -534,6 +536,11 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
             const long long cap = std::max(48LL * 1024, (long long)max_optin / 2 - 8 * 1024);
             G.smem = (size_t)std::min(need, need <= cap ? need : (long long)max_optin / 3);
             if (o->solver == 3 || o->solver == 5) G.smem = 0;   // every arena in global memory
+            if (o->solver == 7) {   // plain per-phase form: global arenas, one CTA per instance
+                G.plain = 1;
+                G.policy = fast::kPolicyCR;
+                G.smem = 0;
+            }
             // few instances whose arenas do not fit: one thread-block cluster per instance
             const bool few_long = o->solver == 0 && need > cap && (long long)G.count * 8 <= h->nsm;
             if (o->solver == 6 || few_long) {
@@ -550,7 +557,9 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
                 if (G.cluster == 0 && o->solver == 6) { tmpc_destroy(h); return TMPC_ERR_UNSUPPORTED; }
                 if (G.cluster > 0) fmax = std::max(fmax, fast::arena_floats_host(G.model, Tmax, G.policy, 1));
             }
-            if (G.cluster == 0) {
+            if (G.plain) {
+                G.grid = G.count;
+            } else if (G.cluster == 0) {
                 int per = 0;
                 e = fast::prepare(G.model, G.policy, G.smem, G.threads, &per);
                 if (e != cudaSuccess || per < 1) { set_err("fast::prepare", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
@@ -582,6 +591,12 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
     ord.insert(ord.end(), bord.begin(), bord.end());
     e = cudaMemcpy(h->order, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { set_err("cudaMemcpy(order)", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
+    bool any_plain = false;
+    for (int g = 0; g < h->n_groups; ++g) any_plain = any_plain || h->groups[g].plain;
+    if (any_plain) {
+        e = cudaMalloc(&h->pstate, sizeof(fast::PlainState) * (size_t)d->batch);
+        if (e != cudaSuccess) { set_err("cudaMalloc(plain state)", e); tmpc_destroy(h); return TMPC_ERR_OOM; }
+    }
     bool any_cluster = false;
     for (int g = 0; g < h->n_groups; ++g) any_cluster = any_cluster || h->groups[g].cluster > 0;
     if (any_cluster) {
@@ -677,7 +692,10 @@ static tmpc_status launch_solve(tmpc_handle* h, const tmpc_params& p, const floa
     const KParams kp = to_kparams(p);
     for (int g = 0; g < h->n_groups; ++g) {
         const tmpc_handle::Group& G = h->groups[g];
-        if (G.model >= 0 && G.cluster > 0) {
+        if (G.model >= 0 && G.plain) {
+            TMPC_CUDA(fast::launch_plain(G.model, G.threads, s, h->L, ko, kp, ks, h->fws, h->fstride,
+                                         h->order + G.offset, G.count, x0, warm, h->pstate));
+        } else if (G.model >= 0 && G.cluster > 0) {
             TMPC_CUDA(fast::launch_cluster(G.model, G.policy, G.cluster, G.grid, G.threads, s, h->L, ko, kp, ks,
                                            h->fws, h->fstride, h->order + G.offset, G.count, x0, warm, h->gflags));
         } else if (G.model >= 0) {
@@ -779,6 +797,7 @@ void tmpc_destroy(tmpc_handle* h) {
     if (h->stage) cudaFree(h->stage);
     if (h->fws) cudaFree(h->fws);
     if (h->gflags) cudaFree(h->gflags);
+    if (h->pstate) cudaFree(h->pstate);
     delete h;
 }
 

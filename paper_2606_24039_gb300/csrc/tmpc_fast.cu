@@ -1484,6 +1484,211 @@ __global__ void __launch_bounds__(256, 2) backward_kernel_cluster(KLayout L, KOp
     }
 }
 
+// ---------------------------------------------------------------------------
+// Plain per-phase form (a measurement baseline, solver 7): the same device
+// code as solve_instance, cut into one launch per phase (initial guess, SQP
+// step start, each ADMM iteration, SQP step end, final) with one CTA per
+// instance, the state in the instance's global arena and PlainState, and the
+// loop on the host.  Fixed iteration counts (early exit is not supported).
+// ---------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ bool plain_bind(Inst<M>& c, const KLayout& L, const KParams& p, float* gws, long long gstride,
+                                           const int* order, int count, const float* x0, PlainState* ps, int& i) {
+    if ((int)blockIdx.x >= count) return false;
+    i = order[blockIdx.x];
+    bind_instance<M>(c, L, p, x0, i);
+    c.tid = threadIdx.x;
+    c.nth = blockDim.x;
+    c.cl = 1;
+    c.rank = 0;
+    c.tflags = ps[i].flags;
+    c.carve(gws + (long long)i * gstride, kCR);
+    return true;
+}
+
+template <int M>
+__global__ void __launch_bounds__(256, 2) plain_init(KLayout L, KOpts o, KParams p, KSol out, float* gws, long long gstride,
+                                                  const int* order, int count, const float* x0, int warm, PlainState* ps) {
+    constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
+    Inst<M> c;
+    int i;
+    if (!plain_bind<M>(c, L, p, gws, gstride, order, count, x0, ps, i)) return;
+    const int T = c.T;
+    if (c.tid == 0) {
+        c.tflags[0] = 0;
+        PlainState& st = ps[i];
+        st.rho = o.rho0; st.rp = 0.f; st.rd = 0.f; st.alpha_last = 1.f;
+        st.admm_total = 0; st.nfact = 0; st.sqp_done = 0; st.ls_hist[0] = 0; st.ls_hist[1] = 0;
+    }
+    c.cache_params();
+    const long long Ts = L.Nmax + 1;
+    if (warm) {
+        const float* z = out.z + i * Ts * L.n;
+        const float* xi = out.xi + i * Ts * L.ng;
+        const float* yf = out.yf + i * Ts * L.nx;
+        const float* yg = out.yg + i * Ts * L.ng;
+        for (int e = c.tid; e < T * N; e += c.nth) c.zb[e] = z[(e / N) * L.n + e % N];
+        for (int e = c.tid; e < T * NG; e += c.nth) {
+            c.xib[e] = xi[(e / NG) * L.ng + e % NG];
+            c.ygb[e] = yg[(e / NG) * L.ng + e % NG];
+        }
+        for (int e = c.tid; e < T * NX; e += c.nth) c.yfb[e] = yf[(e / NX) * L.nx + e % NX];
+        c.sync();
+    } else {
+        rollout<M>(c, o.newton_steps);
+        for (int e = c.tid; e < T * NG; e += c.nth) { c.xib[e] = 0.f; c.ygb[e] = 0.f; }
+        for (int e = c.tid; e < T * NX; e += c.nth) c.yfb[e] = 0.f;
+        c.sync();
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(256, 2) plain_sqp_begin(KLayout L, KOpts o, KParams p, float* gws, long long gstride,
+                                                       const int* order, int count, const float* x0, PlainState* ps) {
+    constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
+    Inst<M> c;
+    int i;
+    if (!plain_bind<M>(c, L, p, gws, gstride, order, count, x0, ps, i)) return;
+    const int T = c.T;
+    const float rho = ps[i].rho;
+    linearize<M>(c);
+    if (!factor<M, kCR>(c, o, rho, c.tflags + 1) && c.tid == 0) c.tflags[0] = 1;
+    for (int e = c.tid; e < T * N; e += c.nth) c.x[e] = 0.f;
+    for (int e = c.tid; e < T * NX; e += c.nth) { c.yf[e] = c.yfb[e]; c.pf[e] = -c.cv[e]; }
+    for (int e = c.tid; e < T * NG; e += c.nth) {
+        c.yg[e] = c.ygb[e];
+        c.zg[e] = 0.f;
+        c.xi[e] = 0.f;
+        c.pg[e] = 0.f;
+    }
+    c.sync();
+    admm_rowvec<M>(c, rho);
+    if (c.tid == 0) ps[i].nfact += 1;
+}
+
+template <int M>
+__global__ void __launch_bounds__(256, 2) plain_admm(KLayout L, KOpts o, KParams p, float* gws, long long gstride,
+                                                  const int* order, int count, const float* x0, PlainState* ps, int k) {
+    Inst<M> c;
+    int i;
+    if (!plain_bind<M>(c, L, p, gws, gstride, order, count, x0, ps, i)) return;
+    __shared__ float red[32 * 8];
+    float rho = ps[i].rho;
+    int nf = 0;
+    admm_iter<M, kCR>(c, rho, o.alpha);
+    const bool cr = (k % o.k_rho_iter == 0) && k < o.max_admm;
+    if (cr || k == o.max_admm) {
+        const Res r = residuals<M>(c, red);
+        const float rp = r.r_prim, rd = r.r_dual;
+        const bool conv = rp <= o.eps_abs + o.eps_rel * r.pn && rd <= o.eps_abs + o.eps_rel * r.dn;
+        if (cr && rd > 0.f && !conv) {
+            const float ratio = (rp / fmaxf(r.pn, 1e-30f)) / fmaxf(rd / fmaxf(r.dn, 1e-30f), 1e-30f);
+            const float cand = fminf(fmaxf(rho * sqrtf(ratio), o.rho_min), o.rho_max);
+            if (fmaxf(cand / rho, rho / cand) > o.k_rho_ratio) {
+                ++nf;
+                if (factor<M, kCR>(c, o, cand, c.tflags + 1)) {
+                    rho = cand;
+                    admm_rowvec<M>(c, rho);
+                } else {
+                    ++nf;
+                    if (!factor<M, kCR>(c, o, rho, c.tflags + 1) && c.tid == 0) c.tflags[0] = 1;
+                }
+            }
+        }
+        if (c.tid == 0) {
+            ps[i].rp = rp;
+            ps[i].rd = rd;
+        }
+    }
+    if (c.tid == 0) {
+        ps[i].rho = rho;
+        ps[i].nfact += nf;
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(256, 2) plain_sqp_end(KLayout L, KOpts o, KParams p, float* gws, long long gstride,
+                                                     const int* order, int count, const float* x0, PlainState* ps, int it) {
+    constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
+    Inst<M> c;
+    int i;
+    if (!plain_bind<M>(c, L, p, gws, gstride, order, count, x0, ps, i)) return;
+    __shared__ float red[32 * 8];
+    __shared__ double redd[64];
+    __shared__ double lsacc[2 * (kMaxLs + 1) + 2];
+    const Red rs{red, redd, lsacc, nullptr};
+    const int T = c.T;
+    float ys[1] = {0.f};
+    for (int e = c.tid; e < T * NX; e += c.nth) ys[0] = fmaxf(ys[0], fin(c.yf[e]));
+    for (int e = c.tid; e < T * NG; e += c.nth) ys[0] = fmaxf(ys[0], fin(c.yg[e]));
+    team_max_k<M, 1>(c, ys, rs.red);
+    const float a = linesearch<M, kCR>(c, o, rs, ys[0]);
+    for (int e = c.tid; e < T * N; e += c.nth) c.zb[e] += a * c.x[e];
+    for (int e = c.tid; e < T * NG; e += c.nth) {
+        c.xib[e] += a * (c.xi[e] - c.xib[e]);
+        c.ygb[e] += a * (c.yg[e] - c.ygb[e]);
+    }
+    for (int e = c.tid; e < T * NX; e += c.nth) c.yfb[e] += a * (c.yf[e] - c.yfb[e]);
+    c.sync();
+    if (c.tid == 0) {
+        PlainState& st = ps[i];
+        st.admm_total += o.max_admm;
+        st.alpha_last = a;
+        if (it < 12) st.ls_hist[it / 6] |= ls_code(a) << (4 * (it % 6));
+        st.sqp_done += 1;
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(256, 2) plain_final(KLayout L, KOpts o, KParams p, KSol out, float* gws,
+                                                   long long gstride, const int* order, int count, const float* x0,
+                                                   PlainState* ps) {
+    constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
+    Inst<M> c;
+    int i;
+    if (!plain_bind<M>(c, L, p, gws, gstride, order, count, x0, ps, i)) return;
+    __shared__ float red[32 * 8];
+    const int T = c.T;
+    linearize<M>(c);
+    const float kk = kkt<M>(c, red);
+    float bad[1] = {0.f};
+    for (int e = c.tid; e < T * N; e += c.nth) bad[0] = fmaxf(bad[0], fin(c.zb[e]));
+    team_max_k<M, 1>(c, bad, red);
+    const long long Ts = L.Nmax + 1;
+    float* z = out.z + i * Ts * L.n;
+    float* xo = out.xi + i * Ts * L.ng;
+    float* yfo = out.yf + i * Ts * L.nx;
+    float* ygo = out.yg + i * Ts * L.ng;
+    for (int e = c.tid; e < Ts * L.n; e += c.nth) {
+        const int t = e / L.n, j = e % L.n;
+        z[e] = (t < T && j < N) ? c.zb[t * N + j] : 0.f;
+    }
+    for (int e = c.tid; e < Ts * L.ng; e += c.nth) {
+        const int t = e / L.ng, r = e % L.ng;
+        const bool ok = t < T && r < NG;
+        xo[e] = ok ? c.xib[t * NG + r] : 0.f;
+        ygo[e] = ok ? c.ygb[t * NG + r] : 0.f;
+    }
+    for (int e = c.tid; e < Ts * L.nx; e += c.nth) {
+        const int t = e / L.nx, k = e % L.nx;
+        yfo[e] = (t < T && k < NX) ? c.yfb[t * NX + k] : 0.f;
+    }
+    if (c.tid == 0) {
+        const PlainState& st = ps[i];
+        int sts = TMPC_INST_OK;
+        if (!(bad[0] < kInf) || !(kk < kInf)) sts = TMPC_INST_NAN;
+        else if (c.tflags[0]) sts = TMPC_INST_NOT_PD;
+        else if (!(kk <= o.eps_c)) sts = TMPC_INST_MAX_ITER;
+        if (out.status) out.status[i] = sts;
+        if (out.stats) {
+            float* s = out.stats + (long long)i * TMPC_STATS;
+            s[0] = (float)st.sqp_done; s[1] = (float)st.admm_total; s[2] = st.rp; s[3] = st.rd;
+            s[4] = st.rho; s[5] = (float)st.nfact; s[6] = kk; s[7] = st.alpha_last;
+            s[8] = (float)st.ls_hist[0]; s[9] = (float)st.ls_hist[1];
+        }
+    }
+}
+
 #define TMPC_INSTANTIATE(M, P)                                                                           \
     template __global__ void solve_kernel<M, P>(KLayout, KOpts, KParams, KSol, float*, long long, const int*, \
                                                 int, int*, const float*, int, long long);                 \
@@ -1668,6 +1873,36 @@ cudaError_t launch_backward(int model, int cl, int grid, int threads, size_t sme
                     (void*)&count, (void*)&queue, (void*)&x0, (void*)&sf, (void*)&dLdz, (void*)&dLdxi, (void*)&g};
     return cudaLaunchKernel(k, dim3(grid), dim3(threads), args, smem_bytes, s);
 }
+
+template <int M>
+static cudaError_t launch_plain_m(int threads, cudaStream_t s, const KLayout& L, const KOpts& o, const KParams& p,
+                                  const KSol& out, float* gws, long long gstride, const int* order, int count,
+                                  const float* x0, int warm, PlainState* ps) {
+    const dim3 g(count), b(threads);
+    plain_init<M><<<g, b, 0, s>>>(L, o, p, out, gws, gstride, order, count, x0, warm, ps);
+    for (int it = 0; it < o.max_sqp; ++it) {
+        plain_sqp_begin<M><<<g, b, 0, s>>>(L, o, p, gws, gstride, order, count, x0, ps);
+        for (int k = 1; k <= o.max_admm; ++k)
+            plain_admm<M><<<g, b, 0, s>>>(L, o, p, gws, gstride, order, count, x0, ps, k);
+        plain_sqp_end<M><<<g, b, 0, s>>>(L, o, p, gws, gstride, order, count, x0, ps, it);
+    }
+    plain_final<M><<<g, b, 0, s>>>(L, o, p, out, gws, gstride, order, count, x0, ps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain(int model, int threads, cudaStream_t s, const KLayout& L, const KOpts& o, const KParams& p,
+                         const KSol& out, float* gws, long long gstride, const int* order, int count,
+                         const float* x0, int warm, PlainState* ps) {
+    switch (model) {
+        case MODEL_DI: return launch_plain_m<MODEL_DI>(threads, s, L, o, p, out, gws, gstride, order, count, x0, warm, ps);
+        case MODEL_BICYCLE:
+            return launch_plain_m<MODEL_BICYCLE>(threads, s, L, o, p, out, gws, gstride, order, count, x0, warm, ps);
+        case MODEL_QUAD: return launch_plain_m<MODEL_QUAD>(threads, s, L, o, p, out, gws, gstride, order, count, x0, warm, ps);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int plain_launches(int max_sqp, int max_admm) { return 2 + max_sqp * (2 + max_admm); }
 
 cudaError_t launch(int model, int policy, int grid, int threads, size_t smem_bytes, cudaStream_t s,
                    const KLayout& L, const KOpts& o, const KParams& p, const KSol& out, float* gws,

@@ -8,6 +8,14 @@
 namespace tmpc {
 namespace fast {
 
+// per-instance state of the plain per-phase form (between launches)
+struct PlainState {
+    float rho, rp, rd, alpha_last;
+    int admm_total, nfact, sqp_done;
+    int ls_hist[2];
+    int flags[4];
+};
+
 // factorisation policies of the shared-memory kernels
 constexpr int kPolicyCR = 0, kPolicyLDL = 1;
 // floats of per-instance storage needed by the shared-memory path for T stages
@@ -36,6 +44,13 @@ cudaError_t launch_backward(int model, int cl, int grid, int threads, size_t sme
                             const KLayout& L, const KOpts& o, const KParams& p, const KSol& sol, float* gws,
                             long long gstride, const int* order, int count, int* queue, const float* x0,
                             int* gflags, const float* dLdz, const float* dLdxi, const KGrads& g);
+
+// plain per-phase form: one launch per phase, fixed counts, one CTA per instance,
+// global arenas; kernels launched on s in host order (plain_launches of them)
+cudaError_t launch_plain(int model, int threads, cudaStream_t s, const KLayout& L, const KOpts& o, const KParams& p,
+                         const KSol& out, float* gws, long long gstride, const int* order, int count,
+                         const float* x0, int warm, PlainState* ps);
+int plain_launches(int max_sqp, int max_admm);
 
 }  // namespace fast
 }  // namespace tmpc

@@ -259,6 +259,22 @@ def test_global_arenas_match_shared_arenas_bitwise(shared, glob):
         assert np.array_equal(a[k], b[k]), k
 
 
+def test_plain_per_phase_form_matches_persistent_kernel_bitwise():
+    """The plain per-phase form (solver 7: one launch per phase, state in global
+    memory) runs the persistent kernel's device code phase by phase: equal to
+    the persistent kernel on global arenas (solver 3) bit for bit."""
+    pb = w.racing(B=6, N=30, max_sqp=3, max_admm=30)
+    pb.N[:] = [30, 7, 22, 1, 30, 15]
+    for i in range(6):
+        N = int(pb.N[i])
+        pb.lin[i, :, 5] = 0.0
+        pb.lin[i, N, 5] = -1.0
+    _, a, _ = _run(pb, solver=3)
+    _, b, _ = _run(pb, solver=7)
+    for k in ("z", "xi", "y_eq", "y_ineq", "status", "stats"):
+        assert np.array_equal(a[k], b[k]), k
+
+
 def test_cluster_team_matches_single_cta_bitwise_on_lq():
     """One thread-block cluster per instance (solver 6) runs the cyclic
     reduction of a single CTA with global arenas (solver 3) with the work of
