@@ -347,6 +347,9 @@ struct tmpc_handle {
     int bwd_generic = 0;       // instances whose backward runs on the generic kernel
     int* gflags = nullptr;     // team flags of cluster-launched instances (4 per instance)
     fast::PlainState* pstate = nullptr;   // per-instance state of the plain per-phase form
+    // several model groups run concurrently on internal streams (fork / join on the caller's stream)
+    cudaStream_t gs[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join[4] = {nullptr, nullptr, nullptr, nullptr};
     int n_groups = 0;
     float* fws = nullptr;      // global arenas of the shared-memory path (instances that do not fit)
     long long fstride = 0;
@@ -591,6 +594,14 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
     ord.insert(ord.end(), bord.begin(), bord.end());
     e = cudaMemcpy(h->order, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { set_err("cudaMemcpy(order)", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
+    if (h->n_groups > 1) {
+        e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+        for (int g = 0; g < h->n_groups && e == cudaSuccess; ++g) {
+            e = cudaStreamCreateWithFlags(&h->gs[g], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join[g], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) { set_err("group streams", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
+    }
     bool any_plain = false;
     for (int g = 0; g < h->n_groups; ++g) any_plain = any_plain || h->groups[g].plain;
     if (any_plain) {
@@ -690,8 +701,15 @@ static tmpc_status launch_solve(tmpc_handle* h, const tmpc_params& p, const floa
     TMPC_CUDA(cudaMemsetAsync(h->queue, 0, sizeof(int) * 5, s));
     const KOpts ko = to_kopts(h->o);
     const KParams kp = to_kparams(p);
+    const bool fork = h->n_groups > 1 && h->ev_fork;
+    const cudaStream_t s0 = s;
+    if (fork) TMPC_CUDA(cudaEventRecord(h->ev_fork, s0));
     for (int g = 0; g < h->n_groups; ++g) {
         const tmpc_handle::Group& G = h->groups[g];
+        if (fork) {
+            s = h->gs[g];
+            TMPC_CUDA(cudaStreamWaitEvent(s, h->ev_fork, 0));
+        }
         if (G.model >= 0 && G.plain) {
             TMPC_CUDA(fast::launch_plain(G.model, G.threads, s, h->L, ko, kp, ks, h->fws, h->fstride,
                                          h->order + G.offset, G.count, x0, warm, h->pstate));
@@ -706,7 +724,10 @@ static tmpc_status launch_solve(tmpc_handle* h, const tmpc_params& p, const floa
                 h->L, ko, kp, ks, h->ws, h->off, h->order + G.offset, G.count, h->queue + g, x0, warm);
             TMPC_CUDA(cudaGetLastError());
         }
+        if (fork) TMPC_CUDA(cudaEventRecord(h->ev_join[g], s));
     }
+    if (fork)
+        for (int g = 0; g < h->n_groups; ++g) TMPC_CUDA(cudaStreamWaitEvent(s0, h->ev_join[g], 0));
     return TMPC_OK;
 }
 
@@ -728,18 +749,33 @@ tmpc_status tmpc_backward(tmpc_handle* h, const float* x0, const tmpc_solution* 
     TMPC_CUDA(cudaMemsetAsync(h->queue, 0, sizeof(int) * 5, s));
     const KOpts ko = to_kopts(h->o);
     const KParams kp = to_kparams(h->p);
+    // one stream per shared-memory group plus the generic backward, forked from s when there are several
+    const bool fork = h->n_groups > 1 && h->ev_fork;
+    if (fork) TMPC_CUDA(cudaEventRecord(h->ev_fork, s));
+    int used = 0;
     for (int gi = 0; gi < h->n_groups; ++gi) {
         const tmpc_handle::Group& G = h->groups[gi];
         if (G.bgrid <= 0) continue;
-        TMPC_CUDA(fast::launch_backward(G.model, G.cluster, G.bgrid, G.threads, G.smem, s, h->L, ko, kp, ks, h->fws,
+        cudaStream_t sg = s;
+        if (fork) {
+            sg = h->gs[gi];
+            TMPC_CUDA(cudaStreamWaitEvent(sg, h->ev_fork, 0));
+        }
+        TMPC_CUDA(fast::launch_backward(G.model, G.cluster, G.bgrid, G.threads, G.smem, sg, h->L, ko, kp, ks, h->fws,
                                         h->fstride, h->order + G.offset, G.count, h->queue + gi, x0, h->gflags,
                                         dL_dz, dL_dxi, kg));
+        if (fork) {
+            TMPC_CUDA(cudaEventRecord(h->ev_join[gi], sg));
+            used |= 1 << gi;
+        }
     }
     if (h->bwd_generic > 0) {
         backward_kernel<<<std::min(h->grid_bwd, h->bwd_generic), h->threads, h->smem, s>>>(
             h->L, ko, kp, ks, h->ws, h->off, h->order + h->d.batch, h->bwd_generic, h->queue + 4, x0, dL_dz, dL_dxi, kg);
         TMPC_CUDA(cudaGetLastError());
     }
+    for (int gi = 0; gi < h->n_groups; ++gi)
+        if (used & (1 << gi)) TMPC_CUDA(cudaStreamWaitEvent(s, h->ev_join[gi], 0));
     return TMPC_OK;
 }
 
@@ -798,6 +834,11 @@ void tmpc_destroy(tmpc_handle* h) {
     if (h->fws) cudaFree(h->fws);
     if (h->gflags) cudaFree(h->gflags);
     if (h->pstate) cudaFree(h->pstate);
+    for (int g = 0; g < 4; ++g) {
+        if (h->gs[g]) cudaStreamDestroy(h->gs[g]);
+        if (h->ev_join[g]) cudaEventDestroy(h->ev_join[g]);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     delete h;
 }
 

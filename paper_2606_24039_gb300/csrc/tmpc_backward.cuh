@@ -105,11 +105,18 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
             const int t = e / n, j = e % n;
             float s = bx[e] - Px_entry(c, ex, t, j);
             s -= Ct_entry(c, t, j, [&](int r, int k) { return lam[r * nx + k]; });
-            const float* G = c.Gt(t);
-            for (int r = 0; r < ng; ++r) {
-                const float cd = code[t * ng + r];
-                if (fabsf(cd) > 1.5f) s -= c.gam2(r) * G[r * n + j] * gz[t * ng + r];
-                else if (cd != 0.f) s -= G[r * n + j] * mu[t * ng + r];
+            if (g_is_selector(c)) {
+                const int r = g_row(c, j);
+                const float cd = r >= 0 ? code[t * ng + r] : 0.f;
+                if (fabsf(cd) > 1.5f) s -= c.gam2(r) * gz[t * ng + r];
+                else if (cd != 0.f) s -= mu[t * ng + r];
+            } else {
+                const float* G = c.Gt(t);
+                for (int r = 0; r < ng; ++r) {
+                    const float cd = code[t * ng + r];
+                    if (fabsf(cd) > 1.5f) s -= c.gam2(r) * G[r * n + j] * gz[t * ng + r];
+                    else if (cd != 0.f) s -= G[r * n + j] * mu[t * ng + r];
+                }
             }
             c.eta[e] = s;
         }
@@ -123,8 +130,13 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
         for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
             const int t = e / n, j = e % n;
             float s = Ct_entry(c, t, j, [&](int r, int k) { return r2[r * nx + k]; });
-            const float* G = c.Gt(t);
-            for (int r = 0; r < ng; ++r) s += G[r * n + j] * r3[t * ng + r];
+            if (g_is_selector(c)) {
+                const int r = g_row(c, j);
+                if (r >= 0) s += r3[t * ng + r];
+            } else {
+                const float* G = c.Gt(t);
+                for (int r = 0; r < ng; ++r) s += G[r * n + j] * r3[t * ng + r];
+            }
             c.eta[e] += rb * s;
         }
         __syncthreads();

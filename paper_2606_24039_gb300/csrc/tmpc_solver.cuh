@@ -334,7 +334,31 @@ __device__ __forceinline__ float Cx_entry(const Ctx& c, const float* x, int r, i
     return s + s2;
 }
 
+// Selector structure of G: for the double integrator, linear and quadrotor
+// models every inequality row selects one stage variable (the bicycle has a
+// dense row).  g_col(c, r): the column row r selects; g_row(c, j): the row
+// that selects column j, -1 if none.  The hot loops use them instead of
+// multiplying through the zeros of G (same values: the other terms are 0).
+__device__ __forceinline__ bool g_is_selector(const Ctx& c) { return c.model != MODEL_BICYCLE; }
+__device__ __forceinline__ int g_col(const Ctx& c, int r) {
+    switch (c.model) {
+        case MODEL_LINEAR: return c.nx + r;
+        case MODEL_DI: return r == 0 ? 4 : r == 1 ? 5 : r == 2 ? 2 : 3;
+        case MODEL_QUAD: return r == 0 ? 6 : 7;
+    }
+    return -1;
+}
+__device__ __forceinline__ int g_row(const Ctx& c, int j) {
+    switch (c.model) {
+        case MODEL_LINEAR: return (j >= c.nx && j - c.nx < c.ng) ? j - c.nx : -1;
+        case MODEL_DI: return j == 4 ? 0 : j == 5 ? 1 : j == 2 ? 2 : j == 3 ? 3 : -1;
+        case MODEL_QUAD: return j == 6 ? 0 : j == 7 ? 1 : -1;
+    }
+    return -1;
+}
+
 __device__ __forceinline__ float Gx_entry(const Ctx& c, const float* x, int t, int r) {
+    if (g_is_selector(c)) return x[t * c.n + g_col(c, r)];
     const float* G = c.Gt(t) + r * c.n;
     const float* a = x + t * c.n;
     float s = 0.f;
@@ -870,8 +894,13 @@ __device__ inline void admm_iter(const Ctx& c, const KOpts& o, float rho_bar, co
         const int t = e / n, j = e % n;
         float s = -(Px_entry(c, c.x, t, j) + c.qv[e]);
         s -= Ct_entry(c, t, j, [&](int r, int k) { return c.yf[r * nx + k] + rho_f * c.pf[r * nx + k]; });
-        const float* G = c.Gt(t);
-        for (int r = 0; r < ng; ++r) s -= G[r * n + j] * (c.yg[t * ng + r] + rho_g * c.pg[t * ng + r]);
+        if (g_is_selector(c)) {
+            const int r = g_row(c, j);
+            if (r >= 0) s -= c.yg[t * ng + r] + rho_g * c.pg[t * ng + r];
+        } else {
+            const float* G = c.Gt(t);
+            for (int r = 0; r < ng; ++r) s -= G[r * n + j] * (c.yg[t * ng + r] + rho_g * c.pg[t * ng + r]);
+        }
         c.eta[e] = s;
     }
     __syncthreads();
@@ -943,8 +972,13 @@ __device__ inline Res residuals(const Ctx& c, const Smem& sm) {
             const float* Ap = c.Apt(t - 1);
             for (int k = 0; k < nx; ++k) atyd += (double)Ap[k * n + j] * (double)c.yf[t * nx + k];
         }
-        const float* G = c.Gt(t);
-        for (int r = 0; r < ng; ++r) atyd += (double)G[r * n + j] * (double)c.yg[t * ng + r];
+        if (g_is_selector(c)) {
+            const int r = g_row(c, j);
+            if (r >= 0) atyd += (double)c.yg[t * ng + r];
+        } else {
+            const float* G = c.Gt(t);
+            for (int r = 0; r < ng; ++r) atyd += (double)G[r * n + j] * (double)c.yg[t * ng + r];
+        }
         const float aty = (float)atyd;
         v[1] = fmaxf(v[1], fin((float)((double)px + (double)c.qv[e] + atyd)));
         v[3] = fmaxf(v[3], fmaxf(fmaxf(fin(px + pzb), fin(aty)), fin(c.qv[e] - pzb)));
