@@ -50,10 +50,17 @@ def test_setup_rejects_bad_arguments_without_a_gpu(lib):
     # dimensions beyond the compiled limits
     d2 = _abi.Dims(4, 10, 70, 10, 4, 1, 0)
     assert lib.tmpc_setup(ctypes.byref(h), ctypes.byref(d2), ctypes.byref(o), ctypes.byref(p)) == 5
+    # empty batch, empty horizon
+    for bad in (_abi.Dims(0, 10, 4, 2, 4, 1, 0), _abi.Dims(4, 0, 4, 2, 4, 1, 0)):
+        assert lib.tmpc_setup(ctypes.byref(h), ctypes.byref(bad), ctypes.byref(o), ctypes.byref(p)) == 1
     # bad options
     o2 = _abi.default_options()
     o2.alpha = 2.5
     assert lib.tmpc_setup(ctypes.byref(h), ctypes.byref(d), ctypes.byref(o2), ctypes.byref(p)) == 1
+    for field, value in (("solver", 8), ("threads", 48), ("threads", 512), ("n_ls", 17), ("max_admm", 0)):
+        o3 = _abi.default_options()
+        setattr(o3, field, value)
+        assert lib.tmpc_setup(ctypes.byref(h), ctypes.byref(d), ctypes.byref(o3), ctypes.byref(p)) == 1, field
     # calls on a null handle
     assert lib.tmpc_solve(None, None, None, 0, None) == 4
     assert lib.tmpc_backward(None, None, None, None, None, None, None) == 4

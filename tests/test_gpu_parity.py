@@ -338,6 +338,26 @@ def test_uneven_full_batch_sampled():
     assert np.all(np.isin(sol["status"], (0, 1)))
 
 
+def test_largest_supported_stage_dimension():
+    """n = nx + nu = 72, the largest stage the library compiles for (linear
+    model, nx = 52, nu = 20), through the generic kernel's streamed solve."""
+    pb = w.tracking(B=2, nx=52, nu=20, N=6, max_admm=150)
+    s, sol, _ = _run(pb)
+    _compare(pb, sol, range(2))
+
+
+def test_unconstrained_lq_matches_the_oracle():
+    """Bounds at +-1e30 (never active): the QP is an LQ problem, the oracle's
+    ADMM converges to the Riccati solution (pinned on the CPU) and the kernels
+    must follow it."""
+    pb = w.double_integrator(B=2, N=15, max_admm=300)
+    pb.lo[:] = -1e30
+    pb.hi[:] = 1e30
+    for solver in (1, 2):
+        s, sol, _ = _run(pb, solver=solver)
+        _compare(pb, sol, range(2))
+
+
 def test_host_entry_point_matches_device_entry_point():
     pb = w.racing(B=4, N=30, max_sqp=3)
     from paper_2606_24039_gb300 import Solver, tensors_from_batch
