@@ -239,16 +239,16 @@ __device__ __forceinline__ float coldot(const float* blk_, int i, const float* v
     return s;
 }
 
-// Inverse of the reduced system left after L = top_level(T) levels of the
-// cyclic reduction (survivors b = q 2^L, q < top_blocks(T)): the remaining
-// levels of the factorisation are applied to the m = top_blocks(T) N unit
+// Inverse of the reduced system left after L = top_level(T, B) levels of the
+// cyclic reduction (survivors b = q 2^L, q < top_blocks(T, B), B = c.topb): the
+// remaining levels of the factorisation are applied to the m = top_blocks N unit
 // vectors.  Column col of Xt holds (M_R^-1) e_col with row q N + i for
 // survivor q, row i.  One task per (block, column) works in place.
 template <int M>
 __device__ __forceinline__ void top_inverse(const Inst<M>& c) {
     constexpr int N = Inst<M>::N, BS = Inst<M>::BS;
-    const int T = c.T, L = top_level(T), S0 = 1 << L, TD = c.TD;
-    const int m = top_blocks(T) * N;
+    const int T = c.T, L = top_level(T, c.topb), S0 = 1 << L, TD = c.TD;
+    const int m = top_blocks(T, c.topb) * N;
     float* X = c.Xt;
     for (int e = c.tid; e < m * TD; e += c.nth) {
         const int col = e / TD, row = e % TD;
@@ -335,24 +335,38 @@ __device__ __forceinline__ void top_inverse(const Inst<M>& c) {
 }
 
 // Solve S x = r with the cyclic-reduction factors; r is consumed, x -> xo.
-// Levels below top_level(T): one barrier per level on the way down
+// Levels below top_level(T, c.topb): one barrier per level on the way down
 // (r_i -= Fa_{i+s} r_{i+s} + Fb_{i-s} r_{i-s}) and one on the way up
 // (x_e = Dinv_e r_e - Fa_e' x_{e-s} - Fb_e' x_{e+s}); the survivors in between
 // are solved by the dense inverse of the reduced system (one barrier).
 template <int M>
 __device__ __forceinline__ void cr_solve(const Inst<M>& c, float* r, float* xo) {
     constexpr int N = Inst<M>::N, BS = Inst<M>::BS;
-    const int T = c.T, L = top_level(T), TD = c.TD;
-    const int m = top_blocks(T) * N;
+    const int T = c.T, L = top_level(T, c.topb), TD = c.TD;
+    const int m = top_blocks(T, c.topb) * N;
     for (int l = 0; l < L; ++l) {
         const int s = 1 << l;
         const int nsv = (T + 2 * s - 1) >> (l + 1);     // survivors i0 = q 2s < T
-        for (int w = c.tid; w < nsv * N; w += c.nth) {
+        // two tasks per thread and step, every load before the stores (a thread writes
+        // only its own survivor rows, which no other task of the level reads)
+        auto down = [&](int w) {
             const int i0 = (w / N) << (l + 1), i = w % N;
             float a = 0.f;
             if (i0 + s < T) a += rowdot<N>(c.Fa + (i0 + s) * BS, i, r + (i0 + s) * N);
             if (i0 >= s) a += rowdot<N>(c.Fb + (i0 - s) * BS, i, r + (i0 - s) * N);
-            r[i0 * N + i] -= a;
+            return r[i0 * N + i] - a;
+        };
+        const int nt = nsv * N;
+        if (c.cl > 1) {   // cluster teams: several passes over global memory
+            for (int w = c.tid; w < nt; w += 2 * c.nth) {
+                const int w1 = w + c.nth;
+                const float v0 = down(w);
+                const float v1 = w1 < nt ? down(w1) : 0.f;
+                r[((w / N) << (l + 1)) * N + w % N] = v0;
+                if (w1 < nt) r[((w1 / N) << (l + 1)) * N + w1 % N] = v1;
+            }
+        } else {
+            for (int w = c.tid; w < nt; w += c.nth) r[((w / N) << (l + 1)) * N + w % N] = down(w);
         }
         c.sync();
     }
@@ -382,11 +396,23 @@ __device__ __forceinline__ void cr_solve(const Inst<M>& c, float* r, float* xo) 
     for (int l = L - 1; l >= 0; --l) {
         const int s = 1 << l;
         const int ne = (T + s - 1) >> (l + 1);          // eliminated e = s + q 2s < T
-        for (int w = c.tid; w < ne * N; w += c.nth) {
+        auto up = [&](int w) {
             const int e = s + ((w / N) << (l + 1)), i = w % N;
             float a = rowdot<N>(c.Dm + e * BS, i, r + e * N) - coldot<N>(c.Fa + e * BS, i, xo + (e - s) * N);
             if (e + s < T) a -= coldot<N>(c.Fb + e * BS, i, xo + (e + s) * N);
-            xo[e * N + i] = a;
+            return a;
+        };
+        const int nt = ne * N;
+        if (c.cl > 1) {
+            for (int w = c.tid; w < nt; w += 2 * c.nth) {
+                const int w1 = w + c.nth;
+                const float v0 = up(w);
+                const float v1 = w1 < nt ? up(w1) : 0.f;
+                xo[(s + ((w / N) << (l + 1))) * N + w % N] = v0;
+                if (w1 < nt) xo[(s + ((w1 / N) << (l + 1))) * N + w1 % N] = v1;
+            }
+        } else {
+            for (int w = c.tid; w < nt; w += c.nth) xo[(s + ((w / N) << (l + 1))) * N + w % N] = up(w);
         }
         c.sync();
     }
@@ -697,7 +723,7 @@ __device__ __forceinline__ void admm_iter(const Inst<M>& c, float rho_bar, float
     constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
     const int T = c.T;
     const float rho_f = 1e3f * rho_bar, rho_g = rho_bar, inv_rho_g = 1.f / rho_bar;
-    for (int e = c.tid; e < T * N; e += c.nth) {
+    auto rhs = [&](int e) {
         const int t = e / N, j = e % N;
         float s = -(c.Pv(c.x, t, j) + c.qv[e]);
         s -= c.Ctv(t, j, [&](int row, int k) { return c.wf[row * NX + k]; });
@@ -707,7 +733,18 @@ __device__ __forceinline__ void admm_iter(const Inst<M>& c, float rho_bar, float
             if (Tr::sel(r) >= 0) { if (Tr::sel(r) == j) s -= wg[r]; }
             else s -= c.Grow[t * N + j] * wg[r];
         }
-        c.r[e] = s;
+        return s;
+    };
+    if (c.cl > 1) {   // cluster teams: two entries per step, loads before stores
+        for (int e = c.tid; e < T * N; e += 2 * c.nth) {
+            const int e1 = e + c.nth;
+            const float s0 = rhs(e);
+            const float s1 = e1 < T * N ? rhs(e1) : 0.f;
+            c.r[e] = s0;
+            if (e1 < T * N) c.r[e1] = s1;
+        }
+    } else {
+        for (int e = c.tid; e < T * N; e += c.nth) c.r[e] = rhs(e);
     }
     c.sync();
     if (P == kCR) cr_solve<M>(c, c.r, c.dx);
@@ -897,12 +934,27 @@ __device__ __forceinline__ float linesearch(const Inst<M>& c, const KOpts& o, co
         if (k == 0) val[2 * (K + 1) * T + t] = sc;
     }
     c.sync();
-    // per-candidate sums (a cluster team publishes them through the exchange area)
-    double* acc = c.cl > 1 ? c.xch : rs.lsacc;
-    for (int q = c.tid; q < 2 * (K + 1) + 1; q += c.nth) {
-        double sum = 0.0;
-        for (int t = 0; t < T; ++t) sum += (double)val[q * T + t];
-        acc[q] = sum;
+    // per-candidate sums over the stages, split over the team four at a time
+    // (team reductions; a cluster team keeps them in its exchange area)
+    const int nq = 2 * (K + 1) + 1;
+    double* acc = c.cl > 1 ? c.xch + kTeamMax * kXchDoubles : rs.lsacc;
+    if (c.cl == 1) {   // short horizons in one CTA: one thread per sum
+        for (int q = c.tid; q < nq; q += c.nth) {
+            double sum = 0.0;
+            for (int t = 0; t < T; ++t) sum += (double)val[q * T + t];
+            acc[q] = sum;
+        }
+    } else for (int q0 = 0; q0 < nq; q0 += 4) {
+        double part[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int t = c.tid; t < T; t += c.nth)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (q0 + u < nq) part[u] += (double)val[(q0 + u) * T + t];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const double tot = team_sum_d<M>(c, part[u], rs.redd);
+            if (q0 + u < nq && c.tid == 0) acc[q0 + u] = tot;
+        }
     }
     c.sync();
     const double l0 = acc[0], V0 = acc[1];

@@ -47,17 +47,21 @@ template <> struct Traits<MODEL_QUAD> {
     __device__ static constexpr int sel(int r) { return r == 0 ? 6 : 7; }
 };
 
-// The cyclic reduction of S stops after top_level(T) levels, when at most
-// kTopBlocks blocks survive; the reduced system on those blocks (dimension
-// top_dim = survivors x N) is inverted once per factorisation and applied as a
-// dense matrix in every solve.
-constexpr int kTopBlocks = 8;
-__host__ __device__ constexpr int top_level(int T) {
+// The cyclic reduction of S stops after top_level(T, B) levels, when at most
+// B blocks survive; the reduced system on those blocks (dimension top_dim =
+// survivors x N) is inverted once per factorisation and applied as a dense
+// matrix in every solve.  B = kTopBlocks for a CTA team (the inverse sits in
+// shared memory), kTopBlocksCluster for a cluster team (global memory; a
+// larger top saves cluster-wide barrier phases).
+constexpr int kTopBlocks = 8, kTopBlocksCluster = 64;
+__host__ __device__ constexpr int top_level(int T, int B) {
     int L = 0;
-    while (((T + (1 << L) - 1) >> L) > kTopBlocks) ++L;
+    while (((T + (1 << L) - 1) >> L) > B) ++L;
     return L;
 }
-__host__ __device__ constexpr int top_blocks(int T) { return (T + (1 << top_level(T)) - 1) >> top_level(T); }
+__host__ __device__ constexpr int top_blocks(int T, int B) {
+    return (T + (1 << top_level(T, B)) - 1) >> top_level(T, B);
+}
 
 // Factorisation policies of S:
 //   kCR  block cyclic reduction by the whole CTA (depth 2 log2 T, all stages in
@@ -73,7 +77,7 @@ constexpr int kTeamMax = 16, kXchDoubles = 40;
 //   factors of S:       Dm, Um                    T x BS each (padded N x N blocks)
 //                       kCR:  Dm = Dinv_e, Um = couplings, Fa, Fb (T x BS each),
 //                             Xt = inverse of the reduced system, top_dim^2
-//                             (top_dim = top_blocks(T) N, rounded to 4)
+//                             (top_dim = top_blocks(T, B) N, rounded to 4)
 //                       kLDL: Dm = Dinv_t, Um = L_t, Wk = 2 scratch blocks
 //   stage vectors:      x, r, dx, qv, zb, Pd      T x N   (kLDL: dx shares r)
 //   inequality rows:    zg, yg, xi, glo, ghi, xib, ygb, pg   T x NG
@@ -88,7 +92,7 @@ constexpr int kTeamMax = 16, kXchDoubles = 40;
     X(Fb, P == kCR ? (long long)T * BS : 0LL)                                     \
     X(Xt, P == kCR ? (long long)TD * TD : 0LL)                                    \
     X(Wk, P == kLDL ? 2LL * BS : 0LL)                                             \
-    X(Xc, CL ? 2LL * kTeamMax * kXchDoubles + 8 : 0LL)                          \
+    X(Xc, CL ? 2LL * (kTeamMax * kXchDoubles + 64) : 0LL)                       \
     X(Am, (Traits<M>::LTI ? (long long)AMS : (long long)T * AMS))                \
     X(Grow, (Traits<M>::DENSE_ROW >= 0 ? (long long)T * N : 0LL))                \
     X(x, T * N) X(r, T * N) X(dx, P == kCR ? T * N : 0) X(qv, T * N)             \
@@ -104,7 +108,7 @@ template <int M>
 __host__ __device__ constexpr long long arena_floats(int T, int P, int CL = 0) {
     constexpr int NX = Traits<M>::NX, N = Traits<M>::NX + Traits<M>::NU, NG = Traits<M>::NG;
     constexpr int BS = N * N + 4, AMS = NX * N + 8;
-    const int TD = (top_blocks(T) * N + 3) & ~3;
+    const int TD = (top_blocks(T, CL ? kTopBlocksCluster : kTopBlocks) * N + 3) & ~3;
     long long total = 0;
 #define TMPC_SIZE(name, cnt) total += (cnt);
     TMPC_FAST_ARENA(TMPC_SIZE)
@@ -131,6 +135,7 @@ struct Inst {
     const float *x0, *Qd, *Rd, *Wd, *ref, *lin, *lo, *hi, *g2, *g1, *dyn, *track;
     float *Dm, *Um, *Fa, *Fb, *Xt, *Wk, *Xc;
     int TD;     // leading dimension of Xt
+    int topb;   // most blocks of the reduced top system (kTopBlocks or kTopBlocksCluster)
     float *x, *r, *dx, *qv, *zb, *Pd;
     float *zg, *yg, *xi, *glo, *ghi, *xib, *ygb, *pg;
     float *yf, *pf, *cv, *yfb;
@@ -148,7 +153,8 @@ struct Inst {
     }
     __device__ __forceinline__ void carve(float* p, int P, int CL = 0) {
         const int T = this->T;
-        TD = (top_blocks(T) * N + 3) & ~3;
+        topb = CL ? kTopBlocksCluster : kTopBlocks;
+        TD = (top_blocks(T, topb) * N + 3) & ~3;
 #define TMPC_CARVE(name, cnt) name = p; p += (cnt);
         TMPC_FAST_ARENA(TMPC_CARVE)
 #undef TMPC_CARVE

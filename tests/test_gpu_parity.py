@@ -275,11 +275,11 @@ def test_plain_per_phase_form_matches_persistent_kernel_bitwise():
         assert np.array_equal(a[k], b[k]), k
 
 
-def test_cluster_team_matches_single_cta_bitwise_on_lq():
+def test_cluster_team_matches_oracle_and_single_cta():
     """One thread-block cluster per instance (solver 6) runs the cyclic
     reduction of a single CTA with global arenas (solver 3) with the work of
-    every phase spread over the cluster: same arithmetic per entry, so equal
-    results on a problem without line search (maxima are order independent)."""
+    every phase spread over the cluster and a larger dense top (64 blocks
+    instead of 8): both within the strict bar of the oracle and of each other."""
     pb = w.double_integrator(B=3, N=900, max_admm=150)
     pb.N[:] = [900, 517, 64]
     for i in range(3):
@@ -287,8 +287,10 @@ def test_cluster_team_matches_single_cta_bitwise_on_lq():
         pb.Qd[i, N, :] = 10 * pb.Qd[i, 0, :]
     _, a, _ = _run(pb, solver=3)
     _, b, _ = _run(pb, solver=6)
-    for k in ("z", "xi", "y_eq", "y_ineq", "status", "stats"):
-        assert np.array_equal(a[k], b[k]), k
+    for i in range(3):
+        N = int(pb.N[i])
+        assert _rel(b["z"][i, :N + 1, :6], a["z"][i, :N + 1, :6]) <= REL_TOL
+    assert np.array_equal(a["status"], b["status"])
     _compare(pb, b, range(3))
 
 
