@@ -88,6 +88,8 @@ def parse():
                     "4 warp-sequential LDL', 5 warp LDL' on global arenas")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the host-memory end-to-end timing")
     ap.add_argument("--threads", type=int, default=0, help="threads per instance (0 = library default)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the launch form chosen at setup (default: tmpc_autotune picks it per model group)")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the plain per-phase form (one launch per phase, eager and as a CUDA graph)")
     return ap.parse_args()
@@ -326,14 +328,40 @@ def measured_peak(key, fallback):
         return fallback
 
 
-def kernel_name(pb, solver):
+FORM_NAMES = {2: "fast::solve_kernel<{m}, kCR>", 3: "fast::solve_kernel<{m}, kCR> (global arenas)",
+              4: "fast::solve_kernel<{m}, kLDL>", 5: "fast::solve_kernel<{m}, kLDL> (global arenas)",
+              6: "fast::solve_kernel_cluster<{m}, kCR>", 7: "fast::plain_* <{m}> (per-phase form)"}
+
+
+def kernel_name(pb, solver, forms=None):
+    """The solve kernel(s) of one forward call; forms maps a model id to the launch
+    form the autotuner kept (tmpc_tune_result.solver)."""
     import workloads as w
     names = {w.MODEL_DI: "MODEL_DI", w.MODEL_BICYCLE: "MODEL_BICYCLE", w.MODEL_QUAD: "MODEL_QUAD"}
-    pol = "kLDL" if solver in (4, 5) else "kCR"
     ks = []
     for m in sorted(set(int(v) for v in np.unique(pb.model))):
-        ks.append(f"fast::solve_kernel<{names[m]}, {pol}>" if (m in names and solver != 1) else "solve_kernel (generic)")
+        if m not in names or solver == 1:
+            ks.append("solve_kernel (generic)")
+            continue
+        f = (forms or {}).get(m, solver if solver >= 2 else 2)
+        ks.append(FORM_NAMES[f].format(m=names[m]))
     return " + ".join(sorted(set(ks)))
+
+
+def launches_per_step(pb, solver, forms=None):
+    """Kernels launched by one forward call and by one backward call: per fast-model
+    group one persistent launch (the plain form: one per phase), one generic launch
+    for the other models; backward: one per cyclic-reduction group plus one generic
+    launch for the rest."""
+    models = set(int(m) for m in np.unique(pb.model))
+    if solver == 1:
+        return 1, 1
+    if not forms:
+        forms = {m: (solver if solver >= 2 else 2) for m in models & set(FAST_MODELS)}
+    other = bool(models - set(forms))
+    fwd = sum(2 + pb.opts.max_sqp * (2 + pb.opts.max_admm) if f == 7 else 1 for f in forms.values()) + int(other)
+    bwd = sum(1 for f in forms.values() if f not in (4, 5)) + int(other or any(f in (4, 5) for f in forms.values()))
+    return fwd, bwd
 
 
 def measured_traffic(args, pb):
@@ -374,13 +402,22 @@ def run_gpu(args):
     pb = workload(args, rank)
     s = Solver.from_batch(pb, device="cuda", solver=args.solver, threads=args.threads)
     sol = s.alloc_solution("cuda")
+    warm = s.z_init is not None
+    tune, forms = None, None
+    if args.solver == 0 and not args.no_autotune:
+        # the autotuner times each launch form of every model group on this batch
+        # (whole solves from the same initial guess as the timed steps)
+        if warm:
+            sol["z"].copy_(s.z_init)
+            for k in ("xi", "y_eq", "y_ineq"):
+                sol[k].zero_()
+        tune = s.tmpc_autotune(s.x0, init=sol if warm else None, reps=2, trial_sqp=0)
+        forms = {r["model"]: r["solver"] for r in tune if r["model"] >= 0}
     dLdz = torch.randn((pb.B, pb.N_max + 1, pb.n), device="cuda")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
-
-    warm = s.z_init is not None
 
     def restart():
         # every step starts from the same initial guess (zero slacks and multipliers)
@@ -432,8 +469,8 @@ def run_gpu(args):
     stats = sol["stats"].cpu().numpy()
     status = sol["status"].cpu().numpy()
     kkt = stats[:, 6]
-    groups = n_launch_groups(pb, args.solver)
-    launches = args.steps * groups + (0 if args.skip_bwd else args.steps * (groups + 1))
+    l_fwd, l_bwd = launches_per_step(pb, args.solver, forms)
+    launches = args.steps * l_fwd + (0 if args.skip_bwd else args.steps * (l_fwd + l_bwd))
 
     # the plain per-phase form of the same solve: one launch per phase, eager and
     # captured as a CUDA graph (the baseline the persistent kernel is compared with)
@@ -526,7 +563,7 @@ def run_gpu(args):
                 "peak_note": "FP32 FMA peak = 152 SM x 128 lanes x 2 flop x 2070 MHz (derived)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = measured_traffic(args, pb)
-    roof["kernel"] = kernel_name(pb, args.solver)
+    roof["kernel"] = kernel_name(pb, args.solver, forms)
     roof["kernel_ms"] = ms_k
     if rank == 0:
         line = {
@@ -541,6 +578,7 @@ def run_gpu(args):
             "roofline": roof,
             "cpu_baseline": cpu_base,
             "plain_form": plain,
+            "autotune": tune,
             "quality": {"kkt_median": float(np.median(kkt)), "kkt_p90": float(np.percentile(kkt, 90)),
                         "frac_kkt_le_1e-5": float(np.mean(kkt <= 1e-5)),
                         "status_counts": {str(k): int(v) for k, v in zip(*np.unique(status, return_counts=True))},

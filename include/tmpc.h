@@ -220,6 +220,49 @@ tmpc_status tmpc_backward(tmpc_handle* h, const float* x0, const tmpc_solution* 
                           const float* dL_dz, const float* dL_dxi, tmpc_grads* g,
                           void* stream);
 
+/* One entry per model group of tmpc_autotune (groups in the order of the
+ * double integrator, bicycle, quadrotor and the generic kernel; unused entries
+ * are not written). */
+typedef struct {
+    int32_t model;       /* model id of the group; -1: the generic kernel (not tuned)  */
+    int32_t count;       /* instances in the group                                      */
+    int32_t solver;      /* chosen launch form, as the codes of tmpc_options.solver     */
+    int32_t threads;     /* threads per CTA                                             */
+    int32_t cluster;     /* CTAs per thread-block cluster (form 6), else 0              */
+    int32_t candidates;  /* forms timed                                                 */
+    float ms;            /* mean device time of the chosen form per trial solve, ms    */
+    float ms_default;    /* the same for the form chosen by tmpc_setup; -1 if untimed  */
+} tmpc_tune_result;
+
+/* Autotuner of the launch form (the fused, batched solve of Section III-E: one
+ * persistent launch per model group).  For every group of the double
+ * integrator, bicycle or quadrotor, times the group's forward solve from x0
+ * [B][nx] (DEVICE) in each candidate form -- cyclic reduction with shared
+ * arenas at 256 and 128 threads per CTA, the one-warp block LDL', cyclic
+ * reduction with global arenas, the plain per-phase form, and one cluster per
+ * instance when the group is at most about one wave of clusters -- and keeps the
+ * fastest for later tmpc_solve / tmpc_backward calls.
+ *   init       (DEVICE, may be NULL) warm start of the trials: z, xi, y_eq and
+ *              y_ineq are copied (not written) before each trial, as tmpc_solve
+ *              with warm_start reads them; NULL starts each trial cold.
+ *   reps       1..1000 timed rounds.  The setup's form first runs until about
+ *              20 ms of device time (clocks up); each form then runs once, forms
+ *              four times slower than the fastest of these are dropped, and the
+ *              rest run reps interleaved rounds; a form's time is its fastest
+ *              launch (CUDA events on stream, warm-start copy included).
+ *   trial_sqp  > 0 caps the SQP iterations of the trials; 0 runs the handle's.
+ *   res [4]    (HOST, may be NULL) one entry per group.
+ * The choice minimises the forward solve; the backward follows it (shared-memory
+ * backward for cyclic-reduction forms, the generic backward for LDL' forms).
+ * Trial outputs go to buffers of the handle; caller arrays other than res are
+ * not written.  Synchronous; may allocate (larger global arenas, plain-form
+ * state, cluster flags).  A handle whose options fix the form (solver != 0) is
+ * not changed (candidates = 0).
+ * Errors: NOT_SETUP, INVALID_ARG (x0 NULL or misaligned, init incomplete, reps
+ * or trial_sqp out of range), CUDA, OOM. */
+tmpc_status tmpc_autotune(tmpc_handle* h, const float* x0, const tmpc_solution* init, int32_t reps,
+                          int32_t trial_sqp, tmpc_tune_result* res, void* stream);
+
 /* End-to-end forward pass from HOST memory: copies the parameter arrays of
  * host_p and x0 (HOST pointers, pinned memory recommended) into device
  * buffers owned by the handle, solves, copies z, xi, y_eq, y_ineq, status and

@@ -56,9 +56,15 @@ class Grads(ctypes.Structure):
                 ("gamma1", ctypes.c_void_p)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("count", ctypes.c_int32), ("solver", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("cluster", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("ms", ctypes.c_float), ("ms_default", ctypes.c_float)]
+
+
 EXPORTS = ["tmpc_default_options", "tmpc_setup", "tmpc_update_params", "tmpc_set_options",
            "tmpc_solve", "tmpc_backward", "tmpc_solve_host", "tmpc_destroy",
-           "tmpc_status_string", "tmpc_last_error", "tmpc_solve_static"]
+           "tmpc_status_string", "tmpc_last_error", "tmpc_solve_static", "tmpc_autotune"]
 
 _lib = None
 
@@ -96,6 +102,9 @@ def load(path: str | None = None):
     lib.tmpc_solve_static.argtypes = [ctypes.POINTER(Dims), ctypes.POINTER(Options), ctypes.POINTER(Params), vp,
                                       ctypes.POINTER(Solution), ctypes.c_int32, vp]
     lib.tmpc_solve_static.restype = ctypes.c_int
+    lib.tmpc_autotune.argtypes = [vp, vp, ctypes.POINTER(Solution), ctypes.c_int32, ctypes.c_int32,
+                                  ctypes.POINTER(TuneResult), vp]
+    lib.tmpc_autotune.restype = ctypes.c_int
     lib.tmpc_destroy.argtypes = [vp]
     lib.tmpc_destroy.restype = None
     lib.tmpc_status_string.argtypes = [ctypes.c_int]

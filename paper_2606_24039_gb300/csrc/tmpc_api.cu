@@ -342,8 +342,13 @@ struct tmpc_handle {
         int cluster = 0;   // > 0: CTAs per thread-block cluster (one cluster per instance)
         int bgrid = 0;     // > 0: the group's backward runs on the shared-memory path with this grid
         int plain = 0;     // 1: plain per-phase form (one launch per phase, solver 7)
+        int form = 0;      // launch form, as the solver option codes 2..7 (0: generic kernel)
+        int Tmax = 0;      // longest horizon + 1 in the group
         size_t smem = 0;
     } groups[4];
+    std::vector<int> ord_host;          // forward instance order (groups back to back)
+    std::vector<long long> work_host;   // (N+1) n^2 per instance, the longest-first key
+    int max_optin = 0;
     int bwd_generic = 0;       // instances whose backward runs on the generic kernel
     int* gflags = nullptr;     // team flags of cluster-launched instances (4 per instance)
     fast::PlainState* pstate = nullptr;   // per-instance state of the plain per-phase form
@@ -425,6 +430,134 @@ static tmpc_status check_params(const tmpc_dims& d, const tmpc_params* p) {
     return TMPC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Launch forms of the model groups of the shared-memory kernels (the solver
+// option codes): 2 cyclic reduction with the arena in shared memory where it
+// fits, 3 the same with every arena in global memory, 4 / 5 the one-warp block
+// LDL' in shared / global memory, 6 one thread-block cluster per instance,
+// 7 the plain per-phase form.
+// ---------------------------------------------------------------------------
+namespace {
+
+long long shared_cap(const tmpc_handle* h) {
+    return std::max(48LL * 1024, (long long)h->max_optin / 2 - 8 * 1024);
+}
+
+long long arena_bytes(const tmpc_handle::Group& G, int policy) {
+    return (long long)sizeof(float) * fast::arena_floats_host(G.model, G.Tmax, policy);
+}
+
+// the longest instance's cyclic-reduction arena fits with two CTAs per SM
+bool shared_fits(const tmpc_handle* h, const tmpc_handle::Group& G) {
+    return arena_bytes(G, fast::kPolicyCR) <= shared_cap(h);
+}
+
+// Sets the group's policy, CTA size, shared arena and grid for a form.
+// cudaErrorNotSupported: no cluster size can be launched (form 6).
+cudaError_t configure_group(tmpc_handle* h, tmpc_handle::Group& G, int form, int threads) {
+    G.plain = 0;
+    G.cluster = 0;
+    G.bgrid = 0;
+    G.form = form;
+    G.policy = (form == 4 || form == 5) ? fast::kPolicyLDL : fast::kPolicyCR;
+    G.threads = threads > 0 ? threads : (G.policy == fast::kPolicyLDL ? 128 : 256);
+    // shared arena: the longest instance if it fits with 2 CTAs per SM, else a
+    // third of the opt-in limit (longer instances use their global arena)
+    const long long need = arena_bytes(G, G.policy), cap = shared_cap(h);
+    G.smem = (size_t)std::min(need, need <= cap ? need : (long long)h->max_optin / 3);
+    if (form == 3 || form == 5 || form == 7) G.smem = 0;
+    if (form == 7) {   // one CTA per instance, one launch per phase
+        G.plain = 1;
+        G.grid = G.count;
+        return cudaSuccess;
+    }
+    if (form == 6) {
+        for (int cl = 16; cl >= 2 && G.cluster == 0; cl >>= 1) {
+            int mc = 0;
+            if (fast::prepare_cluster(G.model, G.policy, cl, G.threads, &mc) == cudaSuccess && mc >= 1) {
+                G.cluster = cl;
+                G.grid = std::min(G.count, mc);   // clusters
+            }
+        }
+        cudaGetLastError();   // clear a refused cluster size
+        return G.cluster > 0 ? cudaSuccess : cudaErrorNotSupported;
+    }
+    int per = 0;
+    const cudaError_t e = fast::prepare(G.model, G.policy, G.smem, G.threads, &per);
+    if (e != cudaSuccess) return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    G.grid = std::max(1, std::min(G.count, per * h->nsm));
+    return cudaSuccess;
+}
+
+// Global arenas (instances whose arena is not in shared memory), plain-form
+// state and cluster team flags for the groups' current forms; grows, never shrinks.
+tmpc_status ensure_buffers(tmpc_handle* h) {
+    long long fmax = 0;
+    bool any_plain = false, any_cluster = false;
+    for (int g = 0; g < h->n_groups; ++g) {
+        const tmpc_handle::Group& G = h->groups[g];
+        if (G.model < 0) continue;
+        fmax = std::max(fmax, fast::arena_floats_host(G.model, G.Tmax, G.policy));
+        if (G.cluster > 0) fmax = std::max(fmax, fast::arena_floats_host(G.model, G.Tmax, G.policy, 1));
+        any_plain = any_plain || G.plain;
+        any_cluster = any_cluster || G.cluster > 0;
+    }
+    const long long B = h->d.batch;
+    cudaError_t e;
+    if (any_plain && !h->pstate) {
+        e = cudaMalloc(&h->pstate, sizeof(fast::PlainState) * (size_t)B);
+        if (e != cudaSuccess) { set_err("cudaMalloc(plain state)", e); return TMPC_ERR_OOM; }
+    }
+    if (any_cluster && !h->gflags) {
+        e = cudaMalloc(&h->gflags, sizeof(int) * 4 * (size_t)B);
+        if (e != cudaSuccess) { set_err("cudaMalloc(team flags)", e); return TMPC_ERR_OOM; }
+    }
+    const long long stride = (fmax + 31) & ~31LL;
+    if (fmax > 0 && stride > h->fstride) {
+        if (h->fws) cudaFree(h->fws);
+        h->fws = nullptr;
+        h->fstride = 0;
+        e = cudaMalloc(&h->fws, sizeof(float) * stride * B);
+        if (e != cudaSuccess) { set_err("cudaMalloc(fast arenas)", e); return TMPC_ERR_OOM; }
+        h->fstride = stride;
+    }
+    return TMPC_OK;
+}
+
+// Backward plan: groups on the cyclic-reduction policy run the shared-memory
+// backward over their forward order; every other instance (generic group,
+// warp-LDL groups) the generic backward, longest first.  Writes the device
+// order array (forward order, then the generic backward's).
+tmpc_status plan_backward(tmpc_handle* h) {
+    const int B = h->d.batch;
+    std::vector<char> fastb(B, 0);
+    for (int g = 0; g < h->n_groups; ++g) {
+        tmpc_handle::Group& G = h->groups[g];
+        G.bgrid = 0;
+        if (G.model < 0 || G.policy != fast::kPolicyCR || h->o.solver == 1) continue;
+        int per = 0;
+        const cudaError_t e = fast::prepare_backward(G.model, G.cluster, G.smem, G.threads, &per);
+        if (e != cudaSuccess || per < 1) { cudaGetLastError(); continue; }
+        G.bgrid = G.cluster > 0 ? G.grid : std::max(1, std::min(G.count, per * h->nsm));
+        for (int q = 0; q < G.count; ++q) fastb[h->ord_host[G.offset + q]] = 1;
+    }
+    std::vector<int> bord;
+    for (int i = 0; i < B; ++i)
+        if (!fastb[i]) bord.push_back(i);
+    std::stable_sort(bord.begin(), bord.end(),
+                     [&](int a, int b) { return h->work_host[a] > h->work_host[b]; });
+    h->bwd_generic = (int)bord.size();
+    bord.resize(B, 0);
+    std::vector<int> ord(h->ord_host);
+    ord.insert(ord.end(), bord.begin(), bord.end());
+    const cudaError_t e = cudaMemcpy(h->order, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { set_err("cudaMemcpy(order)", e); return TMPC_ERR_CUDA; }
+    return TMPC_OK;
+}
+
+}  // namespace
+
 tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options* o, const tmpc_params* p) {
     if (!hp) return TMPC_ERR_INVALID_ARG;
     *hp = nullptr;
@@ -500,8 +633,8 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
-    int max_optin = 0;
-    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&h->max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int max_optin = h->max_optin;
     // work estimate for longest-processing-time-first ordering: (N+1) n^2
     auto work = [&](int i) {
         const ModelDims m = model_dims(Mh[i], d->nx, d->nu, d->ng);
@@ -511,7 +644,6 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
     // forward groups
     std::vector<int> ord;
     ord.reserve(2 * d->batch);
-    long long fmax = 0;
     for (int g = 0; g < 4; ++g) {
         std::vector<int> mem;
         for (int i = 0; i < d->batch; ++i) {
@@ -527,73 +659,23 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
         ord.insert(ord.end(), mem.begin(), mem.end());
         if (g < 3) {
             G.model = Mh[mem[0]];
-            // factorisation policy: solver 4 / 5 sequential LDL' by one warp, else cyclic reduction
-            G.policy = (o->solver == 4 || o->solver == 5) ? fast::kPolicyLDL : fast::kPolicyCR;
-            G.threads = o->threads > 0 ? o->threads : (G.policy == fast::kPolicyLDL ? 128 : 256);
-            int Tmax = 0;
-            for (int i : mem) Tmax = std::max(Tmax, Nh[i] + 1);
-            fmax = std::max(fmax, fast::arena_floats_host(G.model, Tmax, G.policy));
-            // shared arena: the longest instance if it fits with 2 CTAs per SM, else a
-            // third of the opt-in limit (longer instances use their global arena)
-            const long long need = sizeof(float) * fast::arena_floats_host(G.model, Tmax, G.policy);
-            const long long cap = std::max(48LL * 1024, (long long)max_optin / 2 - 8 * 1024);
-            G.smem = (size_t)std::min(need, need <= cap ? need : (long long)max_optin / 3);
-            if (o->solver == 3 || o->solver == 5) G.smem = 0;   // every arena in global memory
-            if (o->solver == 7) {   // plain per-phase form: global arenas, one CTA per instance
-                G.plain = 1;
-                G.policy = fast::kPolicyCR;
-                G.smem = 0;
-            }
-            // few instances whose arenas do not fit: one thread-block cluster per instance
-            const bool few_long = o->solver == 0 && need > cap && (long long)G.count * 8 <= h->nsm;
-            if (o->solver == 6 || few_long) {
-                G.policy = fast::kPolicyCR;
-                G.threads = o->threads > 0 ? o->threads : 256;
-                for (int cl = 16; cl >= 2 && G.cluster == 0; cl >>= 1) {
-                    int mc = 0;
-                    if (fast::prepare_cluster(G.model, G.policy, cl, G.threads, &mc) == cudaSuccess && mc >= 1) {
-                        G.cluster = cl;
-                        G.grid = std::min(G.count, mc);   // clusters
-                    }
-                }
-                cudaGetLastError();   // clear a refused cluster size
-                if (G.cluster == 0 && o->solver == 6) { tmpc_destroy(h); return TMPC_ERR_UNSUPPORTED; }
-                if (G.cluster > 0) fmax = std::max(fmax, fast::arena_floats_host(G.model, Tmax, G.policy, 1));
-            }
-            if (G.plain) {
-                G.grid = G.count;
-            } else if (G.cluster == 0) {
-                int per = 0;
-                e = fast::prepare(G.model, G.policy, G.smem, G.threads, &per);
-                if (e != cudaSuccess || per < 1) { set_err("fast::prepare", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
-                G.grid = std::max(1, std::min(G.count, per * h->nsm));
-            }
+            for (int i : mem) G.Tmax = std::max(G.Tmax, Nh[i] + 1);
+            // few instances whose arenas do not fit in shared memory: one thread-block cluster each
+            const bool few_long = o->solver == 0 && !shared_fits(h, G) && (long long)G.count * 8 <= h->nsm;
+            const int form = o->solver >= 2 ? o->solver : 2;
+            e = cudaErrorNotSupported;
+            if (few_long) e = configure_group(h, G, 6, o->threads);
+            if (e != cudaSuccess) e = configure_group(h, G, form, o->threads);
+            if (e == cudaErrorNotSupported && o->solver == 6) { tmpc_destroy(h); return TMPC_ERR_UNSUPPORTED; }
+            if (e != cudaSuccess) { set_err("fast::prepare", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
         } else {
             G.model = -1;
         }
     }
-    // backward: groups on the cyclic-reduction policy run the shared-memory
-    // backward over their forward order; every other instance (generic group,
-    // warp-LDL groups) the generic backward, longest first
-    std::vector<char> fastb(d->batch, 0);
-    for (int g = 0; g < h->n_groups; ++g) {
-        tmpc_handle::Group& G = h->groups[g];
-        if (G.model < 0 || G.policy != fast::kPolicyCR || o->solver == 1) continue;
-        int per = 0;
-        e = fast::prepare_backward(G.model, G.cluster, G.smem, G.threads, &per);
-        if (e != cudaSuccess || per < 1) { cudaGetLastError(); continue; }
-        G.bgrid = G.cluster > 0 ? G.grid : std::max(1, std::min(G.count, per * h->nsm));
-        for (int q = 0; q < G.count; ++q) fastb[ord[G.offset + q]] = 1;
-    }
-    std::vector<int> bord;
-    for (int i = 0; i < d->batch; ++i)
-        if (!fastb[i]) bord.push_back(i);
-    std::stable_sort(bord.begin(), bord.end(), by_work);
-    h->bwd_generic = (int)bord.size();
-    bord.resize(d->batch, 0);
-    ord.insert(ord.end(), bord.begin(), bord.end());
-    e = cudaMemcpy(h->order, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) { set_err("cudaMemcpy(order)", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
+    h->ord_host = ord;
+    h->work_host.resize(d->batch);
+    for (int i = 0; i < d->batch; ++i) h->work_host[i] = work(i);
+    if (tmpc_status st = plan_backward(h); st != TMPC_OK) { tmpc_destroy(h); return st; }
     if (h->n_groups > 1) {
         e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
         for (int g = 0; g < h->n_groups && e == cudaSuccess; ++g) {
@@ -602,23 +684,7 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
         }
         if (e != cudaSuccess) { set_err("group streams", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
     }
-    bool any_plain = false;
-    for (int g = 0; g < h->n_groups; ++g) any_plain = any_plain || h->groups[g].plain;
-    if (any_plain) {
-        e = cudaMalloc(&h->pstate, sizeof(fast::PlainState) * (size_t)d->batch);
-        if (e != cudaSuccess) { set_err("cudaMalloc(plain state)", e); tmpc_destroy(h); return TMPC_ERR_OOM; }
-    }
-    bool any_cluster = false;
-    for (int g = 0; g < h->n_groups; ++g) any_cluster = any_cluster || h->groups[g].cluster > 0;
-    if (any_cluster) {
-        e = cudaMalloc(&h->gflags, sizeof(int) * 4 * (size_t)d->batch);
-        if (e != cudaSuccess) { set_err("cudaMalloc(team flags)", e); tmpc_destroy(h); return TMPC_ERR_OOM; }
-    }
-    if (fmax > 0) {
-        h->fstride = (fmax + 31) & ~31LL;
-        e = cudaMalloc(&h->fws, sizeof(float) * h->fstride * d->batch);
-        if (e != cudaSuccess) { set_err("cudaMalloc(fast arenas)", e); tmpc_destroy(h); return TMPC_ERR_OOM; }
-    }
+    if (tmpc_status st = ensure_buffers(h); st != TMPC_OK) { tmpc_destroy(h); return st; }
 
     h->threads = o->threads > 0 ? o->threads : (n <= 16 ? 128 : 256);
     // ADMM vectors in shared memory when two CTAs per SM still fit
@@ -695,6 +761,27 @@ tmpc_status tmpc_set_options(tmpc_handle* h, const tmpc_options* o) {
     return TMPC_OK;
 }
 
+// the forward launch(es) of group g on stream s
+static tmpc_status launch_group(tmpc_handle* h, int g, const KOpts& ko, const KParams& kp, const KSol& ks,
+                                const float* x0, int warm, cudaStream_t s) {
+    const tmpc_handle::Group& G = h->groups[g];
+    if (G.model >= 0 && G.plain) {
+        TMPC_CUDA(fast::launch_plain(G.model, G.threads, s, h->L, ko, kp, ks, h->fws, h->fstride,
+                                     h->order + G.offset, G.count, x0, warm, h->pstate));
+    } else if (G.model >= 0 && G.cluster > 0) {
+        TMPC_CUDA(fast::launch_cluster(G.model, G.policy, G.cluster, G.grid, G.threads, s, h->L, ko, kp, ks,
+                                       h->fws, h->fstride, h->order + G.offset, G.count, x0, warm, h->gflags));
+    } else if (G.model >= 0) {
+        TMPC_CUDA(fast::launch(G.model, G.policy, G.grid, G.threads, G.smem, s, h->L, ko, kp, ks, h->fws, h->fstride,
+                               h->order + G.offset, G.count, h->queue + g, x0, warm));
+    } else {
+        solve_kernel<<<std::min(h->grid_solve, G.count), h->threads, h->smem, s>>>(
+            h->L, ko, kp, ks, h->ws, h->off, h->order + G.offset, G.count, h->queue + g, x0, warm);
+        TMPC_CUDA(cudaGetLastError());
+    }
+    return TMPC_OK;
+}
+
 static tmpc_status launch_solve(tmpc_handle* h, const tmpc_params& p, const float* x0,
                                 const tmpc_solution& out, int warm, cudaStream_t s) {
     KSol ks{out.z, out.xi, out.y_eq, out.y_ineq, out.status, out.stats};
@@ -705,25 +792,11 @@ static tmpc_status launch_solve(tmpc_handle* h, const tmpc_params& p, const floa
     const cudaStream_t s0 = s;
     if (fork) TMPC_CUDA(cudaEventRecord(h->ev_fork, s0));
     for (int g = 0; g < h->n_groups; ++g) {
-        const tmpc_handle::Group& G = h->groups[g];
         if (fork) {
             s = h->gs[g];
             TMPC_CUDA(cudaStreamWaitEvent(s, h->ev_fork, 0));
         }
-        if (G.model >= 0 && G.plain) {
-            TMPC_CUDA(fast::launch_plain(G.model, G.threads, s, h->L, ko, kp, ks, h->fws, h->fstride,
-                                         h->order + G.offset, G.count, x0, warm, h->pstate));
-        } else if (G.model >= 0 && G.cluster > 0) {
-            TMPC_CUDA(fast::launch_cluster(G.model, G.policy, G.cluster, G.grid, G.threads, s, h->L, ko, kp, ks,
-                                           h->fws, h->fstride, h->order + G.offset, G.count, x0, warm, h->gflags));
-        } else if (G.model >= 0) {
-            TMPC_CUDA(fast::launch(G.model, G.policy, G.grid, G.threads, G.smem, s, h->L, ko, kp, ks, h->fws, h->fstride,
-                                   h->order + G.offset, G.count, h->queue + g, x0, warm));
-        } else {
-            solve_kernel<<<std::min(h->grid_solve, G.count), h->threads, h->smem, s>>>(
-                h->L, ko, kp, ks, h->ws, h->off, h->order + G.offset, G.count, h->queue + g, x0, warm);
-            TMPC_CUDA(cudaGetLastError());
-        }
+        if (tmpc_status st = launch_group(h, g, ko, kp, ks, x0, warm, s); st != TMPC_OK) return st;
         if (fork) TMPC_CUDA(cudaEventRecord(h->ev_join[g], s));
     }
     if (fork)
@@ -737,6 +810,113 @@ tmpc_status tmpc_solve(tmpc_handle* h, const float* x0, tmpc_solution* out, int3
     if (!aligned4(x0) || !aligned4(out->z) || !aligned4(out->xi) || !aligned4(out->y_eq) || !aligned4(out->y_ineq))
         return TMPC_ERR_INVALID_ARG;
     return launch_solve(h, h->p, x0, *out, warm_start ? 1 : 0, reinterpret_cast<cudaStream_t>(stream));
+}
+
+tmpc_status tmpc_autotune(tmpc_handle* h, const float* x0, const tmpc_solution* init, int32_t reps,
+                          int32_t trial_sqp, tmpc_tune_result* res, void* stream) {
+    if (!h) return TMPC_ERR_NOT_SETUP;
+    if (!x0 || !aligned4(x0) || reps < 1 || reps > 1000 || trial_sqp < 0) return TMPC_ERR_INVALID_ARG;
+    if (init && (!init->z || !init->xi || !init->y_eq || !init->y_ineq)) return TMPC_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    KOpts ko = to_kopts(h->o);
+    if (trial_sqp > 0) ko.max_sqp = std::min(ko.max_sqp, trial_sqp);
+    const KParams kp = to_kparams(h->p);
+    // trial outputs go to the staging buffers of tmpc_solve_host
+    const KSol ks{h->ss.z, h->ss.xi, h->ss.y_eq, h->ss.y_ineq, h->ss.status, h->ss.stats};
+    const long long B = h->d.batch, T = h->d.N_max + 1;
+    const size_t bz = sizeof(float) * B * T * h->L.n, bg = sizeof(float) * B * T * h->d.ng,
+                 bf = sizeof(float) * B * T * h->d.nx;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    TMPC_CUDA(cudaEventCreate(&ev[0]));
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) { cudaEventDestroy(ev[0]); return TMPC_ERR_CUDA; }
+    tmpc_status st = TMPC_OK;
+    // device milliseconds of one forward launch of group g in its current form,
+    // from the caller's warm start when one is given (its copy is timed too)
+    auto time_group = [&](int g, float* ms) -> tmpc_status {
+        if (tmpc_status e = ensure_buffers(h); e != TMPC_OK) return e;
+        TMPC_CUDA(cudaEventRecord(ev[0], s));
+        if (init) {
+            TMPC_CUDA(cudaMemcpyAsync(h->ss.z, init->z, bz, cudaMemcpyDeviceToDevice, s));
+            TMPC_CUDA(cudaMemcpyAsync(h->ss.xi, init->xi, bg, cudaMemcpyDeviceToDevice, s));
+            TMPC_CUDA(cudaMemcpyAsync(h->ss.y_eq, init->y_eq, bf, cudaMemcpyDeviceToDevice, s));
+            TMPC_CUDA(cudaMemcpyAsync(h->ss.y_ineq, init->y_ineq, bg, cudaMemcpyDeviceToDevice, s));
+        }
+        TMPC_CUDA(cudaMemsetAsync(h->queue + g, 0, sizeof(int), s));
+        if (tmpc_status e = launch_group(h, g, ko, kp, ks, x0, init ? 1 : 0, s); e != TMPC_OK) return e;
+        TMPC_CUDA(cudaEventRecord(ev[1], s));
+        TMPC_CUDA(cudaEventSynchronize(ev[1]));
+        TMPC_CUDA(cudaEventElapsedTime(ms, ev[0], ev[1]));
+        return TMPC_OK;
+    };
+    struct Cand { int form, threads; };
+    for (int g = 0; g < h->n_groups && st == TMPC_OK; ++g) {
+        tmpc_handle::Group& G = h->groups[g];
+        tmpc_tune_result r{G.model, G.count, G.form, G.threads, G.cluster, 0, -1.f, -1.f};
+        if (G.model < 0 || h->o.solver != 0) {   // generic kernel, or a form fixed by the options
+            if (res) res[g] = r;
+            continue;
+        }
+        const int def_form = G.form, def_threads = G.threads;
+        const int t_full = h->o.threads > 0 ? h->o.threads : 256, t_half = h->o.threads > 0 ? h->o.threads : 128;
+        std::vector<Cand> cands{{def_form, def_threads}};
+        std::vector<Cand> more{{2, t_full}, {2, t_half}, {4, t_half}, {3, t_full}, {7, t_full}};
+        if ((long long)G.count * 8 <= 2LL * h->nsm) more.push_back({6, t_full});   // about one wave of clusters
+        for (const Cand& c : more) {
+            bool seen = false;
+            for (const Cand& d : cands) seen = seen || (d.form == c.form && d.threads == c.threads);
+            if (!seen) cands.push_back(c);
+        }
+        const size_t nc = cands.size();
+        std::vector<float> first(nc, -1.f), best(nc, -1.f);
+        // clocks up: the setup's form until about 20 ms of device time (at most 10 launches)
+        float warm_ms = 0.f;
+        for (int k = 0; k < 10 && warm_ms < 20.f && st == TMPC_OK; ++k) {
+            float ms = 0.f;
+            if (configure_group(h, G, def_form, def_threads) != cudaSuccess) { st = TMPC_ERR_CUDA; break; }
+            st = time_group(g, &ms);
+            warm_ms += ms;
+        }
+        // one launch per form; forms four times slower than the fastest first launch are dropped
+        for (size_t k = 0; k < nc && st == TMPC_OK; ++k) {
+            if (configure_group(h, G, cands[k].form, cands[k].threads) != cudaSuccess) { cudaGetLastError(); continue; }
+            st = time_group(g, &first[k]);
+        }
+        float fmin = -1.f;
+        for (size_t k = 0; k < nc; ++k)
+            if (first[k] >= 0.f && (fmin < 0.f || first[k] < fmin)) fmin = first[k];
+        // reps interleaved rounds over the remaining forms; a form's time is its fastest launch
+        for (int rep = 0; rep < reps && st == TMPC_OK; ++rep)
+            for (size_t k = 0; k < nc && st == TMPC_OK; ++k) {
+                if (first[k] < 0.f || first[k] > 4.f * fmin) continue;
+                if (configure_group(h, G, cands[k].form, cands[k].threads) != cudaSuccess) { st = TMPC_ERR_CUDA; break; }
+                float ms = 0.f;
+                st = time_group(g, &ms);
+                if (best[k] < 0.f || ms < best[k]) best[k] = ms;
+            }
+        size_t kb = 0;
+        for (size_t k = 0; k < nc; ++k) {
+            if (best[k] < 0.f) continue;
+            ++r.candidates;
+            if (best[kb] < 0.f || best[k] < best[kb]) kb = k;
+        }
+        if (st != TMPC_OK || best[kb] < 0.f || configure_group(h, G, cands[kb].form, cands[kb].threads) != cudaSuccess) {
+            cudaGetLastError();
+            configure_group(h, G, def_form, def_threads);
+            kb = 0;
+        }
+        r.solver = G.form;
+        r.threads = G.threads;
+        r.cluster = G.cluster;
+        r.ms = best[kb];
+        r.ms_default = best[0] >= 0.f ? best[0] : first[0];
+        if (res) res[g] = r;
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (st != TMPC_OK) return st;
+    if (tmpc_status e = ensure_buffers(h); e != TMPC_OK) return e;
+    TMPC_CUDA(cudaStreamSynchronize(s));
+    return plan_backward(h);
 }
 
 tmpc_status tmpc_backward(tmpc_handle* h, const float* x0, const tmpc_solution* sol, const float* dL_dz,

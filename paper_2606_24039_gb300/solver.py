@@ -155,6 +155,19 @@ class Solver:
                                           ctypes.byref(g), _stream_ptr(stream)), "tmpc_backward")
         return grads
 
+    def tmpc_autotune(self, x0, init=None, reps=3, trial_sqp=0, stream=None):
+        """Time each launch form of every model group on x0 and keep the fastest
+        (synchronous).  init: a solution dict read as the trials' warm start (not
+        written); None starts cold.  Returns one dict per group (fields of
+        tmpc_tune_result)."""
+        res = (_abi.TuneResult * 4)()
+        si = None if init is None else self._sol_struct(init)
+        _abi.check(self.lib.tmpc_autotune(self.handle, ctypes.c_void_p(x0.data_ptr()),
+                                          None if si is None else ctypes.byref(si), int(reps),
+                                          int(trial_sqp), res, _stream_ptr(stream)), "tmpc_autotune")
+        # entries of absent groups are left as zeroed by ctypes (count 0)
+        return [{f: getattr(r, f) for f, _ in _abi.TuneResult._fields_} for r in res if r.count > 0]
+
     def tmpc_solve_host(self, host_params: dict, x0_host, out_host: dict, stream=None, z_init_host=None):
         """End-to-end solve from pinned host tensors (copies inside the call)."""
         p = _abi.Params()

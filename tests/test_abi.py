@@ -64,6 +64,8 @@ def test_setup_rejects_bad_arguments_without_a_gpu(lib):
     # calls on a null handle
     assert lib.tmpc_solve(None, None, None, 0, None) == 4
     assert lib.tmpc_backward(None, None, None, None, None, None, None) == 4
+    assert lib.tmpc_autotune(None, None, None, 1, 1, None, None) == 4
+    assert ctypes.sizeof(_abi.TuneResult) == 32
     lib.tmpc_destroy(None)
     assert lib.tmpc_status_string(0) == b"ok"
 

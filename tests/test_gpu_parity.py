@@ -294,6 +294,48 @@ def test_cluster_team_matches_oracle_and_single_cta():
     _compare(pb, b, range(3))
 
 
+def test_autotune_keeps_a_timed_form_and_parity():
+    """tmpc_autotune times every launch form of each model group and keeps the
+    fastest.  After tuning, the forward solve meets the oracle bar, and the
+    forward and the backward of each group equal, bit for bit, those of a handle
+    fixed to the group's chosen form at setup."""
+    from paper_2606_24039_gb300 import Solver
+    pb = w.uneven(B=12, N_lo=10, N_hi=40, seed=77, max_sqp=4, max_admm=50)
+    s = Solver.from_batch(pb, device="cuda")
+    init = s.alloc_solution("cuda")
+    for k in ("z", "xi", "y_eq", "y_ineq"):
+        init[k].zero_()
+    if s.z_init is not None:
+        init["z"].copy_(s.z_init)
+    keep = {k: init[k].clone() for k in ("z", "xi", "y_eq", "y_ineq")}
+    res = s.tmpc_autotune(s.x0, init=init, reps=2, trial_sqp=1)
+    for k, v in keep.items():   # the warm start is read, not written
+        assert torch.equal(init[k], v), k
+    fast = [r for r in res if r["model"] >= 0]
+    assert sum(r["count"] for r in res) == 12 and fast
+    for r in fast:
+        assert r["candidates"] >= 5, r
+        assert r["solver"] in (2, 3, 4, 6, 7), r
+        assert 0.0 < r["ms"] <= r["ms_default"], r
+    sol_d = s.tmpc_solve(s.x0, z_init=s.z_init)
+    gen = torch.Generator().manual_seed(5)
+    dz = torch.randn(sol_d["z"].shape, generator=gen).to("cuda")
+    gr = s.tmpc_backward(s.x0, sol_d, dz)
+    torch.cuda.synchronize()
+    sol = {k: v.cpu().numpy() for k, v in sol_d.items()}
+    _compare(pb, sol, range(12), sensitivity=True)
+    for r in fast:
+        idx = np.flatnonzero(np.asarray(pb.model) == r["model"])
+        f = Solver.from_batch(pb, device="cuda", solver=r["solver"], threads=r["threads"])
+        fsol_d = f.tmpc_solve(f.x0, z_init=f.z_init)
+        fgr = f.tmpc_backward(f.x0, fsol_d, dz)
+        torch.cuda.synchronize()
+        for k in ("z", "xi", "y_eq", "y_ineq", "status"):
+            assert np.array_equal(sol[k][idx], fsol_d[k].cpu().numpy()[idx]), (r, k)
+        for k, v in gr.items():
+            assert np.array_equal(v.cpu().numpy()[idx], fgr[k].cpu().numpy()[idx]), (r, k)
+
+
 @pytest.mark.parametrize("solver", SOLVERS + [pytest.param(6, id="cluster_cr")])
 def test_long_racing_instances_one_sqp_step(solver):
     """Racing instances of 300 to 400 stages (global-memory arenas on the
