@@ -877,6 +877,124 @@ __device__ __forceinline__ void project(float v, float lo, float hi, float rho_g
     }
 }
 
+// ---------------------------------------------------------------------------
+// The linear model's C: A- = [A B], the same block at every stage, and
+// A+ = [-I 0].  With n and nx multiples of 4 the C' and C products of all
+// stages run as register tiles (4 stages x 4 entries per thread, 128-bit
+// loads of A- rows and of the stage vectors) instead of one serial dot
+// product per entry.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool tiled_linear(const Ctx& c) {
+    return c.model == MODEL_LINEAR && (c.n & 3) == 0 && (c.nx & 3) == 0 && c.amS == 0;
+}
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+
+// acc[b][a] += sum over the 4 columns of rows a of `ar` dotted with v[b]
+__device__ __forceinline__ void tile_fma(float (&acc)[4][4], const float4 (&ar)[4], const float4 (&v)[4]) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            float s = acc[b][a];
+            s = fmaf(ar[a].x, v[b].x, s);
+            s = fmaf(ar[a].y, v[b].y, s);
+            s = fmaf(ar[a].z, v[b].z, s);
+            s = fmaf(ar[a].w, v[b].w, s);
+            acc[b][a] = s;
+        }
+}
+
+// eta = -(P x + q) - C'w - G'(y_g + rho_g p_g) with w_r = y_f,r + rho_f p_f,r in
+// W (T rows of nx).  Tile (t0, j0): stages t0..t0+3, entries j0..j0+3;
+// (C'w)_t,j = [t < N] (A-' w_{t+1})_j + [j < nx] ([t = 0] w_0,j - [t > 0] w_t,j).
+__device__ __forceinline__ void rhs_tiled(const Ctx& c, const float* W, float rho_g) {
+    const int n = c.n, nx = c.nx, ng = c.ng, T = c.T, N = c.N;
+    const int nj = n >> 2, ntile = nj * ((T + 3) >> 2);
+    const float* Am = c.Amt(0);
+    for (int w = threadIdx.x; w < ntile; w += blockDim.x) {
+        const int j0 = (w % nj) << 2, t0 = (w / nj) << 2;
+        float acc[4][4];
+        const float* wr[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            wr[b] = W + min(t0 + b + 1, N) * nx;   // stages t >= N take no A- term (zeroed below)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[b][a] = 0.f;
+        }
+        for (int k = 0; k < nx; k += 4) {
+            float4 ar[4], v[4];   // ar[a] = column j0 + a of A- over rows k..k+3
+            const float4 r0 = ldg4(Am + (k + 0) * n + j0), r1 = ldg4(Am + (k + 1) * n + j0);
+            const float4 r2 = ldg4(Am + (k + 2) * n + j0), r3 = ldg4(Am + (k + 3) * n + j0);
+            ar[0] = make_float4(r0.x, r1.x, r2.x, r3.x);
+            ar[1] = make_float4(r0.y, r1.y, r2.y, r3.y);
+            ar[2] = make_float4(r0.z, r1.z, r2.z, r3.z);
+            ar[3] = make_float4(r0.w, r1.w, r2.w, r3.w);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) v[b] = ld4(wr[b] + k);
+            tile_fma(acc, ar, v);
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int t = t0 + b;
+            if (t >= T) break;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int j = j0 + a;
+                float s = t < N ? acc[b][a] : 0.f;
+                if (j < nx) s += (t == 0) ? W[j] : -W[t * nx + j];
+                float e = -(Px_entry(c, c.x, t, j) + c.qv[t * n + j]) - s;
+                const int r = g_row(c, j);
+                if (r >= 0) e -= c.yg[t * ng + r] + rho_g * c.pg[t * ng + r];
+                c.eta[t * n + j] = e;
+            }
+        }
+    }
+}
+
+// cd = C dx row by row and the y_f / p_f updates of the equality rows:
+// row 0 is dx_0; row t + 1 is A- dx_t - dx_{t+1}.  Tile (t0, k0): stages
+// t0..t0+3 (rows t0+1..t0+4), rows k0..k0+3 of A-.
+__device__ __forceinline__ void update_eq_tiled(const Ctx& c, const float* dx, float rho_f, float alpha) {
+    const int n = c.n, nx = c.nx, N = c.N;
+    const int nk = nx >> 2, ntile = nk * ((N + 3) >> 2);
+    const float* Am = c.Amt(0);
+    auto upd = [&](int e, float cd) {
+        c.yf[e] += rho_f * alpha * (c.pf[e] + cd);
+        c.pf[e] += alpha * cd;
+    };
+    for (int w = threadIdx.x; w < ntile; w += blockDim.x) {
+        const int k0 = (w % nk) << 2, t0 = (w / nk) << 2;
+        float acc[4][4];
+        const float* xr[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            xr[b] = dx + min(t0 + b, N - 1) * n;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[b][a] = 0.f;
+        }
+        for (int j = 0; j < n; j += 4) {
+            float4 ar[4], v[4];   // ar[a] = row k0 + a of A- over columns j..j+3
+#pragma unroll
+            for (int a = 0; a < 4; ++a) ar[a] = ldg4(Am + (k0 + a) * n + j);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) v[b] = ld4(xr[b] + j);
+            tile_fma(acc, ar, v);
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int t = t0 + b;
+            if (t >= N) break;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int k = k0 + a;
+                upd((t + 1) * nx + k, acc[b][a] - dx[(t + 1) * n + k]);
+            }
+        }
+    }
+    for (int k = threadIdx.x; k < nx; k += blockDim.x) upd(k, dx[k]);
+}
+
 // one ADMM iteration (Algorithm 3) in increment form.  With p_f = C x - c
 // (tracked, never recomputed from absolute values) and p_g = G x - z_g, the
 // primal system S xt = eta is solved for the increment dx = xt - x:
@@ -888,9 +1006,13 @@ __device__ __forceinline__ void project(float v, float lo, float hi, float rho_g
 __device__ inline void admm_iter(const Ctx& c, const KOpts& o, float rho_bar, const Smem& sm) {
     const int n = c.n, nx = c.nx, ng = c.ng, T = c.T;
     const float rho_f = 1e3f * rho_bar, rho_g = rho_bar, alpha = o.alpha;
+    const bool tiled = tiled_linear(c);
     for (int e = threadIdx.x; e < T * ng; e += blockDim.x) c.pg[e] = Gx_entry(c, c.x, e / ng, e % ng) - c.zg[e];
+    if (tiled)   // w = y_f + rho_f p_f into xt (free until the solve writes it)
+        for (int e = threadIdx.x; e < T * nx; e += blockDim.x) c.xt[e] = c.yf[e] + rho_f * c.pf[e];
     __syncthreads();
-    for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
+    if (tiled) rhs_tiled(c, c.xt, rho_g);
+    else for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
         const int t = e / n, j = e % n;
         float s = -(Px_entry(c, c.x, t, j) + c.qv[e]);
         s -= Ct_entry(c, t, j, [&](int r, int k) { return c.yf[r * nx + k] + rho_f * c.pf[r * nx + k]; });
@@ -905,7 +1027,8 @@ __device__ inline void admm_iter(const Ctx& c, const KOpts& o, float rho_bar, co
     }
     __syncthreads();
     ldl_solve(c, c.eta, c.xt, sm.red8, sm.A, sm.Bm, sm.mbar, sm.flags + 12);
-    for (int e = threadIdx.x; e < T * nx; e += blockDim.x) {
+    if (tiled) update_eq_tiled(c, c.xt, rho_f, alpha);
+    else for (int e = threadIdx.x; e < T * nx; e += blockDim.x) {
         const float cd = Cx_entry(c, c.xt, e / nx, e % nx);
         c.yf[e] += rho_f * alpha * (c.pf[e] + cd);
         c.pf[e] += alpha * cd;
