@@ -529,6 +529,103 @@ __device__ inline void linearize(const Ctx& c) {
 }
 
 // ---------------------------------------------------------------------------
+// Dense n x n block products for n a multiple of 4: register tiles of 4 x 4
+// entries per thread with 128-bit loads (shared or global memory).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 ldv4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void stv4(float* p, float a, float b, float c, float d) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+// acc[a][b] += sum_k X[k][i0 + a] Y[k][j0 + b]   (X, Y: K rows of length ld)
+__device__ __forceinline__ void tile_xty(float (&acc)[4][4], const float* X, const float* Y, int K, int ld,
+                                         int i0, int j0) {
+    for (int k = 0; k < K; ++k) {
+        const float4 x = ldv4(X + k * ld + i0), y = ldv4(Y + k * ld + j0);
+        const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xs[a], ys[b], acc[a][b]);
+    }
+}
+// acc[a][b] += sum_k X[i0 + a][k] Y[j0 + b][k]   (rows of length ld, K % 4 == 0)
+__device__ __forceinline__ void tile_xyt(float (&acc)[4][4], const float* X, const float* Y, int K, int ld,
+                                         int i0, int j0) {
+    for (int k = 0; k < K; k += 4) {
+        float4 xr[4], yr[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) xr[a] = ldv4(X + (i0 + a) * ld + k);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) yr[b] = ldv4(Y + (j0 + b) * ld + k);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                float s = acc[a][b];
+                s = fmaf(xr[a].x, yr[b].x, s);
+                s = fmaf(xr[a].y, yr[b].y, s);
+                s = fmaf(xr[a].z, yr[b].z, s);
+                s = fmaf(xr[a].w, yr[b].w, s);
+                acc[a][b] = s;
+            }
+    }
+}
+
+// In-place inverse of the symmetric positive definite n x n matrix A (n % 4 == 0,
+// row-major) by Gauss-Jordan sweeps over the pivots k = 0 .. n-1 (no pivoting:
+// the pivots are the Schur complements' leading entries, positive for SPD A).
+// Sweep k with pivot p = A_kk, column c and row r of A before the sweep:
+//   A_kk <- 1/p,  A_kj <- r_j / p,  A_ik <- -c_i / p,  A_ij <- A_ij - c_i r_j / p.
+// snap (4n floats) holds the pivot column and row, double-buffered: the threads
+// that write column / row k+1 also write the next sweep's copy, so each sweep
+// needs one barrier.  A pivot that is not positive sets *flag and is taken as 1.
+__device__ inline void gj_inverse(float* A, int n, float* snap, int* flag) {
+    const int nq = n >> 2, ngrp = n * nq;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        snap[i] = A[i * n];
+        snap[n + i] = A[i];
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        const float* col = snap + (k & 1) * 2 * n;
+        const float* row = col + n;
+        float* ncol = snap + ((k + 1) & 1) * 2 * n;
+        float* nrow = ncol + n;
+        float p = col[k];
+        if (!(p > 0.f)) {
+            if (threadIdx.x == 0) *flag = 1;
+            p = 1.f;
+        }
+        const float ip = 1.f / p;
+        for (int g = threadIdx.x; g < ngrp; g += blockDim.x) {
+            const int i = g / nq, j0 = (g % nq) << 2;
+            const float4 a4 = ldv4(A + i * n + j0), r4 = ldv4(row + j0);
+            const float ci = col[i], cs = -ci * ip;
+            float v[4] = {a4.x, a4.y, a4.z, a4.w};
+            const float rr[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = j0 + q;
+                if (i == k) v[q] = (j == k) ? ip : rr[q] * ip;
+                else if (j == k) v[q] = cs;
+                else v[q] = fmaf(cs, rr[q], v[q]);
+            }
+            stv4(A + i * n + j0, v[0], v[1], v[2], v[3]);
+            if (k + 1 < n) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (j0 + q == k + 1) ncol[i] = v[q];
+                if (i == k + 1) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) nrow[j0 + q] = v[q];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // S = P + sigma I + rho_f C'C + G' diag(w) G (Theta_t, Phi_t of App. C) and its
 // block LDL' factorisation, sequential over stages:
 //   Delta_0 = Theta_0,  Om_t = Phi_t Delta_t^{-1},  Delta_{t+1} = Theta_{t+1} - Om_t Phi_t'
@@ -537,8 +634,8 @@ __device__ inline void linearize(const Ctx& c) {
 // Returns false if a pivot block was not positive definite (the factors are then
 // not usable; the failing pivot is replaced by 1 so that no inf/NaN is produced).
 // ---------------------------------------------------------------------------
-__device__ inline bool factor(const Ctx& c, const Smem& sm, float sigma, float rho_f, float rho_g,
-                       bool use_gw) {
+__device__ inline bool factor_rows(const Ctx& c, const Smem& sm, float sigma, float rho_f, float rho_g,
+                            bool use_gw) {
     if (threadIdx.x == 0) sm.flags[1] = 0;
     const int n = c.n, nx = c.nx, ng = c.ng, N = c.N, nn = n * n;
     float* A = sm.A;   // Delta_t -> Cholesky factor L -> Dinv
@@ -636,6 +733,121 @@ __device__ inline bool factor(const Ctx& c, const Smem& sm, float sigma, float r
     const bool ok = sm.flags[1] == 0;
     __syncthreads();
     return ok;
+}
+
+// The same factorisation for n a multiple of 4 (n >= 16): Theta_t - Om_{t-1} Phi_{t-1}',
+// Phi_t and Om_t = Phi_t Dinv_t (Dinv_t symmetric) as register tiles, the pivot block
+// inverted in place by gj_inverse.  Om_{t-1} and Phi_{t-1} stay in shared memory
+// for the next stage; Phi_t is formed once when A- and A+ are constant.
+__device__ inline bool factor_tiled(const Ctx& c, const Smem& sm, float sigma, float rho_f, float rho_g,
+                                    bool use_gw) {
+    if (threadIdx.x == 0) sm.flags[1] = 0;
+    const int n = c.n, nx = c.nx, ng = c.ng, N = c.N, nn = n * n, nb = n >> 2, ntile = nb * nb;
+    float* A = sm.A;     // Delta_t, inverted in place
+    float* Om = sm.Bm;   // Om_{t-1}
+    float* Ph = sm.Cm;   // Phi_{t-1}
+    const bool sel = g_is_selector(c), const_phi = c.amS == 0 && c.apS == 0;
+    for (int t = 0; t <= N; ++t) {
+        const float* Amt = c.Amt(t);
+        const float* Apm = t > 0 ? c.Apt(t - 1) : nullptr;
+        const float* G = c.Gt(t);
+        // Delta_t = Theta_t - Om_{t-1} Phi_{t-1}'
+        for (int w = threadIdx.x; w < ntile; w += blockDim.x) {
+            const int i0 = (w / nb) << 2, j0 = (w % nb) << 2;
+            float acc[4][4], sch[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = sch[a][b] = 0.f;
+            if (t < N) tile_xty(acc, Amt, Amt, nx, n, i0, j0);
+            if (t > 0) {
+                tile_xty(acc, Apm, Apm, nx, n, i0, j0);
+                tile_xyt(sch, Om, Ph, n, n, i0, j0);
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                float v[4];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int i = i0 + a, j = j0 + b;
+                    float s = acc[a][b];
+                    if (t == 0 && i == j && i < nx) s += 1.f;  // A_init' A_init
+                    float u = rho_f * s;
+                    if (sel) {
+                        if (i == j) {
+                            const int r = g_row(c, i);
+                            if (r >= 0) u += use_gw ? c.gw[t * ng + r] : rho_g;
+                        }
+                    } else {
+                        for (int r = 0; r < ng; ++r)
+                            u += (use_gw ? c.gw[t * ng + r] : rho_g) * G[r * n + i] * G[r * n + j];
+                    }
+                    if (i == j) u += c.Pdiag(t, i) + sigma;
+                    v[b] = u - sch[a][b];
+                }
+                stv4(A + (i0 + a) * n + j0, v[0], v[1], v[2], v[3]);
+            }
+        }
+        __syncthreads();
+        gj_inverse(A, n, sm.red8, sm.flags + 1);
+        float* Dinv = c.Dinv + t * nn;
+        for (int e = threadIdx.x << 2; e < nn; e += blockDim.x << 2) {
+            const float4 d = ldv4(A + e);
+            stv4(Dinv + e, d.x, d.y, d.z, d.w);
+        }
+        if (t < N) {
+            if (t == 0 || !const_phi) {   // Phi_t = E_t + rho_f A+_t' A-_t
+                const float* Apt = c.Apt(t);
+                for (int w = threadIdx.x; w < ntile; w += blockDim.x) {
+                    const int i0 = (w / nb) << 2, j0 = (w % nb) << 2;
+                    float acc[4][4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+                    tile_xty(acc, Apt, Amt, nx, n, i0, j0);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        float v[4];
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const int i = i0 + a, j = j0 + b;
+                            v[b] = rho_f * acc[a][b];
+                            if (i == j && i >= nx) v[b] -= c.W(i - nx);
+                        }
+                        stv4(Ph + (i0 + a) * n + j0, v[0], v[1], v[2], v[3]);
+                    }
+                }
+                __syncthreads();
+            }
+            // Om_t = Phi_t Dinv_t = Phi_t Dinv_t'  (shared copy for stage t + 1, and the workspace)
+            float* Omg = c.Om + t * nn;
+            for (int w = threadIdx.x; w < ntile; w += blockDim.x) {
+                const int i0 = (w / nb) << 2, j0 = (w % nb) << 2;
+                float acc[4][4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+                tile_xyt(acc, Ph, A, n, n, i0, j0);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    stv4(Om + (i0 + a) * n + j0, acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+                    stv4(Omg + (i0 + a) * n + j0, acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const bool ok = sm.flags[1] == 0;
+    __syncthreads();
+    return ok;
+}
+
+__device__ inline bool factor(const Ctx& c, const Smem& sm, float sigma, float rho_f, float rho_g,
+                       bool use_gw) {
+    if (c.n % 4 == 0 && c.n >= 16) return factor_tiled(c, sm, sigma, rho_f, rho_g, use_gw);
+    return factor_rows(c, sm, sigma, rho_f, rho_g, use_gw);
 }
 
 // Solve S x = b with the block LDL' factors; b (T x n) is overwritten by the

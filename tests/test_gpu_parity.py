@@ -415,11 +415,12 @@ def test_host_entry_point_matches_device_entry_point():
         assert torch.equal(ho[k], dev[k].cpu()), k
 
 
-@pytest.mark.parametrize("nx,nu", [(12, 5), (24, 10)], ids=["n17", "n34"])
+@pytest.mark.parametrize("nx,nu", [(12, 5), (24, 10), (24, 8)], ids=["n17", "n34", "n32"])
 def test_backward_matches_oracle_on_oracle_solution(nx, nu):
     """The backward kernel is fed the oracle's FP64 solution (rounded to FP32) so
-    that the comparison isolates Algorithm 2 (n = 34 takes the warp-cooperative
-    block solves of the generic kernel)."""
+    that the comparison isolates Algorithm 2 (n = 34 and n = 32 take the
+    warp-cooperative block solves of the generic kernel; n = 32 also the tiled
+    factorisation with the Gauss-Jordan pivot inverse)."""
     pb = w.tracking(B=3, nx=nx, nu=nu, N=16, seed=31, max_admm=3000)
     pb.x0 *= 4.0
     opts = dataclasses.replace(pb.opts, early_exit=1, eps_abs=1e-10, eps_rel=1e-10)
