@@ -97,8 +97,40 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
     // rho_b tenfold, refactor and restart (at most three times)
     float d0 = 0.f, dprev = kInf;
     int restarts = 0;
+    const bool tiled = tiled_linear(c);
     for (int it = 0; it < o.bwd_iters; ++it) {
         for (int e = threadIdx.x; e < T * ng; e += blockDim.x) gz[e] = Gx_entry(c, ex, e / ng, e % ng);
+        if (tiled) {
+            // the same sweep with the C and C' products as register tiles:
+            // r2 = -C eta_x; eta = b - H_r eta_x - C'(lam - rho_b r2) - G_H' mu + rho_b G_H' r3
+            c_tiled(c, ex, [&](int e, float v) { r2[e] = -v; });
+            __syncthreads();
+            for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
+                const float cd = code[e];
+                r3[e] = (cd != 0.f && fabsf(cd) < 1.5f) ? -gz[e] : 0.f;
+            }
+            for (int e = threadIdx.x; e < T * nx; e += blockDim.x) c.xt[e] = lam[e] - rb * r2[e];
+            __syncthreads();
+            ct_tiled(c, c.xt, [&](int t, int j, float ctw) {
+                float s = bx[t * n + j] - Px_entry(c, ex, t, j) - ctw;
+                const int r = g_row(c, j);   // selector rows of the linear model
+                if (r >= 0) {
+                    const float cd = code[t * ng + r];
+                    if (fabsf(cd) > 1.5f) s -= c.gam2(r) * gz[t * ng + r];
+                    else if (cd != 0.f) s -= mu[t * ng + r];
+                    s += rb * r3[t * ng + r];
+                }
+                c.eta[t * n + j] = s;
+            });
+            __syncthreads();
+            ldl_solve(c, c.eta, c.xt, sm.red8, sm.A, sm.Bm, sm.mbar, sm.flags + 12);  // dx
+            c_tiled(c, c.xt, [&](int e, float v) { lam[e] += rb * (v - r2[e]); });
+            for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
+                const float cd = code[e];
+                if (cd != 0.f && fabsf(cd) < 1.5f) mu[e] += rb * (Gx_entry(c, c.xt, e / ng, e % ng) - r3[e]);
+            }
+            __syncthreads();
+        } else {
         __syncthreads();
         // r1 = b - H_r eta_x - C' lam - G_H' mu   (into eta), r2 = -C eta_x, r3 = -G_H eta_x
         for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
@@ -148,6 +180,7 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
             if (cd != 0.f && fabsf(cd) < 1.5f) mu[e] += rb * (Gx_entry(c, c.xt, e / ng, e % ng) - r3[e]);
         }
         __syncthreads();
+        }
         float dm[1] = {0.f};
         for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
             ex[e] += c.xt[e];

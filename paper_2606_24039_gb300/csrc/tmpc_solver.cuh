@@ -1117,11 +1117,12 @@ __device__ __forceinline__ void tile_fma(float (&acc)[4][4], const float4 (&ar)[
         }
 }
 
-// eta = -(P x + q) - C'w - G'(y_g + rho_g p_g) with w_r = y_f,r + rho_f p_f,r in
-// W (T rows of nx).  Tile (t0, j0): stages t0..t0+3, entries j0..j0+3;
-// (C'w)_t,j = [t < N] (A-' w_{t+1})_j + [j < nx] ([t = 0] w_0,j - [t > 0] w_t,j).
-__device__ __forceinline__ void rhs_tiled(const Ctx& c, const float* W, float rho_g) {
-    const int n = c.n, nx = c.nx, ng = c.ng, T = c.T, N = c.N;
+// (C'W)_{t,j} for every stage t and entry j, W: T rows of nx; f(t, j, value).
+// Tile (t0, j0): stages t0..t0+3, entries j0..j0+3;
+// (C'W)_{t,j} = [t < N] (A-' W_{t+1})_j + [j < nx] ([t = 0] W_{0,j} - [t > 0] W_{t,j}).
+template <class F>
+__device__ __forceinline__ void ct_tiled(const Ctx& c, const float* W, F f) {
+    const int n = c.n, nx = c.nx, T = c.T, N = c.N;
     const int nj = n >> 2, ntile = nj * ((T + 3) >> 2);
     const float* Am = c.Amt(0);
     for (int w = threadIdx.x; w < ntile; w += blockDim.x) {
@@ -1155,33 +1156,27 @@ __device__ __forceinline__ void rhs_tiled(const Ctx& c, const float* W, float rh
                 const int j = j0 + a;
                 float s = t < N ? acc[b][a] : 0.f;
                 if (j < nx) s += (t == 0) ? W[j] : -W[t * nx + j];
-                float e = -(Px_entry(c, c.x, t, j) + c.qv[t * n + j]) - s;
-                const int r = g_row(c, j);
-                if (r >= 0) e -= c.yg[t * ng + r] + rho_g * c.pg[t * ng + r];
-                c.eta[t * n + j] = e;
+                f(t, j, s);
             }
         }
     }
 }
 
-// cd = C dx row by row and the y_f / p_f updates of the equality rows:
-// row 0 is dx_0; row t + 1 is A- dx_t - dx_{t+1}.  Tile (t0, k0): stages
-// t0..t0+3 (rows t0+1..t0+4), rows k0..k0+3 of A-.
-__device__ __forceinline__ void update_eq_tiled(const Ctx& c, const float* dx, float rho_f, float alpha) {
+// (C X)_{r,k} for rows r = 0..N, k < nx, X: T rows of n; f(e = r nx + k, value).
+// Row 0 is X_0; row t + 1 is A- X_t - X_{t+1}.  Tile (t0, k0): stages t0..t0+3
+// (rows t0+1..t0+4), rows k0..k0+3 of A-.
+template <class F>
+__device__ __forceinline__ void c_tiled(const Ctx& c, const float* X, F f) {
     const int n = c.n, nx = c.nx, N = c.N;
     const int nk = nx >> 2, ntile = nk * ((N + 3) >> 2);
     const float* Am = c.Amt(0);
-    auto upd = [&](int e, float cd) {
-        c.yf[e] += rho_f * alpha * (c.pf[e] + cd);
-        c.pf[e] += alpha * cd;
-    };
     for (int w = threadIdx.x; w < ntile; w += blockDim.x) {
         const int k0 = (w % nk) << 2, t0 = (w / nk) << 2;
         float acc[4][4];
         const float* xr[4];
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            xr[b] = dx + min(t0 + b, N - 1) * n;
+            xr[b] = X + min(t0 + b, N - 1) * n;
 #pragma unroll
             for (int a = 0; a < 4; ++a) acc[b][a] = 0.f;
         }
@@ -1200,11 +1195,11 @@ __device__ __forceinline__ void update_eq_tiled(const Ctx& c, const float* dx, f
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 const int k = k0 + a;
-                upd((t + 1) * nx + k, acc[b][a] - dx[(t + 1) * n + k]);
+                f((t + 1) * nx + k, acc[b][a] - X[(t + 1) * n + k]);
             }
         }
     }
-    for (int k = threadIdx.x; k < nx; k += blockDim.x) upd(k, dx[k]);
+    for (int k = threadIdx.x; k < nx; k += blockDim.x) f(k, X[k]);
 }
 
 // one ADMM iteration (Algorithm 3) in increment form.  With p_f = C x - c
@@ -1223,8 +1218,14 @@ __device__ inline void admm_iter(const Ctx& c, const KOpts& o, float rho_bar, co
     if (tiled)   // w = y_f + rho_f p_f into xt (free until the solve writes it)
         for (int e = threadIdx.x; e < T * nx; e += blockDim.x) c.xt[e] = c.yf[e] + rho_f * c.pf[e];
     __syncthreads();
-    if (tiled) rhs_tiled(c, c.xt, rho_g);
-    else for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
+    if (tiled) {
+        ct_tiled(c, c.xt, [&](int t, int j, float ctw) {
+            float e = -(Px_entry(c, c.x, t, j) + c.qv[t * n + j]) - ctw;
+            const int r = g_row(c, j);   // the linear model's G selects controls
+            if (r >= 0) e -= c.yg[t * ng + r] + rho_g * c.pg[t * ng + r];
+            c.eta[t * n + j] = e;
+        });
+    } else for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
         const int t = e / n, j = e % n;
         float s = -(Px_entry(c, c.x, t, j) + c.qv[e]);
         s -= Ct_entry(c, t, j, [&](int r, int k) { return c.yf[r * nx + k] + rho_f * c.pf[r * nx + k]; });
@@ -1239,8 +1240,12 @@ __device__ inline void admm_iter(const Ctx& c, const KOpts& o, float rho_bar, co
     }
     __syncthreads();
     ldl_solve(c, c.eta, c.xt, sm.red8, sm.A, sm.Bm, sm.mbar, sm.flags + 12);
-    if (tiled) update_eq_tiled(c, c.xt, rho_f, alpha);
-    else for (int e = threadIdx.x; e < T * nx; e += blockDim.x) {
+    if (tiled) {
+        c_tiled(c, c.xt, [&](int e, float cd) {
+            c.yf[e] += rho_f * alpha * (c.pf[e] + cd);
+            c.pf[e] += alpha * cd;
+        });
+    } else for (int e = threadIdx.x; e < T * nx; e += blockDim.x) {
         const float cd = Cx_entry(c, c.xt, e / nx, e % nx);
         c.yf[e] += rho_f * alpha * (c.pf[e] + cd);
         c.pf[e] += alpha * cd;
