@@ -975,6 +975,78 @@ __device__ inline void ldl_solve(const Ctx& c, float* b, float* xo, float* red, 
         BlockStream bs(sbuf0, sbuf1, mbar, mstate);
         int k = 0;   // step counter of the stream
         if (stream) bs.issue(k, c.Om, bytes);
+        if (n % 4 == 0 && 2 * n <= (int)blockDim.x) {
+            // n a multiple of 4: 128-bit loads of the block rows.  Forward and diagonal:
+            // two threads per row (float4 groups q = h, h + 2, ...) and one shuffle;
+            // backward: thread (column quad cq, part p) sums the rows i = p (mod 8),
+            // combined by three shuffle levels.  Shuffles run on whole warps.
+            const int nq = n >> 2, tid = threadIdx.x;
+            const int ri = tid >> 1, rh = tid & 1;                 // row, half
+            const int cq = tid >> 3, cp = tid & 7;                 // column quad, part
+            const bool rrow = ri < n, rcol = cq < nq;
+            auto rowdot4 = [&](const float* M, const float* v) {  // (M v)_ri over the groups of half rh
+                float s0 = 0.f, s1 = 0.f;
+                if (rrow) {
+                    const float* mr = M + ri * n;
+                    for (int q = rh; q < nq; q += 2) {
+                        const float4 a = ldv4(mr + 4 * q), x = ldv4(v + 4 * q);
+                        s0 = fmaf(a.x, x.x, s0);
+                        s1 = fmaf(a.y, x.y, s1);
+                        s0 = fmaf(a.z, x.z, s0);
+                        s1 = fmaf(a.w, x.w, s1);
+                    }
+                }
+                float sum = s0 + s1;
+                sum += __shfl_xor_sync(0xFFFFFFFFu, sum, 1);
+                return sum;
+            };
+            for (int t = 0; t < N; ++t, ++k) {
+                if (stream) bs.issue(k + 1, t + 1 < N ? c.Om + (t + 1) * nn : c.Dinv, bytes);
+                const float* Om = stream ? bs.get(k, c.Om + t * nn) : c.Om + t * nn;
+                const float s = rowdot4(Om, b + t * n);
+                if (rrow && rh == 0) b[(t + 1) * n + ri] -= s;
+                __syncthreads();
+            }
+            for (int t = 0; t < c.T; ++t, ++k) {
+                if (stream) bs.issue(k + 1, t + 1 < c.T ? c.Dinv + (t + 1) * nn : c.Om + (N - 1) * nn, bytes);
+                const float* D = stream ? bs.get(k, c.Dinv + t * nn) : c.Dinv + t * nn;
+                const float s = rowdot4(D, b + t * n);
+                if (rrow && rh == 0) xo[t * n + ri] = s;
+                __syncthreads();
+            }
+            for (int t = N - 1; t >= 0; --t, ++k) {
+                if (stream && t > 0) bs.issue(k + 1, c.Om + (t - 1) * nn, bytes);
+                const float* Om = stream ? bs.get(k, c.Om + t * nn) : c.Om + t * nn;
+                const float* xn = xo + (t + 1) * n;
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (rcol)
+                    for (int i = cp; i < n; i += 8) {
+                        const float4 a = ldv4(Om + i * n + 4 * cq);
+                        const float xi = xn[i];
+                        acc.x = fmaf(a.x, xi, acc.x);
+                        acc.y = fmaf(a.y, xi, acc.y);
+                        acc.z = fmaf(a.z, xi, acc.z);
+                        acc.w = fmaf(a.w, xi, acc.w);
+                    }
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1) {
+                    acc.x += __shfl_xor_sync(0xFFFFFFFFu, acc.x, o);
+                    acc.y += __shfl_xor_sync(0xFFFFFFFFu, acc.y, o);
+                    acc.z += __shfl_xor_sync(0xFFFFFFFFu, acc.z, o);
+                    acc.w += __shfl_xor_sync(0xFFFFFFFFu, acc.w, o);
+                }
+                if (rcol && cp == 0) {
+                    float* xt = xo + t * n + 4 * cq;
+                    xt[0] -= acc.x;
+                    xt[1] -= acc.y;
+                    xt[2] -= acc.z;
+                    xt[3] -= acc.w;
+                }
+                __syncthreads();
+            }
+            if (stream) bs.finish();
+            return;
+        }
         for (int t = 0; t < N; ++t, ++k) {
             if (stream) bs.issue(k + 1, t + 1 < N ? c.Om + (t + 1) * nn : c.Dinv, bytes);
             const float* Om = stream ? bs.get(k, c.Om + t * nn) : c.Om + t * nn;
