@@ -571,55 +571,119 @@ __device__ __forceinline__ void tile_xyt(float (&acc)[4][4], const float* X, con
     }
 }
 
-// In-place inverse of the symmetric positive definite n x n matrix A (n % 4 == 0,
-// row-major) by Gauss-Jordan sweeps over the pivots k = 0 .. n-1 (no pivoting:
-// the pivots are the Schur complements' leading entries, positive for SPD A).
-// Sweep k with pivot p = A_kk, column c and row r of A before the sweep:
-//   A_kk <- 1/p,  A_kj <- r_j / p,  A_ik <- -c_i / p,  A_ij <- A_ij - c_i r_j / p.
-// snap (4n floats) holds the pivot column and row, double-buffered: the threads
-// that write column / row k+1 also write the next sweep's copy, so each sweep
-// needs one barrier.  A pivot that is not positive sets *flag and is taken as 1.
-__device__ inline void gj_inverse(float* A, int n, float* snap, int* flag) {
-    const int nq = n >> 2, ngrp = n * nq;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        snap[i] = A[i * n];
-        snap[n + i] = A[i];
-    }
-    __syncthreads();
-    for (int k = 0; k < n; ++k) {
-        const float* col = snap + (k & 1) * 2 * n;
-        const float* row = col + n;
-        float* ncol = snap + ((k + 1) & 1) * 2 * n;
-        float* nrow = ncol + n;
-        float p = col[k];
+// 4 x 4 inverse of a symmetric positive definite block in registers by
+// Gauss-Jordan sweeps (no pivoting; see gj_inverse); bad is set if a pivot is
+// not positive (it is then taken as 1).
+__device__ __forceinline__ void inv4_spd(float (&M)[4][4], bool& bad) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float p = M[k][k];
         if (!(p > 0.f)) {
-            if (threadIdx.x == 0) *flag = 1;
+            bad = true;
             p = 1.f;
         }
         const float ip = 1.f / p;
-        for (int g = threadIdx.x; g < ngrp; g += blockDim.x) {
-            const int i = g / nq, j0 = (g % nq) << 2;
-            const float4 a4 = ldv4(A + i * n + j0), r4 = ldv4(row + j0);
-            const float ci = col[i], cs = -ci * ip;
-            float v[4] = {a4.x, a4.y, a4.z, a4.w};
-            const float rr[4] = {r4.x, r4.y, r4.z, r4.w};
+        float c[4], r[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int j = j0 + q;
-                if (i == k) v[q] = (j == k) ? ip : rr[q] * ip;
-                else if (j == k) v[q] = cs;
-                else v[q] = fmaf(cs, rr[q], v[q]);
+        for (int q = 0; q < 4; ++q) {
+            c[q] = M[q][k];
+            r[q] = M[k][q];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (i == k) M[i][j] = (j == k) ? ip : r[j] * ip;
+                else if (j == k) M[i][j] = -c[i] * ip;
+                else M[i][j] = fmaf(-c[i] * ip, r[j], M[i][j]);
             }
-            stv4(A + i * n + j0, v[0], v[1], v[2], v[3]);
-            if (k + 1 < n) {
+    }
+}
+
+// In-place inverse of the symmetric positive definite n x n matrix A (n % 4 == 0,
+// row-major) by block Gauss-Jordan sweeps over the 4 x 4 pivot blocks
+// K = 4s .. 4s+3 (no pivoting: the pivot blocks are Schur complements of an SPD
+// matrix).  With P = A_KK, column block C = A_:K and row block R = A_K: before
+// the sweep:
+//   A_KK <- P^-1,  A_Kj <- P^-1 R_j,  A_iK <- -C_i P^-1,  A_ij <- A_ij - C_i P^-1 R_j.
+// Each sweep: the pivot inverse and P^-1 R into snap (8n + 16 floats), a
+// barrier, the update of every float4 group, a barrier.  A pivot that is not
+// positive sets *flag.
+__device__ inline void gj_inverse(float* A, int n, float* snap, int* flag) {
+    const int nq = n >> 2, tid = threadIdx.x;
+    float* Cs = snap;            // n x 4: column block of the sweep
+    float* Rp = snap + 4 * n;    // 4 x n: P^-1 R
+    float* Pi = snap + 8 * n;    // 4 x 4: P^-1
+    // the thread's float4 groups g = tid + m nth, walked as (row i, group jq) without divisions
+    const int i_first = tid / nq, q_first = tid % nq;
+    const int di = blockDim.x / nq, dq = blockDim.x % nq;
+    for (int s = 0; s < nq; ++s) {
+        const int k0 = s << 2;
+        if (tid < n) {
+            const float4 cb = ldv4(A + tid * n + k0);
+            stv4(Cs + 4 * tid, cb.x, cb.y, cb.z, cb.w);
+            const int a = tid / nq, jq = tid % nq;   // tid < n = 4 nq: row a of P^-1 R, group jq
+            float P[4][4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (j0 + q == k + 1) ncol[i] = v[q];
-                if (i == k + 1) {
+            for (int b = 0; b < 4; ++b) {
+                const float4 r = ldv4(A + (k0 + b) * n + k0);
+                P[b][0] = r.x; P[b][1] = r.y; P[b][2] = r.z; P[b][3] = r.w;
+            }
+            bool bad = false;
+            inv4_spd(P, bad);
+            if (bad && tid == 0) *flag = 1;
+            float pa[4];   // row a of P^-1, selected without dynamic register indexing
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) nrow[j0 + q] = v[q];
+            for (int b = 0; b < 4; ++b) pa[b] = a == 0 ? P[0][b] : a == 1 ? P[1][b] : a == 2 ? P[2][b] : P[3][b];
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const float4 r = ldv4(A + (k0 + b) * n + 4 * jq);
+                const float w = pa[b];
+                acc.x = fmaf(w, r.x, acc.x);
+                acc.y = fmaf(w, r.y, acc.y);
+                acc.z = fmaf(w, r.z, acc.z);
+                acc.w = fmaf(w, r.w, acc.w);
+            }
+            stv4(Rp + a * n + 4 * jq, acc.x, acc.y, acc.z, acc.w);
+            if (tid == 0)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) stv4(Pi + 4 * b, P[b][0], P[b][1], P[b][2], P[b][3]);
+        }
+        __syncthreads();
+        int i = i_first, jq = q_first;
+        for (; i < n; i += di, jq += dq) {
+            if (jq >= nq) { jq -= nq; ++i; if (i >= n) break; }
+            const int j0 = jq << 2, ik = i - k0;
+            const bool inK = ik >= 0 && ik < 4;
+            float4 v;
+            if (jq == s) {
+                if (inK) {
+                    v = ldv4(Pi + 4 * ik);
+                } else {
+                    const float4 ci = ldv4(Cs + 4 * i);
+                    const float4 p0 = ldv4(Pi), p1 = ldv4(Pi + 4), p2 = ldv4(Pi + 8), p3 = ldv4(Pi + 12);
+                    v.x = -(ci.x * p0.x + ci.y * p1.x + ci.z * p2.x + ci.w * p3.x);
+                    v.y = -(ci.x * p0.y + ci.y * p1.y + ci.z * p2.y + ci.w * p3.y);
+                    v.z = -(ci.x * p0.z + ci.y * p1.z + ci.z * p2.z + ci.w * p3.z);
+                    v.w = -(ci.x * p0.w + ci.y * p1.w + ci.z * p2.w + ci.w * p3.w);
+                }
+            } else if (inK) {
+                v = ldv4(Rp + ik * n + j0);
+            } else {
+                v = ldv4(A + i * n + j0);
+                const float4 ci = ldv4(Cs + 4 * i);
+                const float c4[4] = {ci.x, ci.y, ci.z, ci.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float4 r = ldv4(Rp + a * n + j0);
+                    v.x = fmaf(-c4[a], r.x, v.x);
+                    v.y = fmaf(-c4[a], r.y, v.y);
+                    v.z = fmaf(-c4[a], r.z, v.z);
+                    v.w = fmaf(-c4[a], r.w, v.w);
                 }
             }
+            stv4(A + i * n + j0, v.x, v.y, v.z, v.w);
         }
         __syncthreads();
     }
