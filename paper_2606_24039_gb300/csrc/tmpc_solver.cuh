@@ -956,14 +956,17 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
-// wait for phase `parity` of `bar` to complete; false if it did not within kMbarSpin polls
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+// wait for phase `parity` of `bar` to complete; false if it did not within kMbarSpin
+// polls, or as soon as *abort (shared, may be NULL) is set by a thread that gave up
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
+                                          const volatile int* abort = nullptr) {
     for (unsigned k = 0; k < kMbarSpin; ++k) {
         unsigned done;
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}"
                      : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
         if (done) return true;
+        if (abort && *abort) return false;
     }
     return false;
 }
@@ -1012,15 +1015,19 @@ struct BlockStream {
         }
     }
     // every thread: wait for the block of step k; returns the shared copy, or
-    // `fallback` (global memory) if the wait gave up
+    // `fallback` (global memory, the same values) once a wait gave up.  Each thread
+    // waits on the mbarrier itself; a thread that gives up sets state[2], which ends
+    // the other threads' waits, so every thread reads global memory from then on
+    // (thread 0 issues no further copies).
     __device__ const float* get(int k, const float* fallback) {
         if (!ok) return fallback;
-        const bool done = mbar_wait(bar + (k & 1), phase[k & 1]);
-        phase[k & 1] ^= 1u;
-        if (!__syncthreads_and(done)) {
+        const volatile int* gave_up = state + 2;
+        if (*gave_up || !mbar_wait(bar + (k & 1), phase[k & 1], gave_up)) {
             ok = false;
+            state[2] = 1;
             return fallback;
         }
+        phase[k & 1] ^= 1u;
         return buf[k & 1];
     }
 };
