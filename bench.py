@@ -88,6 +88,8 @@ def parse():
                     "4 warp-sequential LDL', 5 warp LDL' on global arenas")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the host-memory end-to-end timing")
     ap.add_argument("--threads", type=int, default=0, help="threads per instance (0 = library default)")
+    ap.add_argument("--clocks-csv", default=None,
+                    help="also keep the raw nvidia-smi clock samples of the timed region in this CSV file")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the launch form chosen at setup (default: tmpc_autotune picks it per model group)")
     ap.add_argument("--no-plain", action="store_true",
@@ -205,14 +207,17 @@ def run_reference(args):
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, path=None):
+        import tempfile
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        # the raw samples go to `path` when given (--clocks-csv), else to a temporary file
+        self.path = path or os.path.join(tempfile.gettempdir(), f"tmpc_clocks_{os.getpid()}_gpu{gpu_index}.csv")
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            if os.path.dirname(self.path):
+                os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
@@ -460,7 +465,7 @@ def run_gpu(args):
             ktimes.append(kev[0].elapsed_time(kev[1]))
         return times, ktimes
 
-    with Clocks(local) as clk:
+    with Clocks(local, args.clocks_csv) as clk:
         t0 = time.time()
         t_fwd, k_fwd = timed(step)
         t_fb, _ = timed(step_fb) if not args.skip_bwd else ([float("nan")], None)

@@ -1,0 +1,46 @@
+"""Host logic of bench.py that needs no GPU: the kernel-launch count it reports
+(gpu_launches) and the kernel it names in the roofline, per launch form."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.abspath(os.path.join(os.path.dirname(__file__), ".."))
+sys.path.insert(0, ROOT)
+
+import workloads as w  # noqa: E402
+
+bench = pytest.importorskip("bench")
+
+
+def test_launches_follow_the_launch_form():
+    pb = w.racing(B=4, N=50)
+    bic = w.MODEL_BICYCLE
+    assert bench.launches_per_step(pb, 0) == (1, 1)                    # one persistent launch each way
+    assert bench.launches_per_step(pb, 1) == (1, 1)                    # generic kernel
+    assert bench.launches_per_step(pb, 0, {bic: 4}) == (1, 1)          # warp LDL': generic backward
+    plain = 2 + pb.opts.max_sqp * (2 + pb.opts.max_admm)
+    assert bench.launches_per_step(pb, 0, {bic: 7}) == (plain, 1)      # one launch per phase
+    assert plain == 522
+
+
+def test_launches_of_a_mixed_batch():
+    pb = w.uneven(B=64, seed=3)
+    models = set(int(m) for m in np.unique(pb.model))
+    fast = models & set(bench.FAST_MODELS)
+    fwd, bwd = bench.launches_per_step(pb, 0)
+    assert fwd == len(fast) and bwd == len(fast)
+    # warp LDL' groups share one generic backward launch
+    fwd, bwd = bench.launches_per_step(pb, 0, {m: 4 for m in fast})
+    assert fwd == len(fast) and bwd == 1
+
+
+def test_kernel_names_per_form():
+    pb = w.racing(B=4, N=50)
+    bic = w.MODEL_BICYCLE
+    assert bench.kernel_name(pb, 0) == "fast::solve_kernel<MODEL_BICYCLE, kCR>"
+    assert bench.kernel_name(pb, 0, {bic: 6}) == "fast::solve_kernel_cluster<MODEL_BICYCLE, kCR>"
+    assert bench.kernel_name(pb, 0, {bic: 4}) == "fast::solve_kernel<MODEL_BICYCLE, kLDL>"
+    assert bench.kernel_name(pb, 1) == "solve_kernel (generic)"
+    assert bench.kernel_name(w.tracking(B=2), 0) == "solve_kernel (generic)"
