@@ -245,10 +245,10 @@ typedef struct {
  *   init       (DEVICE, may be NULL) warm start of the trials: z, xi, y_eq and
  *              y_ineq are copied (not written) before each trial, as tmpc_solve
  *              with warm_start reads them; NULL starts each trial cold.
- *   reps       1..1000 timed rounds.  The setup's form first runs until about
+ *   reps       1..1000 timed passes.  The setup's form first runs until about
  *              20 ms of device time (clocks up); each form then runs once, forms
  *              four times slower than the fastest of these are dropped, and the
- *              rest run reps interleaved rounds; a form's time is its fastest
+ *              rest run reps interleaved passes; a form's time is its fastest
  *              launch (CUDA events on stream, warm-start copy included).
  *   trial_sqp  > 0 caps the SQP iterations of the trials; 0 runs the handle's.
  *   res [4]    (HOST, may be NULL) one entry per group.

@@ -884,7 +884,7 @@ tmpc_status tmpc_autotune(tmpc_handle* h, const float* x0, const tmpc_solution* 
         float fmin = -1.f;
         for (size_t k = 0; k < nc; ++k)
             if (first[k] >= 0.f && (fmin < 0.f || first[k] < fmin)) fmin = first[k];
-        // reps interleaved rounds over the remaining forms; a form's time is its fastest launch
+        // reps interleaved passes over the remaining forms; a form's time is its fastest launch
         for (int rep = 0; rep < reps && st == TMPC_OK; ++rep)
             for (size_t k = 0; k < nc && st == TMPC_OK; ++k) {
                 if (first[k] < 0.f || first[k] > 4.f * fmin) continue;
