@@ -96,3 +96,14 @@ def test_static_entry_validates_before_touching_the_device(lib):
     assert lib.tmpc_solve_static(ctypes.byref(d), ctypes.byref(o), ctypes.byref(p), fake, ctypes.byref(s), 0, None) == 1
     msg = lib.tmpc_last_error().decode()
     assert "static scratch holds %d bytes" % _abi.STATIC_SCRATCH_BYTES in msg
+
+
+def test_tune_result_mirror_matches_the_header():
+    """The ctypes mirror of tmpc_tune_result has the header's fields, in order and type."""
+    from paper_2606_24039_gb300 import _abi
+    src = open(os.path.join(ROOT, "include", "tmpc.h")).read()
+    body = re.search(r"typedef struct \{(.*?)\} tmpc_tune_result;", src, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(int32_t|float)\s+(\w+);", body)
+    ctype = {"int32_t": ctypes.c_int32, "float": ctypes.c_float}
+    assert [(n, ctype[t]) for t, n in fields] == list(_abi.TuneResult._fields_)
