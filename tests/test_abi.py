@@ -102,7 +102,8 @@ def test_tune_result_mirror_matches_the_header():
     """The ctypes mirror of tmpc_tune_result has the header's fields, in order and type."""
     from paper_2606_24039_gb300 import _abi
     src = open(os.path.join(ROOT, "include", "tmpc.h")).read()
-    body = re.search(r"typedef struct \{(.*?)\} tmpc_tune_result;", src, flags=re.S).group(1)
+    end = src.index("} tmpc_tune_result;")
+    body = src[src.rindex("typedef struct {", 0, end) + len("typedef struct {"):end]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     fields = re.findall(r"\b(int32_t|float)\s+(\w+);", body)
     ctype = {"int32_t": ctypes.c_int32, "float": ctypes.c_float}
