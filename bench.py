@@ -312,7 +312,8 @@ def n_launch_groups(pb, solver):
     return fast + (1 if models - set(FAST_MODELS) else 0)
 
 
-KERNEL_SOURCES = ("tmpc_fast.cu", "tmpc_fast.cuh", "tmpc_fast_api.h", "tmpc_solver.cuh", "tmpc_models.cuh")
+KERNEL_SOURCES = ("tmpc_fast_kernels.cuh", "tmpc_fast_model.cuh", "tmpc_fast_bicycle.cu", "tmpc_fast.cuh", "tmpc_fast_api.h",
+                  "tmpc_solver.cuh", "tmpc_models.cuh", "tmpc_backward.cuh")
 
 
 def sources_digest():

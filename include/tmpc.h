@@ -281,15 +281,17 @@ tmpc_status tmpc_solve_host(tmpc_handle* h, const tmpc_params* host_p, const flo
  * entry point for callers that may not allocate device memory when they solve,
  * e.g. a control loop that must not block on the CUDA allocator or risk an
  * out-of-memory failure once it runs, or code running while another component
- * owns all device memory.  It computes what tmpc_setup + tmpc_solve compute with
- * solver 1 (the generic kernel: Algorithm 1 around Algorithm 3), without a handle.
+ * owns all device memory.  It computes the same SQP / ADMM solve as tmpc_setup +
+ * tmpc_solve with solver 1 (the generic kernel), without a handle.
  *
  * d, o, p, x0, out: as for tmpc_setup / tmpc_solve (device pointers for p, x0
  * and out; out->status is required, out->stats may be NULL).  o->solver must be
- * 0 or 1.  Scratch: the instance order, the work-queue counter and one
+ * 0 or 1, and either value runs the generic kernel (the shared-memory kernels
+ * need a handle).  Scratch: the instance order, the work-queue counter and one
  * workspace per instance live in a file-scope device array of
  * TMPC_STATIC_SCRATCH_BYTES.  A batch whose scratch does not fit is rejected
- * with TMPC_ERR_INVALID_ARG before anything is enqueued; tmpc_last_error()
+ * with TMPC_ERR_INVALID_ARG before anything is enqueued, and so is a layout
+ * whose per-instance workspace would exceed 2^31 floats; tmpc_last_error()
  * then gives the bytes it needs (about 81 KB per racing instance of N = 50).
  * Nothing in the scratch has to start at zero: the call's first kernel writes
  * the order and the counter before the solve kernel reads them.

@@ -52,5 +52,22 @@ cudaError_t launch_plain(int model, int threads, cudaStream_t s, const KLayout& 
                          const float* x0, int warm, PlainState* ps);
 int plain_launches(int max_sqp, int max_admm);
 
+// Kernels of one model (each model's kernels live in a translation unit of their
+// own; the host code above dispatches through these tables).
+struct KernelTable {
+    const void* solve[2];     // persistent kernel, policy kCR / kLDL
+    const void* cluster[2];   // one thread-block cluster per instance, kCR / kLDL
+    const void* backward;     // persistent backward kernel (cyclic reduction)
+    const void* backward_cluster;
+    cudaError_t (*plain)(int threads, cudaStream_t s, const KLayout& L, const KOpts& o, const KParams& p,
+                         const KSol& out, float* gws, long long gstride, const int* order, int count,
+                         const float* x0, int warm, PlainState* ps);
+};
+template <int M>
+const KernelTable& kernel_table();
+template <> const KernelTable& kernel_table<MODEL_DI>();
+template <> const KernelTable& kernel_table<MODEL_BICYCLE>();
+template <> const KernelTable& kernel_table<MODEL_QUAD>();
+
 }  // namespace fast
 }  // namespace tmpc

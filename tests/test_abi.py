@@ -108,3 +108,16 @@ def test_tune_result_mirror_matches_the_header():
     fields = re.findall(r"\b(int32_t|float)\s+(\w+);", body)
     ctype = {"int32_t": ctypes.c_int32, "float": ctypes.c_float}
     assert [(n, ctype[t]) for t, n in fields] == list(_abi.TuneResult._fields_)
+
+
+def test_static_entry_rejects_a_workspace_beyond_int_offsets(lib):
+    """A horizon whose per-instance workspace exceeds 2^31 floats is rejected
+    before any CUDA call (the layout is computed in 64-bit; it used to wrap)."""
+    from paper_2606_24039_gb300 import _abi
+    d = _abi.Dims(1, 10873336, 6, 2, 5, 4, 800)
+    o = _abi.default_options()
+    fake = 0x10000
+    p = _abi.Params(*([fake] * 13))
+    s = _abi.Solution(*([fake] * 6))
+    assert lib.tmpc_solve_static(ctypes.byref(d), ctypes.byref(o), ctypes.byref(p), fake, ctypes.byref(s), 0, None) == 1
+    assert "exceeds 2^31 floats" in lib.tmpc_last_error().decode()

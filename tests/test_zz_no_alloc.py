@@ -41,9 +41,58 @@ def test_static_entry_matches_handle_entry_twice(make):
             out["z"].copy_(t["z_init"])
         tmpc_solve_static(dims, t, t["x0"], out, opts, warm_start=t["z_init"] is not None)
         torch.cuda.synchronize()
-        for k in ("z", "xi", "y_eq", "y_ineq", "stats"):
-            np.testing.assert_allclose(out[k].cpu().numpy(), ref[k].cpu().numpy(), rtol=1e-6, atol=1e-7, err_msg=k)
-        assert torch.equal(out["status"], ref["status"])
+        # same kernel and arithmetic per instance, whatever order the queue hands them out in
+        for k in ("z", "xi", "y_eq", "y_ineq", "stats", "status"):
+            assert torch.equal(out[k], ref[k]), k
+
+
+def test_static_entry_allocates_no_device_memory():
+    """The defining property: after a first call (which looks up the scratch
+    address once), further calls change neither the device's free memory nor
+    torch's allocator."""
+    from paper_2606_24039_gb300 import options_from, tmpc_solve_static
+    pb = w.racing(B=8, N=30, max_sqp=2, max_admm=30)
+    t, dims = _inputs(pb)
+    opts = options_from(pb.opts, solver=1)
+    out = {k: torch.zeros((pb.B,) + tuple(v.shape[1:]), device="cuda") for k, v in
+           (("z", t["z_init"]), ("xi", t["lo"]), ("y_eq", t["Qd"]), ("y_ineq", t["lo"]))}
+    out["status"] = torch.zeros(pb.B, dtype=torch.int32, device="cuda")
+    out["stats"] = torch.zeros((pb.B, 10), device="cuda")
+    tmpc_solve_static(dims, t, t["x0"], out, opts)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        tmpc_solve_static(dims, t, t["x0"], out, opts)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0 and torch.cuda.memory_allocated() == alloc0
+    assert np.all(np.isin(out["status"].cpu().numpy(), (0, 1)))
+
+
+def test_handle_still_launches_after_a_smaller_static_call():
+    """A static call with a smaller shared-memory need must not lower the launch
+    limit a handle set up for a larger one relies on (generic kernel, ADMM
+    vectors in shared memory above 48 KB in both calls)."""
+    from paper_2606_24039_gb300 import Solver, options_from, tmpc_solve_static
+    big = w.racing(B=4, N=200, max_sqp=2, max_admm=20)
+    s = Solver.from_batch(big, device="cuda", solver=1)
+    first = {k: v.clone() for k, v in s.tmpc_solve(s.x0, z_init=s.z_init).items()}
+    torch.cuda.synchronize()
+    small = w.racing(B=4, N=170, max_sqp=2, max_admm=20)
+    t, dims = _inputs(small)
+    out = {k: torch.zeros((small.B,) + tuple(v.shape[1:]), device="cuda") for k, v in
+           (("z", t["z_init"]), ("xi", t["lo"]), ("y_eq", t["Qd"]), ("y_ineq", t["lo"]))}
+    out["z"].copy_(t["z_init"])
+    out["status"] = torch.zeros(small.B, dtype=torch.int32, device="cuda")
+    out["stats"] = None
+    tmpc_solve_static(dims, t, t["x0"], out, options_from(small.opts, solver=1), warm_start=True)
+    torch.cuda.synchronize()
+    again = s.tmpc_solve(s.x0, z_init=s.z_init)
+    torch.cuda.synchronize()
+    for k in ("z", "xi", "y_eq", "y_ineq", "status", "stats"):
+        assert torch.equal(again[k], first[k]), k
+    s.close()
 
 
 def test_static_entry_rejects_a_batch_beyond_the_scratch():
@@ -74,4 +123,4 @@ def test_static_entry_marks_out_of_range_instances():
         assert torch.count_nonzero(out["z"][i]) == 0 and torch.count_nonzero(out["stats"][i]) == 0
     for i in (0, 2):
         assert st[i] == ref["status"][i].item()
-        np.testing.assert_allclose(out["z"][i].cpu().numpy(), ref["z"][i].cpu().numpy(), rtol=1e-6, atol=1e-7)
+        assert torch.equal(out["z"][i], ref["z"][i])
