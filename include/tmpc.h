@@ -115,6 +115,15 @@ typedef struct {
                           * iteration and phase, state in global memory, fixed counts: a
                           * measurement baseline).  2-7 apply to the double integrator,
                           * bicycle and quadrotor; other models use 1.                    */
+    /* Failure-path hooks (host-side fault injection; nothing here can fault the GPU):
+     * force_pivot_failure: instance index + 1 whose factorisation of S is treated as
+     *   failed from the first SQP step on (status TMPC_INST_NOT_PD from tmpc_solve and
+     *   tmpc_backward; the arithmetic is unchanged); 0 = none.
+     * wait_polls: polls of each bounded wait on an asynchronous shared-memory copy of
+     *   the generic kernel before it gives up (status TMPC_INST_TIMEOUT; the instance
+     *   finishes on global-memory reads of the same values); 0 = the default, 2^24. */
+    int32_t force_pivot_failure;
+    int32_t wait_polls;
 } tmpc_options;
 
 /* Problem parameters theta (the OCP of Appendix A with the cost of Eq. (cost)).

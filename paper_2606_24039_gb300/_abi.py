@@ -33,7 +33,8 @@ class Options(ctypes.Structure):
                 ("newton_steps", ctypes.c_int32), ("early_exit", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("bwd_rho", ctypes.c_float),
                 ("bwd_sigma", ctypes.c_float), ("bwd_iters", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("solver", ctypes.c_int32)]
+                ("threads", ctypes.c_int32), ("solver", ctypes.c_int32),
+                ("force_pivot_failure", ctypes.c_int32), ("wait_polls", ctypes.c_int32)]
 
 
 class Params(ctypes.Structure):

@@ -43,6 +43,8 @@ KOpts to_kopts(const tmpc_options& o) {
     k.n_ls = o.n_ls; k.newton_steps = o.newton_steps; k.early_exit = o.early_exit;
     k.check_every = o.check_every < 1 ? 1 : o.check_every;
     k.bwd_rho = o.bwd_rho; k.bwd_sigma = o.bwd_sigma; k.bwd_iters = o.bwd_iters;
+    k.force_fail = o.force_pivot_failure;
+    k.wait_polls = o.wait_polls;
     if (k.k_rho_iter < 1) k.k_rho_iter = 1 << 30;
     return k;
 }
@@ -204,6 +206,7 @@ static tmpc_status check_options(const tmpc_options* o) {
     if (o->newton_steps < 0 || o->bwd_iters < 1 || !(o->bwd_rho > 0.f)) return TMPC_ERR_INVALID_ARG;
     if (o->threads < 0 || o->threads > 256 || (o->threads % 32) != 0) return TMPC_ERR_INVALID_ARG;
     if (o->solver < 0 || o->solver > 7) return TMPC_ERR_INVALID_ARG;
+    if (o->force_pivot_failure < 0 || o->wait_polls < 0) return TMPC_ERR_INVALID_ARG;
     return TMPC_OK;
 }
 

@@ -49,7 +49,7 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
     const float* dLdz = dLdz_all + inst * Ts * L.n;
     const float* dLdxi = dLdxi_all ? dLdxi_all + inst * Ts * L.ng : nullptr;
     float rb = o.bwd_rho;
-    if (threadIdx.x == 0) { sm.flags[0] = 0; sm.flags[14] = 0; }
+    if (threadIdx.x == 0) { sm.flags[0] = o.force_fail == inst + 1; if (sm.flags[14] != 2) sm.flags[14] = 0; }
     read_warm(c, L, sol, inst);  // zb, xib, yfb, ygb <- solution
     linearize(c);                // Jacobians and g at the solution
     float* code = c.zg;   // active codes

@@ -1023,6 +1023,34 @@ __device__ __forceinline__ bool factor(const Inst<M>& c, const KOpts& o, float r
     return ok;
 }
 
+// A factorisation of S failed (uniform over the team): classify it.  A NaN entry
+// of S propagates into the factors, so NaN in the factor blocks is a NaN event
+// (bit 2 of the instance flag); otherwise a pivot block was not positive
+// definite (bit 1).  Only the N x N entries of each block are read.
+template <int M>
+__device__ __forceinline__ void note_factor_failure(const Inst<M>& c, float* red) {
+    constexpr int NN = Inst<M>::NN, BS = Inst<M>::BS;
+    float v[1] = {0.f};
+    const int cnt = c.T * NN;
+    for (int e = c.tid; e < cnt; e += c.nth) {
+        const int q = (e / NN) * BS + e % NN;
+        if (c.Dm[q] != c.Dm[q] || c.Um[q] != c.Um[q]) v[0] = 1.f;
+    }
+    team_max_k<M, 1>(c, v, red);
+    if (c.tid == 0) c.tflags[0] |= v[0] > 0.f ? 2 : 1;
+    c.sync();
+}
+
+// per-instance status from the instance flag (bit 1: a pivot block was not
+// positive definite, bit 2: NaN met by a factorisation), the final point and
+// its KKT residual: the root cause first
+__device__ __forceinline__ int instance_status(int flags, bool finite, float kkt, float eps_c) {
+    if (flags & 2) return TMPC_INST_NAN;
+    if (flags & 1) return TMPC_INST_NOT_PD;
+    if (!finite || !(kkt < kInf)) return TMPC_INST_NAN;
+    return kkt <= eps_c ? TMPC_INST_OK : TMPC_INST_MAX_ITER;
+}
+
 // ---------------------------------------------------------------------------
 // Algorithm 1 for one instance
 // ---------------------------------------------------------------------------
@@ -1031,7 +1059,7 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
                                int inst, int warm) {
     constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
     const int T = c.T;
-    if (c.tid == 0) c.tflags[0] = 0;
+    if (c.tid == 0) c.tflags[0] = o.force_fail == inst + 1;   // NOT_PD flag (forced by the caller for one instance)
     c.cache_params();
     const long long Ts = L.Nmax + 1;
     if (warm) {
@@ -1061,7 +1089,7 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
             if (kkt<M>(c, rs.red) <= o.eps_c) break;
         }
         ++nfact;
-        if (!factor<M, P>(c, o, rho, c.tflags + 1) && c.tid == 0) c.tflags[0] = 1;
+        if (!factor<M, P>(c, o, rho, c.tflags + 1)) note_factor_failure<M>(c, rs.red);
         for (int e = c.tid; e < T * N; e += c.nth) c.x[e] = 0.f;
         for (int e = c.tid; e < T * NX; e += c.nth) { c.yf[e] = c.yfb[e]; c.pf[e] = -c.cv[e]; }
         for (int e = c.tid; e < T * NG; e += c.nth) {
@@ -1093,7 +1121,7 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
                             admm_rowvec<M>(c, rho);
                         } else {
                             ++nfact;
-                            if (!factor<M, P>(c, o, rho, c.tflags + 1) && c.tid == 0) c.tflags[0] = 1;
+                            if (!factor<M, P>(c, o, rho, c.tflags + 1)) note_factor_failure<M>(c, rs.red);
                         }
                     }
                 }
@@ -1141,10 +1169,7 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
         yfo[e] = (t < T && k < NX) ? c.yfb[t * NX + k] : 0.f;
     }
     if (c.tid == 0) {
-        int st = TMPC_INST_OK;
-        if (!(bad[0] < kInf) || !(kk < kInf)) st = TMPC_INST_NAN;
-        else if (c.tflags[0]) st = TMPC_INST_NOT_PD;
-        else if (!(kk <= o.eps_c)) st = TMPC_INST_MAX_ITER;
+        const int st = instance_status(c.tflags[0], bad[0] < kInf, kk, o.eps_c);
         if (out.status) out.status[inst] = st;
         if (out.stats) {
             float* s = out.stats + (long long)inst * TMPC_STATS;
@@ -1173,7 +1198,7 @@ __device__ __forceinline__ void backward_instance_team(Inst<M>& c, const KOpts& 
     const float* dLdz = dLdz_all + inst * Ts * L.n;
     const float* dLdxi = dLdxi_all ? dLdxi_all + inst * Ts * L.ng : nullptr;
     float rb = o.bwd_rho;
-    if (c.tid == 0) c.tflags[0] = 0;
+    if (c.tid == 0) c.tflags[0] = o.force_fail == inst + 1;
     c.cache_params();
     // the solution is the point of the linearisation
     {
@@ -1573,7 +1598,7 @@ __global__ void __launch_bounds__(256, 2) plain_init(KLayout L, KOpts o, KParams
     if (!plain_bind<M>(c, L, p, gws, gstride, order, count, x0, ps, i)) return;
     const int T = c.T;
     if (c.tid == 0) {
-        c.tflags[0] = 0;
+        c.tflags[0] = o.force_fail == i + 1;
         PlainState& st = ps[i];
         st.rho = o.rho0; st.rp = 0.f; st.rd = 0.f; st.alpha_last = 1.f;
         st.admm_total = 0; st.nfact = 0; st.sqp_done = 0; st.ls_hist[0] = 0; st.ls_hist[1] = 0;
@@ -1607,10 +1632,11 @@ __global__ void __launch_bounds__(256, 2) plain_sqp_begin(KLayout L, KOpts o, KP
     Inst<M> c;
     int i;
     if (!plain_bind<M>(c, L, p, gws, gstride, order, count, x0, ps, i)) return;
+    __shared__ float red[32 * 8];
     const int T = c.T;
     const float rho = ps[i].rho;
     linearize<M>(c);
-    if (!factor<M, kCR>(c, o, rho, c.tflags + 1) && c.tid == 0) c.tflags[0] = 1;
+    if (!factor<M, kCR>(c, o, rho, c.tflags + 1)) note_factor_failure<M>(c, red);
     for (int e = c.tid; e < T * N; e += c.nth) c.x[e] = 0.f;
     for (int e = c.tid; e < T * NX; e += c.nth) { c.yf[e] = c.yfb[e]; c.pf[e] = -c.cv[e]; }
     for (int e = c.tid; e < T * NG; e += c.nth) {
@@ -1649,7 +1675,7 @@ __global__ void __launch_bounds__(256, 2) plain_admm(KLayout L, KOpts o, KParams
                     admm_rowvec<M>(c, rho);
                 } else {
                     ++nf;
-                    if (!factor<M, kCR>(c, o, rho, c.tflags + 1) && c.tid == 0) c.tflags[0] = 1;
+                    if (!factor<M, kCR>(c, o, rho, c.tflags + 1)) note_factor_failure<M>(c, red);
                 }
             }
         }
@@ -1733,10 +1759,7 @@ __global__ void __launch_bounds__(256, 2) plain_final(KLayout L, KOpts o, KParam
     }
     if (c.tid == 0) {
         const PlainState& st = ps[i];
-        int sts = TMPC_INST_OK;
-        if (!(bad[0] < kInf) || !(kk < kInf)) sts = TMPC_INST_NAN;
-        else if (c.tflags[0]) sts = TMPC_INST_NOT_PD;
-        else if (!(kk <= o.eps_c)) sts = TMPC_INST_MAX_ITER;
+        const int sts = instance_status(c.tflags[0], bad[0] < kInf, kk, o.eps_c);
         if (out.status) out.status[i] = sts;
         if (out.stats) {
             float* s = out.stats + (long long)i * TMPC_STATS;

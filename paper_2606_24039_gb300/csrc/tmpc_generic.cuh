@@ -137,10 +137,28 @@ __device__ inline void write_solution(const Ctx& c, const KLayout& L, const KSol
     }
 }
 
+// A factorisation of S failed (uniform over the CTA): NaN in the factor blocks
+// (from a NaN entry of S) is a NaN event, bit 2 of sm.flags[0]; otherwise a pivot
+// block was not positive definite, bit 1.
+__device__ inline void note_factor_failure(const Ctx& c, const Smem& sm) {
+    const long long nn = (long long)c.n * c.n;
+    float v[1] = {0.f};
+    for (long long e = threadIdx.x; e < c.T * nn; e += blockDim.x) {
+        const float d = c.Dinv[e];
+        const float u = e < c.N * nn ? c.Om[e] : 0.f;
+        if (d != d || u != u) v[0] = 1.f;
+    }
+    cta_max_k<1>(v, sm.red);
+    if (threadIdx.x == 0) sm.flags[0] |= v[0] > 0.f ? 2 : 1;
+    __syncthreads();
+}
+
 __device__ inline void solve_instance(const Ctx& c, const KOpts& o, const Smem& sm, const KLayout& L,
                                const KSol& out, int inst, int warm) {
     const int n = c.n, nx = c.nx, ng = c.ng, T = c.T;
-    if (threadIdx.x == 0) { sm.flags[0] = 0; sm.flags[14] = 0; }
+    // NOT_PD flag (set by a failed factorisation, or from the start for the instance a
+    // caller forces to fail); a wait whose copy never landed (2) stays for the launch
+    if (threadIdx.x == 0) { sm.flags[0] = o.force_fail == inst + 1; if (sm.flags[14] != 2) sm.flags[14] = 0; }
     if (warm) {
         read_warm(c, L, out, inst);
     } else {
@@ -159,7 +177,7 @@ __device__ inline void solve_instance(const Ctx& c, const KOpts& o, const Smem& 
             if (kk <= o.eps_c) break;
         }
         ++nfact;
-        if (!factor(c, sm, o.sigma, 1e3f * rho, rho, false) && threadIdx.x == 0) sm.flags[0] = 1;
+        if (!factor(c, sm, o.sigma, 1e3f * rho, rho, false)) note_factor_failure(c, sm);
         // warm start of the QP from the current primal-dual point (x = zb, z_g = G zb),
         // i.e. zero step, with the equality defect p_f = C x - c = -cv
         for (int e = threadIdx.x; e < T * n; e += blockDim.x) c.x[e] = 0.f;
@@ -194,7 +212,7 @@ __device__ inline void solve_instance(const Ctx& c, const KOpts& o, const Smem& 
                             rho = cand;
                         } else {
                             ++nfact;
-                            if (!factor(c, sm, o.sigma, 1e3f * rho, rho, false) && threadIdx.x == 0) sm.flags[0] = 1;
+                            if (!factor(c, sm, o.sigma, 1e3f * rho, rho, false)) note_factor_failure(c, sm);
                         }
                     }
                 }
@@ -226,9 +244,12 @@ __device__ inline void solve_instance(const Ctx& c, const KOpts& o, const Smem& 
     write_solution(c, L, out, inst);
     if (threadIdx.x == 0) {
         int st = TMPC_INST_OK;
-        if (!(bad[0] < kInf) || !(kk < kInf)) st = TMPC_INST_NAN;
-        else if (sm.flags[14]) st = TMPC_INST_TIMEOUT;
-        else if (sm.flags[0]) st = TMPC_INST_NOT_PD;
+        // root cause first: a wait that gave up, NaN met by a factorisation, a pivot block
+        // that was not positive definite, then NaN in the result
+        if (sm.flags[14]) st = TMPC_INST_TIMEOUT;
+        else if (sm.flags[0] & 2) st = TMPC_INST_NAN;
+        else if (sm.flags[0] & 1) st = TMPC_INST_NOT_PD;
+        else if (!(bad[0] < kInf) || !(kk < kInf)) st = TMPC_INST_NAN;
         else if (!(kk <= o.eps_c)) st = TMPC_INST_MAX_ITER;
         if (out.status) out.status[inst] = st;
         if (out.stats) {

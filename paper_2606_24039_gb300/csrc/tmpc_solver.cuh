@@ -32,6 +32,8 @@ struct KOpts {
     int max_sqp, max_admm, n_ls, newton_steps, early_exit, check_every;
     float bwd_rho, bwd_sigma;
     int bwd_iters;
+    int force_fail;   // instance index + 1 whose NOT_PD flag starts set (0: none)
+    int wait_polls;   // polls of a bounded wait on an asynchronous copy (0: kMbarSpin)
 };
 
 struct KLayout {
@@ -959,8 +961,8 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
 // wait for phase `parity` of `bar` to complete; false if it did not within kMbarSpin
 // polls, or as soon as *abort (shared, may be NULL) is set by a thread that gave up
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
-                                          const volatile int* abort = nullptr) {
-    for (unsigned k = 0; k < kMbarSpin; ++k) {
+                                          const volatile int* abort = nullptr, unsigned polls = kMbarSpin) {
+    for (unsigned k = 0; k < polls; ++k) {
         unsigned done;
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}"
@@ -972,12 +974,14 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 }
 
 // once per CTA, before the first stream: both mbarriers and the stream state
-__device__ inline void block_stream_init(unsigned long long* mbar, int* state) {
+// (state[3]: polls of a bounded wait, the wait_polls option or kMbarSpin)
+__device__ inline void block_stream_init(unsigned long long* mbar, int* state, int polls = 0) {
     if (threadIdx.x == 0) {
         mbar_init(mbar, 1);
         mbar_init(mbar + 1, 1);
         fence_mbar_init();
         state[0] = state[1] = state[2] = 0;
+        state[3] = polls > 0 ? polls : (int)kMbarSpin;
     }
     __syncthreads();
 }
@@ -989,21 +993,37 @@ struct BlockStream {
     float* buf[2];
     unsigned long long* bar;
     unsigned phase[2];
+    unsigned inflight;   // thread 0: buffers with a copy issued and not yet waited for
+    unsigned polls;
     bool ok;
-    int* state;   // shared: [0], [1] phase bits of the two mbarriers, [2] set if a wait gave up
-    __device__ BlockStream(float* b0, float* b1, unsigned long long* bars, int* st) : bar(bars), ok(true), state(st) {
+    int* state;   // shared: [0], [1] phase bits of the two mbarriers, [2] set if a wait gave up, [3] polls
+    __device__ BlockStream(float* b0, float* b1, unsigned long long* bars, int* st)
+        : bar(bars), inflight(0u), state(st) {
         buf[0] = b0;
         buf[1] = b1;
         phase[0] = (unsigned)st[0];
         phase[1] = (unsigned)st[1];
+        polls = (unsigned)st[3];
+        ok = st[2] == 0;   // after a wait gave up, the rest of the instance reads global memory
     }
-    // after the last get / sync of a solve: store the phase bits for the next solve
+    // after the last get / sync of a solve: store the phase bits for the next solve.
+    // If a wait gave up, copies may still be in flight into the two buffers, which
+    // the factorisation reuses as scratch: thread 0 waits (bounded) for each of them
+    // to land before the buffers are released; state[2] = 2 records a copy that
+    // did not land (the buffers are then not safe for the rest of the launch, and
+    // every later wait of the CTA gives up at once).
     __device__ void finish() {
         __syncthreads();
         if (threadIdx.x == 0) {
+            for (int b = 0; b < 2; ++b) {
+                if (!(inflight & (1u << b))) continue;
+                if (mbar_wait(bar + b, phase[b], nullptr, (unsigned)kMbarSpin)) phase[b] ^= 1u;
+                else state[2] = 2;
+            }
+            inflight = 0u;
             state[0] = (int)phase[0];
             state[1] = (int)phase[1];
-            if (!ok) state[2] = 1;
+            if (!ok && state[2] == 0) state[2] = 1;
         }
         __syncthreads();
     }
@@ -1012,6 +1032,7 @@ struct BlockStream {
         if (threadIdx.x == 0 && ok) {
             fence_proxy_async();
             bulk_load(buf[k & 1], src, bytes, bar + (k & 1));
+            inflight |= 1u << (k & 1);
         }
     }
     // every thread: wait for the block of step k; returns the shared copy, or
@@ -1022,17 +1043,18 @@ struct BlockStream {
     __device__ const float* get(int k, const float* fallback) {
         if (!ok) return fallback;
         const volatile int* gave_up = state + 2;
-        if (*gave_up || !mbar_wait(bar + (k & 1), phase[k & 1], gave_up)) {
+        if (*gave_up || !mbar_wait(bar + (k & 1), phase[k & 1], gave_up, polls)) {
             ok = false;
-            state[2] = 1;
+            if (*gave_up == 0) state[2] = 1;
             return fallback;
         }
         phase[k & 1] ^= 1u;
+        inflight &= ~(1u << (k & 1));
         return buf[k & 1];
     }
 };
 
-// sbuf0/sbuf1 (n^2 floats each), mbar (2 mbarriers) and mstate (3 ints) enable
+// sbuf0/sbuf1 (n^2 floats each), mbar (2 mbarriers) and mstate (4 ints) enable
 // the shared-memory block stream; without them the blocks are read from global memory.
 __device__ inline void ldl_solve(const Ctx& c, float* b, float* xo, float* red, float* sbuf0 = nullptr,
                                  float* sbuf1 = nullptr, unsigned long long* mbar = nullptr, int* mstate = nullptr) {

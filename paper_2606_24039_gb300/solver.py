@@ -215,30 +215,43 @@ def tmpc_solve_static(dims: dict, params: dict, x0, sol: dict, options: _abi.Opt
 
 
 class TmpcFunction(torch.autograd.Function):
-    """z, xi = OCP-solve(x0, Qd, Rd, ref, lo, hi) with the implicit-differentiation
-    backward of the library.  The solver handle carries the remaining parameters."""
+    """(z, xi, status) = OCP solve of Algorithm 1 as a function of x0 and the cost
+    and bound parameters, with the implicit-differentiation backward of the
+    library (Algorithm 2).  Differentiable inputs: x0, Qd, Rd, ref, lo, hi and,
+    when given (not None), Wd, lin, gamma2, gamma1; the solver handle carries
+    the remaining parameters (dynamics, track).  The forward keeps only the
+    solution and the inputs: the backward refactors the adjoint system from
+    the solution instead of storing any ADMM iterate."""
 
     @staticmethod
-    def forward(ctx, solver: Solver, x0, Qd, Rd, ref, lo, hi):
-        x0, Qd, Rd, ref, lo, hi = (t.detach().float().contiguous() for t in (x0, Qd, Rd, ref, lo, hi))
-        solver.tmpc_update_params(dict(Qd=Qd, Rd=Rd, ref=ref, lo=lo, hi=hi))
+    def forward(ctx, solver: Solver, x0, Qd, Rd, ref, lo, hi, Wd=None, lin=None, gamma2=None, gamma1=None):
+        names = ("Qd", "Rd", "ref", "lo", "hi", "Wd", "lin", "gamma2", "gamma1")
+        vals = [None if t is None else t.detach().float().contiguous() for t in (Qd, Rd, ref, lo, hi, Wd, lin, gamma2, gamma1)]
+        x0 = x0.detach().float().contiguous()
+        params = {k: v for k, v in zip(names, vals) if v is not None}
+        solver.tmpc_update_params(params)
         sol = solver.tmpc_solve(x0)
         ctx.solver = solver
         ctx.sol = sol
-        ctx.save_for_backward(x0, Qd, Rd, ref, lo, hi)
+        ctx.names = [k for k, v in zip(names, vals) if v is not None]
+        ctx.given = [v is not None for v in vals]
+        ctx.save_for_backward(x0, *[v for v in vals if v is not None])
         ctx.mark_non_differentiable(sol["status"])
         return sol["z"], sol["xi"], sol["status"]
 
     @staticmethod
     def backward(ctx, dz, dxi, _dstatus):
-        x0, Qd, Rd, ref, lo, hi = ctx.saved_tensors
+        x0, *vals = ctx.saved_tensors
         solver = ctx.solver
-        solver.tmpc_update_params(dict(Qd=Qd, Rd=Rd, ref=ref, lo=lo, hi=hi))
+        solver.tmpc_update_params(dict(zip(ctx.names, vals)))
         g = solver.tmpc_backward(x0, ctx.sol, dz.contiguous().float(),
                                  None if dxi is None else dxi.contiguous().float())
-        return None, g["x0"], g["Qd"], g["Rd"], g["ref"], g["lo"], g["hi"]
+        out = [g["x0"]]
+        for k, given in zip(("Qd", "Rd", "ref", "lo", "hi", "Wd", "lin", "gamma2", "gamma1"), ctx.given):
+            out.append(g.get(k) if given else None)
+        return (None, *out)
 
 
-def solve_ocp(solver: Solver, x0, Qd, Rd, ref, lo, hi):
+def solve_ocp(solver: Solver, x0, Qd, Rd, ref, lo, hi, Wd=None, lin=None, gamma2=None, gamma1=None):
     """Differentiable forward solve; returns (z, xi, status)."""
-    return TmpcFunction.apply(solver, x0, Qd, Rd, ref, lo, hi)
+    return TmpcFunction.apply(solver, x0, Qd, Rd, ref, lo, hi, Wd, lin, gamma2, gamma1)

@@ -121,3 +121,17 @@ def test_static_entry_rejects_a_workspace_beyond_int_offsets(lib):
     s = _abi.Solution(*([fake] * 6))
     assert lib.tmpc_solve_static(ctypes.byref(d), ctypes.byref(o), ctypes.byref(p), fake, ctypes.byref(s), 0, None) == 1
     assert "exceeds 2^31 floats" in lib.tmpc_last_error().decode()
+
+
+def test_options_mirror_matches_the_header():
+    """The ctypes mirror of tmpc_options has the header's fields, in order and type."""
+    from paper_2606_24039_gb300 import _abi
+    src = open(os.path.join(ROOT, "include", "tmpc.h")).read()
+    end = src.index("} tmpc_options;")
+    body = src[src.rindex("typedef struct {", 0, end) + len("typedef struct {"):end]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in re.findall(r"\b(int32_t|float)\s+([^;]+);", body):
+        for name in decl[1].split(","):
+            fields.append((name.strip(), {"int32_t": ctypes.c_int32, "float": ctypes.c_float}[decl[0]]))
+    assert fields == list(_abi.Options._fields_)

@@ -511,10 +511,14 @@ def test_backward_racing_on_oracle_point(solver):
     g = s.tmpc_backward(s.x0, sol, torch.tensor(dLdz, dtype=torch.float32, device="cuda"))
     torch.cuda.synchronize()
     keys = ("x0", "Qd", "Rd", "Wd", "ref", "lin", "lo", "hi", "gamma2", "gamma1")
+    compared = 0
     for i in range(pb.B):
         gr, info = obwd.backward(pb.instance(i), refs[i], dLdz[i], eps_g=pb.opts.eps_g)
-        if info["singular"]:
+        if info["singular"]:     # LICQ fails: the active-set KKT matrix has no inverse
             continue
-        a = np.concatenate([g[k][i].cpu().numpy().reshape(-1) for k in keys])
-        b = np.concatenate([gr[k].reshape(-1) for k in keys])
-        assert np.linalg.norm(a - b) / np.linalg.norm(b) < GRAD_TOL, (i, np.linalg.norm(a - b) / np.linalg.norm(b))
+        compared += 1
+        scale = max(np.linalg.norm(gr[k]) for k in keys)
+        for k in keys:   # per parameter: a wrong W or gamma gradient cannot hide under x0 / ref
+            rel = _grad_rel(g[k][i].cpu().numpy().reshape(-1), gr[k].reshape(-1), scale)
+            assert rel < GRAD_TOL, (i, k, rel)
+    assert compared >= 2
