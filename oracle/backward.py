@@ -106,7 +106,10 @@ def backward(inst, sol, dLdz, dLdxi=None, eps_g=1e-4, exact_hessian=False):
     rhs = np.concatenate([dLdz.reshape(-1), dLdxi.reshape(-1)[slk_idx], np.zeros(nf + na)])
     singular = False
     with np.errstate(all="ignore"):
-        eta = spla.spsolve(K, rhs)
+        try:
+            eta = spla.spsolve(K, rhs)
+        except RuntimeError:        # the LU met an exactly zero pivot: singular, as a non-finite result
+            eta = np.full(rhs.shape, np.nan)
     if not np.all(np.isfinite(eta)):
         singular = True
         reg = sp.diags(np.concatenate([np.zeros(nz + ns), -1e-10 * np.ones(nf + na)]))

@@ -107,13 +107,24 @@ bool ws_layout(const tmpc_dims& d, WsOff& off) {
 }
 
 // The generic kernels may be launched with any dynamic shared-memory size up to
-// the device's opt-in maximum; the attribute is a limit, not a reservation, so it
-// is raised once to that maximum and never lowered by a later, smaller launch.
+// the device's opt-in maximum less their static shared memory; the attribute is a
+// limit, not a reservation, so it is raised to that maximum and never lowered by a
+// later, smaller launch.  A failed attribute call is cleared from the runtime's
+// last error so that it cannot be reported by a later launch check.
 cudaError_t allow_max_smem(int max_optin) {
-    cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin);
-    return e;
+    const void* kernels[2] = {(const void*)solve_kernel, (const void*)backward_kernel};
+    for (const void* k : kernels) {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, k);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     max_optin - (int)fa.sharedSizeBytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
+    }
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -461,7 +472,10 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
     // ADMM vectors in shared memory when two CTAs per SM still fit
     h->L.vs = choose_vs(h->L, h->threads, max_optin);
     h->smem = smem_bytes(h->L);
-    if (h->smem > 48 * 1024) allow_max_smem(max_optin);
+    if (h->smem > 48 * 1024) {
+        e = allow_max_smem(max_optin);
+        if (e != cudaSuccess) { set_err("generic kernels: shared-memory limit", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
+    }
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel, h->threads, h->smem);
     h->grid_solve = std::max(1, std::min(d->batch, std::max(per_sm, 1) * h->nsm));
