@@ -64,7 +64,8 @@ enum {
 /* model ids (problem families; dynamics as in Appendix A of the paper, Remark A1) */
 enum {
     TMPC_MODEL_DOUBLE_INTEGRATOR = 0, /* nx=4 nu=2 ng=4, ZOH.  dyn = [dt]                          */
-    TMPC_MODEL_LINEAR = 1,            /* layout nx, nu, ng=nu; x+ = A x + B u.  dyn = [A, B]      */
+    TMPC_MODEL_LINEAR = 1,            /* layout nx, nu, ng=nu; x+ = A x + B u + b.  dyn = [A, B, b]
+                                         (row-major; b is optional: 0 when n_dyn < nx^2 + nx nu + nx) */
     TMPC_MODEL_BICYCLE = 2,           /* nx=6 nu=2 ng=5, implicit midpoint.  dyn = [dt, L, ds, nt] */
     TMPC_MODEL_QUADROTOR = 3          /* nx=6 nu=2 ng=2, RK4.  dyn = [dt, m, I, arm, g]            */
 };
@@ -121,9 +122,13 @@ typedef struct {
      *   tmpc_backward; the arithmetic is unchanged); 0 = none.
      * wait_polls: polls of each bounded wait on an asynchronous shared-memory copy of
      *   the generic kernel before it gives up (status TMPC_INST_TIMEOUT; the instance
-     *   finishes on global-memory reads of the same values); 0 = the default, 2^24. */
+     *   finishes on global-memory reads of the same values); 0 = the default, 2^24.
+     * force_wait_timeout: nonzero makes every such wait give up at once, as if its
+     *   copy had not landed in time (the copies still in flight are then waited for,
+     *   bounded, before their shared buffers are reused). */
     int32_t force_pivot_failure;
     int32_t wait_polls;
+    int32_t force_wait_timeout;
 } tmpc_options;
 
 /* Problem parameters theta (the OCP of Appendix A with the cost of Eq. (cost)).
@@ -271,6 +276,24 @@ typedef struct {
  * or trial_sqp out of range), CUDA, OOM. */
 tmpc_status tmpc_autotune(tmpc_handle* h, const float* x0, const tmpc_solution* init, int32_t reps,
                           int32_t trial_sqp, tmpc_tune_result* res, void* stream);
+
+/* Device time of the last launches of a handle, one entry per model group of the
+ * forward (the order of tmpc_tune_result) and, when the generic backward kernel
+ * ran for instances outside the generic group, one more entry for it.  The paper
+ * has no counterpart: it is the measurement hook of the roofline report, timing
+ * each persistent kernel by CUDA events recorded on the stream it is launched on
+ * (not recorded while that stream is being captured into a graph). */
+typedef struct {
+    int32_t model;   /* model id of the group; -1: the generic kernel                    */
+    int32_t form;    /* launch form, as the codes of tmpc_options.solver                 */
+    int32_t count;   /* instances                                                          */
+    float fwd_ms;    /* the group's last forward launch(es), ms; -1 if not timed           */
+    float bwd_ms;    /* the group's last backward launch, ms; -1 if not timed or none     */
+} tmpc_group_time;
+
+/* out [5] (HOST) receives *n_out entries.  Synchronises on the recorded events.
+ * Errors: NOT_SETUP, INVALID_ARG (out or n_out NULL). */
+tmpc_status tmpc_group_times(tmpc_handle* h, tmpc_group_time* out, int32_t* n_out);
 
 /* End-to-end forward pass from HOST memory: copies the parameter arrays of
  * host_p and x0 (HOST pointers, pinned memory recommended) into device

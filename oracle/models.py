@@ -141,11 +141,15 @@ def di_matrices(dt):
 
 
 def linear_matrices(inst):
+    """A, B and the affine term b of x+ = A x + B u + b (b = 0 when the
+    parameters stop after B)."""
     nx, nu = inst["nx"], inst["nu"]
     d = inst["dyn"]
     A = d[:nx * nx].reshape(nx, nx)
     B = d[nx * nx:nx * nx + nx * nu].reshape(nx, nu)
-    return A, B
+    o = nx * nx + nx * nu
+    b = d[o:o + nx].copy() if d.size >= o + nx else np.zeros(nx)
+    return A, B, b
 
 
 # ----------------------------------------------------------------------------
@@ -164,8 +168,8 @@ def dynamics(inst, z):
         if model == MODEL_QUAD:
             phi, Jx, Ju = quad_rk4(x[:-1], u[:-1], inst["dyn"])
         else:
-            A, B = di_matrices(inst["dyn"][0]) if model == MODEL_DI else linear_matrices(inst)
-            phi = x[:-1] @ A.T + u[:-1] @ B.T
+            A, B, b = (*di_matrices(inst["dyn"][0]), np.zeros(nx)) if model == MODEL_DI else linear_matrices(inst)
+            phi = x[:-1] @ A.T + u[:-1] @ B.T + b
             Jx = np.broadcast_to(A, (N, nx, nx))
             Ju = np.broadcast_to(B, (N, nx, nu))
         f = phi - x[1:]
@@ -196,8 +200,8 @@ def rollout_guess(inst, x, u):
         A, B = di_matrices(inst["dyn"][0])
         return A @ x + B @ u
     if model == MODEL_LINEAR:
-        A, B = linear_matrices(inst)
-        return A @ x + B @ u
+        A, B, b = linear_matrices(inst)
+        return A @ x + B @ u + b
     if model == MODEL_BICYCLE:
         fc, _, _ = bicycle_fc(x[None], u[None], inst["dyn"], inst["track"])
         return x + inst["dyn"][0] * fc[0]

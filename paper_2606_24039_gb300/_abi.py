@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
                 ("check_every", ctypes.c_int32), ("bwd_rho", ctypes.c_float),
                 ("bwd_sigma", ctypes.c_float), ("bwd_iters", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("solver", ctypes.c_int32),
-                ("force_pivot_failure", ctypes.c_int32), ("wait_polls", ctypes.c_int32)]
+                ("force_pivot_failure", ctypes.c_int32), ("wait_polls", ctypes.c_int32),
+                ("force_wait_timeout", ctypes.c_int32)]
 
 
 class Params(ctypes.Structure):
@@ -68,6 +69,11 @@ EXPORTS = ["tmpc_default_options", "tmpc_setup", "tmpc_update_params", "tmpc_set
            "tmpc_status_string", "tmpc_last_error", "tmpc_solve_static", "tmpc_autotune"]
 
 _lib = None
+
+
+class GroupTime(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("form", ctypes.c_int32), ("count", ctypes.c_int32),
+                ("fwd_ms", ctypes.c_float), ("bwd_ms", ctypes.c_float)]
 
 
 class TmpcError(RuntimeError):
@@ -106,6 +112,8 @@ def load(path: str | None = None):
     lib.tmpc_autotune.argtypes = [vp, vp, ctypes.POINTER(Solution), ctypes.c_int32, ctypes.c_int32,
                                   ctypes.POINTER(TuneResult), vp]
     lib.tmpc_autotune.restype = ctypes.c_int
+    lib.tmpc_group_times.argtypes = [vp, ctypes.POINTER(GroupTime), ctypes.POINTER(ctypes.c_int32)]
+    lib.tmpc_group_times.restype = ctypes.c_int
     lib.tmpc_destroy.argtypes = [vp]
     lib.tmpc_destroy.restype = None
     lib.tmpc_status_string.argtypes = [ctypes.c_int]

@@ -45,6 +45,7 @@ KOpts to_kopts(const tmpc_options& o) {
     k.bwd_rho = o.bwd_rho; k.bwd_sigma = o.bwd_sigma; k.bwd_iters = o.bwd_iters;
     k.force_fail = o.force_pivot_failure;
     k.wait_polls = o.wait_polls;
+    k.force_timeout = o.force_wait_timeout;
     if (k.k_rho_iter < 1) k.k_rho_iter = 1 << 30;
     return k;
 }
@@ -158,6 +159,10 @@ struct tmpc_handle {
     // several model groups run concurrently on internal streams (fork / join on the caller's stream)
     cudaStream_t gs[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t ev_fork = nullptr, ev_join[4] = {nullptr, nullptr, nullptr, nullptr};
+    // device timing of the last launches, per forward group (slots 0..3) and the generic
+    // backward (slot 4): [slot][0..1] forward start / stop, [slot][2..3] backward start / stop
+    cudaEvent_t tev[5][4] = {};
+    bool timed[5][2] = {};
     int n_groups = 0;
     float* fws = nullptr;      // global arenas of the shared-memory path (instances that do not fit)
     long long fstride = 0;
@@ -467,6 +472,9 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
         if (e != cudaSuccess) { set_err("group streams", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
     }
     if (tmpc_status st = ensure_buffers(h); st != TMPC_OK) { tmpc_destroy(h); return st; }
+    for (int g = 0; g < 5 && e == cudaSuccess; ++g)
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&h->tev[g][k]);
+    if (e != cudaSuccess) { set_err("timing events", e); tmpc_destroy(h); return TMPC_ERR_CUDA; }
 
     h->threads = o->threads > 0 ? o->threads : (n <= 16 ? 128 : 256);
     // ADMM vectors in shared memory when two CTAs per SM still fit
@@ -564,6 +572,16 @@ static tmpc_status launch_group(tmpc_handle* h, int g, const KOpts& ko, const KP
     return TMPC_OK;
 }
 
+// launches are timed by events on their stream unless the stream is being captured
+static bool timing_ok(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs == cudaStreamCaptureStatusNone;
+}
+
 static tmpc_status launch_solve(tmpc_handle* h, const tmpc_params& p, const float* x0,
                                 const tmpc_solution& out, int warm, cudaStream_t s) {
     KSol ks{out.z, out.xi, out.y_eq, out.y_ineq, out.status, out.stats};
@@ -578,7 +596,11 @@ static tmpc_status launch_solve(tmpc_handle* h, const tmpc_params& p, const floa
             s = h->gs[g];
             TMPC_CUDA(cudaStreamWaitEvent(s, h->ev_fork, 0));
         }
+        const bool t = timing_ok(s);
+        if (t) TMPC_CUDA(cudaEventRecord(h->tev[g][0], s));
         if (tmpc_status st = launch_group(h, g, ko, kp, ks, x0, warm, s); st != TMPC_OK) return st;
+        if (t) TMPC_CUDA(cudaEventRecord(h->tev[g][1], s));
+        h->timed[g][0] = t;
         if (fork) TMPC_CUDA(cudaEventRecord(h->ev_join[g], s));
     }
     if (fork)
@@ -715,6 +737,7 @@ tmpc_status tmpc_backward(tmpc_handle* h, const float* x0, const tmpc_solution* 
     const bool fork = h->n_groups > 1 && h->ev_fork;
     if (fork) TMPC_CUDA(cudaEventRecord(h->ev_fork, s));
     int used = 0;
+    for (int gi = 0; gi < 5; ++gi) h->timed[gi][1] = false;
     for (int gi = 0; gi < h->n_groups; ++gi) {
         const tmpc_handle::Group& G = h->groups[gi];
         if (G.bgrid <= 0) continue;
@@ -723,18 +746,26 @@ tmpc_status tmpc_backward(tmpc_handle* h, const float* x0, const tmpc_solution* 
             sg = h->gs[gi];
             TMPC_CUDA(cudaStreamWaitEvent(sg, h->ev_fork, 0));
         }
+        const bool t = timing_ok(sg);
+        if (t) TMPC_CUDA(cudaEventRecord(h->tev[gi][2], sg));
         TMPC_CUDA(fast::launch_backward(G.model, G.cluster, G.bgrid, G.threads, G.smem, sg, h->L, ko, kp, ks, h->fws,
                                         h->fstride, h->order + G.offset, G.count, h->queue + gi, x0, h->gflags,
                                         dL_dz, dL_dxi, kg));
+        if (t) TMPC_CUDA(cudaEventRecord(h->tev[gi][3], sg));
+        h->timed[gi][1] = t;
         if (fork) {
             TMPC_CUDA(cudaEventRecord(h->ev_join[gi], sg));
             used |= 1 << gi;
         }
     }
     if (h->bwd_generic > 0) {
+        const bool t = timing_ok(s);
+        if (t) TMPC_CUDA(cudaEventRecord(h->tev[4][2], s));
         backward_kernel<<<std::min(h->grid_bwd, h->bwd_generic), h->threads, h->smem, s>>>(
             h->L, ko, kp, ks, h->ws, h->off, h->order + h->d.batch, h->bwd_generic, h->queue + 4, x0, dL_dz, dL_dxi, kg);
         TMPC_CUDA(cudaGetLastError());
+        if (t) TMPC_CUDA(cudaEventRecord(h->tev[4][3], s));
+        h->timed[4][1] = t;
     }
     for (int gi = 0; gi < h->n_groups; ++gi)
         if (used & (1 << gi)) TMPC_CUDA(cudaStreamWaitEvent(s, h->ev_join[gi], 0));
@@ -801,7 +832,45 @@ void tmpc_destroy(tmpc_handle* h) {
         if (h->ev_join[g]) cudaEventDestroy(h->ev_join[g]);
     }
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    for (int g = 0; g < 5; ++g)
+        for (int k = 0; k < 4; ++k)
+            if (h->tev[g][k]) cudaEventDestroy(h->tev[g][k]);
     delete h;
+}
+
+tmpc_status tmpc_group_times(tmpc_handle* h, tmpc_group_time* out, int32_t* n_out) {
+    if (!h) return TMPC_ERR_NOT_SETUP;
+    if (!out || !n_out) return TMPC_ERR_INVALID_ARG;
+    auto elapsed = [&](int slot, int k) -> float {
+        if (!h->timed[slot][k / 2]) return -1.f;
+        if (cudaEventSynchronize(h->tev[slot][k + 1]) != cudaSuccess) { cudaGetLastError(); return -1.f; }
+        float ms = -1.f;
+        if (cudaEventElapsedTime(&ms, h->tev[slot][k], h->tev[slot][k + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            return -1.f;
+        }
+        return ms;
+    };
+    int n = 0;
+    for (int g = 0; g < h->n_groups; ++g) {
+        const tmpc_handle::Group& G = h->groups[g];
+        tmpc_group_time& r = out[n++];
+        r.model = G.model;
+        r.form = G.model < 0 ? 1 : G.form;
+        r.count = G.count;
+        r.fwd_ms = elapsed(g, 0);
+        r.bwd_ms = G.model >= 0 && G.bgrid > 0 ? elapsed(g, 2) : -1.f;
+    }
+    if (h->bwd_generic > 0) {   // the generic backward (generic group and the LDL forms' instances)
+        tmpc_group_time& r = out[n++];
+        r.model = -1;
+        r.form = 1;
+        r.count = h->bwd_generic;
+        r.fwd_ms = -1.f;
+        r.bwd_ms = elapsed(4, 2);
+    }
+    *n_out = n;
+    return TMPC_OK;
 }
 
 }  // extern "C"

@@ -1023,18 +1023,23 @@ __device__ __forceinline__ bool factor(const Inst<M>& c, const KOpts& o, float r
     return ok;
 }
 
-// A factorisation of S failed (uniform over the team): classify it.  A NaN entry
-// of S propagates into the factors, so NaN in the factor blocks is a NaN event
-// (bit 2 of the instance flag); otherwise a pivot block was not positive
-// definite (bit 1).  Only the N x N entries of each block are read.
+// A factorisation of S failed (uniform over the team): classify it by the data S
+// is formed from.  A NaN in the stage Jacobians A^-_t, the dense G row or the
+// cost Hessian diagonal is a NaN event (bit 2 of the instance flag); otherwise a
+// pivot block of a finite S was not positive definite (bit 1).
 template <int M>
 __device__ __forceinline__ void note_factor_failure(const Inst<M>& c, float* red) {
-    constexpr int NN = Inst<M>::NN, BS = Inst<M>::BS;
+    using Tr = Traits<M>;
+    constexpr int N = Inst<M>::N, NX = Inst<M>::NX, AMS = Inst<M>::AMS;
     float v[1] = {0.f};
-    const int cnt = c.T * NN;
-    for (int e = c.tid; e < cnt; e += c.nth) {
-        const int q = (e / NN) * BS + e % NN;
-        if (c.Dm[q] != c.Dm[q] || c.Um[q] != c.Um[q]) v[0] = 1.f;
+    const int nam = (Tr::LTI ? 1 : c.Nh) * NX * N;   // A^-_t is written for t < N only
+    for (int e = c.tid; e < nam; e += c.nth) {
+        const float a = c.Am[(e / (NX * N)) * AMS + e % (NX * N)];
+        if (a != a) v[0] = 1.f;
+    }
+    for (int e = c.tid; e < c.T * N; e += c.nth) {
+        const float g = Tr::DENSE_ROW >= 0 ? c.Grow[e] : 0.f;
+        if (c.Pd[e] != c.Pd[e] || g != g) v[0] = 1.f;
     }
     team_max_k<M, 1>(c, v, red);
     if (c.tid == 0) c.tflags[0] |= v[0] > 0.f ? 2 : 1;

@@ -78,6 +78,8 @@ __device__ inline Ctx make_ctx(const KLayout& L, const KParams& p, float* ws, co
     c.g1 = p.g1 ? p.g1 + (long long)i * L.ng : nullptr;
     c.dyn = p.dyn + (long long)i * L.n_dyn;
     c.track = p.track ? p.track + (long long)i * (L.n_track + 1) * 4 : nullptr;
+    c.bv = (c.model == MODEL_LINEAR && L.n_dyn >= L.nx * L.nx + L.nx * L.nu + L.nx)
+               ? c.dyn + L.nx * L.nx + L.nx * L.nu : nullptr;
     if (c.model == MODEL_BICYCLE) {  // table intervals, clamped to the layout's table size
         const float ntf = c.dyn[3];
         int nt = (ntf == ntf) ? (int)fminf(fmaxf(ntf + 0.5f, 1.f), (float)L.n_track) : 1;
@@ -137,16 +139,21 @@ __device__ inline void write_solution(const Ctx& c, const KLayout& L, const KSol
     }
 }
 
-// A factorisation of S failed (uniform over the CTA): NaN in the factor blocks
-// (from a NaN entry of S) is a NaN event, bit 2 of sm.flags[0]; otherwise a pivot
-// block was not positive definite, bit 1.
+// A factorisation of S failed (uniform over the CTA): classify it by the data S
+// is formed from.  A NaN in the stage Jacobians A^-_t, A^+_t, G_t or in the cost
+// weights is a NaN event (bit 2 of sm.flags[0]); otherwise a pivot block of a
+// finite S was not positive definite (bit 1).
 __device__ inline void note_factor_failure(const Ctx& c, const Smem& sm) {
-    const long long nn = (long long)c.n * c.n;
     float v[1] = {0.f};
-    for (long long e = threadIdx.x; e < c.T * nn; e += blockDim.x) {
-        const float d = c.Dinv[e];
-        const float u = e < c.N * nn ? c.Om[e] : 0.f;
-        if (d != d || u != u) v[0] = 1.f;
+    const int jac = c.nx * c.n;
+    const int na = (c.amS ? c.N : 1) * jac, np = (c.apS ? c.N : 1) * jac, ngm = (c.gS ? c.T : 1) * c.ng * c.n;
+    for (int e = threadIdx.x; e < na; e += blockDim.x) if (c.Am[e] != c.Am[e]) v[0] = 1.f;
+    for (int e = threadIdx.x; e < np; e += blockDim.x) if (c.Ap[e] != c.Ap[e]) v[0] = 1.f;
+    for (int e = threadIdx.x; e < ngm; e += blockDim.x) if (c.Gm[e] != c.Gm[e]) v[0] = 1.f;
+    for (int e = threadIdx.x; e < c.T * c.n; e += blockDim.x) {
+        const int t = e / c.n, j = e % c.n;
+        const float w = j < c.nx ? c.Q(t, j) : c.R(t, j - c.nx);
+        if (w != w) v[0] = 1.f;
     }
     cta_max_k<1>(v, sm.red);
     if (threadIdx.x == 0) sm.flags[0] |= v[0] > 0.f ? 2 : 1;

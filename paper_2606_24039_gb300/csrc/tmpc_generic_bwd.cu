@@ -10,7 +10,7 @@ __global__ void __launch_bounds__(256, 2) backward_kernel(KLayout L, KOpts o, KP
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     const Smem sm = carve_smem(smem_raw, L);
-    block_stream_init(sm.mbar, sm.flags + 12, o.wait_polls);
+    block_stream_init(sm.mbar, sm.flags + 12, o.wait_polls, o.force_timeout);
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
         __syncthreads();

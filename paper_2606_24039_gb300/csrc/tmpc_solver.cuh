@@ -34,6 +34,7 @@ struct KOpts {
     int bwd_iters;
     int force_fail;   // instance index + 1 whose NOT_PD flag starts set (0: none)
     int wait_polls;   // polls of a bounded wait on an asynchronous copy (0: kMbarSpin)
+    int force_timeout;   // nonzero: every bounded wait gives up at once (test hook)
 };
 
 struct KLayout {
@@ -92,6 +93,7 @@ struct Ctx {
     int N, T, nx, nu, n, ng, model, nt;
     int lnx, lnu, ln, lng;
     const float *x0, *Qd, *Rd, *Wd, *ref, *lin, *lo, *hi, *g2, *g1, *dyn, *track;
+    const float* bv;   // linear model: affine term b of x+ = A x + B u + b (nullptr: b = 0)
     float *Am, *Ap, *cv, *fv, *Gm, *gv, *glo, *ghi, *qv, *Dinv, *Om, *x, *xt, *eta, *zg, *yg, *xi, *yf;
     float *zb, *xib, *yfb, *ygb, *gw, *czb, *gzb, *pf, *pg;
     int amS, apS, gS;
@@ -178,7 +180,7 @@ __device__ inline void stage_dyn(const Ctx& c, int t, const float* zt, const flo
             const float* A = c.dyn;
             const float* B = c.dyn + nx * nx;
             for (int k = 0; k < nx; ++k) {
-                float a = -zn[k];
+                float a = (c.bv ? c.bv[k] : 0.f) - zn[k];
                 for (int j = 0; j < nx; ++j) a += A[k * nx + j] * zt[j];
                 for (int j = 0; j < c.nu; ++j) a += B[k * c.nu + j] * zt[nx + j];
                 f[k] = a;
@@ -386,7 +388,7 @@ __device__ inline void rollout(const Ctx& c, const KOpts& o) {
         for (int t = 0; t < c.N; ++t) {
             const float* z = c.zb + t * n;
             for (int k = threadIdx.x; k < nx; k += blockDim.x) {
-                float a = 0.f;
+                float a = c.bv ? c.bv[k] : 0.f;
                 for (int j = 0; j < nx; ++j) a += A[k * nx + j] * z[j];
                 for (int j = 0; j < c.nu; ++j) a += B[k * c.nu + j] * z[nx + j];
                 c.zb[(t + 1) * n + k] = a;
@@ -480,6 +482,7 @@ __device__ inline void linearize(const Ctx& c) {
             if (c.model == MODEL_LINEAR) {
                 const float* A = c.dyn;
                 const float* B = c.dyn + nx * nx;
+                if (c.bv) a += c.bv[k];
                 for (int j = 0; j < nx; ++j) a += A[k * nx + j] * zt[j];
                 for (int j = 0; j < c.nu; ++j) a += B[k * c.nu + j] * zt[nx + j];
             } else {
@@ -974,14 +977,15 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 }
 
 // once per CTA, before the first stream: both mbarriers and the stream state
-// (state[3]: polls of a bounded wait, the wait_polls option or kMbarSpin)
-__device__ inline void block_stream_init(unsigned long long* mbar, int* state, int polls = 0) {
+// (state[3]: polls of a bounded wait, the wait_polls option or kMbarSpin; 0 when
+// the caller forces every wait to give up at once)
+__device__ inline void block_stream_init(unsigned long long* mbar, int* state, int polls = 0, int force = 0) {
     if (threadIdx.x == 0) {
         mbar_init(mbar, 1);
         mbar_init(mbar + 1, 1);
         fence_mbar_init();
         state[0] = state[1] = state[2] = 0;
-        state[3] = polls > 0 ? polls : (int)kMbarSpin;
+        state[3] = force ? 0 : (polls > 0 ? polls : (int)kMbarSpin);
     }
     __syncthreads();
 }
@@ -1043,7 +1047,7 @@ struct BlockStream {
     __device__ const float* get(int k, const float* fallback) {
         if (!ok) return fallback;
         const volatile int* gave_up = state + 2;
-        if (*gave_up || !mbar_wait(bar + (k & 1), phase[k & 1], gave_up, polls)) {
+        if (*gave_up || polls == 0 || !mbar_wait(bar + (k & 1), phase[k & 1], gave_up, polls)) {
             ok = false;
             if (*gave_up == 0) state[2] = 1;
             return fallback;

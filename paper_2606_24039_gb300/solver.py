@@ -168,6 +168,14 @@ class Solver:
         # entries of absent groups are left as zeroed by ctypes (count 0)
         return [{f: getattr(r, f) for f, _ in _abi.TuneResult._fields_} for r in res if r.count > 0]
 
+    def tmpc_group_times(self):
+        """Device milliseconds of the last forward / backward launch of each model
+        group (CUDA events on the launching streams); list of dicts."""
+        res = (_abi.GroupTime * 5)()
+        n = ctypes.c_int32(0)
+        _abi.check(self.lib.tmpc_group_times(self.handle, res, ctypes.byref(n)), "tmpc_group_times")
+        return [{f: getattr(r, f) for f, _ in _abi.GroupTime._fields_} for r in res[:n.value]]
+
     def tmpc_solve_host(self, host_params: dict, x0_host, out_host: dict, stream=None, z_init_host=None):
         """End-to-end solve from pinned host tensors (copies inside the call)."""
         p = _abi.Params()

@@ -135,3 +135,16 @@ def test_options_mirror_matches_the_header():
         for name in decl[1].split(","):
             fields.append((name.strip(), {"int32_t": ctypes.c_int32, "float": ctypes.c_float}[decl[0]]))
     assert fields == list(_abi.Options._fields_)
+
+
+def test_group_time_mirror_matches_the_header():
+    from paper_2606_24039_gb300 import _abi
+    src = open(os.path.join(ROOT, "include", "tmpc.h")).read()
+    end = src.index("} tmpc_group_time;")
+    body = src[src.rindex("typedef struct {", 0, end) + len("typedef struct {"):end]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(int32_t|float)\s+(\w+);", body)
+    ctype = {"int32_t": ctypes.c_int32, "float": ctypes.c_float}
+    assert [(n, ctype[t]) for t, n in fields] == list(_abi.GroupTime._fields_)
+    lib = _abi.load()
+    assert lib.tmpc_group_times(None, None, None) == 4

@@ -104,7 +104,7 @@ def test_unconstrained_lq_matches_riccati(which):
         p = w.tracking(B=1, nx=6, nu=3, N=15)
         inst = p.instance(0)
         inst["ref"][:] = 0.0
-        A, B = models.linear_matrices(inst)
+        A, B, _ = models.linear_matrices(inst)
     inst["lo"][:] = -np.inf
     inst["hi"][:] = np.inf
     N = inst["N"]

@@ -47,7 +47,7 @@ import math
 import numpy as np
 
 MODEL_DI = 0        # 2-D double integrator, ZOH.          dyn = [dt]
-MODEL_LINEAR = 1    # x+ = A x + B u (explicit).           dyn = [A (nx*nx), B (nx*nu)] row-major
+MODEL_LINEAR = 1    # x+ = A x + B u + b (explicit).       dyn = [A (nx*nx), B (nx*nu), b (nx, optional)] row-major
 MODEL_BICYCLE = 2   # kinematic bicycle, implicit midpoint. dyn = [dt, wheelbase, ds, n_track]
 MODEL_QUAD = 3      # planar quadrotor, explicit RK4.       dyn = [dt, mass, inertia, arm, gravity]
 
@@ -484,3 +484,49 @@ def long_horizon(B=8, N=8192, seed=1005, max_sqp=5, max_admm=100, dt=0.01,
     opts = Options(max_sqp=max_sqp, max_admm=max_admm, n_ls=8)
     return ProblemBatch(nx, nu, ng, N, np.full(B, N, np.int32), np.full(B, MODEL_BICYCLE, np.int32),
                         opts=opts, name=f"long_horizon_B{B}_N{N}", **a)
+
+
+def stable_linear_system(rng, nx, nu, scale=0.1, lam_max=0.99, b_std=1e-2):
+    """A = I + scale * dA with dA_ij ~ N(0, 1) and its eigenvalues scaled onto the
+    disc |lambda| <= lam_max (A = V diag(lambda) V^-1 with each lambda that lies
+    outside multiplied by lam_max / |lambda|; conjugate pairs stay conjugate, so A
+    stays real); B_ij ~ N(0, 1); b ~ N(0, b_std^2 I)."""
+    A = np.eye(nx) + scale * rng.normal(0, 1, size=(nx, nx))
+    lam, V = np.linalg.eig(A)
+    lam = lam * np.minimum(1.0, lam_max / np.maximum(np.abs(lam), 1e-300))
+    A = np.real(V @ np.diag(lam) @ np.linalg.inv(V))
+    B = rng.normal(0, 1, size=(nx, nu))
+    b = rng.normal(0, b_std, size=nx)
+    return A, B, b
+
+
+def linear_rl(B=64, N=40, nx=8, nu=4, u_max=1.0, seed=1006, theta=None, tol=1e-5, max_admm=1000,
+              max_sqp=10) -> ProblemBatch:
+    """The linear-system RL problem family: x+ = A x + B u + b (one system drawn
+    per seed, see stable_linear_system), x0 ~ N(0, 25 I) per instance, stage
+    cost x' Q x + ||u||^2 with Q = diag(theta) (written with the 1/2 of the
+    cost convention: Qd = 2 theta, Rd = 2; theta = 1 unless given), the same
+    cost at the terminal stage, control box |u|_inf <= u_max on every stage.
+    The solver runs to the tolerance tol (early exit at eps_abs = eps_rel =
+    eps_c = tol) with at most max_admm ADMM iterations per QP."""
+    rng = np.random.default_rng(seed)
+    A, Bm, b = stable_linear_system(rng, nx, nu)
+    th = np.ones(nx) if theta is None else np.asarray(theta, dtype=np.float64)
+    ng = nu
+    n_dyn = nx * nx + nx * nu + nx
+    a = _empty(B, nx, nu, ng, N, n_dyn, 0)
+    for i in range(B):
+        r = np.random.default_rng([seed, i])
+        a["x0"][i] = r.normal(0, 5.0, nx)
+        a["Qd"][i] = 2.0 * th
+        a["Rd"][i] = 2.0
+        a["lo"][i] = -u_max
+        a["hi"][i] = u_max
+        a["dyn"][i, :nx * nx] = A.ravel()
+        a["dyn"][i, nx * nx:nx * nx + nx * nu] = Bm.ravel()
+        a["dyn"][i, nx * nx + nx * nu:] = b
+    opts = Options(max_sqp=max_sqp, max_admm=max_admm, n_ls=1, early_exit=1, eps_abs=tol, eps_rel=tol, eps_c=tol)
+    pb = ProblemBatch(nx, nu, ng, N, np.full(B, N, np.int32), np.full(B, MODEL_LINEAR, np.int32),
+                      opts=opts, name=f"linear_rl_B{B}_N{N}_nx{nx}_nu{nu}_umax{u_max:g}", **a)
+    pb.extra = dict(A=A, B=Bm, b=b, theta=th, u_max=u_max)
+    return pb
