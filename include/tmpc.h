@@ -129,6 +129,12 @@ typedef struct {
     int32_t force_pivot_failure;
     int32_t wait_polls;
     int32_t force_wait_timeout;
+    /* backward solver of the double integrator, bicycle and quadrotor: 0 = one direct
+     * FP64 block LDL' factorisation of the interleaved active-set KKT system (exact up
+     * to rounding, also when the active rows are nearly dependent); 1 = the iterative
+     * refinement preconditioned by the forward's FP32 factorisation (bwd_rho,
+     * bwd_sigma, bwd_iters).  The generic kernel always uses the refinement. */
+    int32_t bwd_refine;
 } tmpc_options;
 
 /* Problem parameters theta (the OCP of Appendix A with the cost of Eq. (cost)).

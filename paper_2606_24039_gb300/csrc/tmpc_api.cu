@@ -46,6 +46,7 @@ KOpts to_kopts(const tmpc_options& o) {
     k.force_fail = o.force_pivot_failure;
     k.wait_polls = o.wait_polls;
     k.force_timeout = o.force_wait_timeout;
+    k.bwd_refine = o.bwd_refine;
     if (k.k_rho_iter < 1) k.k_rho_iter = 1 << 30;
     return k;
 }
@@ -166,6 +167,8 @@ struct tmpc_handle {
     int n_groups = 0;
     float* fws = nullptr;      // global arenas of the shared-memory path (instances that do not fit)
     long long fstride = 0;
+    double* dws = nullptr;     // FP64 workspace of the direct backward of the small models
+    long long dstride = 0;
     int nsm = 0;
     int threads = 128;
     size_t smem = 0;
@@ -320,6 +323,18 @@ tmpc_status ensure_buffers(tmpc_handle* h) {
     if (any_cluster && !h->gflags) {
         e = cudaMalloc(&h->gflags, sizeof(int) * 4 * (size_t)B);
         if (e != cudaSuccess) { set_err("cudaMalloc(team flags)", e); return TMPC_ERR_OOM; }
+    }
+    long long tmax = 0;
+    for (int g = 0; g < h->n_groups; ++g)
+        if (h->groups[g].model >= 0) tmax = std::max(tmax, (long long)h->groups[g].Tmax);
+    const long long dneed = fast::direct_ws_doubles((int)tmax);
+    if (tmax > 0 && dneed > h->dstride) {
+        if (h->dws) cudaFree(h->dws);
+        h->dws = nullptr;
+        h->dstride = 0;
+        e = cudaMalloc(&h->dws, sizeof(double) * dneed * B);
+        if (e != cudaSuccess) { set_err("cudaMalloc(direct backward workspace)", e); return TMPC_ERR_OOM; }
+        h->dstride = dneed;
     }
     const long long stride = (fmax + 31) & ~31LL;
     if (fmax > 0 && stride > h->fstride) {
@@ -750,7 +765,7 @@ tmpc_status tmpc_backward(tmpc_handle* h, const float* x0, const tmpc_solution* 
         if (t) TMPC_CUDA(cudaEventRecord(h->tev[gi][2], sg));
         TMPC_CUDA(fast::launch_backward(G.model, G.cluster, G.bgrid, G.threads, G.smem, sg, h->L, ko, kp, ks, h->fws,
                                         h->fstride, h->order + G.offset, G.count, h->queue + gi, x0, h->gflags,
-                                        dL_dz, dL_dxi, kg));
+                                        dL_dz, dL_dxi, kg, h->dws, h->dstride));
         if (t) TMPC_CUDA(cudaEventRecord(h->tev[gi][3], sg));
         h->timed[gi][1] = t;
         if (fork) {
@@ -825,6 +840,7 @@ void tmpc_destroy(tmpc_handle* h) {
     if (h->order) cudaFree(h->order);
     if (h->stage) cudaFree(h->stage);
     if (h->fws) cudaFree(h->fws);
+    if (h->dws) cudaFree(h->dws);
     if (h->gflags) cudaFree(h->gflags);
     if (h->pstate) cudaFree(h->pstate);
     for (int g = 0; g < 4; ++g) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/tmpc.h"
+#include "tmpc_direct.cuh"
 #include "tmpc_fast.cuh"
 #include "tmpc_fast_api.h"
 
@@ -22,6 +23,8 @@ long long arena_floats_host(int model, int T, int policy, int cluster) {
     }
     return -1;
 }
+
+long long direct_ws_doubles(int T) { return (long long)T * kDirectStage; }
 
 bool supported(int model) { return model == MODEL_DI || model == MODEL_BICYCLE || model == MODEL_QUAD; }
 
@@ -120,7 +123,8 @@ cudaError_t prepare_backward(int model, int cl, size_t smem_bytes, int threads, 
 cudaError_t launch_backward(int model, int cl, int grid, int threads, size_t smem_bytes, cudaStream_t s,
                             const KLayout& L, const KOpts& o, const KParams& p, const KSol& sol, float* gws,
                             long long gstride, const int* order, int count, int* queue, const float* x0,
-                            int* gflags, const float* dLdz, const float* dLdxi, const KGrads& g) {
+                            int* gflags, const float* dLdz, const float* dLdxi, const KGrads& g, double* dws,
+                            long long dstride) {
     const void* k = bwd_kernel_of(model, cl > 0);
     if (!k) return cudaErrorInvalidValue;
     if (cl > 0) {
@@ -137,12 +141,14 @@ cudaError_t launch_backward(int model, int cl, int grid, int threads, size_t sme
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         void* args[] = {(void*)&L, (void*)&o, (void*)&p, (void*)&sol, (void*)&gws, (void*)&gstride, (void*)&order,
-                        (void*)&count, (void*)&x0, (void*)&gflags, (void*)&dLdz, (void*)&dLdxi, (void*)&g};
+                        (void*)&count, (void*)&x0, (void*)&gflags, (void*)&dLdz, (void*)&dLdxi, (void*)&g,
+                        (void*)&dws, (void*)&dstride};
         return cudaLaunchKernelExC(&cfg, k, args);
     }
     const long long sf = (long long)(smem_bytes / sizeof(float));
     void* args[] = {(void*)&L, (void*)&o, (void*)&p, (void*)&sol, (void*)&gws, (void*)&gstride, (void*)&order,
-                    (void*)&count, (void*)&queue, (void*)&x0, (void*)&sf, (void*)&dLdz, (void*)&dLdxi, (void*)&g};
+                    (void*)&count, (void*)&queue, (void*)&x0, (void*)&sf, (void*)&dLdz, (void*)&dLdxi, (void*)&g,
+                    (void*)&dws, (void*)&dstride};
     return cudaLaunchKernel(k, dim3(grid), dim3(threads), args, smem_bytes, s);
 }
 

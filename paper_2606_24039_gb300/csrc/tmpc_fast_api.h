@@ -43,7 +43,10 @@ cudaError_t prepare_backward(int model, int cl, size_t smem_bytes, int threads, 
 cudaError_t launch_backward(int model, int cl, int grid, int threads, size_t smem_bytes, cudaStream_t s,
                             const KLayout& L, const KOpts& o, const KParams& p, const KSol& sol, float* gws,
                             long long gstride, const int* order, int count, int* queue, const float* x0,
-                            int* gflags, const float* dLdz, const float* dLdxi, const KGrads& g);
+                            int* gflags, const float* dLdz, const float* dLdxi, const KGrads& g, double* dws,
+                            long long dstride);
+// doubles of the direct backward's FP64 workspace per instance of T stages
+long long direct_ws_doubles(int T);
 
 // plain per-phase form: one launch per phase, fixed counts, one CTA per instance,
 // global arenas; kernels launched on s in host order (plain_launches of them)

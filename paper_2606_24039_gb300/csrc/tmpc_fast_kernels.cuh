@@ -9,6 +9,7 @@
 
 #include "../../include/tmpc.h"
 #include "tmpc_backward.cuh"
+#include "tmpc_direct.cuh"
 #include "tmpc_fast.cuh"
 #include "tmpc_fast_api.h"
 
@@ -1195,7 +1196,7 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
 template <int M>
 __device__ __forceinline__ void backward_instance_team(Inst<M>& c, const KOpts& o, const Red& rs, const KLayout& L,
                                                        const KSol& sol, int inst, const float* dLdz_all,
-                                                       const float* dLdxi_all, const KGrads& g) {
+                                                       const float* dLdxi_all, const KGrads& g, double* dws) {
     using Tr = Traits<M>;
     constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NU = Inst<M>::NU, NG = Inst<M>::NG;
     const int T = c.T;
@@ -1258,85 +1259,91 @@ __device__ __forceinline__ void backward_instance_team(Inst<M>& c, const KOpts& 
         ex[e] = 0.f;
     }
     c.sync();
-    // S_b = H + sigma_b I + rho_b C'C + G' diag(w) G; FP32 safeguard: lower rho_b up to three times
-    form_S<M>(c, o.bwd_sigma, rb, rb, gw);
-    bool ok = cr_factor<M>(c, c.tflags + 1);
-    for (int tries = 0; !ok && tries < 3; ++tries) {
-        rb *= 0.1f;
-        for (int e = c.tid; e < T * NG; e += c.nth)
-            if (code[e] != 0.f && fabsf(code[e]) < 1.5f) gw[e] = rb;
-        c.sync();
+    if (!o.bwd_refine && dws) {
+        // direct FP64 block LDL' of the interleaved active-set KKT system (tmpc_direct.cuh);
+        // the factor blocks of the forward (Dm onwards) are free here and serve as scratch
+        direct_adjoint<M>(c, code, bx, ex, lam, mu, dws, reinterpret_cast<double*>(c.Dm), c.tflags + 2);
+    } else {
+        // S_b = H + sigma_b I + rho_b C'C + G' diag(w) G; FP32 safeguard: lower rho_b up to three times
         form_S<M>(c, o.bwd_sigma, rb, rb, gw);
-        ok = cr_factor<M>(c, c.tflags + 1);
-    }
-    if (!ok && c.tid == 0) c.tflags[0] = 1;
-    top_inverse<M>(c);
-    // divergence guard (see tmpc_backward.cuh): growing steps lower rho_b and restart
-    float d0 = 0.f, dprev = kInf;
-    int restarts = 0;
-    for (int it = 0; it < o.bwd_iters; ++it) {
-        for (int e = c.tid; e < T * NG; e += c.nth) gz[e] = c.Gx(ex, e / NG, e % NG);
-        c.sync();
-        for (int e = c.tid; e < T * N; e += c.nth) {
-            const int t = e / N, j = e % N;
-            float sv = bx[e] - c.Pv(ex, t, j);
-            sv -= c.Ctv(t, j, [&](int row, int k) { return lam[row * NX + k]; });
-#pragma unroll
-            for (int r = 0; r < NG; ++r) {
-                const float cd = code[t * NG + r];
-                if (fabsf(cd) > 1.5f) sv -= c.gam2(r) * c.Gval(t, r, j) * gz[t * NG + r];
-                else if (cd != 0.f) sv -= c.Gval(t, r, j) * mu[t * NG + r];
-            }
-            c.r[e] = sv;
-        }
-        for (int e = c.tid; e < T * NX; e += c.nth) r2[e] = -c.Cx(ex, e / NX, e % NX);
-        for (int e = c.tid; e < T * NG; e += c.nth) {
-            const float cd = code[e];
-            r3[e] = (cd != 0.f && fabsf(cd) < 1.5f) ? -gz[e] : 0.f;
-        }
-        c.sync();
-        for (int e = c.tid; e < T * N; e += c.nth) {
-            const int t = e / N, j = e % N;
-            float sv = c.Ctv(t, j, [&](int row, int k) { return r2[row * NX + k]; });
-            sv += c.Gtw(t, j, [&](int r) { return r3[t * NG + r]; });
-            c.r[e] += rb * sv;
-        }
-        c.sync();
-        cr_solve<M>(c, c.r, c.dx);
-        for (int e = c.tid; e < T * NX; e += c.nth) lam[e] += rb * (c.Cx(c.dx, e / NX, e % NX) - r2[e]);
-        for (int e = c.tid; e < T * NG; e += c.nth) {
-            const float cd = code[e];
-            if (cd != 0.f && fabsf(cd) < 1.5f) mu[e] += rb * (c.Gx(c.dx, e / NG, e % NG) - r3[e]);
-        }
-        c.sync();
-        float dm[1] = {0.f};
-        for (int e = c.tid; e < T * N; e += c.nth) {
-            ex[e] += c.dx[e];
-            dm[0] = fmaxf(dm[0], fin(c.dx[e]));
-        }
-        team_max_k<M, 1>(c, dm, rs.red);
-        if (it == 0) d0 = dm[0];
-        const bool diverging = !(dm[0] < kInf) || (it >= 2 && dm[0] > 2.f * dprev && dm[0] > 1e-4f * d0);
-        if (diverging && restarts < 3) {
-            ++restarts;
+        bool ok = cr_factor<M>(c, c.tflags + 1);
+        for (int tries = 0; !ok && tries < 3; ++tries) {
             rb *= 0.1f;
-            for (int e = c.tid; e < T * NG; e += c.nth) {
+            for (int e = c.tid; e < T * NG; e += c.nth)
                 if (code[e] != 0.f && fabsf(code[e]) < 1.5f) gw[e] = rb;
-                mu[e] = 0.f;
-            }
-            for (int e = c.tid; e < T * NX; e += c.nth) lam[e] = 0.f;
-            for (int e = c.tid; e < T * N; e += c.nth) ex[e] = 0.f;
             c.sync();
             form_S<M>(c, o.bwd_sigma, rb, rb, gw);
-            if (!cr_factor<M>(c, c.tflags + 1) && c.tid == 0) c.tflags[0] = 1;
-            top_inverse<M>(c);
-            d0 = 0.f;
-            dprev = kInf;
-            it = -1;
-            continue;
+            ok = cr_factor<M>(c, c.tflags + 1);
         }
-        dprev = dm[0];
-        c.sync();
+        if (!ok && c.tid == 0) c.tflags[0] = 1;
+        top_inverse<M>(c);
+        // divergence guard (see tmpc_backward.cuh): growing steps lower rho_b and restart
+        float d0 = 0.f, dprev = kInf;
+        int restarts = 0;
+        for (int it = 0; it < o.bwd_iters; ++it) {
+            for (int e = c.tid; e < T * NG; e += c.nth) gz[e] = c.Gx(ex, e / NG, e % NG);
+            c.sync();
+            for (int e = c.tid; e < T * N; e += c.nth) {
+                const int t = e / N, j = e % N;
+                float sv = bx[e] - c.Pv(ex, t, j);
+                sv -= c.Ctv(t, j, [&](int row, int k) { return lam[row * NX + k]; });
+    #pragma unroll
+                for (int r = 0; r < NG; ++r) {
+                    const float cd = code[t * NG + r];
+                    if (fabsf(cd) > 1.5f) sv -= c.gam2(r) * c.Gval(t, r, j) * gz[t * NG + r];
+                    else if (cd != 0.f) sv -= c.Gval(t, r, j) * mu[t * NG + r];
+                }
+                c.r[e] = sv;
+            }
+            for (int e = c.tid; e < T * NX; e += c.nth) r2[e] = -c.Cx(ex, e / NX, e % NX);
+            for (int e = c.tid; e < T * NG; e += c.nth) {
+                const float cd = code[e];
+                r3[e] = (cd != 0.f && fabsf(cd) < 1.5f) ? -gz[e] : 0.f;
+            }
+            c.sync();
+            for (int e = c.tid; e < T * N; e += c.nth) {
+                const int t = e / N, j = e % N;
+                float sv = c.Ctv(t, j, [&](int row, int k) { return r2[row * NX + k]; });
+                sv += c.Gtw(t, j, [&](int r) { return r3[t * NG + r]; });
+                c.r[e] += rb * sv;
+            }
+            c.sync();
+            cr_solve<M>(c, c.r, c.dx);
+            for (int e = c.tid; e < T * NX; e += c.nth) lam[e] += rb * (c.Cx(c.dx, e / NX, e % NX) - r2[e]);
+            for (int e = c.tid; e < T * NG; e += c.nth) {
+                const float cd = code[e];
+                if (cd != 0.f && fabsf(cd) < 1.5f) mu[e] += rb * (c.Gx(c.dx, e / NG, e % NG) - r3[e]);
+            }
+            c.sync();
+            float dm[1] = {0.f};
+            for (int e = c.tid; e < T * N; e += c.nth) {
+                ex[e] += c.dx[e];
+                dm[0] = fmaxf(dm[0], fin(c.dx[e]));
+            }
+            team_max_k<M, 1>(c, dm, rs.red);
+            if (it == 0) d0 = dm[0];
+            const bool diverging = !(dm[0] < kInf) || (it >= 2 && dm[0] > 2.f * dprev && dm[0] > 1e-4f * d0);
+            if (diverging && restarts < 3) {
+                ++restarts;
+                rb *= 0.1f;
+                for (int e = c.tid; e < T * NG; e += c.nth) {
+                    if (code[e] != 0.f && fabsf(code[e]) < 1.5f) gw[e] = rb;
+                    mu[e] = 0.f;
+                }
+                for (int e = c.tid; e < T * NX; e += c.nth) lam[e] = 0.f;
+                for (int e = c.tid; e < T * N; e += c.nth) ex[e] = 0.f;
+                c.sync();
+                form_S<M>(c, o.bwd_sigma, rb, rb, gw);
+                if (!cr_factor<M>(c, c.tflags + 1) && c.tid == 0) c.tflags[0] = 1;
+                top_inverse<M>(c);
+                d0 = 0.f;
+                dprev = kInf;
+                it = -1;
+                continue;
+            }
+            dprev = dm[0];
+            c.sync();
+        }
     }
     for (int e = c.tid; e < T * NG; e += c.nth) gz[e] = c.Gx(ex, e / NG, e % NG);
     c.sync();
@@ -1514,7 +1521,8 @@ template <int M>
 __global__ void __launch_bounds__(256, 2) backward_kernel(KLayout L, KOpts o, KParams p, KSol sol, float* gws,
                                                        long long gstride, const int* order, int count,
                                                        int* queue, const float* x0, long long smem_floats,
-                                                       const float* dLdz, const float* dLdxi, KGrads g) {
+                                                       const float* dLdz, const float* dLdxi, KGrads g,
+                                                       double* dws, long long dstride) {
     extern __shared__ __align__(16) float arena[];
     __shared__ float red[32 * 8];
     __shared__ double redd[64];
@@ -1538,7 +1546,7 @@ __global__ void __launch_bounds__(256, 2) backward_kernel(KLayout L, KOpts o, KP
         c.tflags = flags;
         const long long need = arena_floats<M>(c.T, kCR);
         c.carve(need <= smem_floats ? arena : gws + (long long)i * gstride, kCR);
-        backward_instance_team<M>(c, o, rs, L, sol, i, dLdz, dLdxi, g);
+        backward_instance_team<M>(c, o, rs, L, sol, i, dLdz, dLdxi, g, dws ? dws + (long long)i * dstride : nullptr);
     }
 }
 
@@ -1546,7 +1554,8 @@ template <int M>
 __global__ void __launch_bounds__(256, 2) backward_kernel_cluster(KLayout L, KOpts o, KParams p, KSol sol, float* gws,
                                                                long long gstride, const int* order, int count,
                                                                const float* x0, int* gflags, const float* dLdz,
-                                                               const float* dLdxi, KGrads g) {
+                                                               const float* dLdxi, KGrads g, double* dws,
+                                                               long long dstride) {
     __shared__ float red[32 * 8];
     __shared__ double redd[64];
     __shared__ double lsacc[2 * (kMaxLs + 1) + 2];
@@ -1567,7 +1576,7 @@ __global__ void __launch_bounds__(256, 2) backward_kernel_cluster(KLayout L, KOp
         c.rank = (int)rank;
         c.tflags = gflags + 4LL * i;
         c.carve(gws + (long long)i * gstride, kCR, 1);
-        backward_instance_team<M>(c, o, rs, L, sol, i, dLdz, dLdxi, g);
+        backward_instance_team<M>(c, o, rs, L, sol, i, dLdz, dLdxi, g, dws ? dws + (long long)i * dstride : nullptr);
         c.sync();
     }
 }

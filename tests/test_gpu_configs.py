@@ -270,3 +270,39 @@ def test_autograd_function_through_cost_mlp():
         assert abs(du_ora - q) <= 1e-3 * max(abs(q), 1e-6), (du_ora, q)
         assert abs(du_gpu - q) <= 2e-3 * max(abs(q), 1e-6), (du_gpu, q)
     assert same or same_x or same_u   # at least one difference quotient was taken
+
+
+# ---------------------------------------------------------------------------
+# backward of the uneven batch at full size, on the GPU's own forward output
+# ---------------------------------------------------------------------------
+def test_backward_uneven_full_batch_on_gpu_forward():
+    """The uneven batch (4096 instances, N in 10..200, three models, 10 SQP x 50
+    ADMM) forward and backward in the launch configuration the benchmark times;
+    16 sampled instances: the direct FP64 adjoint solve of the small models and
+    the oracle's sparse LU of the same active-set KKT system at the GPU's
+    forward point agree per parameter (instances whose KKT matrix the oracle
+    finds singular are compared after the same -1e-10 regularisation)."""
+    from paper_2606_24039_gb300 import Solver
+    pb = w.uneven(B=4096)
+    s = Solver.from_batch(pb, device="cuda")
+    sol = s.tmpc_solve(s.x0, z_init=s.z_init)
+    rng = np.random.default_rng(3)
+    dLdz = rng.normal(size=(pb.B, pb.N_max + 1, pb.n)).astype(np.float32)
+    g = s.tmpc_backward(s.x0, sol, torch.tensor(dLdz, device="cuda"))
+    torch.cuda.synchronize()
+    keys = ("x0", "Qd", "Rd", "Wd", "ref", "lin", "lo", "hi", "gamma2", "gamma1")
+    idx = np.random.default_rng(8).choice(pb.B, 16, replace=False)
+    worst = []
+    for i in idx:
+        inst = pb.instance(i)
+        T, n, nx, nu, ng = inst["N"] + 1, inst["nx"] + inst["nu"], inst["nx"], inst["nu"], inst["ng"]
+        p = _as_oracle_solution(sol, i, inst)
+        gr, info = obwd.backward(inst, p, dLdz[i, :T, :n].astype(np.float64), eps_g=pb.opts.eps_g)
+        cut = {"x0": (nx,), "Qd": (T, nx), "Rd": (T, nu), "Wd": (nu,), "ref": (T, n), "lin": (T, n),
+               "lo": (T, ng), "hi": (T, ng), "gamma2": (ng,), "gamma1": (ng,)}
+        scale = max(np.linalg.norm(gr[k]) for k in keys)
+        for k in keys:
+            ga = g[k][i].cpu().numpy()[tuple(slice(0, m) for m in cut[k])]
+            rel = _grad_rel(ga.reshape(-1), gr[k].reshape(-1), scale)
+            worst.append((rel, int(i), k, bool(info["singular"])))
+            assert rel < GRAD_TOL, (int(i), inst["model"], k, rel, info["singular"])
