@@ -1,18 +1,32 @@
 """Throughput benchmark of the batched SQP/ADMM OCP solver on one node.
 
-Default workload: kinematic-bicycle racing, B = 1024 instances, N = 50,
-implicit midpoint dynamics, L1+L2-softened track constraint, control-rate
-cost, 10 SQP x 50 ADMM iterations (FP32 on the GPU).
+Headline workload (the largest single-GPU configuration): the uneven batch,
+4096 instances whose horizons are drawn from 10..200 and whose models mix
+the double integrator, the kinematic bicycle (implicit midpoint, soft track
+row) and the planar quadrotor 1:2:1, 10 SQP x 50 ADMM iterations, forward
+and forward + backward in one persistent launch per model group (FP32; the
+direct backward of the small models in FP64).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--workload uneven|racing|tracking|long_horizon|double_integrator|linear_rl] [--no-suite]
 
-One step = one forward solve of the whole batch (every instance, every SQP and
-ADMM iteration); a second timed pass measures forward + backward.  Inputs are
-resident in HBM; the L2 is flushed (a 512 MB write) between timed steps.  The
-`e2e` figure times the host-memory entry point (tmpc_solve_host): copy of every
+One step = one forward solve of the whole batch (every instance, every SQP
+and ADMM iteration); a second timed pass measures forward + backward.  Inputs
+are resident in HBM; the L2 is flushed (a 512 MB write) between timed steps.
+`e2e` times the host-memory entry point (tmpc_solve_host): the copy of every
 parameter array from pinned host memory, the solve, and the copy of the whole
-solution back.  `--impl reference` times the FP64 CPU oracle (the baseline arm)
-on a bounded sample of the same workload on the host cores.
+solution back.  With the default workload the line also carries
+  - `workloads`: the racing (B=1024, N=50), tracking (B=512, nx=48, nu=20,
+    N=32), long-horizon (B=8, N=8192), double-integrator (B=1, N=20) and
+    linear-system RL (B=64, N=40, nx=8, nu=4, tolerance 1e-5) workloads,
+    each timed the same way (fewer steps) with its dominant kernel's roofline;
+  - `at_1e-5`: every workload solved to the tolerance 1e-5 (early exit at
+    eps_abs = eps_rel = eps_c = 1e-5, at most 1000 ADMM iterations per QP,
+    at most 10 SQP iterations for the linear problems and 20 otherwise):
+    solves/s and the fraction of instances whose SQP KKT residual
+    (Eq. sqp_stop) reaches 1e-5.
+`--impl reference` times the FP64 CPU oracle (the baseline arm) on a bounded
+sample of the same workload on the host cores.
 
 Under torchrun (N > 1) every rank solves its own batch on its own GPU (weak
 scaling, no collective on the data path); rank 0 prints one JSON line with the
@@ -64,28 +78,29 @@ def bytes_admm_stage(n, nx, lti):
     return 4 * (2 * n * n + (0 if lti else 2 * nx * n))
 
 
-SMS, FP32_LANES = 152, 128
+
+
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per Blackwell SM
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="racing",
-                    choices=["racing", "double_integrator", "tracking", "uneven", "long_horizon"],
-                    help="racing (default): bicycle B=1024 N=50; double_integrator: B=1 N=20; "
-                         "tracking: linear nx=48 nu=20 N=32 B=512; uneven: B=4096 N in 10..200, "
-                         "three models; long_horizon: bicycle B=8 N=8192")
+    ap.add_argument("--workload", default="uneven", choices=list(WORKLOADS),
+                    help="uneven (default): B=4096 N in 10..200, three models; racing: bicycle B=1024 N=50; "
+                         "tracking: linear nx=48 nu=20 N=32 B=512; long_horizon: bicycle B=8 N=8192; "
+                         "double_integrator: B=1 N=20; linear_rl: B=64 N=40 nx=8 nu=4 at tolerance 1e-5")
     ap.add_argument("--batch", type=int, default=0, help="instances (0 = the workload's size)")
     ap.add_argument("--horizon", type=int, default=0, help="horizon N (0 = the workload's; fixed-N workloads)")
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="oracle instances timed for cpu_baseline (0 = about 10-30 CPU-seconds of the workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-bwd", action="store_true", help="time the forward pass only")
-    ap.add_argument("--solver", type=int, default=0, help="0 auto, 1 generic sequential LDL', 2 shared-memory CR, 3 CR on global arenas, "
-                    "4 warp-sequential LDL', 5 warp LDL' on global arenas")
+    ap.add_argument("--solver", type=int, default=0, help="0 auto, 1 generic sequential LDL', 2 shared-memory CR, "
+                    "3 CR on global arenas, 4 warp-sequential LDL', 5 warp LDL' on global arenas, 6 cluster CR")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the host-memory end-to-end timing")
     ap.add_argument("--threads", type=int, default=0, help="threads per instance (0 = library default)")
     ap.add_argument("--clocks-csv", default=None,
@@ -94,46 +109,62 @@ def parse():
                     help="keep the launch form chosen at setup (default: tmpc_autotune picks it per model group)")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the plain per-phase form (one launch per phase, eager and as a CUDA graph)")
+    ap.add_argument("--no-suite", action="store_true",
+                    help="only the selected workload: no `workloads` and no `at_1e-5` records")
     return ap.parse_args()
 
 
-CPU_SAMPLE = {"racing": 128, "double_integrator": 512, "tracking": 96, "uneven": 192, "long_horizon": 16}
+CPU_SAMPLE = {"racing": 128, "double_integrator": 512, "tracking": 96, "uneven": 160, "long_horizon": 16,
+              "linear_rl": 256}
 
 WORKLOADS = {
     # name: (generator, default batch, default horizon, seed, description)
+    "uneven": ("uneven", 4096, 0, 1004, "uneven batch N in 10..200, double integrator / bicycle / quadrotor 1:2:1"),
     "racing": ("racing", 1024, 50, 1002, "kinematic-bicycle racing (implicit midpoint, L1+L2 soft track row, "
                                          "rate cost, progress cost)"),
-    "double_integrator": ("double_integrator", 1, 20, 1001, "2-D double integrator, box bounds on u and v"),
     "tracking": ("tracking", 512, 32, 1003, "linear tracking nx=48 nu=20, MLP cost weights, |u| <= 1"),
-    "uneven": ("uneven", 4096, 0, 1004, "uneven batch N in 10..200, double integrator / bicycle / quadrotor 1:2:1"),
     "long_horizon": ("long_horizon", 8, 8192, 1005, "kinematic-bicycle racing, dt=0.01, closed 2 km track"),
+    "double_integrator": ("double_integrator", 1, 20, 1001, "2-D double integrator, box bounds on u and v"),
+    "linear_rl": ("linear_rl", 64, 40, 1006, "linear-system RL: x+ = A x + B u + b, nx=8 nu=4, |u| <= 1, "
+                                             "Q = diag(theta), tolerance 1e-5 (<= 1000 ADMM per QP)"),
 }
+SUITE = ("racing", "tracking", "long_horizon", "double_integrator", "linear_rl")
+LINEAR = ("tracking", "double_integrator", "linear_rl")
 
 
-def make_batch(name, B, N, seed):
+def make_batch(name, B, N, seed, **kw):
     import workloads as w
     gen = getattr(w, WORKLOADS[name][0])
     if name == "uneven":
-        return gen(B=B, seed=seed)
-    return gen(B=B, N=N, seed=seed)
+        return gen(B=B, seed=seed, **kw)
+    return gen(B=B, N=N, seed=seed, **kw)
 
 
-def workload(args, rank=0):
-    _, B0, N0, seed, _ = WORKLOADS[args.workload]
-    return make_batch(args.workload, args.batch or B0, args.horizon or N0, seed + 7919 * rank)
+def workload(args, rank=0, name=None):
+    name = name or args.workload
+    _, B0, N0, seed, _ = WORKLOADS[name]
+    return make_batch(name, (args.batch if name == args.workload else 0) or B0,
+                      (args.horizon if name == args.workload else 0) or N0, seed + 7919 * rank)
 
 
-def config_of(args, pb):
-    desc = WORKLOADS[args.workload][4]
+def describe(name, pb, world=1, solver=0):
+    desc = WORKLOADS[name][4]
     Ns = f"N={pb.N_max}" if np.all(pb.N == pb.N_max) else f"N={int(pb.N.min())}..{int(pb.N.max())}"
-    return {"workload": f"{args.workload}: {desc}, B={pb.B} {Ns}, {pb.opts.max_sqp} SQP x {pb.opts.max_admm} ADMM",
+    its = (f"{pb.opts.max_sqp} SQP x {pb.opts.max_admm} ADMM" if not pb.opts.early_exit else
+           f"to tolerance {pb.opts.eps_c:g} (<= {pb.opts.max_sqp} SQP, <= {pb.opts.max_admm} ADMM per QP)")
+    return {"workload": f"{name}: {desc}, B={pb.B} {Ns}, {its}",
             "batch": pb.B, "horizon": pb.N_max, "nx": pb.nx, "nu": pb.nu, "ng": pb.ng,
-            "sqp_iters": pb.opts.max_sqp, "admm_iters": pb.opts.max_admm,
-            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{args.gpus}",
+            "sqp_iters": pb.opts.max_sqp, "admm_iters": pb.opts.max_admm, "early_exit": bool(pb.opts.early_exit),
+            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}",
             "solver": {0: "auto", 1: "generic sequential block LDL'", 2: "shared-memory block cyclic reduction",
                        3: "block cyclic reduction, global-memory arenas",
                        4: "shared-memory sequential block LDL' by one warp",
-                       5: "sequential block LDL' by one warp, global-memory arenas"}[args.solver]}
+                       5: "sequential block LDL' by one warp, global-memory arenas",
+                       6: "block cyclic reduction by one thread-block cluster per instance"}.get(solver, str(solver))}
+
+
+def config_of(args, pb):
+    return describe(args.workload, pb, args.gpus, args.solver)
 
 
 # ----------------------------------------------------------------------------
@@ -370,19 +401,326 @@ def launches_per_step(pb, solver, forms=None):
     return fwd, bwd
 
 
-def measured_traffic(args, pb):
-    """DRAM bytes (read + write) per launch of the solve kernel from the committed
-    ncu summary, scaled to this batch by instances; None when the kernel sources
-    changed since the counters were taken or no summary matches the workload."""
-    path = os.path.join(ROOT, "profiles", "solve_kernel_bicycle_racing_traffic.json")
+def measured_traffic(name, pb, kernel):
+    """DRAM bytes (read + write) per launch of a solve kernel from the committed
+    ncu records, scaled to this batch by instances; None when the kernel sources
+    changed since the counters were taken or no record matches."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*_traffic.json"))):
+        try:
+            rec = json.load(open(path))
+        except Exception:
+            continue
+        if (rec.get("sources_sha256") == sources_digest() and rec.get("workload_name") == name
+                and rec.get("kernel") == kernel and rec.get("horizon") == pb.N_max):
+            return rec["dram_bytes_per_launch"] * pb.B / rec["batch"]
+    return None
+
+
+def max_sm_clock_mhz(gpu_index):
     try:
-        rec = json.load(open(path))
+        out = subprocess.run(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+        return float(out.stdout.strip().splitlines()[0])
     except Exception:
+        return measured_peak("sm_max_mhz", 2070.0)
+
+
+def fp32_peak(gpu_index):
+    """FP32 FMA peak of the device: SM count (device properties) x 128 lanes x
+    2 flop x the maximum SM clock (nvidia-smi); TFLOP/s, SMs, MHz."""
+    import torch
+    sms = torch.cuda.get_device_properties(gpu_index).multi_processor_count
+    mhz = max_sm_clock_mhz(gpu_index)
+    return sms * FP32_LANES_PER_SM * 2.0 * mhz * 1e6 / 1e12, sms, mhz
+
+
+GROUP_MODELS = {0: "MODEL_DI", 2: "MODEL_BICYCLE", 3: "MODEL_QUAD"}
+
+
+def group_kernel(model, form):
+    if model < 0 or form == 1:
+        return "solve_kernel (generic)"
+    return FORM_NAMES[form].format(m=GROUP_MODELS[model])
+
+
+def group_members(pb, model, solver):
+    """Instances of the model group `model` (-1: the generic kernel's group)."""
+    m = np.asarray(pb.model)
+    if solver == 1:
+        return np.arange(pb.B)
+    if model < 0:
+        return np.flatnonzero(~np.isin(m, FAST_MODELS))
+    return np.flatnonzero(m == model)
+
+
+def roofline_of(name, pb, stats, gtimes, solver, peak):
+    """Roofline of the dominant forward kernel (largest mean device time per
+    launch over the timed steps, CUDA events on its launching stream)."""
+    import workloads as w
+    groups = [g for g in gtimes if g["fwd_ms"] > 0]
+    if not groups:
         return None
-    if (rec.get("sources_sha256") != sources_digest() or rec.get("horizon") != pb.N_max
-            or rec.get("workload_name", "racing") != args.workload):
-        return None
-    return rec["dram_bytes_per_launch"] * pb.B / rec["batch"]
+    g = max(groups, key=lambda r: r["fwd_ms"])
+    idx = group_members(pb, g["model"], solver)
+    sub = pb.subset(idx)
+    st = stats[idx]
+    ms = g["fwd_ms"]
+    kernel = group_kernel(g["model"], g["form"])
+    lti = bool(np.all(np.isin(sub.model, (w.MODEL_LINEAR,))))
+    if lti and g["model"] < 0:
+        # factor blocks that do not fit on chip stream from HBM every ADMM iteration
+        achieved = algorithmic_bytes(sub, st) / (ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": measured_peak("hbm_gbs", 6800.0), "unit": "GB/s",
+                "peak_note": "STREAM-style copy bandwidth of this GPU pool (MEASURED_PEAKS.json hbm_gbs), of measured",
+                "flops_tflops": algorithmic_flops(sub, st) / (ms * 1e-3) / 1e12}
+    else:
+        achieved = algorithmic_flops(sub, st) / (ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak[0], "unit": "TFLOP/s",
+                "peak_note": f"FP32 FMA peak = {peak[1]} SMs (device properties) x {FP32_LANES_PER_SM} lanes x 2 flop "
+                             f"x {peak[2]:.0f} MHz (maximum SM clock), derived"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = measured_traffic(name, pb, kernel)
+    roof["kernel"] = kernel
+    roof["kernel_ms"] = ms
+    roof["instances"] = int(len(idx))
+    return roof
+
+
+def mean_group_times(samples):
+    """Average the per-group device times of several steps (tmpc_group_times)."""
+    out = []
+    for k in range(len(samples[0])):
+        rows = [s[k] for s in samples if k < len(s)]
+        r = dict(rows[0])
+        for f in ("fwd_ms", "bwd_ms"):
+            vals = [x[f] for x in rows if x[f] > 0]
+            r[f] = float(np.mean(vals)) if vals else -1.0
+        out.append(r)
+    return out
+
+
+def measure(name, pb, args, peak, flush, steps, warmup, autotune=False, plain=False, e2e=False, bwd=True,
+            solver=0, world=1):
+    """Time one workload: forward steps and forward + backward steps (CUDA events
+    on the caller's stream, L2 flushed before each), the per-group kernel times
+    (events on the launching streams), quality of the returned points."""
+    import torch
+    from paper_2606_24039_gb300 import Solver, tensors_from_batch
+    s = Solver.from_batch(pb, device="cuda", solver=solver, threads=args.threads)
+    sol = s.alloc_solution("cuda")
+    warm = s.z_init is not None
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    rec = {"config": describe(name, pb, world, solver)}
+    tune, forms = None, None
+    if autotune and solver == 0:
+        if warm:
+            sol["z"].copy_(s.z_init)
+            for k in ("xi", "y_eq", "y_ineq"):
+                sol[k].zero_()
+        tune = s.tmpc_autotune(s.x0, init=sol if warm else None, reps=2, trial_sqp=0)
+        forms = {r["model"]: r["solver"] for r in tune if r["model"] >= 0}
+        rec["autotune"] = tune
+    dLdz = torch.randn((pb.B, pb.N_max + 1, pb.n), device="cuda")
+
+    def restart():
+        if warm:   # every step starts from the same initial guess (zero slacks and multipliers)
+            sol["z"].copy_(s.z_init)
+            for k in ("xi", "y_eq", "y_ineq"):
+                sol[k].zero_()
+
+    def step():
+        restart()
+        s.tmpc_solve(s.x0, sol, warm_start=warm)
+
+    def step_fb():
+        step()
+        s.tmpc_backward(s.x0, sol, dLdz)
+
+    for _ in range(warmup):
+        step()
+        if bwd:
+            step_fb()
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        times, gts = [], []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            a, b = ev(), ev()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+            gts.append(s.tmpc_group_times())
+        return times, gts
+
+    t_fwd, g_fwd = timed(step)
+    stats = sol["stats"].cpu().numpy()
+    status = sol["status"].cpu().numpy()
+    t_fb, g_fb = timed(step_fb) if bwd else ([float("nan")], None)
+    gt = mean_group_times(g_fwd)
+    if g_fb:
+        gb = mean_group_times(g_fb)
+        for r, q in zip(gt, gb):
+            r["bwd_ms"] = q["bwd_ms"]
+        gt += gb[len(gt):]
+    kkt = stats[:, 6]
+    l_fwd, l_bwd = launches_per_step(pb, solver, forms)
+    ms_f, ms_fb = float(np.mean(t_fwd)), float(np.mean(t_fb))
+    rec.update({
+        "ms_per_step": ms_f, "value": pb.B / (ms_f * 1e-3), "unit": UNIT,
+        "fwd_bwd": {"value": pb.B / (ms_fb * 1e-3), "unit": UNIT, "ms_per_step": ms_fb} if bwd else None,
+        "group_times": gt,
+        "roofline": roofline_of(name, pb, stats, gt, solver, peak),
+        "gpu_launches": steps * l_fwd + (steps * (l_fwd + l_bwd) if bwd else 0),
+        "quality": {"kkt_median": float(np.median(kkt)), "kkt_p90": float(np.percentile(kkt, 90)),
+                    "frac_kkt_le_1e-5": float(np.mean(kkt <= 1e-5)),
+                    "status_counts": {str(k): int(v) for k, v in zip(*np.unique(status, return_counts=True))},
+                    "sqp_iters_mean": float(stats[:, 0].mean()), "admm_iters_mean": float(stats[:, 1].mean()),
+                    "factorizations_mean": float(stats[:, 5].mean())},
+    })
+    rec["_kkt"] = kkt
+    if plain and solver in (0, 2) and set(int(m) for m in np.unique(pb.model)) <= set(FAST_MODELS):
+        rec["plain_form"] = plain_form(pb, args, flush, ms_f, kkt)
+    if e2e:
+        hp = {k: (v.cpu().pin_memory() if v is not None else None) for k, v in tensors_from_batch(pb, "cpu").items()}
+        ho = {k: v.cpu().pin_memory() for k, v in s.alloc_solution("cpu").items()}
+        h2d = sum(v.numel() * v.element_size() for v in hp.values() if v is not None)
+        d2h = sum(v.numel() * v.element_size() for v in ho.values())
+        for _ in range(max(1, warmup)):
+            s.tmpc_solve_host(hp, hp["x0"], ho, z_init_host=hp["z_init"])
+        e2e_t = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            s.tmpc_solve_host(hp, hp["x0"], ho, z_init_host=hp["z_init"])
+            e2e_t.append(time.perf_counter() - t)
+        rec["e2e"] = {"ms": 1e3 * float(np.mean(e2e_t)), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    s.close()
+    return rec
+
+
+def plain_form(pb, args, flush, persistent_ms, kkt):
+    """The plain per-phase form of the same solve (one launch per phase, eager
+    and captured as a CUDA graph): the baseline the persistent kernel beats."""
+    import torch
+    from paper_2606_24039_gb300 import Solver
+    sp = Solver.from_batch(pb, device="cuda", solver=7, threads=args.threads)
+    solp = sp.alloc_solution("cuda")
+    warm = sp.z_init is not None
+    side = torch.cuda.Stream()
+    stream = torch.cuda.current_stream()
+
+    def pstep():
+        if warm:
+            solp["z"].copy_(sp.z_init)
+            for k in ("xi", "y_eq", "y_ineq"):
+                solp[k].zero_()
+        sp.tmpc_solve(sp.x0, solp, warm_start=warm)
+
+    for _ in range(2):
+        pstep()
+    torch.cuda.synchronize()
+
+    def time_fn(fn, n=3):
+        ts = []
+        for _ in range(n):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.mean(ts))
+
+    eager_ms = time_fn(pstep)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        pstep()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=side):
+            pstep()
+    torch.cuda.synchronize()
+    graph_ms = time_fn(g.replay)
+    kp = solp["stats"][:, 6].cpu().numpy()
+    groups_p = n_launch_groups(pb, 2)
+    out = {"eager_ms": eager_ms, "graph_ms": graph_ms, "persistent_ms": persistent_ms,
+           "launches_per_step": groups_p * (2 + pb.opts.max_sqp * (2 + pb.opts.max_admm)),
+           "kkt_median": float(np.median(kp)), "kkt_median_persistent": float(np.median(kkt)),
+           "speedup_vs_eager": eager_ms / persistent_ms, "speedup_vs_graph": graph_ms / persistent_ms}
+    del g
+    sp.close()
+    return out
+
+
+def closed_loop(pb, H, flush, steps=3):
+    """Closed-loop MPC episodes of the linear-system RL problem: H steps, each an
+    MPC solve of the whole batch through the differentiable layer, the first
+    control applied to x+ = A x + B u + b; the reward -(sum ||x||^2 + ||u||^2) is
+    differentiated with respect to theta = diag(Q) by autograd (the backward
+    chains every step's implicit-differentiation pass)."""
+    import torch
+    from paper_2606_24039_gb300 import Solver, solve_ocp
+    s = Solver.from_batch(pb, device="cuda")
+    A = torch.tensor(pb.extra["A"], dtype=torch.float32, device="cuda")
+    Bm = torch.tensor(pb.extra["B"], dtype=torch.float32, device="cuda")
+    b = torch.tensor(pb.extra["b"], dtype=torch.float32, device="cuda")
+    Rd = torch.tensor(pb.Rd, dtype=torch.float32, device="cuda")
+    ref = torch.zeros((pb.B, pb.N_max + 1, pb.n), device="cuda")
+    lo = torch.tensor(pb.lo, dtype=torch.float32, device="cuda")
+    hi = torch.tensor(pb.hi, dtype=torch.float32, device="cuda")
+    x0 = torch.tensor(pb.x0, dtype=torch.float32, device="cuda")
+    nx = pb.nx
+
+    def episode(grad):
+        theta = torch.tensor(pb.extra["theta"], dtype=torch.float32, device="cuda", requires_grad=grad)
+        x, R = x0, torch.zeros((), device="cuda")
+        for _ in range(H):
+            Qd = (2.0 * theta)[None, None, :].expand(pb.B, pb.N_max + 1, nx).contiguous()
+            z, _, _ = solve_ocp(s, x, Qd, Rd, ref, lo, hi)
+            u = z[:, 0, nx:]
+            R = R - (x * x).sum() - (u * u).sum()
+            x = x @ A.T + u @ Bm.T + b
+        if grad:
+            R.backward()
+        return R
+
+    for _ in range(2):
+        episode(True)
+    torch.cuda.synchronize()
+    out = {}
+    for key, grad in (("fwd", False), ("fwd_bwd", True)):
+        ts = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            with torch.set_grad_enabled(grad):
+                episode(grad)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t)
+        ms = 1e3 * float(np.mean(ts))
+        out[key] = {"ms_per_episode": ms, "solves_per_s": pb.B * H / (ms * 1e-3)}
+    s.close()
+    return {"H": H, "batch": pb.B, **out,
+            "note": "wall clock per episode (host loop over H MPC solves, each through TmpcFunction)"}
+
+
+def converged_batch(name, pb):
+    """The workload solved to the tolerance 1e-5 (early exit at eps_abs = eps_rel =
+    eps_c = 1e-5, <= 1000 ADMM iterations per QP, <= 10 SQP iterations for the
+    linear problems and <= 20 otherwise)."""
+    import dataclasses
+    pb.opts = dataclasses.replace(pb.opts, early_exit=1, eps_abs=1e-5, eps_rel=1e-5, eps_c=1e-5, max_admm=1000,
+                                  max_sqp=10 if name in LINEAR else 20, check_every=25)
+    return pb
 
 
 def run_gpu(args):
@@ -403,195 +741,76 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_2606_24039_gb300 import Solver, build, tensors_from_batch
+    from paper_2606_24039_gb300 import build
     build.build()
-    pb = workload(args, rank)
-    s = Solver.from_batch(pb, device="cuda", solver=args.solver, threads=args.threads)
-    sol = s.alloc_solution("cuda")
-    warm = s.z_init is not None
-    tune, forms = None, None
-    if args.solver == 0 and not args.no_autotune:
-        # the autotuner times each launch form of every model group on this batch
-        # (whole solves from the same initial guess as the timed steps)
-        if warm:
-            sol["z"].copy_(s.z_init)
-            for k in ("xi", "y_eq", "y_ineq"):
-                sol[k].zero_()
-        tune = s.tmpc_autotune(s.x0, init=sol if warm else None, reps=2, trial_sqp=0)
-        forms = {r["model"]: r["solver"] for r in tune if r["model"] >= 0}
-    dLdz = torch.randn((pb.B, pb.N_max + 1, pb.n), device="cuda")
+    peak = fp32_peak(local)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    ev = lambda: torch.cuda.Event(enable_timing=True)
-
-    def restart():
-        # every step starts from the same initial guess (zero slacks and multipliers)
-        if warm:
-            sol["z"].copy_(s.z_init)
-            for k in ("xi", "y_eq", "y_ineq"):
-                sol[k].zero_()
-
-    def step(kev=None):
-        restart()
-        if kev is not None:
-            kev[0].record(stream)
-        s.tmpc_solve(s.x0, sol, warm_start=warm)
-        if kev is not None:
-            kev[1].record(stream)
-
-    def step_fb(kev=None):
-        step(kev)
-        s.tmpc_backward(s.x0, sol, dLdz)
-
-    for _ in range(args.warmup):
-        step()
-        if not args.skip_bwd:
-            step_fb()
-    torch.cuda.synchronize()
-
-    def timed(fn):
-        times, ktimes = [], []
-        for _ in range(args.steps):
-            flush.fill_(1.0)
-            torch.cuda.synchronize()
-            if world > 1:
-                dist.barrier()
-            a, b, kev = ev(), ev(), (ev(), ev())
-            a.record(stream)
-            fn(kev)
-            b.record(stream)
-            b.synchronize()
-            times.append(a.elapsed_time(b))
-            ktimes.append(kev[0].elapsed_time(kev[1]))
-        return times, ktimes
-
+    pb = workload(args, rank)
+    suite = not args.no_suite and args.workload == "uneven" and world == 1
+    if world > 1:
+        dist.barrier()
     with Clocks(local, args.clocks_csv) as clk:
         t0 = time.time()
-        t_fwd, k_fwd = timed(step)
-        t_fb, _ = timed(step_fb) if not args.skip_bwd else ([float("nan")], None)
+        head = measure(args.workload, pb, args, peak, flush, args.steps, args.warmup,
+                       autotune=(args.solver == 0 and not args.no_autotune), plain=not args.no_plain,
+                       e2e=not args.skip_e2e, bwd=not args.skip_bwd, solver=args.solver, world=world)
         t1 = time.time()
+        subs, conv = {}, {}
+        if suite:
+            for name in SUITE:
+                spb = workload(args, rank, name)
+                r = measure(name, spb, args, peak, flush, max(3, args.steps // 4), max(3, args.warmup // 2),
+                            autotune=(name == "racing"), bwd=True)
+                if name == "linear_rl":
+                    r["closed_loop"] = closed_loop(spb, 50, flush)
+                r.pop("_kkt", None)
+                subs[name] = r
+            for name in ("uneven",) + SUITE:
+                cpb = converged_batch(name, workload(args, rank, name))
+                r = measure(name, cpb, args, peak, flush, 2, 1, bwd=False)
+                kkt = r.pop("_kkt")
+                conv[name] = {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
+                              "frac_kkt_le_1e-5": float(np.mean(kkt <= 1e-5)),
+                              "solves_at_1e-5_per_s": float(np.sum(kkt <= 1e-5)) / (r["ms_per_step"] * 1e-3),
+                              "kkt_median": float(np.median(kkt)), "kkt_p90": float(np.percentile(kkt, 90)),
+                              "sqp_iters_mean": r["quality"]["sqp_iters_mean"],
+                              "admm_iters_mean": r["quality"]["admm_iters_mean"],
+                              "status_counts": r["quality"]["status_counts"], "config": r["config"]["workload"]}
+        t2 = time.time()
+    head.pop("_kkt", None)
     clocks = clk.summary(t0, t1)
-    stats = sol["stats"].cpu().numpy()
-    status = sol["status"].cpu().numpy()
-    kkt = stats[:, 6]
-    l_fwd, l_bwd = launches_per_step(pb, args.solver, forms)
-    launches = args.steps * l_fwd + (0 if args.skip_bwd else args.steps * (l_fwd + l_bwd))
-
-    # the plain per-phase form of the same solve: one launch per phase, eager and
-    # captured as a CUDA graph (the baseline the persistent kernel is compared with)
-    plain = None
-    if not args.no_plain and args.workload in ("racing", "double_integrator", "uneven") and args.solver in (0, 2):
-        sp = Solver.from_batch(pb, device="cuda", solver=7, threads=args.threads)
-        solp = sp.alloc_solution("cuda")
-        side = torch.cuda.Stream()
-
-        def pstep():
-            if warm:
-                solp["z"].copy_(sp.z_init)
-                for k in ("xi", "y_eq", "y_ineq"):
-                    solp[k].zero_()
-            sp.tmpc_solve(sp.x0, solp, warm_start=warm)
-
-        for _ in range(2):
-            pstep()
-        torch.cuda.synchronize()
-        n_plain = max(2, min(args.steps, 5))
-
-        def time_fn(fn):
-            ts = []
-            for _ in range(n_plain):
-                flush.fill_(1.0)
-                torch.cuda.synchronize()
-                a, b = ev(), ev()
-                a.record(stream)
-                fn()
-                b.record(stream)
-                b.synchronize()
-                ts.append(a.elapsed_time(b))
-            return float(np.mean(ts))
-
-        eager_ms = time_fn(pstep)
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.stream(side):
-            pstep()
-            torch.cuda.synchronize()
-            with torch.cuda.graph(g, stream=side):
-                pstep()
-        torch.cuda.synchronize()
-        graph_ms = time_fn(g.replay)
-        kp = solp["stats"][:, 6].cpu().numpy()
-        groups_p = n_launch_groups(pb, 2)
-        plain = {"eager_ms": eager_ms, "graph_ms": graph_ms, "persistent_ms": float(np.mean(t_fwd)),
-                 "launches_per_step": groups_p * (2 + pb.opts.max_sqp * (2 + pb.opts.max_admm)),
-                 "kkt_median": float(np.median(kp)), "kkt_median_persistent": float(np.median(kkt)),
-                 "speedup_vs_eager": eager_ms / float(np.mean(t_fwd)), "speedup_vs_graph": graph_ms / float(np.mean(t_fwd))}
-        del g
-        sp.close()
-
-    # end to end through the host-memory entry point
-    hp = {k: (v.cpu().pin_memory() if v is not None else None) for k, v in tensors_from_batch(pb, "cpu").items()}
-    ho = {k: v.cpu().pin_memory() for k, v in s.alloc_solution("cpu").items()}
-    h2d = sum(v.numel() * v.element_size() for v in hp.values() if v is not None)
-    d2h = sum(v.numel() * v.element_size() for v in ho.values())
-    for _ in range(0 if args.skip_e2e else max(1, args.warmup)):
-        s.tmpc_solve_host(hp, hp["x0"], ho, z_init_host=hp["z_init"])
-    e2e_t = [float("nan")]
-    for _ in range(0 if args.skip_e2e else args.steps):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        s.tmpc_solve_host(hp, hp["x0"], ho, z_init_host=hp["z_init"])
-        e2e_t.append(time.perf_counter() - t)
-    e2e_t = [v for v in e2e_t if v == v] or [float("nan")]
-
-    ms_f = float(np.mean(t_fwd))
-    ms_fb = float(np.mean(t_fb))
-    ms_e2e = 1e3 * float(np.mean(e2e_t))
+    clocks_all = clk.summary(t0, t2)
+    ms_f = head["ms_per_step"]
+    ms_fb = head["fwd_bwd"]["ms_per_step"] if head["fwd_bwd"] else float("nan")
+    ms_e2e = head["e2e"]["ms"] if "e2e" in head else float("nan")
     if world > 1:   # the slowest rank sets the job time (no collective on the data path)
         from paper_2606_24039_gb300.shard import max_over_ranks
         ms_f, ms_fb, ms_e2e = (max_over_ranks(v, device="cuda") for v in (ms_f, ms_fb, ms_e2e))
     total = pb.B * world
-    value = total / (ms_f * 1e-3)
-    flops = algorithmic_flops(pb, stats)
-    ms_k = float(np.mean(k_fwd))          # the solve kernel(s) of one forward step, on the launching stream
-    peak_clock = 2070.0
-    fp32_peak = SMS * FP32_LANES * 2 * peak_clock * 1e6 / 1e12
-    if args.workload == "tracking":
-        # factors of 0.74 MB per instance do not fit on chip: streamed from HBM every ADMM iteration
-        achieved = algorithmic_bytes(pb, stats) / (ms_k * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": measured_peak("hbm_gbs", 6800.0), "unit": "GB/s",
-                "flops_tflops": flops / (ms_k * 1e-3) / 1e12,
-                "peak_note": "STREAM-style copy bandwidth of this GPU pool (MEASURED_PEAKS.json hbm_gbs)"}
-    else:
-        achieved = flops / (ms_k * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "peak_note": "FP32 FMA peak = 152 SM x 128 lanes x 2 flop x 2070 MHz (derived)"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = measured_traffic(args, pb)
-    roof["kernel"] = kernel_name(pb, args.solver, forms)
-    roof["kernel_ms"] = ms_k
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": METRIC, "value": total / (ms_f * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_f, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(args, pb),
             "fwd_bwd": {"value": total / (ms_fb * 1e-3), "unit": UNIT, "ms_per_step": ms_fb},
             "clocks": clocks,
-            "e2e": {"value": total / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": launches,
-            "roofline": roof,
+            "e2e": ({"value": total / (ms_e2e * 1e-3), "unit": UNIT,
+                     "h2d_bytes_per_step": head["e2e"]["h2d_bytes_per_step"],
+                     "d2h_bytes_per_step": head["e2e"]["d2h_bytes_per_step"]} if "e2e" in head else None),
+            "gpu_launches": head["gpu_launches"],
+            "roofline": head["roofline"],
+            "group_times": head["group_times"],
             "cpu_baseline": cpu_base,
-            "plain_form": plain,
-            "autotune": tune,
-            "quality": {"kkt_median": float(np.median(kkt)), "kkt_p90": float(np.percentile(kkt, 90)),
-                        "frac_kkt_le_1e-5": float(np.mean(kkt <= 1e-5)),
-                        "status_counts": {str(k): int(v) for k, v in zip(*np.unique(status, return_counts=True))},
-                        "admm_iters_mean": float(stats[:, 1].mean()), "factorizations_mean": float(stats[:, 5].mean())},
+            "plain_form": head.get("plain_form"),
+            "autotune": head.get("autotune"),
+            "quality": head["quality"],
+            "fp32_peak": {"tflops": peak[0], "sms": peak[1], "sm_max_mhz": peak[2]},
         }
+        if suite:
+            line["workloads"] = subs
+            line["at_1e-5"] = conv
+            line["clocks_suite"] = clocks_all
         print(json.dumps(line), flush=True)
-    s.close()
     if world > 1:
         dist.destroy_process_group()
 

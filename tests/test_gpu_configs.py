@@ -91,6 +91,14 @@ def test_racing_from_the_newton_rollout(solver):
 # ---------------------------------------------------------------------------
 # backward at the tracking dimensions, on the GPU's own forward output
 # ---------------------------------------------------------------------------
+def _rounded_to_fp32(inst):
+    """The instance with every array rounded to FP32, as the GPU receives it (an
+    ill-conditioned active-set KKT system amplifies an input difference of one
+    FP32 rounding far beyond the gradient bar)."""
+    return {k: (v.astype(np.float32).astype(np.float64) if isinstance(v, np.ndarray) and v.dtype == np.float64 else v)
+            for k, v in inst.items()}
+
+
 def _as_oracle_solution(sol, i, inst):
     T, n, nx, ng = inst["N"] + 1, inst["nx"] + inst["nu"], inst["nx"], inst["ng"]
     g = lambda k, m: sol[k][i, :T, :m].cpu().numpy().astype(np.float64)
@@ -279,9 +287,10 @@ def test_backward_uneven_full_batch_on_gpu_forward():
     """The uneven batch (4096 instances, N in 10..200, three models, 10 SQP x 50
     ADMM) forward and backward in the launch configuration the benchmark times;
     16 sampled instances: the direct FP64 adjoint solve of the small models and
-    the oracle's sparse LU of the same active-set KKT system at the GPU's
-    forward point agree per parameter (instances whose KKT matrix the oracle
-    finds singular are compared after the same -1e-10 regularisation)."""
+    the oracle's sparse LU of the same active-set KKT system, built from the
+    same (FP32) parameters at the GPU's forward point, agree per parameter
+    (instances whose KKT matrix the oracle finds singular are compared after
+    the same -1e-10 regularisation)."""
     from paper_2606_24039_gb300 import Solver
     pb = w.uneven(B=4096)
     s = Solver.from_batch(pb, device="cuda")
@@ -294,7 +303,7 @@ def test_backward_uneven_full_batch_on_gpu_forward():
     idx = np.random.default_rng(8).choice(pb.B, 16, replace=False)
     worst = []
     for i in idx:
-        inst = pb.instance(i)
+        inst = _rounded_to_fp32(pb.instance(i))   # the parameters the GPU solved with
         T, n, nx, nu, ng = inst["N"] + 1, inst["nx"] + inst["nu"], inst["nx"], inst["nu"], inst["ng"]
         p = _as_oracle_solution(sol, i, inst)
         gr, info = obwd.backward(inst, p, dLdz[i, :T, :n].astype(np.float64), eps_g=pb.opts.eps_g)
