@@ -31,9 +31,11 @@
 namespace tmpc {
 namespace fast {
 
-// doubles of the FP64 workspace per stage: S_t^-1 (MB^2) and y_t (MB), MB <= kDirectMB
+// doubles of the FP64 workspace per stage: S_t^-1 (MB^2), y_t (MB), then the FP64
+// Jacobian A^-_t (NX x N) and the dense row of G_t (N); MB <= kDirectMB, NX N <= 48, N <= 8
 constexpr int kDirectMB = 19;
-constexpr long long kDirectStage = (long long)kDirectMB * kDirectMB + kDirectMB;
+constexpr long long kDirectJac = (long long)kDirectMB * kDirectMB + kDirectMB;
+constexpr long long kDirectStage = kDirectJac + 48 + 8;
 
 template <int M>
 struct Kkt {
@@ -49,6 +51,70 @@ struct Kkt {
 template <int M>
 __device__ __forceinline__ double Hsub(const Inst<M>& c, int j, int b) {
     return (j == b && j >= Inst<M>::NX) ? -(double)c.W(j - Inst<M>::NX) : 0.0;
+}
+
+// Diagonal of the cost Hessian block D_t (App. B: D_t = H^+_{t-1} + H^-_t), in FP64
+template <int M>
+__device__ __forceinline__ double Hdiag(const Inst<M>& c, int t, int j) {
+    double d = (double)c.Cw(t, j);
+    if (j >= Inst<M>::NX) {
+        const double w = (double)c.W(j - Inst<M>::NX);
+        if (t < c.Nh) d += w;
+        if (t > 0) d += w;
+    }
+    return d;
+}
+
+// FP64 Jacobian A^-_t = d f_t / d z_t (NX x N) at the FP32 point (zt, zn) and the
+// dense row of G_t, evaluated by the model functions in double precision, so that
+// the KKT system is the one at the returned point up to FP64 rounding.
+template <int M>
+__device__ __forceinline__ void jacobians_fp64(const Inst<M>& c, int t, double* Ad, double* Gd) {
+    using Tr = Traits<M>;
+    constexpr int N = Inst<M>::N, NX = Inst<M>::NX;
+    double zt[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) zt[j] = (double)c.zb[t * N + j];
+    if (t < c.Nh) {
+        if constexpr (M == MODEL_DI) {
+            const double dt = (double)c.dyn[0];
+#pragma unroll
+            for (int i = 0; i < NX * N; ++i) Ad[i] = 0.0;
+            for (int k = 0; k < 4; ++k) Ad[k * N + k] = 1.0;
+            Ad[0 * N + 2] = dt; Ad[1 * N + 3] = dt;
+            Ad[0 * N + 4] = 0.5 * dt * dt; Ad[1 * N + 5] = 0.5 * dt * dt;
+            Ad[2 * N + 4] = dt; Ad[3 * N + 5] = dt;
+        } else if constexpr (M == MODEL_QUAD) {
+            double phi[6], dPx[36], dPu[12];
+            quad_rk4<double>(zt, zt + 6, c.dyn, phi, dPx, dPu);
+            for (int k = 0; k < 6; ++k) {
+                for (int j = 0; j < 6; ++j) Ad[k * N + j] = dPx[k * 6 + j];
+                Ad[k * N + 6] = dPu[k * 2];
+                Ad[k * N + 7] = dPu[k * 2 + 1];
+            }
+        } else {   // bicycle, implicit midpoint
+            const double dt = (double)c.dyn[0];
+            double mid[6], fc[6], Jx[36], Ju[12];
+            for (int k = 0; k < 6; ++k) mid[k] = 0.5 * (zt[k] + (double)c.zb[(t + 1) * N + k]);
+            bicycle_fc<double>(mid, zt + 6, c.dyn[1], c.track, c.nt, c.dyn[2], fc, Jx, Ju);
+            for (int k = 0; k < 6; ++k) {
+                for (int j = 0; j < 6; ++j) Ad[k * N + j] = (k == j ? 1.0 : 0.0) + 0.5 * dt * Jx[k * 6 + j];
+                Ad[k * N + 6] = dt * Ju[k * 2];
+                Ad[k * N + 7] = dt * Ju[k * 2 + 1];
+            }
+        }
+    }
+    if constexpr (Tr::DENSE_ROW >= 0) {   // lateral track error of the bicycle
+        TrackPtR<double> tp = track_eval<double>(c.track, c.nt, (double)c.dyn[2], zt[5]);
+        double sp, cp;
+        msincos(tp.psic, &sp, &cp);
+        const double dx = zt[0] - tp.xc, dy = zt[1] - tp.yc;
+#pragma unroll
+        for (int j = 0; j < N; ++j) Gd[j] = 0.0;
+        Gd[0] = -sp;
+        Gd[1] = cp;
+        Gd[5] = tp.dxc * sp - tp.dyc * cp - tp.dpsic * (dx * cp + dy * sp);
+    }
 }
 
 // Solve by warp 0 of the team.  code: active-set codes (0 inactive, +-1 hard,
@@ -70,8 +136,24 @@ __device__ bool direct_adjoint(const Inst<M>& c, const float* code, const float*
     const bool warp0 = c.tid < 32;
     const int lane = c.tid & 31;
     const bool row = warp0 && lane < MB;
+    for (int t = c.tid; t < T; t += c.nth) {
+        double* st = dws + (long long)t * kDirectStage + kDirectJac;
+        jacobians_fp64<M>(c, t, st, st + 48);
+    }
     if (c.tid == 0) *flag = 0;
     c.sync();
+    // FP64 blocks: A^-_t, A^+_t (implicit: A^-_x - 2I; explicit: -I on the states), G_t
+    auto Amd = [&](int t) -> const double* { return dws + (long long)t * kDirectStage + kDirectJac; };
+    auto Apd = [&](int t, int k, int j) -> double {
+        if (j >= NX) return 0.0;
+        if (Traits<M>::IMPLICIT) return Amd(t)[k * N + j] - (k == j ? 2.0 : 0.0);
+        return k == j ? -1.0 : 0.0;
+    };
+    auto Gd = [&](int t, int q, int j) -> double {
+        const int s = Traits<M>::sel(q);
+        if (s >= 0) return j == s ? 1.0 : 0.0;
+        return (dws + (long long)t * kDirectStage + kDirectJac + 48)[j];
+    };
     for (int pass = 0; pass < 2; ++pass) {
         const double delta = pass == 0 ? 0.0 : 1e-10;
         if (warp0) {
@@ -86,22 +168,22 @@ __device__ bool direct_adjoint(const Inst<M>& c, const float* code, const float*
                         const int k = lane;
 #pragma unroll
                         for (int j = 0; j < N; ++j)
-                            a[XZ + j] = t == 0 ? (j == k ? 1.0 : 0.0) : (double)c.Ap(t - 1, k, j);
+                            a[XZ + j] = t == 0 ? (j == k ? 1.0 : 0.0) : Apd(t - 1, k, j);
                         a[k] = -delta;
                     } else if (lane < XH) {                  // eta_x,t row j
                         const int j = lane - XZ;
 #pragma unroll
                         for (int k = 0; k < NX; ++k)
-                            a[k] = t == 0 ? (j == k ? 1.0 : 0.0) : (double)c.Ap(t - 1, k, j);
-                        a[XZ + j] = (double)c.Pd[t * N + j];
+                            a[k] = t == 0 ? (j == k ? 1.0 : 0.0) : Apd(t - 1, k, j);
+                        a[XZ + j] = Hdiag<M>(c, t, j);
 #pragma unroll
                         for (int q = 0; q < NG; ++q) {
                             const float cd = code[t * NG + q];
-                            const double g = (double)c.Gval(t, q, j);
+                            const double g = Gd(t, q, j);
                             if (fabsf(cd) > 1.5f) {          // slack-active: gamma2 G_q' G_q
 #pragma unroll
                                 for (int jj = 0; jj < N; ++jj)
-                                    a[XZ + jj] += (double)c.gam2(q) * g * (double)c.Gval(t, q, jj);
+                                    a[XZ + jj] += (double)c.gam2(q) * g * Gd(t, q, jj);
                             } else if (cd != 0.f) {
                                 a[XH + q] = g;
                             }
@@ -111,7 +193,7 @@ __device__ bool direct_adjoint(const Inst<M>& c, const float* code, const float*
                         const float cd = code[t * NG + q];
                         if (cd != 0.f && fabsf(cd) < 1.5f) {
 #pragma unroll
-                            for (int j = 0; j < N; ++j) a[XZ + j] = (double)c.Gval(t, q, j);
+                            for (int j = 0; j < N; ++j) a[XZ + j] = Gd(t, q, j);
                             a[lane] = -delta;
                         } else {
                             a[lane] = 1.0;
@@ -122,7 +204,7 @@ __device__ bool direct_adjoint(const Inst<M>& c, const float* code, const float*
                         double pr[N];   // row `lane` of P_t
 #pragma unroll
                         for (int b = 0; b < N; ++b)
-                            pr[b] = lane < XZ ? (double)c.Amt(t - 1)[lane * N + b] : Hsub<M>(c, lane - XZ, b);
+                            pr[b] = lane < XZ ? Amd(t - 1)[lane * N + b] : Hsub<M>(c, lane - XZ, b);
                         double u[N];
 #pragma unroll
                         for (int b = 0; b < N; ++b) {
@@ -136,7 +218,7 @@ __device__ bool direct_adjoint(const Inst<M>& c, const float* code, const float*
                             double s = 0.0;
 #pragma unroll
                             for (int b = 0; b < N; ++b)
-                                s += u[b] * (col < XZ ? (double)c.Amt(t - 1)[col * N + b] : Hsub<M>(c, col - XZ, b));
+                                s += u[b] * (col < XZ ? Amd(t - 1)[col * N + b] : Hsub<M>(c, col - XZ, b));
                             a[col] -= s;
                         }
                     }
@@ -195,7 +277,7 @@ __device__ bool direct_adjoint(const Inst<M>& c, const float* code, const float*
                     if (t > 0 && lane < XH) {
 #pragma unroll
                         for (int b = 0; b < N; ++b)
-                            y -= (lane < XZ ? (double)c.Amt(t - 1)[lane * N + b] : Hsub<M>(c, lane - XZ, b)) * wv[b];
+                            y -= (lane < XZ ? Amd(t - 1)[lane * N + b] : Hsub<M>(c, lane - XZ, b)) * wv[b];
                     }
                     yv[lane] = y;
                     Sinv[MB * MB + lane] = y;
@@ -222,7 +304,7 @@ __device__ bool direct_adjoint(const Inst<M>& c, const float* code, const float*
                         const int b = lane - XZ;
                         double s = 0.0;
 #pragma unroll
-                        for (int k = 0; k < NX; ++k) s += (double)c.Amt(t)[k * N + b] * yv[k];
+                        for (int k = 0; k < NX; ++k) s += Amd(t)[k * N + b] * yv[k];
 #pragma unroll
                         for (int j = 0; j < N; ++j) s += Hsub<M>(c, j, b) * xnext[j];
                         v -= s;

@@ -618,7 +618,7 @@ __device__ __forceinline__ void rollout(const Inst<M>& c, int newton_steps) {
             const float* z = c.zb + t * N;
             float xn[NX];
             if constexpr (M == MODEL_QUAD) {
-                quad_rk4(z, z + 6, c.dyn, xn, nullptr, nullptr);
+                quad_rk4<float>(z, z + 6, c.dyn, xn, nullptr, nullptr);
             } else if constexpr (M == MODEL_DI) {
                 const float dt = c.dyn[0];
                 xn[0] = z[0] + dt * z[2] + 0.5f * dt * dt * z[4];
@@ -627,7 +627,7 @@ __device__ __forceinline__ void rollout(const Inst<M>& c, int newton_steps) {
                 xn[3] = z[3] + dt * z[5];
             } else {
                 float fc[6], zn[8], f[6], Am[6 * 8], Mx[36];
-                bicycle_fc(z, z + 6, c.dyn[1], c.track, c.nt, c.dyn[2], fc, nullptr, nullptr);
+                bicycle_fc<float>(z, z + 6, c.dyn[1], c.track, c.nt, c.dyn[2], fc, nullptr, nullptr);
 #pragma unroll
                 for (int k = 0; k < 6; ++k) xn[k] = z[k] + c.dyn[0] * fc[k];
                 for (int it = 0; it < newton_steps; ++it) {

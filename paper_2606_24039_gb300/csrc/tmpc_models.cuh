@@ -38,27 +38,40 @@ __host__ __device__ inline bool model_linear_dyn(int m) { return m == MODEL_DI |
 // racing centreline: periodic table (x_c, y_c, psi_c, kappa) every ds metres,
 // cubic Hermite interpolation with knot derivatives (cos psi, sin psi, kappa)
 // ---------------------------------------------------------------------------
-struct TrackPt {
-    float xc, yc, psic, dxc, dyc, dpsic;
-};
+// math of either precision (the FP32 forward and the FP64 Jacobians of the direct backward)
+__device__ __forceinline__ void msincos(float a, float* s, float* c) { sincosf(a, s, c); }
+__device__ __forceinline__ void msincos(double a, double* s, double* c) { sincos(a, s, c); }
+__device__ __forceinline__ float mfloor(float a) { return floorf(a); }
+__device__ __forceinline__ double mfloor(double a) { return floor(a); }
+__device__ __forceinline__ float mtan(float a) { return tanf(a); }
+__device__ __forceinline__ double mtan(double a) { return tan(a); }
+__device__ __forceinline__ float mcos(float a) { return cosf(a); }
+__device__ __forceinline__ double mcos(double a) { return cos(a); }
 
-__device__ __forceinline__ TrackPt track_eval(const float* tab, int nt, float ds, float s) {
-    const float L = nt * ds;
-    float sm = s - L * floorf(s / L);
-    int k = (int)floorf(sm / ds);
+template <class R>
+struct TrackPtR {
+    R xc, yc, psic, dxc, dyc, dpsic;
+};
+using TrackPt = TrackPtR<float>;
+
+template <class R>
+__device__ __forceinline__ TrackPtR<R> track_eval(const float* tab, int nt, R ds, R s) {
+    const R L = nt * ds;
+    R sm = s - L * mfloor(s / L);
+    int k = (int)mfloor(sm / ds);
     k = k < 0 ? 0 : (k > nt - 1 ? nt - 1 : k);
-    const float tau = (sm - k * ds) / ds;
+    const R tau = (sm - k * ds) / ds;
     const float* a = tab + 4 * k;
     const float* b = a + 4;
-    const float t2 = tau * tau, t3 = t2 * tau;
-    const float h00 = 2.f * t3 - 3.f * t2 + 1.f, h10 = t3 - 2.f * t2 + tau;
-    const float h01 = -2.f * t3 + 3.f * t2, h11 = t3 - t2;
-    const float d00 = 6.f * t2 - 6.f * tau, d10 = 3.f * t2 - 4.f * tau + 1.f;
-    const float d01 = -6.f * t2 + 6.f * tau, d11 = 3.f * t2 - 2.f * tau;
-    float sa, ca, sb, cb;
-    sincosf(a[2], &sa, &ca);
-    sincosf(b[2], &sb, &cb);
-    TrackPt p;
+    const R t2 = tau * tau, t3 = t2 * tau;
+    const R h00 = R(2) * t3 - R(3) * t2 + R(1), h10 = t3 - R(2) * t2 + tau;
+    const R h01 = R(-2) * t3 + R(3) * t2, h11 = t3 - t2;
+    const R d00 = R(6) * t2 - R(6) * tau, d10 = R(3) * t2 - R(4) * tau + R(1);
+    const R d01 = R(-6) * t2 + R(6) * tau, d11 = R(3) * t2 - R(2) * tau;
+    R sa, ca, sb, cb;
+    msincos((R)a[2], &sa, &ca);
+    msincos((R)b[2], &sb, &cb);
+    TrackPtR<R> p;
     p.xc = h00 * a[0] + h10 * ds * ca + h01 * b[0] + h11 * ds * cb;
     p.yc = h00 * a[1] + h10 * ds * sa + h01 * b[1] + h11 * ds * sb;
     p.psic = h00 * a[2] + h10 * ds * a[3] + h01 * b[2] + h11 * ds * b[3];
@@ -70,16 +83,17 @@ __device__ __forceinline__ TrackPt track_eval(const float* tab, int nt, float ds
 
 // kinematic bicycle: state (px, py, psi, v, delta, s), control (a, steer rate);
 // ds/dt = v cos(psi - psi_c(s)).  Jx [6][6], Ju [6][2] row-major (nullable).
-__device__ __forceinline__ void bicycle_fc(const float* x, const float* u, float L,
-                                           const float* tab, int nt, float ds,
-                                           float* f, float* Jx, float* Ju) {
-    const float psi = x[2], v = x[3], dl = x[4], s = x[5];
-    TrackPt tp = track_eval(tab, nt, ds, s);
-    float sp, cp;
-    sincosf(psi, &sp, &cp);
-    const float tn = tanf(dl);
-    float sd, cd;
-    sincosf(psi - tp.psic, &sd, &cd);
+template <class R>
+__device__ __forceinline__ void bicycle_fc(const R* x, const R* u, float Lf, const float* tab, int nt, float ds,
+                                           R* f, R* Jx, R* Ju) {
+    const R L = (R)Lf;
+    const R psi = x[2], v = x[3], dl = x[4], s = x[5];
+    TrackPtR<R> tp = track_eval<R>(tab, nt, (R)ds, s);
+    R sp, cp;
+    msincos(psi, &sp, &cp);
+    const R tn = mtan(dl);
+    R sd, cd;
+    msincos(psi - tp.psic, &sd, &cd);
     f[0] = v * cp;
     f[1] = v * sp;
     f[2] = v * tn / L;
@@ -87,8 +101,8 @@ __device__ __forceinline__ void bicycle_fc(const float* x, const float* u, float
     f[4] = u[1];
     f[5] = v * cd;
     if (Jx) {
-        for (int i = 0; i < 36; ++i) Jx[i] = 0.f;
-        const float cdl = cosf(dl);
+        for (int i = 0; i < 36; ++i) Jx[i] = R(0);
+        const R cdl = mcos(dl);
         Jx[0 * 6 + 2] = -v * sp;
         Jx[0 * 6 + 3] = cp;
         Jx[1 * 6 + 2] = v * cp;
@@ -100,19 +114,19 @@ __device__ __forceinline__ void bicycle_fc(const float* x, const float* u, float
         Jx[5 * 6 + 5] = v * sd * tp.dpsic;
     }
     if (Ju) {
-        for (int i = 0; i < 12; ++i) Ju[i] = 0.f;
-        Ju[3 * 2 + 0] = 1.f;
-        Ju[4 * 2 + 1] = 1.f;
+        for (int i = 0; i < 12; ++i) Ju[i] = R(0);
+        Ju[3 * 2 + 0] = R(1);
+        Ju[4 * 2 + 1] = R(1);
     }
 }
 
 // planar quadrotor: state (px, pz, theta, vx, vz, omega), control (T1, T2)
-__device__ __forceinline__ void quad_fc(const float* x, const float* u, const float* dyn,
-                                        float* f, float* Jx, float* Ju) {
-    const float m = dyn[1], I = dyn[2], arm = dyn[3], g = dyn[4];
-    float s, c;
-    sincosf(x[2], &s, &c);
-    const float T = u[0] + u[1];
+template <class R>
+__device__ __forceinline__ void quad_fc(const R* x, const R* u, const float* dyn, R* f, R* Jx, R* Ju) {
+    const R m = dyn[1], I = dyn[2], arm = dyn[3], g = dyn[4];
+    R s, c;
+    msincos(x[2], &s, &c);
+    const R T = u[0] + u[1];
     f[0] = x[3];
     f[1] = x[4];
     f[2] = x[5];
@@ -120,15 +134,15 @@ __device__ __forceinline__ void quad_fc(const float* x, const float* u, const fl
     f[4] = T * c / m - g;
     f[5] = (u[1] - u[0]) * arm / I;
     if (Jx) {
-        for (int i = 0; i < 36; ++i) Jx[i] = 0.f;
-        Jx[0 * 6 + 3] = 1.f;
-        Jx[1 * 6 + 4] = 1.f;
-        Jx[2 * 6 + 5] = 1.f;
+        for (int i = 0; i < 36; ++i) Jx[i] = R(0);
+        Jx[0 * 6 + 3] = R(1);
+        Jx[1 * 6 + 4] = R(1);
+        Jx[2 * 6 + 5] = R(1);
         Jx[3 * 6 + 2] = -T * c / m;
         Jx[4 * 6 + 2] = -T * s / m;
     }
     if (Ju) {
-        Ju[0] = Ju[1] = Ju[2] = Ju[3] = Ju[4] = Ju[5] = 0.f;
+        Ju[0] = Ju[1] = Ju[2] = Ju[3] = Ju[4] = Ju[5] = R(0);
         Ju[6] = Ju[7] = -s / m;
         Ju[8] = Ju[9] = c / m;
         Ju[10] = -arm / I;
@@ -137,35 +151,36 @@ __device__ __forceinline__ void quad_fc(const float* x, const float* u, const fl
 }
 
 // RK4 step of the quadrotor; with Jacobians by the chain rule through the stages.
-__device__ inline void quad_rk4(const float* x, const float* u, const float* dyn, float* phi,
-                                float* dPx /*36 or null*/, float* dPu /*12 or null*/) {
-    const float dt = dyn[0];
-    float k[4][6], xs[6];
-    float dkx[6 * 6], dku[6 * 2], J[36], Ju[12], accx[36], accu[12], tx[36], tu[12];
-    const float cst[4] = {0.f, 0.5f, 0.5f, 1.f};
-    const float wgt[4] = {1.f, 2.f, 2.f, 1.f};
+template <class R>
+__device__ inline void quad_rk4(const R* x, const R* u, const float* dyn, R* phi, R* dPx /*36 or null*/,
+                                R* dPu /*12 or null*/) {
+    const R dt = dyn[0];
+    R k[4][6], xs[6];
+    R dkx[6 * 6], dku[6 * 2], J[36], Ju[12], accx[36], accu[12], tx[36], tu[12];
+    const R cst[4] = {R(0), R(0.5), R(0.5), R(1)};
+    const R wgt[4] = {R(1), R(2), R(2), R(1)};
     const bool jac = dPx != nullptr;
     if (jac) {
-        for (int i = 0; i < 36; ++i) accx[i] = 0.f;
-        for (int i = 0; i < 12; ++i) accu[i] = 0.f;
+        for (int i = 0; i < 36; ++i) accx[i] = R(0);
+        for (int i = 0; i < 12; ++i) accu[i] = R(0);
     }
     for (int st = 0; st < 4; ++st) {
-        for (int i = 0; i < 6; ++i) xs[i] = x[i] + (st ? cst[st] * dt * k[st - 1][i] : 0.f);
-        quad_fc(xs, u, dyn, k[st], jac ? J : nullptr, jac ? Ju : nullptr);
+        for (int i = 0; i < 6; ++i) xs[i] = x[i] + (st ? cst[st] * dt * k[st - 1][i] : R(0));
+        quad_fc<R>(xs, u, dyn, k[st], jac ? J : nullptr, jac ? Ju : nullptr);
         if (jac) {
             // d xs / dx = I + c dt dk_{prev}/dx,  d xs / du = c dt dk_{prev}/du
             for (int i = 0; i < 6; ++i)
                 for (int j = 0; j < 6; ++j) {
-                    float a = 0.f;
+                    R a = R(0);
                     for (int l = 0; l < 6; ++l) {
-                        float dxs = (l == j ? 1.f : 0.f) + (st ? cst[st] * dt * dkx[l * 6 + j] : 0.f);
+                        R dxs = (l == j ? R(1) : R(0)) + (st ? cst[st] * dt * dkx[l * 6 + j] : R(0));
                         a += J[i * 6 + l] * dxs;
                     }
                     tx[i * 6 + j] = a;
                 }
             for (int i = 0; i < 6; ++i)
                 for (int j = 0; j < 2; ++j) {
-                    float a = Ju[i * 2 + j];
+                    R a = Ju[i * 2 + j];
                     if (st)
                         for (int l = 0; l < 6; ++l) a += J[i * 6 + l] * cst[st] * dt * dku[l * 2 + j];
                     tu[i * 2 + j] = a;
@@ -175,11 +190,11 @@ __device__ inline void quad_rk4(const float* x, const float* u, const float* dyn
         }
     }
     for (int i = 0; i < 6; ++i)
-        phi[i] = x[i] + dt / 6.f * (k[0][i] + 2.f * k[1][i] + 2.f * k[2][i] + k[3][i]);
+        phi[i] = x[i] + dt / R(6) * (k[0][i] + R(2) * k[1][i] + R(2) * k[2][i] + k[3][i]);
     if (jac) {
         for (int i = 0; i < 6; ++i)
-            for (int j = 0; j < 6; ++j) dPx[i * 6 + j] = (i == j ? 1.f : 0.f) + dt / 6.f * accx[i * 6 + j];
-        for (int i = 0; i < 12; ++i) dPu[i] = dt / 6.f * accu[i];
+            for (int j = 0; j < 6; ++j) dPx[i * 6 + j] = (i == j ? R(1) : R(0)) + dt / R(6) * accx[i * 6 + j];
+        for (int i = 0; i < 12; ++i) dPu[i] = dt / R(6) * accu[i];
     }
 }
 

@@ -403,7 +403,7 @@ __device__ inline void rollout(const Ctx& c, const KOpts& o) {
         for (int t = 0; t < c.N; ++t) {
             const float* z = c.zb + t * n;
             if (c.model == MODEL_QUAD) {
-                quad_rk4(z, z + 6, c.dyn, xn, nullptr, nullptr);
+                quad_rk4<float>(z, z + 6, c.dyn, xn, nullptr, nullptr);
             } else if (c.model == MODEL_DI) {
                 const float dt = c.dyn[0];
                 xn[0] = z[0] + dt * z[2] + 0.5f * dt * dt * z[4];
@@ -412,7 +412,7 @@ __device__ inline void rollout(const Ctx& c, const KOpts& o) {
                 xn[3] = z[3] + dt * z[5];
             } else {  // bicycle: explicit Euler predictor + Newton on f_t(z_t, x_{t+1}) = 0
                 float fc[6];
-                bicycle_fc(z, z + 6, c.dyn[1], c.track, c.nt, c.dyn[2], fc, nullptr, nullptr);
+                bicycle_fc<float>(z, z + 6, c.dyn[1], c.track, c.nt, c.dyn[2], fc, nullptr, nullptr);
                 for (int k = 0; k < 6; ++k) xn[k] = z[k] + c.dyn[0] * fc[k];
                 for (int it = 0; it < o.newton_steps; ++it) {
                     for (int k = 0; k < 6; ++k) zn[k] = xn[k];

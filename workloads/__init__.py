@@ -501,14 +501,19 @@ def stable_linear_system(rng, nx, nu, scale=0.1, lam_max=0.99, b_std=1e-2):
 
 
 def linear_rl(B=64, N=40, nx=8, nu=4, u_max=1.0, seed=1006, theta=None, tol=1e-5, max_admm=1000,
-              max_sqp=10) -> ProblemBatch:
+              max_sqp=10, rho_max=1.0) -> ProblemBatch:
     """The linear-system RL problem family: x+ = A x + B u + b (one system drawn
     per seed, see stable_linear_system), x0 ~ N(0, 25 I) per instance, stage
     cost x' Q x + ||u||^2 with Q = diag(theta) (written with the 1/2 of the
     cost convention: Qd = 2 theta, Rd = 2; theta = 1 unless given), the same
     cost at the terminal stage, control box |u|_inf <= u_max on every stage.
     The solver runs to the tolerance tol (early exit at eps_abs = eps_rel =
-    eps_c = tol) with at most max_admm ADMM iterations per QP."""
+    eps_c = tol) with at most max_admm ADMM iterations per QP.  rho_bar is
+    capped at rho_max = 1 (rho_f <= 1e3): with x0 ~ N(0, 25 I) and saturated
+    controls the rho rule asks for rho_bar ~ 10, where S reaches a condition
+    number near 1e5 and an FP32 solve no longer keeps the ADMM iteration
+    stable (an FP64 run with S perturbed by one FP32 rounding already loses
+    three digits)."""
     rng = np.random.default_rng(seed)
     A, Bm, b = stable_linear_system(rng, nx, nu)
     th = np.ones(nx) if theta is None else np.asarray(theta, dtype=np.float64)
@@ -525,7 +530,8 @@ def linear_rl(B=64, N=40, nx=8, nu=4, u_max=1.0, seed=1006, theta=None, tol=1e-5
         a["dyn"][i, :nx * nx] = A.ravel()
         a["dyn"][i, nx * nx:nx * nx + nx * nu] = Bm.ravel()
         a["dyn"][i, nx * nx + nx * nu:] = b
-    opts = Options(max_sqp=max_sqp, max_admm=max_admm, n_ls=1, early_exit=1, eps_abs=tol, eps_rel=tol, eps_c=tol)
+    opts = Options(max_sqp=max_sqp, max_admm=max_admm, n_ls=1, early_exit=1, eps_abs=tol, eps_rel=tol, eps_c=tol,
+                   rho_max=rho_max)
     pb = ProblemBatch(nx, nu, ng, N, np.full(B, N, np.int32), np.full(B, MODEL_LINEAR, np.int32),
                       opts=opts, name=f"linear_rl_B{B}_N{N}_nx{nx}_nu{nu}_umax{u_max:g}", **a)
     pb.extra = dict(A=A, B=Bm, b=b, theta=th, u_max=u_max)
