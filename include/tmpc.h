@@ -67,7 +67,11 @@ enum {
     TMPC_MODEL_LINEAR = 1,            /* layout nx, nu, ng=nu; x+ = A x + B u + b.  dyn = [A, B, b]
                                          (row-major; b is optional: 0 when n_dyn < nx^2 + nx nu + nx) */
     TMPC_MODEL_BICYCLE = 2,           /* nx=6 nu=2 ng=5, implicit midpoint.  dyn = [dt, L, ds, nt] */
-    TMPC_MODEL_QUADROTOR = 3          /* nx=6 nu=2 ng=2, RK4.  dyn = [dt, m, I, arm, g]            */
+    TMPC_MODEL_QUADROTOR = 3,         /* nx=6 nu=2 ng=2, RK4.  dyn = [dt, m, I, arm, g]            */
+    TMPC_MODEL_BICYCLE_TRAP = 4,      /* as 2 with the trapezoidal constraint of Remark A1         */
+    TMPC_MODEL_BICYCLE_NEWTON = 5     /* as 2 with the explicit map x+ = Phi(x, u) that 3 Newton
+                                         steps on the midpoint rule define, Jacobians by the
+                                         implicit function theorem (generic kernel only)          */
 };
 
 /* number of floats per instance in tmpc_solution.stats */

@@ -5,8 +5,11 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
 Dynamics constraints follow Remark A1 of the paper: an explicit model is
 f_t = Phi(x_t, u_t) - x_{t+1}; the racing model uses an implicit midpoint
-rule f_t = x_t + dt f_c((x_t + x_{t+1})/2, u_t) - x_{t+1} (the paper shows the
-trapezoidal variant; both keep C block-bidiagonal, Remark 2).  Jacobians are
+rule f_t = x_t + dt f_c((x_t + x_{t+1})/2, u_t) - x_{t+1}, or the paper's
+trapezoidal rule f_t = x_t + dt/2 (f_c(z_t) + f_c(z_{t+1})) - x_{t+1} (both keep
+C block-bidiagonal, Remark 2), or the explicit map x_{t+1} = Phi(x_t, u_t)
+that 3 Newton steps on the midpoint rule define (Jacobians by the implicit
+function theorem).  Jacobians are
 returned as the blocks A^-_t = d f_t / d(x_t, u_t) and
 A^+_t = d f_t / d(x_{t+1}, u_{t+1}) of Appendix B ("Equality constraints").
 All functions act on one instance and are vectorised over stages.
@@ -17,7 +20,10 @@ import math
 
 import numpy as np
 
-from workloads import MODEL_BICYCLE, MODEL_DI, MODEL_LINEAR, MODEL_QUAD
+from workloads import (BICYCLES, MODEL_BICYCLE, MODEL_BICYCLE_NEWTON, MODEL_BICYCLE_TRAP, MODEL_DI,
+                       MODEL_LINEAR, MODEL_QUAD)
+
+NEWTON_MAP_STEPS = 3   # Newton steps that define the explicit map of MODEL_BICYCLE_NEWTON
 
 
 # ----------------------------------------------------------------------------
@@ -187,7 +193,50 @@ def dynamics(inst, z):
         Am[:, :, nx:] = dt * Ju
         Ap[:, :, :nx] = -I + 0.5 * dt * Jx
         return f, Am, Ap
+    if model == MODEL_BICYCLE_TRAP:
+        # Remark A1: f_t = x_t + dt/2 (f_c(x_t, u_t) + f_c(x_{t+1}, u_{t+1})) - x_{t+1}
+        dt = inst["dyn"][0]
+        fa, Jxa, Jua = bicycle_fc(x[:-1], u[:-1], inst["dyn"], inst["track"])
+        fb, Jxb, Jub = bicycle_fc(x[1:], u[1:], inst["dyn"], inst["track"])
+        f = x[:-1] + 0.5 * dt * (fa + fb) - x[1:]
+        I = np.eye(nx)
+        Am[:, :, :nx] = I + 0.5 * dt * Jxa
+        Am[:, :, nx:] = 0.5 * dt * Jua
+        Ap[:, :, :nx] = -I + 0.5 * dt * Jxb
+        Ap[:, :, nx:] = 0.5 * dt * Jub
+        return f, Am, Ap
+    if model == MODEL_BICYCLE_NEWTON:
+        # explicit map Phi(x_t, u_t) - x_{t+1} (Remark A1, explicit form)
+        phi, dpx, dpu = newton_map(x[:-1], u[:-1], inst["dyn"], inst["track"])
+        f = phi - x[1:]
+        Am[:, :, :nx] = dpx
+        Am[:, :, nx:] = dpu
+        Ap[:, :, :nx] = -np.eye(nx)
+        return f, Am, Ap
     raise ValueError(f"unknown model {model}")
+
+
+def newton_map(x, u, dyn, tab, steps=NEWTON_MAP_STEPS):
+    """x+ = Phi(x, u): `steps` Newton steps on the implicit midpoint residual
+    r(x+) = x + dt f_c((x + x+)/2, u) - x+ from the explicit Euler step, and its
+    Jacobians by the implicit function theorem at the returned x+:
+    dPhi/dx = -(dr/dx+)^-1 dr/dx, dPhi/du = -(dr/dx+)^-1 dr/du, with
+    dr/dx+ = -I + dt/2 J_x(mid), dr/dx = I + dt/2 J_x(mid), dr/du = dt J_u(mid).
+    Vectorised over the first axis of x, u."""
+    dt = dyn[0]
+    T = x.shape[0]
+    I = np.broadcast_to(np.eye(6), (T, 6, 6))
+    fc, _, _ = bicycle_fc(x, u, dyn, tab)
+    xp = x + dt * fc
+    for _ in range(steps):
+        fm, Jx, _ = bicycle_fc(0.5 * (x + xp), u, dyn, tab)
+        r = x + dt * fm - xp
+        xp = xp - np.linalg.solve(-I + 0.5 * dt * Jx, r[..., None])[..., 0]
+    _, Jx, Ju = bicycle_fc(0.5 * (x + xp), u, dyn, tab)
+    Mp = -I + 0.5 * dt * Jx
+    dpx = -np.linalg.solve(Mp, I + 0.5 * dt * Jx)
+    dpu = -np.linalg.solve(Mp, dt * Ju)
+    return xp, dpx, dpu
 
 
 def rollout_guess(inst, x, u):
@@ -202,9 +251,11 @@ def rollout_guess(inst, x, u):
     if model == MODEL_LINEAR:
         A, B, b = linear_matrices(inst)
         return A @ x + B @ u + b
-    if model == MODEL_BICYCLE:
+    if model in (MODEL_BICYCLE, MODEL_BICYCLE_TRAP):
         fc, _, _ = bicycle_fc(x[None], u[None], inst["dyn"], inst["track"])
         return x + inst["dyn"][0] * fc[0]
+    if model == MODEL_BICYCLE_NEWTON:
+        return newton_map(x[None], u[None], inst["dyn"], inst["track"])[0][0]
     raise ValueError(model)
 
 
@@ -232,7 +283,7 @@ def constraints(inst, z):
         g = z[:, 6:8].copy()
         G[:, 0, 6] = G[:, 1, 7] = 1.0
         return g, G
-    if model == MODEL_BICYCLE:
+    if model in BICYCLES:
         # rows: accel, steer rate, speed, steering angle, lateral error e(px, py, s)
         tab, dsk = inst["track"], inst["dyn"][2]
         px, py, s = z[:, 0], z[:, 1], z[:, 5]

@@ -397,12 +397,12 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
     TMPC_CUDA(cudaMemcpy(Mh.data(), p->model, sizeof(int) * d->batch, cudaMemcpyDeviceToHost));
     for (int i = 0; i < d->batch; ++i) {
         if (Nh[i] < 1 || Nh[i] > d->N_max) return TMPC_ERR_INVALID_ARG;
-        if (Mh[i] < 0 || Mh[i] > 3) return TMPC_ERR_INVALID_ARG;
+        if (Mh[i] < 0 || Mh[i] >= MODEL_COUNT) return TMPC_ERR_INVALID_ARG;
         const ModelDims md = model_dims(Mh[i], d->nx, d->nu, d->ng);
         if (md.nx > d->nx || md.nu > d->nu || md.ng > d->ng) return TMPC_ERR_INVALID_ARG;
         if (Mh[i] == MODEL_LINEAR && (d->n_dyn < d->nx * d->nx + d->nx * d->nu || d->ng > d->nu))
             return TMPC_ERR_INVALID_ARG;
-        if (Mh[i] == MODEL_BICYCLE && (d->n_track < 1 || d->n_dyn < 4)) return TMPC_ERR_INVALID_ARG;
+        if (is_bicycle(Mh[i]) && (d->n_track < 1 || d->n_dyn < 4)) return TMPC_ERR_INVALID_ARG;
         if (Mh[i] == MODEL_QUAD && d->n_dyn < 5) return TMPC_ERR_INVALID_ARG;
     }
 
@@ -935,12 +935,12 @@ __global__ void static_prologue(KLayout L, const int* N, const int* model, int* 
     const long long T = L.Nmax + 1;
     for (int i = threadIdx.x; i < L.B; i += blockDim.x) {
         const int Ni = N[i], m = model[i];
-        bool ok = Ni >= 1 && Ni <= L.Nmax && m >= 0 && m <= 3;
+        bool ok = Ni >= 1 && Ni <= L.Nmax && m >= 0 && m < MODEL_COUNT;
         if (ok) {
             const ModelDims md = model_dims(m, L.nx, L.nu, L.ng);
             ok = md.nx <= L.nx && md.nu <= L.nu && md.ng <= L.ng;
             if (m == MODEL_LINEAR) ok = ok && L.n_dyn >= L.nx * L.nx + L.nx * L.nu && L.ng <= L.nu;
-            if (m == MODEL_BICYCLE) ok = ok && L.n_track >= 1 && L.n_dyn >= 4;
+            if (is_bicycle(m)) ok = ok && L.n_track >= 1 && L.n_dyn >= 4;
             if (m == MODEL_QUAD) ok = ok && L.n_dyn >= 5;
         }
         if (ok) {

@@ -80,7 +80,7 @@ __device__ inline Ctx make_ctx(const KLayout& L, const KParams& p, float* ws, co
     c.track = p.track ? p.track + (long long)i * (L.n_track + 1) * 4 : nullptr;
     c.bv = (c.model == MODEL_LINEAR && L.n_dyn >= L.nx * L.nx + L.nx * L.nu + L.nx)
                ? c.dyn + L.nx * L.nx + L.nx * L.nu : nullptr;
-    if (c.model == MODEL_BICYCLE) {  // table intervals, clamped to the layout's table size
+    if (is_bicycle(c.model)) {  // table intervals, clamped to the layout's table size
         const float ntf = c.dyn[3];
         int nt = (ntf == ntf) ? (int)fminf(fmaxf(ntf + 0.5f, 1.f), (float)L.n_track) : 1;
         c.nt = nt < 1 ? 1 : nt;

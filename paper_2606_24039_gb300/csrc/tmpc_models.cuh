@@ -13,7 +13,15 @@
 
 namespace tmpc {
 
-enum { MODEL_DI = 0, MODEL_LINEAR = 1, MODEL_BICYCLE = 2, MODEL_QUAD = 3 };
+enum { MODEL_DI = 0, MODEL_LINEAR = 1, MODEL_BICYCLE = 2, MODEL_QUAD = 3, MODEL_BICYCLE_TRAP = 4,
+       MODEL_BICYCLE_NEWTON = 5, MODEL_COUNT = 6 };
+
+// the kinematic bicycle under its three time discretisations (Remark A1): implicit
+// midpoint, trapezoidal, and the explicit map defined by Newton steps on the midpoint rule
+__host__ __device__ inline bool is_bicycle(int m) {
+    return m == MODEL_BICYCLE || m == MODEL_BICYCLE_TRAP || m == MODEL_BICYCLE_NEWTON;
+}
+constexpr int kNewtonMapSteps = 3;   // Newton steps that define the explicit map of MODEL_BICYCLE_NEWTON
 
 struct ModelDims {
     int nx, nu, ng;
@@ -22,7 +30,9 @@ struct ModelDims {
 __host__ __device__ inline ModelDims model_dims(int model, int lnx, int lnu, int lng) {
     switch (model) {
         case MODEL_DI: return {4, 2, 4};
-        case MODEL_BICYCLE: return {6, 2, 5};
+        case MODEL_BICYCLE:
+        case MODEL_BICYCLE_TRAP:
+        case MODEL_BICYCLE_NEWTON: return {6, 2, 5};
         case MODEL_QUAD: return {6, 2, 2};
         default: return {lnx, lnu, lng};
     }
@@ -30,8 +40,8 @@ __host__ __device__ inline ModelDims model_dims(int model, int lnx, int lnu, int
 
 // Am / Ap / G blocks identical for every stage -> stored once (stage stride 0)
 __host__ __device__ inline bool model_const_Am(int m) { return m == MODEL_DI || m == MODEL_LINEAR; }
-__host__ __device__ inline bool model_const_Ap(int m) { return m != MODEL_BICYCLE; }
-__host__ __device__ inline bool model_const_G(int m) { return m != MODEL_BICYCLE; }
+__host__ __device__ inline bool model_const_Ap(int m) { return m != MODEL_BICYCLE && m != MODEL_BICYCLE_TRAP; }
+__host__ __device__ inline bool model_const_G(int m) { return !is_bicycle(m); }
 __host__ __device__ inline bool model_linear_dyn(int m) { return m == MODEL_DI || m == MODEL_LINEAR; }
 
 // ---------------------------------------------------------------------------

@@ -161,6 +161,31 @@ __device__ __forceinline__ double cta_sum_d(double v, double* redd) {
 
 __device__ __forceinline__ float fin(float v) { return (v == v) ? fabsf(v) : kInf; }
 
+// small dense solve (Gaussian elimination, partial pivoting), M is m x m row-major, in place
+__device__ inline void small_solve(float* M, float* b, int m) {
+    for (int k = 0; k < m; ++k) {
+        int p = k;
+        float best = fabsf(M[k * m + k]);
+        for (int i = k + 1; i < m; ++i)
+            if (fabsf(M[i * m + k]) > best) { best = fabsf(M[i * m + k]); p = i; }
+        if (p != k) {
+            for (int j = 0; j < m; ++j) { float tmp = M[k * m + j]; M[k * m + j] = M[p * m + j]; M[p * m + j] = tmp; }
+            float tmp = b[k]; b[k] = b[p]; b[p] = tmp;
+        }
+        const float d = M[k * m + k];
+        for (int i = k + 1; i < m; ++i) {
+            const float l = M[i * m + k] / d;
+            for (int j = k; j < m; ++j) M[i * m + j] -= l * M[k * m + j];
+            b[i] -= l * b[k];
+        }
+    }
+    for (int i = m - 1; i >= 0; --i) {
+        float a = b[i];
+        for (int j = i + 1; j < m; ++j) a -= M[i * m + j] * b[j];
+        b[i] = a / M[i * m + i];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // model evaluation per stage (one thread)
 // ---------------------------------------------------------------------------
@@ -196,6 +221,66 @@ __device__ inline void stage_dyn(const Ctx& c, int t, const float* zt, const flo
                 for (int k = 0; k < 6; ++k) {
                     for (int j = 0; j < 6; ++j) Am[k * n + j] = dPx[k * 6 + j];
                     for (int j = 0; j < 2; ++j) Am[k * n + 6 + j] = dPu[k * 2 + j];
+                }
+            }
+            break;
+        }
+        case MODEL_BICYCLE_TRAP: {
+            // f_t = x_t + dt/2 (f_c(z_t) + f_c(z_{t+1})) - x_{t+1}  (Remark A1)
+            const float dt = c.dyn[0];
+            float fa[6], fb[6], Jxa[36], Jua[12], Jxb[36], Jub[12];
+            const bool jac = Am != nullptr;
+            bicycle_fc<float>(zt, zt + 6, c.dyn[1], c.track, c.nt, c.dyn[2], fa, jac ? Jxa : nullptr, jac ? Jua : nullptr);
+            bicycle_fc<float>(zn, zn + 6, c.dyn[1], c.track, c.nt, c.dyn[2], fb, jac ? Jxb : nullptr, jac ? Jub : nullptr);
+            for (int k = 0; k < 6; ++k) f[k] = zt[k] + 0.5f * dt * (fa[k] + fb[k]) - zn[k];
+            if (jac) {
+                for (int k = 0; k < 6; ++k) {
+                    for (int j = 0; j < 6; ++j) {
+                        Am[k * n + j] = (k == j ? 1.f : 0.f) + 0.5f * dt * Jxa[k * 6 + j];
+                        Ap[k * n + j] = (k == j ? -1.f : 0.f) + 0.5f * dt * Jxb[k * 6 + j];
+                    }
+                    for (int j = 0; j < 2; ++j) {
+                        Am[k * n + 6 + j] = 0.5f * dt * Jua[k * 2 + j];
+                        Ap[k * n + 6 + j] = 0.5f * dt * Jub[k * 2 + j];
+                    }
+                }
+            }
+            break;
+        }
+        case MODEL_BICYCLE_NEWTON: {
+            // x_{t+1} = Phi(x_t, u_t): kNewtonMapSteps Newton steps on the midpoint residual
+            // r(p) = x + dt f_c((x + p)/2, u) - p from the explicit Euler step; Jacobians by
+            // the implicit function theorem at the returned p (A^+ = [-I 0], constant)
+            const float dt = c.dyn[0];
+            float p[6], mid[6], fc[6], Jx[36], Ju[12], Mp[36], r[6];
+            bicycle_fc<float>(zt, zt + 6, c.dyn[1], c.track, c.nt, c.dyn[2], fc, nullptr, nullptr);
+            for (int k = 0; k < 6; ++k) p[k] = zt[k] + dt * fc[k];
+            for (int it = 0; it < kNewtonMapSteps; ++it) {
+                for (int k = 0; k < 6; ++k) mid[k] = 0.5f * (zt[k] + p[k]);
+                bicycle_fc<float>(mid, zt + 6, c.dyn[1], c.track, c.nt, c.dyn[2], fc, Jx, nullptr);
+                for (int k = 0; k < 6; ++k) {
+                    r[k] = zt[k] + dt * fc[k] - p[k];
+                    for (int j = 0; j < 6; ++j) Mp[k * 6 + j] = (k == j ? -1.f : 0.f) + 0.5f * dt * Jx[k * 6 + j];
+                }
+                small_solve(Mp, r, 6);
+                for (int k = 0; k < 6; ++k) p[k] -= r[k];
+            }
+            for (int k = 0; k < 6; ++k) f[k] = p[k] - zn[k];
+            if (Ap)
+                for (int k = 0; k < 6; ++k)
+                    for (int j = 0; j < n; ++j) Ap[k * n + j] = (k == j) ? -1.f : 0.f;
+            if (Am) {
+                for (int k = 0; k < 6; ++k) mid[k] = 0.5f * (zt[k] + p[k]);
+                bicycle_fc<float>(mid, zt + 6, c.dyn[1], c.track, c.nt, c.dyn[2], fc, Jx, Ju);
+                // column j of dPhi/dz = -(dr/dp)^-1 (dr/dz)_j, dr/dx = I + dt/2 J_x, dr/du = dt J_u
+                for (int j = 0; j < 8; ++j) {
+                    float col[6], M[36];
+                    for (int k = 0; k < 6; ++k) {
+                        col[k] = -(j < 6 ? (k == j ? 1.f : 0.f) + 0.5f * dt * Jx[k * 6 + j] : dt * Ju[k * 2 + j - 6]);
+                        for (int l = 0; l < 6; ++l) M[k * 6 + l] = (k == l ? -1.f : 0.f) + 0.5f * dt * Jx[k * 6 + l];
+                    }
+                    small_solve(M, col, 6);
+                    for (int k = 0; k < 6; ++k) Am[k * n + j] = col[k];
                 }
             }
             break;
@@ -246,7 +331,9 @@ __device__ inline void stage_con(const Ctx& c, const float* z, float* g, float* 
             g[0] = z[6]; g[1] = z[7];
             if (G) { G[0 * n + 6] = 1.f; G[1 * n + 7] = 1.f; }
             break;
-        case MODEL_BICYCLE: {  // accel, steer rate, speed, steering angle, lateral error
+        case MODEL_BICYCLE:
+        case MODEL_BICYCLE_TRAP:
+        case MODEL_BICYCLE_NEWTON: {  // accel, steer rate, speed, steering angle, lateral error
             TrackPt tp = track_eval(c.track, c.nt, c.dyn[2], z[5]);
             float sp, cp;
             sincosf(tp.psic, &sp, &cp);
@@ -264,30 +351,6 @@ __device__ inline void stage_con(const Ctx& c, const float* z, float* g, float* 
     }
 }
 
-// small dense solve (Gaussian elimination, partial pivoting), M is m x m row-major, in place
-__device__ inline void small_solve(float* M, float* b, int m) {
-    for (int k = 0; k < m; ++k) {
-        int p = k;
-        float best = fabsf(M[k * m + k]);
-        for (int i = k + 1; i < m; ++i)
-            if (fabsf(M[i * m + k]) > best) { best = fabsf(M[i * m + k]); p = i; }
-        if (p != k) {
-            for (int j = 0; j < m; ++j) { float tmp = M[k * m + j]; M[k * m + j] = M[p * m + j]; M[p * m + j] = tmp; }
-            float tmp = b[k]; b[k] = b[p]; b[p] = tmp;
-        }
-        const float d = M[k * m + k];
-        for (int i = k + 1; i < m; ++i) {
-            const float l = M[i * m + k] / d;
-            for (int j = k; j < m; ++j) M[i * m + j] -= l * M[k * m + j];
-            b[i] -= l * b[k];
-        }
-    }
-    for (int i = m - 1; i >= 0; --i) {
-        float a = b[i];
-        for (int j = i + 1; j < m; ++j) a -= M[i * m + j] * b[j];
-        b[i] = a / M[i * m + i];
-    }
-}
 
 // y = P x  (cost Hessian, block-tridiagonal with diagonal blocks), stage t, entry j
 __device__ __forceinline__ float Px_entry(const Ctx& c, const float* x, int t, int j) {
@@ -344,7 +407,7 @@ __device__ __forceinline__ float Cx_entry(const Ctx& c, const float* x, int r, i
 // dense row).  g_col(c, r): the column row r selects; g_row(c, j): the row
 // that selects column j, -1 if none.  The hot loops use them instead of
 // multiplying through the zeros of G (same values: the other terms are 0).
-__device__ __forceinline__ bool g_is_selector(const Ctx& c) { return c.model != MODEL_BICYCLE; }
+__device__ __forceinline__ bool g_is_selector(const Ctx& c) { return !is_bicycle(c.model); }
 __device__ __forceinline__ int g_col(const Ctx& c, int r) {
     switch (c.model) {
         case MODEL_LINEAR: return c.nx + r;

@@ -522,3 +522,57 @@ def test_backward_racing_on_oracle_point(solver, refine):
             rel = _grad_rel(g[k][i].cpu().numpy().reshape(-1), gr[k].reshape(-1), scale)
             assert rel < GRAD_TOL, (i, k, rel)
     assert compared >= 2
+
+
+@pytest.mark.parametrize("integrator", ["trapezoidal", "newton_map"])
+def test_racing_other_time_discretisations(integrator):
+    """The bicycle under the trapezoidal constraint and under the explicit map
+    that 3 Newton steps on the midpoint rule define (IFT Jacobians), on the
+    generic kernel: first the rollout (no SQP step), then 3 SQP x 50 ADMM."""
+    from paper_2606_24039_gb300 import Solver
+    pb = w.racing(B=6, N=30, max_sqp=0, max_admm=1, integrator=integrator)
+    pb.z_init = None
+    s = Solver.from_batch(pb, device="cuda")
+    sol = s.tmpc_solve(s.x0)
+    torch.cuda.synchronize()
+    z = sol["z"].cpu().numpy()
+    for i in range(pb.B):
+        assert _rel(z[i], osqp.rollout(pb.instance(i), newton_steps=3)) <= REL_TOL, i
+    pb = w.racing(B=6, N=30, max_sqp=3, max_admm=50, integrator=integrator)
+    s, sol, _ = _run(pb)
+    _compare(pb, sol, range(6), sensitivity=True)
+    assert np.all(np.isin(sol["status"], (0, 1)))
+
+
+@pytest.mark.parametrize("integrator", ["trapezoidal", "newton_map"])
+def test_backward_other_time_discretisations_on_oracle_point(integrator):
+    """Backward (generic kernel) of the trapezoidal and Newton-map bicycles at
+    the oracle's SQP point, per parameter."""
+    pb = w.racing(B=3, N=20, max_sqp=3, max_admm=200, integrator=integrator)
+    from paper_2606_24039_gb300 import Solver
+    s = Solver.from_batch(pb, device="cuda")
+    refs = [osqp.solve(pb.instance(i), pb.opts) for i in range(pb.B)]
+    sol = {}
+    for k, kk in (("z", "z"), ("xi", "xi"), ("y_eq", "yf"), ("y_ineq", "yg")):
+        sol[k] = torch.tensor(np.stack([r[kk] for r in refs]), dtype=torch.float32, device="cuda")
+    sol["status"] = torch.zeros(pb.B, dtype=torch.int32, device="cuda")
+    rng = np.random.default_rng(13)
+    dLdz = rng.normal(size=(pb.B, pb.N_max + 1, pb.n))
+    g = s.tmpc_backward(s.x0, sol, torch.tensor(dLdz, dtype=torch.float32, device="cuda"))
+    torch.cuda.synchronize()
+    keys = ("x0", "Qd", "Rd", "Wd", "ref", "lin", "lo", "hi", "gamma2", "gamma1")
+    compared = 0
+    for i in range(pb.B):
+        inst = {k: (v.astype(np.float32).astype(np.float64) if isinstance(v, np.ndarray) and v.dtype == np.float64
+                    else v) for k, v in pb.instance(i).items()}
+        point = {k: np.asarray(sol[kk][i].cpu().numpy(), dtype=np.float64) for k, kk in
+                 (("z", "z"), ("xi", "xi"), ("yf", "y_eq"), ("yg", "y_ineq"))}
+        gr, info = obwd.backward(inst, point, dLdz[i], eps_g=pb.opts.eps_g)
+        if info["singular"]:
+            continue
+        compared += 1
+        scale = max(np.linalg.norm(gr[k]) for k in keys)
+        for k in keys:
+            rel = _grad_rel(g[k][i].cpu().numpy().reshape(-1), gr[k].reshape(-1), scale)
+            assert rel < GRAD_TOL, (i, k, rel)
+    assert compared >= 2

@@ -21,8 +21,9 @@ def _instances():
     out = []
     p = w.double_integrator(N=4)
     out.append(p.instance(0))
-    p = w.racing(B=1, N=4, track_length=100.0)
-    out.append(p.instance(0))
+    for integ in ("midpoint", "trapezoidal", "newton_map"):
+        p = w.racing(B=1, N=4, track_length=100.0, integrator=integ)
+        out.append(p.instance(0))
     p = w.tracking(B=1, nx=5, nu=3, N=4)
     out.append(p.instance(0))
     p = w.uneven(B=8, N_lo=4, N_hi=6, seed=3)
@@ -38,7 +39,7 @@ def test_dynamics_and_constraint_jacobians(inst):
     rng = np.random.default_rng(0)
     nx, nu, N = inst["nx"], inst["nu"], inst["N"]
     z = rng.normal(0, 1, (N + 1, nx + nu))
-    if inst["model"] == w.MODEL_BICYCLE:
+    if inst["model"] in w.BICYCLES:
         z[:, 3] = 10 + rng.uniform(0, 5, N + 1)      # speed
         z[:, 4] *= 0.2                                # steering angle
         z[:, 5] = 3.0 + np.arange(N + 1) * 0.7 + 0.13  # progress, off the knots
@@ -50,6 +51,8 @@ def test_dynamics_and_constraint_jacobians(inst):
             zz[t + 1] = v[nx + nu:]
             return models.dynamics(inst, zz)[0][t]
         J = _fd_jac(ft, np.concatenate([z[t], z[t + 1]]))
+        # (the Newton map's Jacobian comes from the implicit function theorem at the
+        # 3-step Newton point; it matches the map's own derivative to the Newton residual)
         assert np.allclose(J[:, :nx + nu], Am[t], atol=1e-6, rtol=1e-6)
         assert np.allclose(J[:, nx + nu:], Ap[t], atol=1e-6, rtol=1e-6)
     g, G = models.constraints(inst, z)
@@ -102,3 +105,41 @@ def test_newton_rollout_satisfies_dynamics():
         z = sqp.rollout(inst, newton_steps=3)
         f, _, _ = models.dynamics(inst, z)
         assert np.max(np.abs(f)) < 1e-9
+
+
+def test_newton_map_is_the_midpoint_solution():
+    """The explicit map of the Newton-map variant: 3 Newton steps from the explicit
+    Euler step solve the implicit midpoint equation to rounding (quadratic
+    convergence on a smooth motion), so it equals a 30-step Newton solve, and its
+    IFT Jacobian equals the central-difference derivative of that solution."""
+    p = w.racing(B=1, N=4, track_length=100.0, integrator="newton_map")
+    inst = p.instance(0)
+    rng = np.random.default_rng(2)
+    x = np.array([[3.0, 1.0, 0.2, 11.0, 0.05, 4.1]])
+    u = np.array([[0.8, -0.3]])
+    phi, dpx, dpu = models.newton_map(x, u, inst["dyn"], inst["track"])
+    ref, _, _ = models.newton_map(x, u, inst["dyn"], inst["track"], steps=30)
+    assert np.max(np.abs(phi - ref)) < 1e-12
+    dt = inst["dyn"][0]
+    fm, _, _ = models.bicycle_fc(0.5 * (x + phi), u, inst["dyn"], inst["track"])
+    assert np.max(np.abs(x + dt * fm - phi)) < 1e-12          # midpoint residual
+    J = _fd_jac(lambda v: models.newton_map(v[None, :6], v[None, 6:], inst["dyn"], inst["track"], steps=30)[0][0],
+                np.concatenate([x[0], u[0]]))
+    assert np.allclose(J[:, :6], dpx[0], atol=1e-7) and np.allclose(J[:, 6:], dpu[0], atol=1e-7)
+
+
+def test_trapezoidal_rule_is_exact_for_uniform_motion():
+    """x_{t+1} = x_t + dt/2 (f_c(z_t) + f_c(z_{t+1})) holds exactly for a straight
+    line at constant speed on a straight track aligned with it (f_c is constant
+    along that motion)."""
+    s = np.arange(0.0, 200.25, w.TRACK_DS)
+    tab = np.stack([s * np.cos(0.3), s * np.sin(0.3), np.full_like(s, 0.3), np.zeros_like(s)], 1)
+    dyn = np.array([0.05, 2.7, w.TRACK_DS, float(len(s) - 1)])
+    v, dt = 8.0, 0.05
+    z = np.zeros((5, 8))
+    for t in range(5):
+        q = 5.0 + v * dt * t
+        z[t, :6] = [q * np.cos(0.3), q * np.sin(0.3), 0.3, v, 0.0, q]
+    inst = dict(model=w.MODEL_BICYCLE_TRAP, nx=6, nu=2, dyn=dyn, track=tab)
+    f, _, _ = models.dynamics(inst, z)
+    assert np.max(np.abs(f)) < 1e-12

@@ -50,12 +50,19 @@ MODEL_DI = 0        # 2-D double integrator, ZOH.          dyn = [dt]
 MODEL_LINEAR = 1    # x+ = A x + B u + b (explicit).       dyn = [A (nx*nx), B (nx*nu), b (nx, optional)] row-major
 MODEL_BICYCLE = 2   # kinematic bicycle, implicit midpoint. dyn = [dt, wheelbase, ds, n_track]
 MODEL_QUAD = 3      # planar quadrotor, explicit RK4.       dyn = [dt, mass, inertia, arm, gravity]
+MODEL_BICYCLE_TRAP = 4    # kinematic bicycle, trapezoidal rule (implicit).        dyn as MODEL_BICYCLE
+MODEL_BICYCLE_NEWTON = 5  # kinematic bicycle, explicit map x+ = Phi(x, u) defined by 3 Newton steps
+                          # on the implicit midpoint rule, Jacobians by the implicit function theorem
 
 MODEL_NAMES = {MODEL_DI: "double_integrator", MODEL_LINEAR: "linear",
-               MODEL_BICYCLE: "bicycle", MODEL_QUAD: "planar_quadrotor"}
+               MODEL_BICYCLE: "bicycle", MODEL_QUAD: "planar_quadrotor",
+               MODEL_BICYCLE_TRAP: "bicycle_trapezoidal", MODEL_BICYCLE_NEWTON: "bicycle_newton_map"}
+BICYCLES = (MODEL_BICYCLE, MODEL_BICYCLE_TRAP, MODEL_BICYCLE_NEWTON)
+INTEGRATORS = {"midpoint": MODEL_BICYCLE, "trapezoidal": MODEL_BICYCLE_TRAP, "newton_map": MODEL_BICYCLE_NEWTON}
 
 # fixed (nx, nu, ng) of the nonlinear / fixed-size models
-MODEL_DIMS = {MODEL_DI: (4, 2, 4), MODEL_BICYCLE: (6, 2, 5), MODEL_QUAD: (6, 2, 2)}
+MODEL_DIMS = {MODEL_DI: (4, 2, 4), MODEL_BICYCLE: (6, 2, 5), MODEL_QUAD: (6, 2, 2),
+              MODEL_BICYCLE_TRAP: (6, 2, 5), MODEL_BICYCLE_NEWTON: (6, 2, 5)}
 
 INF = np.inf
 
@@ -146,7 +153,7 @@ class ProblemBatch:
         ref = self.ref[i, :T, :nx + nu].copy()
         lin = self.lin[i, :T, :nx + nu].copy()
         tr = None
-        if self.track is not None and int(self.model[i]) == MODEL_BICYCLE:
+        if self.track is not None and int(self.model[i]) in BICYCLES:
             nt = int(round(self.dyn[i, 3]))
             tr = self.track[i, :nt + 1].copy()
         z0 = None if self.z_init is None else self.z_init[i, :T, :nx + nu].copy()
@@ -360,12 +367,16 @@ def double_integrator(B=1, N=20, seed=1001, max_admm=200) -> ProblemBatch:
                         opts=opts, name=f"double_integrator_B{B}_N{N}", **a)
 
 
-def racing(B=1024, N=50, seed=1002, max_sqp=10, max_admm=50, track_length=400.0) -> ProblemBatch:
+def racing(B=1024, N=50, seed=1002, max_sqp=10, max_admm=50, track_length=400.0,
+           integrator="midpoint") -> ProblemBatch:
     """Kinematic-bicycle racing (nx=6: x, y, psi, v, delta, s; nu=2: accel,
     steer-rate), implicit midpoint dt=0.05, N=50, random curvature-spline
     centrelines (curvature knots every 10 m in U[-0.2, 0.2]), box bounds on the
     controls, speed and steering angle, the lateral track error softened by L1+L2 slacks,
-    control-rate cost and a min-time (progress) terminal cost."""
+    control-rate cost and a min-time (progress) terminal cost.  integrator:
+    "midpoint" (the implicit midpoint constraint), "trapezoidal" (the trapezoidal
+    constraint) or "newton_map" (the explicit map defined by 3 Newton steps on
+    the midpoint rule)."""
     nx, nu, ng = 6, 2, 5
     nt = int(round(track_length / TRACK_DS))
     a = _empty(B, nx, nu, ng, N, 4, nt)
@@ -375,8 +386,9 @@ def racing(B=1024, N=50, seed=1002, max_sqp=10, max_admm=50, track_length=400.0)
         tab = open_spline_track(r, length=track_length)
         _fill_bicycle(r, a, i, N, tab)
     opts = Options(max_sqp=max_sqp, max_admm=max_admm, n_ls=8)
-    return ProblemBatch(nx, nu, ng, N, np.full(B, N, np.int32), np.full(B, MODEL_BICYCLE, np.int32),
-                        opts=opts, name=f"racing_B{B}_N{N}", **a)
+    return ProblemBatch(nx, nu, ng, N, np.full(B, N, np.int32), np.full(B, INTEGRATORS[integrator], np.int32),
+                        opts=opts, name=f"racing_B{B}_N{N}" + ("" if integrator == "midpoint" else "_" + integrator),
+                        **a)
 
 
 def mlp_init(rng, sizes=(16, 64, 64, 68)):
