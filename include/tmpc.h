@@ -139,6 +139,11 @@ typedef struct {
      * refinement preconditioned by the forward's FP32 factorisation (bwd_rho,
      * bwd_sigma, bwd_iters).  The generic kernel always uses the refinement. */
     int32_t bwd_refine;
+    /* 1: the direct backward uses the exact Lagrangian Hessian H = Hessian of
+     * l + y_f' f + y_A' g_A (App. E) at the solution, the constraint curvature by FP64
+     * central differences of the analytic Jacobians; 0: the cost Hessian (the paper's
+     * Hessian approximation; exact for linear dynamics).  Needs bwd_refine = 0. */
+    int32_t exact_hessian;
 } tmpc_options;
 
 /* Problem parameters theta (the OCP of Appendix A with the cost of Eq. (cost)).

@@ -47,6 +47,7 @@ KOpts to_kopts(const tmpc_options& o) {
     k.wait_polls = o.wait_polls;
     k.force_timeout = o.force_wait_timeout;
     k.bwd_refine = o.bwd_refine;
+    k.exact_hessian = o.exact_hessian;
     if (k.k_rho_iter < 1) k.k_rho_iter = 1 << 30;
     return k;
 }
@@ -324,11 +325,15 @@ tmpc_status ensure_buffers(tmpc_handle* h) {
         e = cudaMalloc(&h->gflags, sizeof(int) * 4 * (size_t)B);
         if (e != cudaSuccess) { set_err("cudaMalloc(team flags)", e); return TMPC_ERR_OOM; }
     }
+    // FP64 workspace of the direct backward: the small models' kernels and, where the
+    // layout's interleaved KKT block fits, the generic kernel (every instance's slot)
     long long tmax = 0;
     for (int g = 0; g < h->n_groups; ++g)
         if (h->groups[g].model >= 0) tmax = std::max(tmax, (long long)h->groups[g].Tmax);
-    const long long dneed = fast::direct_ws_doubles((int)tmax);
-    if (tmax > 0 && dneed > h->dstride) {
+    long long dneed = tmax > 0 ? fast::direct_ws_doubles((int)tmax) : 0;
+    const int mbg = gen_direct_mb(h->L.nx, h->L.n, h->L.ng);
+    if (mbg <= kGenDirectMB) dneed = std::max(dneed, (long long)(h->L.Nmax + 1) * gen_direct_stage(mbg));
+    if (dneed > 0 && dneed > h->dstride) {
         if (h->dws) cudaFree(h->dws);
         h->dws = nullptr;
         h->dstride = 0;
@@ -777,7 +782,8 @@ tmpc_status tmpc_backward(tmpc_handle* h, const float* x0, const tmpc_solution* 
         const bool t = timing_ok(s);
         if (t) TMPC_CUDA(cudaEventRecord(h->tev[4][2], s));
         backward_kernel<<<std::min(h->grid_bwd, h->bwd_generic), h->threads, h->smem, s>>>(
-            h->L, ko, kp, ks, h->ws, h->off, h->order + h->d.batch, h->bwd_generic, h->queue + 4, x0, dL_dz, dL_dxi, kg);
+            h->L, ko, kp, ks, h->ws, h->off, h->order + h->d.batch, h->bwd_generic, h->queue + 4, x0, dL_dz, dL_dxi, kg,
+            h->dws, h->dstride);
         TMPC_CUDA(cudaGetLastError());
         if (t) TMPC_CUDA(cudaEventRecord(h->tev[4][3], s));
         h->timed[4][1] = t;

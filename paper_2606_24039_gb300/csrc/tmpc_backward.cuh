@@ -21,6 +21,7 @@
 //  4. vector-Jacobian product of Eq. (loss_gradient) into the gradient arrays.
 // H is the cost Hessian (the Hessian approximation the paper's code supports).
 #pragma once
+#include "tmpc_direct_generic.cuh"
 #include "tmpc_solver.cuh"
 
 namespace tmpc {
@@ -43,7 +44,7 @@ __device__ __forceinline__ float active_code(float y, float val, float lo, float
 
 __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Smem& sm, const KLayout& L,
                                   const KSol& sol, int inst, const float* dLdz_all,
-                                  const float* dLdxi_all, const KGrads& g) {
+                                  const float* dLdxi_all, const KGrads& g, double* dws, double* dsh) {
     const int n = c.n, nx = c.nx, ng = c.ng, T = c.T, N = c.N;
     const long long Ts = L.Nmax + 1;
     const float* dLdz = dLdz_all + inst * Ts * L.n;
@@ -82,131 +83,136 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
         ex[e] = 0.f;
     }
     __syncthreads();
-    // FP32 safeguard: if S_b cannot be factored, lower rho_b (at most three times)
-    bool ok = factor(c, sm, o.bwd_sigma, rb, rb, true);
-    for (int tries = 0; !ok && tries < 3; ++tries) {
-        rb *= 0.1f;
-        for (int e = threadIdx.x; e < T * ng; e += blockDim.x)
-            if (code[e] != 0.f && fabsf(code[e]) < 1.5f) c.gw[e] = rb;
-        __syncthreads();
-        ok = factor(c, sm, o.bwd_sigma, rb, rb, true);
-    }
-    if (!ok && threadIdx.x == 0) sm.flags[0] = 1;
-    // divergence guard: the refinement contracts in exact arithmetic; if the
-    // steps grow (an FP32 factor of S_b too inaccurate for this rho_b), lower
-    // rho_b tenfold, refactor and restart (at most three times)
-    float d0 = 0.f, dprev = kInf;
-    int restarts = 0;
-    const bool tiled = tiled_linear(c);
-    for (int it = 0; it < o.bwd_iters; ++it) {
-        for (int e = threadIdx.x; e < T * ng; e += blockDim.x) gz[e] = Gx_entry(c, ex, e / ng, e % ng);
-        if (tiled) {
-            // the same sweep with the C and C' products as register tiles:
-            // r2 = -C eta_x; eta = b - H_r eta_x - C'(lam - rho_b r2) - G_H' mu + rho_b G_H' r3
-            c_tiled(c, ex, [&](int e, float v) { r2[e] = -v; });
+    if (!o.bwd_refine && dws && gen_direct_mb(nx, n, ng) <= kGenDirectMB) {
+        // one direct FP64 block LDL' of the interleaved active-set KKT system
+        direct_adjoint_ctx(c, code, bx, ex, lam, mu, dws, dsh, sm.flags + 3);
+    } else {
+        // FP32 safeguard: if S_b cannot be factored, lower rho_b (at most three times)
+        bool ok = factor(c, sm, o.bwd_sigma, rb, rb, true);
+        for (int tries = 0; !ok && tries < 3; ++tries) {
+            rb *= 0.1f;
+            for (int e = threadIdx.x; e < T * ng; e += blockDim.x)
+                if (code[e] != 0.f && fabsf(code[e]) < 1.5f) c.gw[e] = rb;
             __syncthreads();
+            ok = factor(c, sm, o.bwd_sigma, rb, rb, true);
+        }
+        if (!ok && threadIdx.x == 0) sm.flags[0] = 1;
+        // divergence guard: the refinement contracts in exact arithmetic; if the
+        // steps grow (an FP32 factor of S_b too inaccurate for this rho_b), lower
+        // rho_b tenfold, refactor and restart (at most three times)
+        float d0 = 0.f, dprev = kInf;
+        int restarts = 0;
+        const bool tiled = tiled_linear(c);
+        for (int it = 0; it < o.bwd_iters; ++it) {
+            for (int e = threadIdx.x; e < T * ng; e += blockDim.x) gz[e] = Gx_entry(c, ex, e / ng, e % ng);
+            if (tiled) {
+                // the same sweep with the C and C' products as register tiles:
+                // r2 = -C eta_x; eta = b - H_r eta_x - C'(lam - rho_b r2) - G_H' mu + rho_b G_H' r3
+                c_tiled(c, ex, [&](int e, float v) { r2[e] = -v; });
+                __syncthreads();
+                for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
+                    const float cd = code[e];
+                    r3[e] = (cd != 0.f && fabsf(cd) < 1.5f) ? -gz[e] : 0.f;
+                }
+                for (int e = threadIdx.x; e < T * nx; e += blockDim.x) c.xt[e] = lam[e] - rb * r2[e];
+                __syncthreads();
+                ct_tiled(c, c.xt, [&](int t, int j, float ctw) {
+                    float s = bx[t * n + j] - Px_entry(c, ex, t, j) - ctw;
+                    const int r = g_row(c, j);   // selector rows of the linear model
+                    if (r >= 0) {
+                        const float cd = code[t * ng + r];
+                        if (fabsf(cd) > 1.5f) s -= c.gam2(r) * gz[t * ng + r];
+                        else if (cd != 0.f) s -= mu[t * ng + r];
+                        s += rb * r3[t * ng + r];
+                    }
+                    c.eta[t * n + j] = s;
+                });
+                __syncthreads();
+                ldl_solve(c, c.eta, c.xt, sm.red8, sm.A, sm.Bm, sm.mbar, sm.flags + 12);  // dx
+                c_tiled(c, c.xt, [&](int e, float v) { lam[e] += rb * (v - r2[e]); });
+                for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
+                    const float cd = code[e];
+                    if (cd != 0.f && fabsf(cd) < 1.5f) mu[e] += rb * (Gx_entry(c, c.xt, e / ng, e % ng) - r3[e]);
+                }
+                __syncthreads();
+            } else {
+            __syncthreads();
+            // r1 = b - H_r eta_x - C' lam - G_H' mu   (into eta), r2 = -C eta_x, r3 = -G_H eta_x
+            for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
+                const int t = e / n, j = e % n;
+                float s = bx[e] - Px_entry(c, ex, t, j);
+                s -= Ct_entry(c, t, j, [&](int r, int k) { return lam[r * nx + k]; });
+                if (g_is_selector(c)) {
+                    const int r = g_row(c, j);
+                    const float cd = r >= 0 ? code[t * ng + r] : 0.f;
+                    if (fabsf(cd) > 1.5f) s -= c.gam2(r) * gz[t * ng + r];
+                    else if (cd != 0.f) s -= mu[t * ng + r];
+                } else {
+                    const float* G = c.Gt(t);
+                    for (int r = 0; r < ng; ++r) {
+                        const float cd = code[t * ng + r];
+                        if (fabsf(cd) > 1.5f) s -= c.gam2(r) * G[r * n + j] * gz[t * ng + r];
+                        else if (cd != 0.f) s -= G[r * n + j] * mu[t * ng + r];
+                    }
+                }
+                c.eta[e] = s;
+            }
+            for (int e = threadIdx.x; e < T * nx; e += blockDim.x) r2[e] = -Cx_entry(c, ex, e / nx, e % nx);
             for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
                 const float cd = code[e];
                 r3[e] = (cd != 0.f && fabsf(cd) < 1.5f) ? -gz[e] : 0.f;
             }
-            for (int e = threadIdx.x; e < T * nx; e += blockDim.x) c.xt[e] = lam[e] - rb * r2[e];
             __syncthreads();
-            ct_tiled(c, c.xt, [&](int t, int j, float ctw) {
-                float s = bx[t * n + j] - Px_entry(c, ex, t, j) - ctw;
-                const int r = g_row(c, j);   // selector rows of the linear model
-                if (r >= 0) {
-                    const float cd = code[t * ng + r];
-                    if (fabsf(cd) > 1.5f) s -= c.gam2(r) * gz[t * ng + r];
-                    else if (cd != 0.f) s -= mu[t * ng + r];
-                    s += rb * r3[t * ng + r];
+            // rhs of the Schur system: r1 + rho_b (C' r2 + G_H' r3)
+            for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
+                const int t = e / n, j = e % n;
+                float s = Ct_entry(c, t, j, [&](int r, int k) { return r2[r * nx + k]; });
+                if (g_is_selector(c)) {
+                    const int r = g_row(c, j);
+                    if (r >= 0) s += r3[t * ng + r];
+                } else {
+                    const float* G = c.Gt(t);
+                    for (int r = 0; r < ng; ++r) s += G[r * n + j] * r3[t * ng + r];
                 }
-                c.eta[t * n + j] = s;
-            });
+                c.eta[e] += rb * s;
+            }
             __syncthreads();
             ldl_solve(c, c.eta, c.xt, sm.red8, sm.A, sm.Bm, sm.mbar, sm.flags + 12);  // dx
-            c_tiled(c, c.xt, [&](int e, float v) { lam[e] += rb * (v - r2[e]); });
+            for (int e = threadIdx.x; e < T * nx; e += blockDim.x)
+                lam[e] += rb * (Cx_entry(c, c.xt, e / nx, e % nx) - r2[e]);
             for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
                 const float cd = code[e];
                 if (cd != 0.f && fabsf(cd) < 1.5f) mu[e] += rb * (Gx_entry(c, c.xt, e / ng, e % ng) - r3[e]);
             }
             __syncthreads();
-        } else {
-        __syncthreads();
-        // r1 = b - H_r eta_x - C' lam - G_H' mu   (into eta), r2 = -C eta_x, r3 = -G_H eta_x
-        for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
-            const int t = e / n, j = e % n;
-            float s = bx[e] - Px_entry(c, ex, t, j);
-            s -= Ct_entry(c, t, j, [&](int r, int k) { return lam[r * nx + k]; });
-            if (g_is_selector(c)) {
-                const int r = g_row(c, j);
-                const float cd = r >= 0 ? code[t * ng + r] : 0.f;
-                if (fabsf(cd) > 1.5f) s -= c.gam2(r) * gz[t * ng + r];
-                else if (cd != 0.f) s -= mu[t * ng + r];
-            } else {
-                const float* G = c.Gt(t);
-                for (int r = 0; r < ng; ++r) {
-                    const float cd = code[t * ng + r];
-                    if (fabsf(cd) > 1.5f) s -= c.gam2(r) * G[r * n + j] * gz[t * ng + r];
-                    else if (cd != 0.f) s -= G[r * n + j] * mu[t * ng + r];
+            }
+            float dm[1] = {0.f};
+            for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
+                ex[e] += c.xt[e];
+                dm[0] = fmaxf(dm[0], fin(c.xt[e]));
+            }
+            cta_max_k<1>(dm, sm.red);
+            if (it == 0) d0 = dm[0];
+            const bool diverging = !(dm[0] < kInf) || (it >= 2 && dm[0] > 2.f * dprev && dm[0] > 1e-4f * d0);
+            if (diverging && restarts < 3) {
+                ++restarts;
+                rb *= 0.1f;
+                for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
+                    if (code[e] != 0.f && fabsf(code[e]) < 1.5f) c.gw[e] = rb;
+                    mu[e] = 0.f;
                 }
+                for (int e = threadIdx.x; e < T * nx; e += blockDim.x) lam[e] = 0.f;
+                for (int e = threadIdx.x; e < T * n; e += blockDim.x) ex[e] = 0.f;
+                __syncthreads();
+                if (!factor(c, sm, o.bwd_sigma, rb, rb, true) && threadIdx.x == 0) sm.flags[0] = 1;
+                d0 = 0.f;
+                dprev = kInf;
+                it = -1;
+                continue;
             }
-            c.eta[e] = s;
-        }
-        for (int e = threadIdx.x; e < T * nx; e += blockDim.x) r2[e] = -Cx_entry(c, ex, e / nx, e % nx);
-        for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
-            const float cd = code[e];
-            r3[e] = (cd != 0.f && fabsf(cd) < 1.5f) ? -gz[e] : 0.f;
-        }
-        __syncthreads();
-        // rhs of the Schur system: r1 + rho_b (C' r2 + G_H' r3)
-        for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
-            const int t = e / n, j = e % n;
-            float s = Ct_entry(c, t, j, [&](int r, int k) { return r2[r * nx + k]; });
-            if (g_is_selector(c)) {
-                const int r = g_row(c, j);
-                if (r >= 0) s += r3[t * ng + r];
-            } else {
-                const float* G = c.Gt(t);
-                for (int r = 0; r < ng; ++r) s += G[r * n + j] * r3[t * ng + r];
-            }
-            c.eta[e] += rb * s;
-        }
-        __syncthreads();
-        ldl_solve(c, c.eta, c.xt, sm.red8, sm.A, sm.Bm, sm.mbar, sm.flags + 12);  // dx
-        for (int e = threadIdx.x; e < T * nx; e += blockDim.x)
-            lam[e] += rb * (Cx_entry(c, c.xt, e / nx, e % nx) - r2[e]);
-        for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
-            const float cd = code[e];
-            if (cd != 0.f && fabsf(cd) < 1.5f) mu[e] += rb * (Gx_entry(c, c.xt, e / ng, e % ng) - r3[e]);
-        }
-        __syncthreads();
-        }
-        float dm[1] = {0.f};
-        for (int e = threadIdx.x; e < T * n; e += blockDim.x) {
-            ex[e] += c.xt[e];
-            dm[0] = fmaxf(dm[0], fin(c.xt[e]));
-        }
-        cta_max_k<1>(dm, sm.red);
-        if (it == 0) d0 = dm[0];
-        const bool diverging = !(dm[0] < kInf) || (it >= 2 && dm[0] > 2.f * dprev && dm[0] > 1e-4f * d0);
-        if (diverging && restarts < 3) {
-            ++restarts;
-            rb *= 0.1f;
-            for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
-                if (code[e] != 0.f && fabsf(code[e]) < 1.5f) c.gw[e] = rb;
-                mu[e] = 0.f;
-            }
-            for (int e = threadIdx.x; e < T * nx; e += blockDim.x) lam[e] = 0.f;
-            for (int e = threadIdx.x; e < T * n; e += blockDim.x) ex[e] = 0.f;
+            dprev = dm[0];
             __syncthreads();
-            if (!factor(c, sm, o.bwd_sigma, rb, rb, true) && threadIdx.x == 0) sm.flags[0] = 1;
-            d0 = 0.f;
-            dprev = kInf;
-            it = -1;
-            continue;
         }
-        dprev = dm[0];
-        __syncthreads();
     }
     for (int e = threadIdx.x; e < T * ng; e += blockDim.x) gz[e] = Gx_entry(c, ex, e / ng, e % ng);
     __syncthreads();

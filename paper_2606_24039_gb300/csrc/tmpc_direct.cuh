@@ -32,10 +32,17 @@ namespace tmpc {
 namespace fast {
 
 // doubles of the FP64 workspace per stage: S_t^-1 (MB^2), y_t (MB), then the FP64
-// Jacobian A^-_t (NX x N) and the dense row of G_t (N); MB <= kDirectMB, NX N <= 48, N <= 8
+// Jacobian A^-_t (NX x N) and the dense row of G_t (N), then (exact Hessian) the
+// constraint-curvature blocks of the Lagrangian: Ccur_tt from f_t and the track row,
+// C'_tt from f_{t-1}, C_{t,t-1} from f_{t-1} (N x N each);
+// MB <= kDirectMB, NX N <= 48, N <= 8
 constexpr int kDirectMB = 19;
 constexpr long long kDirectJac = (long long)kDirectMB * kDirectMB + kDirectMB;
-constexpr long long kDirectStage = kDirectJac + 48 + 8;
+constexpr long long kDirectCurv = kDirectJac + 48 + 8;
+constexpr long long kDirectStage = kDirectCurv + 3 * 64;
+constexpr double kCurvStep = 1e-6;   // central-difference step of the constraint curvature
+// shared scratch of the sweep (X, pivot row, y / v, w): N^2 + 2 MB + MB + N doubles
+constexpr int kDirectScratch = 64 + 3 * kDirectMB + 8;
 
 template <int M>
 struct Kkt {
@@ -69,13 +76,9 @@ __device__ __forceinline__ double Hdiag(const Inst<M>& c, int t, int j) {
 // dense row of G_t, evaluated by the model functions in double precision, so that
 // the KKT system is the one at the returned point up to FP64 rounding.
 template <int M>
-__device__ __forceinline__ void jacobians_fp64(const Inst<M>& c, int t, double* Ad, double* Gd) {
-    using Tr = Traits<M>;
+__device__ __forceinline__ void jac_at(const Inst<M>& c, const double* zt, const double* zn, double* Ad) {
     constexpr int N = Inst<M>::N, NX = Inst<M>::NX;
-    double zt[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) zt[j] = (double)c.zb[t * N + j];
-    if (t < c.Nh) {
+    {
         if constexpr (M == MODEL_DI) {
             const double dt = (double)c.dyn[0];
 #pragma unroll
@@ -95,7 +98,7 @@ __device__ __forceinline__ void jacobians_fp64(const Inst<M>& c, int t, double* 
         } else {   // bicycle, implicit midpoint
             const double dt = (double)c.dyn[0];
             double mid[6], fc[6], Jx[36], Ju[12];
-            for (int k = 0; k < 6; ++k) mid[k] = 0.5 * (zt[k] + (double)c.zb[(t + 1) * N + k]);
+            for (int k = 0; k < 6; ++k) mid[k] = 0.5 * (zt[k] + zn[k]);
             bicycle_fc<double>(mid, zt + 6, c.dyn[1], c.track, c.nt, c.dyn[2], fc, Jx, Ju);
             for (int k = 0; k < 6; ++k) {
                 for (int j = 0; j < 6; ++j) Ad[k * N + j] = (k == j ? 1.0 : 0.0) + 0.5 * dt * Jx[k * 6 + j];
@@ -104,16 +107,124 @@ __device__ __forceinline__ void jacobians_fp64(const Inst<M>& c, int t, double* 
             }
         }
     }
-    if constexpr (Tr::DENSE_ROW >= 0) {   // lateral track error of the bicycle
-        TrackPtR<double> tp = track_eval<double>(c.track, c.nt, (double)c.dyn[2], zt[5]);
-        double sp, cp;
-        msincos(tp.psic, &sp, &cp);
-        const double dx = zt[0] - tp.xc, dy = zt[1] - tp.yc;
+}
+
+// dense row of G_t (the bicycle's lateral track error) at z, FP64
+template <int M>
+__device__ __forceinline__ void gtrack_at(const Inst<M>& c, const double* z, double* Gd) {
+    constexpr int N = Inst<M>::N;
+    TrackPtR<double> tp = track_eval<double>(c.track, c.nt, (double)c.dyn[2], z[5]);
+    double sp, cp;
+    msincos(tp.psic, &sp, &cp);
+    const double dx = z[0] - tp.xc, dy = z[1] - tp.yc;
 #pragma unroll
-        for (int j = 0; j < N; ++j) Gd[j] = 0.0;
-        Gd[0] = -sp;
-        Gd[1] = cp;
-        Gd[5] = tp.dxc * sp - tp.dyc * cp - tp.dpsic * (dx * cp + dy * sp);
+    for (int j = 0; j < N; ++j) Gd[j] = 0.0;
+    Gd[0] = -sp;
+    Gd[1] = cp;
+    Gd[5] = tp.dxc * sp - tp.dyc * cp - tp.dpsic * (dx * cp + dy * sp);
+}
+
+template <int M>
+__device__ __forceinline__ void jacobians_fp64(const Inst<M>& c, int t, double* Ad, double* Gd) {
+    constexpr int N = Inst<M>::N;
+    double zt[N], zn[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        zt[j] = (double)c.zb[t * N + j];
+        zn[j] = t < c.Nh ? (double)c.zb[(t + 1) * N + j] : 0.0;
+    }
+    if (t < c.Nh) jac_at<M>(c, zt, zn, Ad);
+    if constexpr (Traits<M>::DENSE_ROW >= 0) gtrack_at<M>(c, zt, Gd);
+}
+
+// Constraint curvature of the Lagrangian (the exact-Hessian backward; App. E:
+// H = Hessian of l + y_f' f + y_A' g_A), by FP64 central differences (step
+// kCurvStep) of the FP64 analytic Jacobians:
+//   f_t with multiplier y = y_f[t+1]: psi(z_t, z_{t+1}) = [A^-' y; A^+' y] over the 2N
+//   coordinates -> blocks (t,t) into Ct[t], (t+1,t+1) into Cn[t+1], (t+1,t) into Cl[t+1];
+//   the active track row with multiplier y_g: Hessian of g into Ct[t].
+// Stage t's thread writes Ct[t] and the Cn, Cl slots of stage t+1 (no other writer).
+template <int M>
+__device__ __forceinline__ void curvature_fp64(const Inst<M>& c, const float* code, int t, double* dws) {
+    using Tr = Traits<M>;
+    constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
+    double* Ct = dws + (long long)t * kDirectStage + kDirectCurv;
+    double* Cn = dws + (long long)(t + 1) * kDirectStage + kDirectCurv + 64;
+    double* Cl = Cn + 64;
+    double z0[2 * N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        z0[j] = (double)c.zb[t * N + j];
+        z0[N + j] = t < c.Nh ? (double)c.zb[(t + 1) * N + j] : 0.0;
+    }
+    for (int i = 0; i < N * N; ++i) Ct[i] = 0.0;
+    if (t == 0) {
+        double* C0 = dws + kDirectCurv + 64;
+        for (int i = 0; i < 2 * N * N; ++i) C0[i] = 0.0;
+    }
+    if (t < c.Nh && M != MODEL_DI) {
+        double y[NX];
+#pragma unroll
+        for (int k = 0; k < NX; ++k) y[k] = (double)c.yfb[(t + 1) * NX + k];
+        // psi(v) = [A^-' y; A^+' y], A^+ = A^-_x - 2I (implicit midpoint) or [-I 0] (explicit)
+        auto psi = [&](const double* v, double* g) {
+            double Ad[NX * N];
+            jac_at<M>(c, v, v + N, Ad);
+            for (int j = 0; j < N; ++j) {
+                double a = 0.0, b = 0.0;
+                for (int k = 0; k < NX; ++k) {
+                    a += Ad[k * N + j] * y[k];
+                    if (j < NX) b += (Tr::IMPLICIT ? Ad[k * N + j] - (k == j ? 2.0 : 0.0) : (k == j ? -1.0 : 0.0)) * y[k];
+                }
+                g[j] = a;
+                g[N + j] = b;
+            }
+        };
+        double Hc[2 * N][2 * N];
+        for (int q = 0; q < 2 * N; ++q) {
+            double vp[2 * N], vm[2 * N], gp[2 * N], gm[2 * N];
+            for (int j = 0; j < 2 * N; ++j) { vp[j] = z0[j]; vm[j] = z0[j]; }
+            vp[q] += kCurvStep;
+            vm[q] -= kCurvStep;
+            psi(vp, gp);
+            psi(vm, gm);
+            for (int j = 0; j < 2 * N; ++j) Hc[j][q] = (gp[j] - gm[j]) / (2.0 * kCurvStep);
+        }
+        for (int i = 0; i < 2 * N; ++i)
+            for (int j = 0; j < i; ++j) {
+                const double m = 0.5 * (Hc[i][j] + Hc[j][i]);
+                Hc[i][j] = m;
+                Hc[j][i] = m;
+            }
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j) {
+                Ct[i * N + j] = Hc[i][j];
+                Cn[i * N + j] = Hc[N + i][N + j];
+                Cl[i * N + j] = Hc[N + i][j];
+            }
+    } else if (t < c.Nh) {
+        for (int i = 0; i < 2 * N * N; ++i) Cn[i] = 0.0;
+    }
+    if constexpr (Tr::DENSE_ROW >= 0) {
+        const int q = Tr::DENSE_ROW;
+        if (code[t * NG + q] != 0.f) {   // active (hard or slack): multiplier y_g of the row
+            const double yg = (double)c.ygb[t * NG + q];
+            for (int k = 0; k < N; ++k) {
+                double vp[N], vm[N], gp[N], gm[N];
+                for (int j = 0; j < N; ++j) { vp[j] = z0[j]; vm[j] = z0[j]; }
+                vp[k] += kCurvStep;
+                vm[k] -= kCurvStep;
+                gtrack_at<M>(c, vp, gp);
+                gtrack_at<M>(c, vm, gm);
+                for (int j = 0; j < N; ++j) Ct[j * N + k] += yg * (gp[j] - gm[j]) / (2.0 * kCurvStep);
+            }
+            for (int i = 0; i < N; ++i)
+                for (int j = 0; j < i; ++j) {
+                    const double m = 0.5 * (Ct[i * N + j] + Ct[j * N + i]);
+                    Ct[i * N + j] = m;
+                    Ct[j * N + i] = m;
+                }
+        }
     }
 }
 
@@ -125,7 +236,7 @@ __device__ __forceinline__ void jacobians_fp64(const Inst<M>& c, int t, double* 
 // Returns (to every thread of the team) true if the regularised solve was needed.
 template <int M>
 __device__ bool direct_adjoint(const Inst<M>& c, const float* code, const float* bx, float* ex, float* lam,
-                               float* mu, double* dws, double* sh, int* flag) {
+                               float* mu, double* dws, double* sh, int* flag, bool exact) {
     using K = Kkt<M>;
     constexpr int NX = K::NX, N = K::N, NG = K::NG, MB = K::MB, XZ = K::XZ, XH = K::XH;
     const int T = c.T;
@@ -139,6 +250,7 @@ __device__ bool direct_adjoint(const Inst<M>& c, const float* code, const float*
     for (int t = c.tid; t < T; t += c.nth) {
         double* st = dws + (long long)t * kDirectStage + kDirectJac;
         jacobians_fp64<M>(c, t, st, st + 48);
+        if (exact) curvature_fp64<M>(c, code, t, dws);
     }
     if (c.tid == 0) *flag = 0;
     c.sync();
@@ -148,6 +260,20 @@ __device__ bool direct_adjoint(const Inst<M>& c, const float* code, const float*
         if (j >= NX) return 0.0;
         if (Traits<M>::IMPLICIT) return Amd(t)[k * N + j] - (k == j ? 2.0 : 0.0);
         return k == j ? -1.0 : 0.0;
+    };
+    // cost Hessian blocks plus, with the exact Hessian, the constraint curvature
+    auto Htt = [&](int t, int j, int jj) -> double {
+        double h = j == jj ? Hdiag<M>(c, t, j) : 0.0;
+        if (exact) {
+            const double* cv = dws + (long long)t * kDirectStage + kDirectCurv;
+            h += cv[j * N + jj] + (t > 0 ? cv[64 + j * N + jj] : 0.0);
+        }
+        return h;
+    };
+    auto Hlow = [&](int t, int j, int b) -> double {   // (t, t-1) block, t >= 1
+        double h = Hsub<M>(c, j, b);
+        if (exact) h += (dws + (long long)t * kDirectStage + kDirectCurv + 128)[j * N + b];
+        return h;
     };
     auto Gd = [&](int t, int q, int j) -> double {
         const int s = Traits<M>::sel(q);
@@ -175,7 +301,8 @@ __device__ bool direct_adjoint(const Inst<M>& c, const float* code, const float*
 #pragma unroll
                         for (int k = 0; k < NX; ++k)
                             a[k] = t == 0 ? (j == k ? 1.0 : 0.0) : Apd(t - 1, k, j);
-                        a[XZ + j] = Hdiag<M>(c, t, j);
+#pragma unroll
+                        for (int jj = 0; jj < N; ++jj) a[XZ + jj] = Htt(t, j, jj);
 #pragma unroll
                         for (int q = 0; q < NG; ++q) {
                             const float cd = code[t * NG + q];
@@ -204,7 +331,7 @@ __device__ bool direct_adjoint(const Inst<M>& c, const float* code, const float*
                         double pr[N];   // row `lane` of P_t
 #pragma unroll
                         for (int b = 0; b < N; ++b)
-                            pr[b] = lane < XZ ? Amd(t - 1)[lane * N + b] : Hsub<M>(c, lane - XZ, b);
+                            pr[b] = lane < XZ ? Amd(t - 1)[lane * N + b] : Hlow(t, lane - XZ, b);
                         double u[N];
 #pragma unroll
                         for (int b = 0; b < N; ++b) {
@@ -218,7 +345,7 @@ __device__ bool direct_adjoint(const Inst<M>& c, const float* code, const float*
                             double s = 0.0;
 #pragma unroll
                             for (int b = 0; b < N; ++b)
-                                s += u[b] * (col < XZ ? Amd(t - 1)[col * N + b] : Hsub<M>(c, col - XZ, b));
+                                s += u[b] * (col < XZ ? Amd(t - 1)[col * N + b] : Hlow(t, col - XZ, b));
                             a[col] -= s;
                         }
                     }
@@ -277,7 +404,7 @@ __device__ bool direct_adjoint(const Inst<M>& c, const float* code, const float*
                     if (t > 0 && lane < XH) {
 #pragma unroll
                         for (int b = 0; b < N; ++b)
-                            y -= (lane < XZ ? Amd(t - 1)[lane * N + b] : Hsub<M>(c, lane - XZ, b)) * wv[b];
+                            y -= (lane < XZ ? Amd(t - 1)[lane * N + b] : Hlow(t, lane - XZ, b)) * wv[b];
                     }
                     yv[lane] = y;
                     Sinv[MB * MB + lane] = y;
@@ -306,7 +433,7 @@ __device__ bool direct_adjoint(const Inst<M>& c, const float* code, const float*
 #pragma unroll
                         for (int k = 0; k < NX; ++k) s += Amd(t)[k * N + b] * yv[k];
 #pragma unroll
-                        for (int j = 0; j < N; ++j) s += Hsub<M>(c, j, b) * xnext[j];
+                        for (int j = 0; j < N; ++j) s += Hlow(t + 1, j, b) * xnext[j];
                         v -= s;
                     }
                     prow[lane] = v;

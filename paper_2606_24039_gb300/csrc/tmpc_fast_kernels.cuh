@@ -1196,7 +1196,8 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
 template <int M>
 __device__ __forceinline__ void backward_instance_team(Inst<M>& c, const KOpts& o, const Red& rs, const KLayout& L,
                                                        const KSol& sol, int inst, const float* dLdz_all,
-                                                       const float* dLdxi_all, const KGrads& g, double* dws) {
+                                                       const float* dLdxi_all, const KGrads& g, double* dws,
+                                                       double* dsh) {
     using Tr = Traits<M>;
     constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NU = Inst<M>::NU, NG = Inst<M>::NG;
     const int T = c.T;
@@ -1260,9 +1261,9 @@ __device__ __forceinline__ void backward_instance_team(Inst<M>& c, const KOpts& 
     }
     c.sync();
     if (!o.bwd_refine && dws) {
-        // direct FP64 block LDL' of the interleaved active-set KKT system (tmpc_direct.cuh);
-        // the factor blocks of the forward (Dm onwards) are free here and serve as scratch
-        direct_adjoint<M>(c, code, bx, ex, lam, mu, dws, reinterpret_cast<double*>(c.Dm), c.tflags + 2);
+        // direct FP64 block LDL' of the interleaved active-set KKT system (tmpc_direct.cuh),
+        // its broadcast rows in the CTA's shared scratch dsh
+        direct_adjoint<M>(c, code, bx, ex, lam, mu, dws, dsh, c.tflags + 2, o.exact_hessian != 0);
     } else {
         // S_b = H + sigma_b I + rho_b C'C + G' diag(w) G; FP32 safeguard: lower rho_b up to three times
         form_S<M>(c, o.bwd_sigma, rb, rb, gw);
@@ -1524,6 +1525,7 @@ __global__ void __launch_bounds__(256, 2) backward_kernel(KLayout L, KOpts o, KP
                                                        const float* dLdz, const float* dLdxi, KGrads g,
                                                        double* dws, long long dstride) {
     extern __shared__ __align__(16) float arena[];
+    __shared__ double dsh[kDirectScratch];
     __shared__ float red[32 * 8];
     __shared__ double redd[64];
     __shared__ double lsacc[2 * (kMaxLs + 1) + 2];
@@ -1546,7 +1548,8 @@ __global__ void __launch_bounds__(256, 2) backward_kernel(KLayout L, KOpts o, KP
         c.tflags = flags;
         const long long need = arena_floats<M>(c.T, kCR);
         c.carve(need <= smem_floats ? arena : gws + (long long)i * gstride, kCR);
-        backward_instance_team<M>(c, o, rs, L, sol, i, dLdz, dLdxi, g, dws ? dws + (long long)i * dstride : nullptr);
+        backward_instance_team<M>(c, o, rs, L, sol, i, dLdz, dLdxi, g, dws ? dws + (long long)i * dstride : nullptr,
+                                  dsh);
     }
 }
 
@@ -1556,6 +1559,7 @@ __global__ void __launch_bounds__(256, 2) backward_kernel_cluster(KLayout L, KOp
                                                                const float* x0, int* gflags, const float* dLdz,
                                                                const float* dLdxi, KGrads g, double* dws,
                                                                long long dstride) {
+    __shared__ double dsh[kDirectScratch];
     __shared__ float red[32 * 8];
     __shared__ double redd[64];
     __shared__ double lsacc[2 * (kMaxLs + 1) + 2];
@@ -1576,7 +1580,8 @@ __global__ void __launch_bounds__(256, 2) backward_kernel_cluster(KLayout L, KOp
         c.rank = (int)rank;
         c.tflags = gflags + 4LL * i;
         c.carve(gws + (long long)i * gstride, kCR, 1);
-        backward_instance_team<M>(c, o, rs, L, sol, i, dLdz, dLdxi, g, dws ? dws + (long long)i * dstride : nullptr);
+        backward_instance_team<M>(c, o, rs, L, sol, i, dLdz, dLdxi, g, dws ? dws + (long long)i * dstride : nullptr,
+                                  dsh);
         c.sync();
     }
 }

@@ -274,6 +274,6 @@ __global__ void __launch_bounds__(256, 2) solve_kernel(KLayout L, KOpts o, KPara
                              const int* order, int count, int* queue, const float* x0, int warm);
 __global__ void __launch_bounds__(256, 2) backward_kernel(KLayout L, KOpts o, KParams p, KSol sol, float* ws, WsOff off,
                                 const int* order, int count, int* queue, const float* x0, const float* dLdz,
-                                const float* dLdxi, KGrads g);
+                                const float* dLdxi, KGrads g, double* dws, long long dstride);
 
 }  // namespace tmpc

@@ -6,8 +6,9 @@ namespace tmpc {
 
 __global__ void __launch_bounds__(256, 2) backward_kernel(KLayout L, KOpts o, KParams p, KSol sol, float* ws, WsOff off,
                                 const int* order, int count, int* queue, const float* x0, const float* dLdz,
-                                const float* dLdxi, KGrads g) {
+                                const float* dLdxi, KGrads g, double* dws, long long dstride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double dsh[kGenDirectScratch];
     __shared__ int s_item;
     const Smem sm = carve_smem(smem_raw, L);
     block_stream_init(sm.mbar, sm.flags + 12, o.wait_polls, o.force_timeout);
@@ -19,7 +20,7 @@ __global__ void __launch_bounds__(256, 2) backward_kernel(KLayout L, KOpts o, KP
         if (q >= count) break;
         const int i = order[q];
         const Ctx c = make_ctx(L, p, ws, off, i, x0, sm.vs);
-        backward_instance(c, o, sm, L, sol, i, dLdz, dLdxi, g);
+        backward_instance(c, o, sm, L, sol, i, dLdz, dLdxi, g, dws ? dws + (long long)i * dstride : nullptr, dsh);
     }
 }
 

@@ -36,6 +36,7 @@ struct KOpts {
     int wait_polls;   // polls of a bounded wait on an asynchronous copy (0: kMbarSpin)
     int force_timeout;   // nonzero: every bounded wait gives up at once (test hook)
     int bwd_refine;      // 1: small models' backward by iterative refinement instead of the direct solve
+    int exact_hessian;   // 1: the direct backward adds the constraint curvature of the Lagrangian
 };
 
 struct KLayout {

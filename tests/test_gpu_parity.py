@@ -576,3 +576,54 @@ def test_backward_other_time_discretisations_on_oracle_point(integrator):
             rel = _grad_rel(g[k][i].cpu().numpy().reshape(-1), gr[k].reshape(-1), scale)
             assert rel < GRAD_TOL, (i, k, rel)
     assert compared >= 2
+
+
+@pytest.mark.parametrize("which", ["racing", "quadrotor"])
+def test_backward_exact_hessian_matches_oracle(which):
+    """The exact Lagrangian Hessian H = Hessian of l + y_f' f + y_A' g_A (App. E;
+    exact_hessian = 1, direct backward) on the implicit-midpoint bicycle (dynamics
+    and track-row curvature) and the RK4 quadrotor, at the oracle's SQP point,
+    against oracle.backward(..., exact_hessian=True) with the same FP32 inputs."""
+    from paper_2606_24039_gb300 import Solver
+    if which == "racing":
+        pb = w.racing(B=3, N=20, max_sqp=3, max_admm=200)
+    else:
+        pb = w.uneven(B=64, N_lo=10, N_hi=20, seed=21, max_sqp=3, max_admm=200)
+        pb = pb.subset(np.flatnonzero(pb.model == w.MODEL_QUAD)[:3])
+    s = Solver.from_batch(pb, device="cuda", exact_hessian=1)
+    refs = [osqp.solve(pb.instance(i), pb.opts) for i in range(pb.B)]
+    T, n = pb.N_max + 1, pb.n
+    sol = {}
+    for k, kk, m in (("z", "z", pb.n), ("xi", "xi", pb.ng), ("y_eq", "yf", pb.nx), ("y_ineq", "yg", pb.ng)):
+        a = np.zeros((pb.B, T, m), np.float32)
+        for i, r in enumerate(refs):
+            a[i, :r[kk].shape[0], :r[kk].shape[1]] = r[kk]
+        sol[k] = torch.tensor(a, device="cuda")
+    sol["status"] = torch.zeros(pb.B, dtype=torch.int32, device="cuda")
+    rng = np.random.default_rng(19)
+    dLdz = rng.normal(size=(pb.B, T, n))
+    g = s.tmpc_backward(s.x0, sol, torch.tensor(dLdz, dtype=torch.float32, device="cuda"))
+    torch.cuda.synchronize()
+    keys = ("x0", "Qd", "Rd", "Wd", "ref", "lin", "lo", "hi")
+    compared = 0
+    for i in range(pb.B):
+        inst = {k: (v.astype(np.float32).astype(np.float64) if isinstance(v, np.ndarray) and v.dtype == np.float64
+                    else v) for k, v in pb.instance(i).items()}
+        Ti, ni, nx, nu, ng = inst["N"] + 1, inst["nx"] + inst["nu"], inst["nx"], inst["nu"], inst["ng"]
+        point = {k: sol[kk][i, :Ti, :m].cpu().numpy().astype(np.float64) for k, kk, m in
+                 (("z", "z", ni), ("xi", "xi", ng), ("yf", "y_eq", nx), ("yg", "y_ineq", ng))}
+        gr, info = obwd.backward(inst, point, dLdz[i, :Ti, :ni], eps_g=pb.opts.eps_g, exact_hessian=True)
+        gc, _ = obwd.backward(inst, point, dLdz[i, :Ti, :ni], eps_g=pb.opts.eps_g)
+        if info["singular"]:
+            continue
+        compared += 1
+        cut = {"x0": (nx,), "Qd": (Ti, nx), "Rd": (Ti, nu), "Wd": (nu,), "ref": (Ti, ni), "lin": (Ti, ni),
+               "lo": (Ti, ng), "hi": (Ti, ng)}
+        scale = max(np.linalg.norm(gr[k]) for k in keys)
+        # the curvature must matter, else the test would not tell the Hessians apart
+        assert max(np.linalg.norm(gr[k] - gc[k]) for k in keys) > 10 * GRAD_TOL * scale
+        for k in keys:
+            ga = g[k][i].cpu().numpy()[tuple(slice(0, m) for m in cut[k])]
+            rel = _grad_rel(ga.reshape(-1), gr[k].reshape(-1), scale)
+            assert rel < GRAD_TOL, (i, k, rel)
+    assert compared >= 2
