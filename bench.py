@@ -455,18 +455,27 @@ def group_members(pb, model, solver):
 
 
 def roofline_of(name, pb, stats, gtimes, solver, peak):
-    """Roofline of the dominant forward kernel (largest mean device time per
-    launch over the timed steps, CUDA events on its launching stream)."""
+    """Roofline of the forward kernel: the one persistent launch of a single
+    model group, or, when the model groups run concurrently on their streams,
+    their concurrent launches together (all their instances' work over the span
+    of the longest launch); device times by CUDA events on the launching streams."""
     import workloads as w
     groups = [g for g in gtimes if g["fwd_ms"] > 0]
     if not groups:
         return None
     g = max(groups, key=lambda r: r["fwd_ms"])
-    idx = group_members(pb, g["model"], solver)
+    ms = g["fwd_ms"]
+    if len(groups) > 1:
+        idx = np.concatenate([group_members(pb, r["model"], solver) for r in groups])
+        kernel = " + ".join(group_kernel(r["model"], r["form"]) for r in groups) + " (concurrent)"
+        for r in groups:   # each group's own rate, for reference
+            gi = group_members(pb, r["model"], solver)
+            r["fwd_tflops"] = algorithmic_flops(pb.subset(gi), stats[gi]) / (r["fwd_ms"] * 1e-3) / 1e12
+    else:
+        idx = group_members(pb, g["model"], solver)
+        kernel = group_kernel(g["model"], g["form"])
     sub = pb.subset(idx)
     st = stats[idx]
-    ms = g["fwd_ms"]
-    kernel = group_kernel(g["model"], g["form"])
     lti = bool(np.all(np.isin(sub.model, (w.MODEL_LINEAR,))))
     if lti and g["model"] < 0:
         # factor blocks that do not fit on chip stream from HBM every ADMM iteration

@@ -133,16 +133,19 @@ typedef struct {
     int32_t force_pivot_failure;
     int32_t wait_polls;
     int32_t force_wait_timeout;
-    /* backward solver of the double integrator, bicycle and quadrotor: 0 = one direct
-     * FP64 block LDL' factorisation of the interleaved active-set KKT system (exact up
-     * to rounding, also when the active rows are nearly dependent); 1 = the iterative
-     * refinement preconditioned by the forward's FP32 factorisation (bwd_rho,
-     * bwd_sigma, bwd_iters).  The generic kernel always uses the refinement. */
-    int32_t bwd_refine;
+    /* backward solver.  1 = the iterative refinement preconditioned by an FP32
+     * factorisation of the regularised system (bwd_rho, bwd_sigma, bwd_iters); 2 = one
+     * direct FP64 block LDL' factorisation of the interleaved active-set KKT system
+     * (exact up to rounding, also when the active rows are nearly dependent); 0 (the
+     * default) = the refinement, then the direct solve for every instance whose
+     * refinement did not converge.  The direct solve exists for the small models and,
+     * on the generic kernel, when nx + (nx + nu) + ng <= 32; elsewhere 0 and 2 mean 1. */
+    int32_t bwd_solver;
     /* 1: the direct backward uses the exact Lagrangian Hessian H = Hessian of
      * l + y_f' f + y_A' g_A (App. E) at the solution, the constraint curvature by FP64
      * central differences of the analytic Jacobians; 0: the cost Hessian (the paper's
-     * Hessian approximation; exact for linear dynamics).  Needs bwd_refine = 0. */
+     * Hessian approximation; exact for linear dynamics).  Implies the direct solve
+     * (small models). */
     int32_t exact_hessian;
 } tmpc_options;
 

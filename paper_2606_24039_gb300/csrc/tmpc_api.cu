@@ -46,7 +46,7 @@ KOpts to_kopts(const tmpc_options& o) {
     k.force_fail = o.force_pivot_failure;
     k.wait_polls = o.wait_polls;
     k.force_timeout = o.force_wait_timeout;
-    k.bwd_refine = o.bwd_refine;
+    k.bwd_solver = o.bwd_solver;
     k.exact_hessian = o.exact_hessian;
     if (k.k_rho_iter < 1) k.k_rho_iter = 1 << 30;
     return k;
@@ -227,6 +227,7 @@ static tmpc_status check_options(const tmpc_options* o) {
     if (o->threads < 0 || o->threads > 256 || (o->threads % 32) != 0) return TMPC_ERR_INVALID_ARG;
     if (o->solver < 0 || o->solver > 7) return TMPC_ERR_INVALID_ARG;
     if (o->force_pivot_failure < 0 || o->wait_polls < 0) return TMPC_ERR_INVALID_ARG;
+    if (o->bwd_solver < 0 || o->bwd_solver > 2) return TMPC_ERR_INVALID_ARG;
     return TMPC_OK;
 }
 

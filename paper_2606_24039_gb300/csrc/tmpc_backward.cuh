@@ -83,7 +83,12 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
         ex[e] = 0.f;
     }
     __syncthreads();
-    if (!o.bwd_refine && dws && gen_direct_mb(nx, n, ng) <= kGenDirectMB) {
+    // backward solver: 0 hybrid (refinement, then the direct FP64 solve where it did not
+    // converge), 1 refinement only, 2 direct only (where the interleaved block fits)
+    const bool direct_ok = dws != nullptr && gen_direct_mb(nx, n, ng) <= kGenDirectMB;
+    const bool direct_only = direct_ok && o.bwd_solver == 2;
+    bool refined_ok = true;
+    if (direct_only) {
         // one direct FP64 block LDL' of the interleaved active-set KKT system
         direct_adjoint_ctx(c, code, bx, ex, lam, mu, dws, dsh, sm.flags + 3);
     } else {
@@ -100,7 +105,7 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
         // divergence guard: the refinement contracts in exact arithmetic; if the
         // steps grow (an FP32 factor of S_b too inaccurate for this rho_b), lower
         // rho_b tenfold, refactor and restart (at most three times)
-        float d0 = 0.f, dprev = kInf;
+        float d0 = 0.f, dprev = kInf, dprev2 = kInf;
         int restarts = 0;
         const bool tiled = tiled_linear(c);
         for (int it = 0; it < o.bwd_iters; ++it) {
@@ -210,9 +215,22 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
                 it = -1;
                 continue;
             }
+            dprev2 = dprev;
             dprev = dm[0];
             __syncthreads();
         }
+        // convergence of the refinement (as on the small models' kernels)
+        float xm[1] = {0.f};
+        for (int e = threadIdx.x; e < T * n; e += blockDim.x) xm[0] = fmaxf(xm[0], fin(ex[e]));
+        cta_max_k<1>(xm, sm.red);
+        const float q = dprev / fmaxf(dprev2, 1e-30f);
+        refined_ok = dprev <= 1e-6f * xm[0] || (q < 0.9f && dprev * q / (1.f - q) <= 1e-4f * xm[0]);
+        refined_ok = refined_ok && restarts == 0 && xm[0] < kInf;
+    }
+    if (!direct_only && !refined_ok && direct_ok && o.bwd_solver == 0) {
+        for (int e = threadIdx.x; e < T * ng; e += blockDim.x) mu[e] = 0.f;
+        __syncthreads();
+        direct_adjoint_ctx(c, code, bx, ex, lam, mu, dws, dsh, sm.flags + 3);
     }
     for (int e = threadIdx.x; e < T * ng; e += blockDim.x) gz[e] = Gx_entry(c, ex, e / ng, e % ng);
     __syncthreads();

@@ -1260,7 +1260,12 @@ __device__ __forceinline__ void backward_instance_team(Inst<M>& c, const KOpts& 
         ex[e] = 0.f;
     }
     c.sync();
-    if (!o.bwd_refine && dws) {
+    // backward solver: 0 hybrid (refinement, then the direct solve where it did not
+    // converge), 1 refinement only, 2 direct only; the exact Hessian needs the direct solve
+    const bool direct_ok = dws != nullptr;
+    const bool direct_only = direct_ok && (o.bwd_solver == 2 || o.exact_hessian);
+    bool refined_ok = true;
+    if (direct_only) {
         // direct FP64 block LDL' of the interleaved active-set KKT system (tmpc_direct.cuh),
         // its broadcast rows in the CTA's shared scratch dsh
         direct_adjoint<M>(c, code, bx, ex, lam, mu, dws, dsh, c.tflags + 2, o.exact_hessian != 0);
@@ -1279,7 +1284,7 @@ __device__ __forceinline__ void backward_instance_team(Inst<M>& c, const KOpts& 
         if (!ok && c.tid == 0) c.tflags[0] = 1;
         top_inverse<M>(c);
         // divergence guard (see tmpc_backward.cuh): growing steps lower rho_b and restart
-        float d0 = 0.f, dprev = kInf;
+        float d0 = 0.f, dprev = kInf, dprev2 = kInf;
         int restarts = 0;
         for (int it = 0; it < o.bwd_iters; ++it) {
             for (int e = c.tid; e < T * NG; e += c.nth) gz[e] = c.Gx(ex, e / NG, e % NG);
@@ -1342,9 +1347,23 @@ __device__ __forceinline__ void backward_instance_team(Inst<M>& c, const KOpts& 
                 it = -1;
                 continue;
             }
+            dprev2 = dprev;
             dprev = dm[0];
             c.sync();
         }
+        // convergence of the refinement: the last step at the FP32 floor of the solution, or a
+        // contraction whose geometric tail (last step q / (1 - q)) is below 1e-4 of it
+        float xm[1] = {0.f};
+        for (int e = c.tid; e < T * N; e += c.nth) xm[0] = fmaxf(xm[0], fin(ex[e]));
+        team_max_k<M, 1>(c, xm, rs.red);
+        const float q = dprev / fmaxf(dprev2, 1e-30f);
+        refined_ok = dprev <= 1e-6f * xm[0] || (q < 0.9f && dprev * q / (1.f - q) <= 1e-4f * xm[0]);
+        refined_ok = refined_ok && restarts == 0 && xm[0] < kInf;
+    }
+    if (!direct_only && !refined_ok && direct_ok && o.bwd_solver == 0) {
+        for (int e = c.tid; e < T * NG; e += c.nth) mu[e] = 0.f;
+        c.sync();
+        direct_adjoint<M>(c, code, bx, ex, lam, mu, dws, dsh, c.tflags + 2, false);
     }
     for (int e = c.tid; e < T * NG; e += c.nth) gz[e] = c.Gx(ex, e / NG, e % NG);
     c.sync();

@@ -35,7 +35,7 @@ struct KOpts {
     int force_fail;   // instance index + 1 whose NOT_PD flag starts set (0: none)
     int wait_polls;   // polls of a bounded wait on an asynchronous copy (0: kMbarSpin)
     int force_timeout;   // nonzero: every bounded wait gives up at once (test hook)
-    int bwd_refine;      // 1: small models' backward by iterative refinement instead of the direct solve
+    int bwd_solver;      // backward: 0 hybrid (refinement, direct where it does not converge), 1 refinement, 2 direct
     int exact_hessian;   // 1: the direct backward adds the constraint curvature of the Lagrangian
 };
 

@@ -491,16 +491,17 @@ def test_backward_soft_rows_match_oracle(solver):
             assert rel < GRAD_TOL, (i, k, rel)
 
 
-@pytest.mark.parametrize("solver,refine", [pytest.param(1, 0, id="generic"), pytest.param(0, 0, id="smem_direct"),
-                                           pytest.param(0, 1, id="smem_refine"), pytest.param(6, 0, id="cluster_direct")])
-def test_backward_racing_on_oracle_point(solver, refine):
+@pytest.mark.parametrize("solver,bwd", [pytest.param(1, 0, id="generic_hybrid"), pytest.param(1, 2, id="generic_direct"),
+                                        pytest.param(0, 0, id="smem_hybrid"), pytest.param(0, 1, id="smem_refine"),
+                                        pytest.param(0, 2, id="smem_direct"), pytest.param(6, 2, id="cluster_direct")])
+def test_backward_racing_on_oracle_point(solver, bwd):
     """Backward of the bicycle model (implicit midpoint Jacobians, the soft
     track row, rate cost) at the oracle's SQP point: the linear algebra of
     Algorithm 2 compared at the same point, on the shared-memory, cluster and
     generic kernels."""
     pb = w.racing(B=3, N=30, max_sqp=3, max_admm=200)
     from paper_2606_24039_gb300 import Solver
-    s = Solver.from_batch(pb, device="cuda", solver=solver, bwd_refine=refine)
+    s = Solver.from_batch(pb, device="cuda", solver=solver, bwd_solver=bwd)
     refs = [osqp.solve(pb.instance(i), pb.opts) for i in range(pb.B)]
     sol = {}
     for k, kk in (("z", "z"), ("xi", "xi"), ("y_eq", "yf"), ("y_ineq", "yg")):
