@@ -134,12 +134,13 @@ typedef struct {
     int32_t wait_polls;
     int32_t force_wait_timeout;
     /* backward solver.  1 = the iterative refinement preconditioned by an FP32
-     * factorisation of the regularised system (bwd_rho, bwd_sigma, bwd_iters); 2 = one
-     * direct FP64 block LDL' factorisation of the interleaved active-set KKT system
-     * (exact up to rounding, also when the active rows are nearly dependent); 0 (the
-     * default) = the refinement, then the direct solve for every instance whose
-     * refinement did not converge.  The direct solve exists for the small models and,
-     * on the generic kernel, when nx + (nx + nu) + ng <= 32; elsewhere 0 and 2 mean 1. */
+     * factorisation of the regularised system (bwd_rho, bwd_sigma, bwd_iters); 2 (the
+     * default) = one direct FP64 block LDL' factorisation of the interleaved active-set
+     * KKT system (exact up to rounding, also when the active rows are nearly
+     * dependent); 0 = the refinement, then the direct solve for every instance whose
+     * refinement did not converge by its own step test.  The direct solve exists for
+     * the small models and, on the generic kernel, when nx + (nx + nu) + ng <= 32;
+     * elsewhere 0 and 2 mean 1. */
     int32_t bwd_solver;
     /* 1: the direct backward uses the exact Lagrangian Hessian H = Hessian of
      * l + y_f' f + y_A' g_A (App. E) at the solution, the constraint curvature by FP64

@@ -170,6 +170,7 @@ struct tmpc_handle {
     long long fstride = 0;
     double* dws = nullptr;     // FP64 workspace of the direct backward of the small models
     long long dstride = 0;
+    int* dq = nullptr;         // direct-solve queues: 4 counters per group (20), then a flag per instance
     int nsm = 0;
     int threads = 128;
     size_t smem = 0;
@@ -203,6 +204,7 @@ void tmpc_default_options(tmpc_options* o) {
     o->k_rho_iter = 25; o->k_rho_ratio = 5.f; o->max_sqp = 1; o->max_admm = 200; o->n_ls = 8;
     o->newton_steps = 3; o->early_exit = 0; o->check_every = 25;
     o->bwd_rho = 1e4f; o->bwd_sigma = 1e-6f; o->bwd_iters = 30;
+    o->bwd_solver = 2;
     o->threads = 0; o->solver = 0;
 }
 
@@ -328,10 +330,14 @@ tmpc_status ensure_buffers(tmpc_handle* h) {
     }
     // FP64 workspace of the direct backward: the small models' kernels and, where the
     // layout's interleaved KKT block fits, the generic kernel (every instance's slot)
-    long long tmax = 0;
+    long long dneed = 0;
     for (int g = 0; g < h->n_groups; ++g)
-        if (h->groups[g].model >= 0) tmax = std::max(tmax, (long long)h->groups[g].Tmax);
-    long long dneed = tmax > 0 ? fast::direct_ws_doubles((int)tmax) : 0;
+        if (h->groups[g].model >= 0)
+            dneed = std::max(dneed, fast::direct_ws_doubles(h->groups[g].model, h->groups[g].Tmax));
+    if (dneed > 0 && !h->dq) {
+        e = cudaMalloc(&h->dq, sizeof(int) * (20 + (size_t)B));
+        if (e != cudaSuccess) { set_err("cudaMalloc(direct-solve queues)", e); return TMPC_ERR_OOM; }
+    }
     const int mbg = gen_direct_mb(h->L.nx, h->L.n, h->L.ng);
     if (mbg <= kGenDirectMB) dneed = std::max(dneed, (long long)(h->L.Nmax + 1) * gen_direct_stage(mbg));
     if (dneed > 0 && dneed > h->dstride) {
@@ -752,6 +758,7 @@ tmpc_status tmpc_backward(tmpc_handle* h, const float* x0, const tmpc_solution* 
     KSol ks{sol->z, sol->xi, sol->y_eq, sol->y_ineq, sol->status, sol->stats};
     KGrads kg{g->x0, g->Qd, g->Rd, g->Wd, g->ref, g->lin, g->lo, g->hi, g->gamma2, g->gamma1};
     TMPC_CUDA(cudaMemsetAsync(h->queue, 0, sizeof(int) * 5, s));
+    if (h->dq) TMPC_CUDA(cudaMemsetAsync(h->dq, 0, sizeof(int) * (20 + (size_t)h->d.batch), s));
     const KOpts ko = to_kopts(h->o);
     const KParams kp = to_kparams(h->p);
     // one stream per shared-memory group plus the generic backward, forked from s when there are several
@@ -771,7 +778,9 @@ tmpc_status tmpc_backward(tmpc_handle* h, const float* x0, const tmpc_solution* 
         if (t) TMPC_CUDA(cudaEventRecord(h->tev[gi][2], sg));
         TMPC_CUDA(fast::launch_backward(G.model, G.cluster, G.bgrid, G.threads, G.smem, sg, h->L, ko, kp, ks, h->fws,
                                         h->fstride, h->order + G.offset, G.count, h->queue + gi, x0, h->gflags,
-                                        dL_dz, dL_dxi, kg, h->dws, h->dstride));
+                                        dL_dz, dL_dxi, kg, h->dws, h->dstride,
+                                        h->dq ? h->dq + 20 : nullptr, h->dq ? h->dq + 4 * gi : nullptr,
+                                        h->nsm));
         if (t) TMPC_CUDA(cudaEventRecord(h->tev[gi][3], sg));
         h->timed[gi][1] = t;
         if (fork) {
@@ -848,6 +857,7 @@ void tmpc_destroy(tmpc_handle* h) {
     if (h->stage) cudaFree(h->stage);
     if (h->fws) cudaFree(h->fws);
     if (h->dws) cudaFree(h->dws);
+    if (h->dq) cudaFree(h->dq);
     if (h->gflags) cudaFree(h->gflags);
     if (h->pstate) cudaFree(h->pstate);
     for (int g = 0; g < 4; ++g) {

@@ -224,7 +224,7 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
         for (int e = threadIdx.x; e < T * n; e += blockDim.x) xm[0] = fmaxf(xm[0], fin(ex[e]));
         cta_max_k<1>(xm, sm.red);
         const float q = dprev / fmaxf(dprev2, 1e-30f);
-        refined_ok = dprev <= 1e-6f * xm[0] || (q < 0.9f && dprev * q / (1.f - q) <= 1e-4f * xm[0]);
+        refined_ok = dprev <= 1e-6f * xm[0] || (q < 0.9f && dprev * q / (1.f - q) <= 1e-6f * xm[0]);
         refined_ok = refined_ok && restarts == 0 && xm[0] < kInf;
     }
     if (!direct_only && !refined_ok && direct_ok && o.bwd_solver == 0) {

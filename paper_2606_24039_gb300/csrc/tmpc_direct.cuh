@@ -9,56 +9,81 @@
 // b = dL/dz - G_s' dL/dxi, G_h the hard-active rows), is ordered stage by
 // stage with the multipliers interleaved: block t = [lambda_t (the nx rows of
 // C that start at stage t: x_0 = x_init for t = 0, f_{t-1} = 0 otherwise),
-// eta_x,t (n), eta_h,t (ng rows; an inactive row is an identity row)].  In this
-// order the matrix is block tridiagonal: the diagonal block D_t holds H_s,tt,
-// A^+_{t-1} (A_init at t = 0) and G_h,t; the coupling of block t to block t-1
-// is P_t = [A^-_{t-1}; H_{t,t-1}] on the eta_x,t-1 columns.  It is symmetric
-// and indefinite, and is factored by block LDL' without pivoting across blocks:
+// eta_x,t (n), eta_h,t (the hard-active rows of stage t)].  In this order the
+// matrix is block tridiagonal: the diagonal block D_t holds H_s,tt, A^+_{t-1}
+// (A_init at t = 0) and G_h,t; the coupling of block t to block t-1 is
+// P_t = [A^-_{t-1}; H_{t,t-1}] on the eta_x,t-1 columns.  It is symmetric and
+// indefinite, and is factored by block LDL' without pivoting across blocks:
 //     S_0 = D_0,   S_t = D_t - P_t (S_{t-1}^-1)_xx P_t',
-// each S_t inverted by Gauss-Jordan elimination with partial pivoting inside
-// the block (one warp, lane r holding row r).  The forward sweep also carries
-// y_t = r_t - P_t (S_{t-1}^-1 y_{t-1})_x; the backward sweep returns
-// x_t = S_t^-1 (y_t - P_{t+1}' x_{t+1}).  One factorisation, no refinement.
+// each S_t inverted in place by Gauss-Jordan elimination with partial pivoting
+// inside the block.  The forward sweep also carries y_t = r_t - P_t w_{t-1},
+// w_t = (S_t^-1 y_t)_x; the backward sweep returns x_t = S_t^-1 (y_t - P_{t+1}' x_{t+1}).
+// One factorisation, no refinement.
 //
 // FP64 because the active-set KKT of a constrained OCP can be ill-conditioned
 // (condition numbers near 1e10 on the racing model where bound rows nearly
 // repeat the dynamics rows), beyond what an FP32 factorisation resolves.  If a
 // pivot block is numerically singular (the active rows are linearly dependent),
 // the solve is repeated with -1e-10 on the multiplier diagonal.
+//
+// Work split: the instance's team evaluates everything that is parallel over
+// the stages (FP64 Jacobians at the returned point, the constraint curvature of
+// the exact Hessian, the active codes, the right-hand side and the cost
+// diagonal) into a per-stage FP64 record; the sweeps, sequential over the
+// stages, are one warp's (lane r holds row r of the block).  GB300 executes FP64
+// at a small fraction of its FP32 rate, so the sweeps are bound by the FP64 pipe
+// of the SM sub-partition the warp runs on: the CTA kernels hand the sweeps to
+// a kernel of independent warps (one instance each, all four sub-partitions of
+// every SM busy) and finish the gradients in a third pass; a cluster team runs
+// them on its first warp.  To keep the FP64 instruction count low, the block
+// drops the inactive bound rows (size nx + n + active rows, a template
+// parameter), the inversion is in place (one row of the block per lane, half
+// the work of inverting [S | I]), and the Schur complement is spread over all
+// 32 lanes.
 #pragma once
 #include "tmpc_fast.cuh"
 
 namespace tmpc {
 namespace fast {
 
-// doubles of the FP64 workspace per stage: S_t^-1 (MB^2), y_t (MB), then the FP64
-// Jacobian A^-_t (NX x N) and the dense row of G_t (N), then (exact Hessian) the
-// constraint-curvature blocks of the Lagrangian: Ccur_tt from f_t and the track row,
-// C'_tt from f_{t-1}, C_{t,t-1} from f_{t-1} (N x N each);
-// MB <= kDirectMB, NX N <= 48, N <= 8
-constexpr int kDirectMB = 19;
-constexpr long long kDirectJac = (long long)kDirectMB * kDirectMB + kDirectMB;
-constexpr long long kDirectCurv = kDirectJac + 48 + 8;
-constexpr long long kDirectStage = kDirectCurv + 3 * 64;
 constexpr double kCurvStep = 1e-6;   // central-difference step of the constraint curvature
-// shared scratch of the sweep (X, pivot row, y / v, w): N^2 + 2 MB + MB + N doubles
-constexpr int kDirectScratch = 64 + 3 * kDirectMB + 8;
 
+// Per-stage FP64 record of one instance (doubles), and the compile-time sizes
+//   MB  = nx + n + ng: largest block (every bound row hard-active)
+//   XH  = nx + n: the lambda and eta_x rows, always present
 template <int M>
-struct Kkt {
-    static constexpr int NX = Traits<M>::NX, N = NX + Traits<M>::NU, NG = Traits<M>::NG;
-    static constexpr int MB = NX + N + NG;   // block size
-    static constexpr int XZ = NX;            // first eta_x row of a block
-    static constexpr int XH = NX + N;        // first eta_h row
-    static_assert(MB <= kDirectMB, "block of the direct adjoint solve");
+struct DRec {
+    static constexpr int NX = Traits<M>::NX, NU = Traits<M>::NU, N = NX + NU, NG = Traits<M>::NG;
+    static constexpr int MB = NX + N + NG, XZ = NX, XH = NX + N;
+    static constexpr int Inv = 0;                 // S_t^-1, MB x MB (active-row order)
+    static constexpr int Y = Inv + MB * MB;       // y_t, MB
+    static constexpr int Am = Y + MB;             // A^-_t, NX x N
+    static constexpr int G = Am + NX * N;         // dense row of G_t, N
+    static constexpr int Ct = G + N;              // exact Hessian: curvature of stage t's terms, N x N
+    static constexpr int Cn = Ct + N * N;         //   of f_{t-1} on z_t (t >= 1), N x N
+    static constexpr int Cl = Cn + N * N;         //   of f_{t-1}, block (t, t-1), N x N
+    static constexpr int Code = Cl + N * N;       // active codes, NG
+    static constexpr int B = Code + NG;           // right-hand side b, N
+    static constexpr int Hd = B + N;              // diagonal of the cost Hessian block, N
+    static constexpr int X = Hd + N;              // solution [lambda_t, eta_x,t, eta_h,t] (all NG rows), MB
+    static constexpr int Par = X + MB;            // stage 0 only: W (NU), gamma2 (NG)
+    static constexpr int Stage = (Par + NU + NG + 1) & ~1;
+    // per-warp shared scratch of the sweeps: X_{t-1} (N^2), P_t and U = P_t X_{t-1}
+    // (XH N each), U P_t' (XH^2), pivot row (MB), y_t (MB), w_{t-1} (N), x_{t+1} (XH)
+    static constexpr int Scratch = N * N + 2 * XH * N + XH * XH + 2 * MB + N + XH;
+    static_assert(MB <= 32, "one lane per row of the block");
 };
 
-// Entry (j, b) of P_t restricted to the eta_x rows: H_{t,t-1}, the (t, t-1) block
-// of the cost Hessian (-W on the control diagonal, from the rate cost).
-template <int M>
-__device__ __forceinline__ double Hsub(const Inst<M>& c, int j, int b) {
-    return (j == b && j >= Inst<M>::NX) ? -(double)c.W(j - Inst<M>::NX) : 0.0;
-}
+// Largest per-warp scratch over the small models (the bicycle's)
+constexpr int kDirectScratch = 544;
+
+// Instances handed from the backward kernel to the sweep kernel: flag[i] = 1 for
+// instance i (global index); the sweep kernel and the finishing pass walk the
+// group's instance order (longest first) and take the flagged ones
+struct DirectQueue {
+    int* flag;
+};
+constexpr int kDirectWarps = 8;   // warps per CTA of the sweep kernel
 
 // Diagonal of the cost Hessian block D_t (App. B: D_t = H^+_{t-1} + H^-_t), in FP64
 template <int M>
@@ -141,16 +166,18 @@ __device__ __forceinline__ void jacobians_fp64(const Inst<M>& c, int t, double* 
 // H = Hessian of l + y_f' f + y_A' g_A), by FP64 central differences (step
 // kCurvStep) of the FP64 analytic Jacobians:
 //   f_t with multiplier y = y_f[t+1]: psi(z_t, z_{t+1}) = [A^-' y; A^+' y] over the 2N
-//   coordinates -> blocks (t,t) into Ct[t], (t+1,t+1) into Cn[t+1], (t+1,t) into Cl[t+1];
-//   the active track row with multiplier y_g: Hessian of g into Ct[t].
-// Stage t's thread writes Ct[t] and the Cn, Cl slots of stage t+1 (no other writer).
+//   coordinates -> blocks (t,t) into Ct of stage t, (t+1,t+1) into Cn and (t+1,t)
+//   into Cl of stage t+1;
+//   the active track row with multiplier y_g: Hessian of g into Ct of stage t.
+// Stage t's thread writes Ct of stage t and Cn, Cl of stage t+1 (no other writer).
 template <int M>
 __device__ __forceinline__ void curvature_fp64(const Inst<M>& c, const float* code, int t, double* dws) {
     using Tr = Traits<M>;
+    using R = DRec<M>;
     constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
-    double* Ct = dws + (long long)t * kDirectStage + kDirectCurv;
-    double* Cn = dws + (long long)(t + 1) * kDirectStage + kDirectCurv + 64;
-    double* Cl = Cn + 64;
+    double* Ct = dws + (long long)t * R::Stage + R::Ct;
+    double* Cn = dws + (long long)(t + 1) * R::Stage + R::Cn;
+    double* Cl = dws + (long long)(t + 1) * R::Stage + R::Cl;
     double z0[2 * N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
@@ -158,10 +185,11 @@ __device__ __forceinline__ void curvature_fp64(const Inst<M>& c, const float* co
         z0[N + j] = t < c.Nh ? (double)c.zb[(t + 1) * N + j] : 0.0;
     }
     for (int i = 0; i < N * N; ++i) Ct[i] = 0.0;
-    if (t == 0) {
-        double* C0 = dws + kDirectCurv + 64;
-        for (int i = 0; i < 2 * N * N; ++i) C0[i] = 0.0;
-    }
+    if (t == 0)
+        for (int i = 0; i < N * N; ++i) {
+            dws[R::Cn + i] = 0.0;
+            dws[R::Cl + i] = 0.0;
+        }
     if (t < c.Nh && M != MODEL_DI) {
         double y[NX];
 #pragma unroll
@@ -203,7 +231,10 @@ __device__ __forceinline__ void curvature_fp64(const Inst<M>& c, const float* co
                 Cl[i * N + j] = Hc[N + i][j];
             }
     } else if (t < c.Nh) {
-        for (int i = 0; i < 2 * N * N; ++i) Cn[i] = 0.0;
+        for (int i = 0; i < N * N; ++i) {
+            Cn[i] = 0.0;
+            Cl[i] = 0.0;
+        }
     }
     if constexpr (Tr::DENSE_ROW >= 0) {
         const int q = Tr::DENSE_ROW;
@@ -228,241 +259,366 @@ __device__ __forceinline__ void curvature_fp64(const Inst<M>& c, const float* co
     }
 }
 
-// Solve by warp 0 of the team.  code: active-set codes (0 inactive, +-1 hard,
-// +-2 slack-active) per row; bx: the right-hand side b per stage entry; outputs
-// eta_x -> ex, eta_f -> lam (per stage, nx), eta_h -> mu (hard-active rows, 0
-// elsewhere).  dws: the instance's FP64 workspace (T kDirectStage doubles);
-// sh: shared scratch of at least (N^2 + 3 MB + N) doubles, 8-byte aligned.
-// Returns (to every thread of the team) true if the regularised solve was needed.
+// The team's part before the sweeps: per stage the FP64 Jacobians (and, with
+// the exact Hessian, the constraint curvature), the active codes, the
+// right-hand side b and the diagonal of the cost Hessian; W and gamma2 in
+// stage 0's record.  code: 0 inactive, +-1 hard-active, +-2 slack-active.
 template <int M>
-__device__ bool direct_adjoint(const Inst<M>& c, const float* code, const float* bx, float* ex, float* lam,
-                               float* mu, double* dws, double* sh, int* flag, bool exact) {
-    using K = Kkt<M>;
-    constexpr int NX = K::NX, N = K::N, NG = K::NG, MB = K::MB, XZ = K::XZ, XH = K::XH;
-    const int T = c.T;
-    double* X = sh;                 // (S_{t-1}^-1)_xx, N x N
-    double* prow = X + N * N;       // pivot row broadcast: [a | e], 2 MB
-    double* yv = prow + 2 * MB;     // y_t / v_t broadcast, MB
-    double* wv = yv + MB;           // w_{t-1} = (S_{t-1}^-1 y_{t-1})_x, N
-    const bool warp0 = c.tid < 32;
-    const int lane = c.tid & 31;
-    const bool row = warp0 && lane < MB;
-    for (int t = c.tid; t < T; t += c.nth) {
-        double* st = dws + (long long)t * kDirectStage + kDirectJac;
-        jacobians_fp64<M>(c, t, st, st + 48);
+__device__ void direct_store(const Inst<M>& c, const float* code, const float* bx, double* dws, bool exact) {
+    using R = DRec<M>;
+    constexpr int N = R::N, NG = R::NG, NU = R::NU;
+    for (int t = c.tid; t < c.T; t += c.nth) {
+        double* r = dws + (long long)t * R::Stage;
+        jacobians_fp64<M>(c, t, r + R::Am, r + R::G);
         if (exact) curvature_fp64<M>(c, code, t, dws);
+#pragma unroll
+        for (int q = 0; q < NG; ++q) r[R::Code + q] = (double)code[t * NG + q];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            r[R::B + j] = (double)bx[t * N + j];
+            r[R::Hd + j] = Hdiag<M>(c, t, j);
+        }
+        if (t == 0) {
+#pragma unroll
+            for (int k = 0; k < NU; ++k) r[R::Par + k] = (double)c.W(k);
+#pragma unroll
+            for (int q = 0; q < NG; ++q) r[R::Par + NU + q] = (double)c.gam2(q);
+        }
     }
-    if (c.tid == 0) *flag = 0;
-    c.sync();
-    // FP64 blocks: A^-_t, A^+_t (implicit: A^-_x - 2I; explicit: -I on the states), G_t
-    auto Amd = [&](int t) -> const double* { return dws + (long long)t * kDirectStage + kDirectJac; };
-    auto Apd = [&](int t, int k, int j) -> double {
+}
+
+// The team's part after the sweeps: eta_x -> ex, eta_f -> lam, eta_h -> mu
+// (hard-active rows; 0 elsewhere), rounded to FP32.
+template <int M>
+__device__ void direct_load(const Inst<M>& c, const double* dws, float* ex, float* lam, float* mu) {
+    using R = DRec<M>;
+    constexpr int NX = R::NX, N = R::N, NG = R::NG;
+    for (int e = c.tid; e < c.T * R::MB; e += c.nth) {
+        const int t = e / R::MB, r = e % R::MB;
+        const double* rt = dws + (long long)t * R::Stage;
+        const double x = rt[R::X + r];
+        if (r < NX) lam[t * NX + r] = (float)x;
+        else if (r < R::XH) ex[t * N + r - NX] = (float)x;
+        else mu[t * NG + r - R::XH] = (float)x;
+    }
+}
+
+// FP64 reciprocal by Newton-Raphson iteration y <- y (2 - x y) from the FP32
+// estimate (two steps: the relative error squares from ~2^-23 to below FP64
+// rounding).  For |x| well inside the FP32 normal range; the caller divides
+// outside it.
+__device__ __forceinline__ double recip_nr(double x) {
+    double y = (double)(1.0f / (float)x);
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+
+// In-place Gauss-Jordan inversion of the K x K block held one row per lane
+// (lanes K..31 idle), partial pivoting on the rows not yet pivoted.  Step p: the
+// pivot row is broadcast unscaled (its entry p replaced by 1) and every lane
+// applies one FMA per column, v = v inv on the pivot row, v -= (v_p inv) prow on
+// the others (the in-place form, entry p first set to 1 or 0).  On return the
+// lane that pivoted at step p holds row p of S^-1 with its entries in the order of
+// the pivot steps: v[j] = (S^-1)(p, pw[j]), pw[j] the lane (row) that pivoted at
+// step j.  Returns 1 if a pivot fell below 1e-13 of the block's largest entry
+// (numerically singular).
+template <int MB, int K>
+__device__ __forceinline__ int gj_inplace(double (&v)[MB], int (&pw)[MB], int& mypiv, double* prow, int lane) {
+    static_assert(K <= MB && K <= 32, "block size");
+    double amax = 0.0;
+#pragma unroll
+    for (int q = 0; q < K; ++q) amax = fmax(amax, fabs(v[q]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    const double tiny = 1e-13 * (amax > 0.0 ? amax : 1.0);
+    bool used = lane >= K;
+    int singular = 0;
+    mypiv = -1;
+#pragma unroll
+    for (int p = 0; p < K; ++p) {
+        double cand = used ? -1.0 : fabs(v[p]);
+        int who = lane;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double oc = __shfl_xor_sync(0xffffffffu, cand, o);
+            const int ow = __shfl_xor_sync(0xffffffffu, who, o);
+            if (oc > cand || (oc == cand && ow < who)) { cand = oc; who = ow; }
+        }
+        pw[p] = who;
+        const bool ok = cand > tiny;
+        if (!ok) singular = 1;
+        const double piv = __shfl_sync(0xffffffffu, v[p], who);
+        const double ap = fabs(piv);
+        const double inv = (ap > 1e-30 && ap < 1e30) ? recip_nr(piv) : (piv != 0.0 ? 1.0 / piv : 0.0);
+        const bool me = lane == who;
+        if (me) {
+            used = true;
+            mypiv = p;
+#pragma unroll
+            for (int q = 0; q < K; ++q) prow[q] = q == p ? 1.0 : v[q];
+        }
+        __syncwarp();
+        const double g = me ? 0.0 : v[p] * inv;
+        v[p] = me ? 1.0 : 0.0;
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const double pq = prow[q];
+            v[q] = me ? v[q] * inv : fma(-g, pq, v[q]);
+        }
+        __syncwarp();
+    }
+    return singular;
+}
+
+// One stage of the forward sweep after D_t - P_t X_{t-1} P_t' is in v (row `lane`):
+// invert in place, store S_t^-1 (active-row order), w_t = (S_t^-1 y_t)_x into wv and
+// X_t = (S_t^-1)_xx into X.  yv holds y_t.
+template <int M, int K>
+__device__ __forceinline__ int sweep_block(double (&v)[DRec<M>::MB], double* rt, double* X, double* prow,
+                                           const double* yv, double* wv, int lane) {
+    using R = DRec<M>;
+    constexpr int MB = R::MB, XZ = R::XZ, XH = R::XH, N = R::N;
+    int pw[MB];
+    int mypiv;
+    const int sing = gj_inplace<MB, K>(v, pw, mypiv, prow, lane);
+    if (mypiv >= 0) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            rt[R::Inv + mypiv * MB + pw[j]] = v[j];
+            s += v[j] * yv[pw[j]];
+        }
+        if (mypiv >= XZ && mypiv < XH) {
+            wv[mypiv - XZ] = s;
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if (pw[j] >= XZ && pw[j] < XH) X[(mypiv - XZ) * N + pw[j] - XZ] = v[j];
+        }
+    }
+    __syncwarp();
+    return sing;
+}
+
+template <int M, int E>
+__device__ __forceinline__ int sweep_block_k(int K, double (&v)[DRec<M>::MB], double* rt, double* X, double* prow,
+                                             const double* yv, double* wv, int lane) {
+    using R = DRec<M>;
+    if constexpr (E >= R::NG) {
+        return sweep_block<M, R::XH + R::NG>(v, rt, X, prow, yv, wv, lane);
+    } else {
+        if (K == R::XH + E) return sweep_block<M, R::XH + E>(v, rt, X, prow, yv, wv, lane);
+        return sweep_block_k<M, E + 1>(K, v, rt, X, prow, yv, wv, lane);
+    }
+}
+
+// The sweeps of one instance (T stages, records at dws), by one warp; sh: the
+// warp's DRec<M>::Scratch doubles of shared memory.  Leaves the solution in the
+// records (DRec::X).  Returns (warp-uniform) 1 if the regularised solve was needed.
+template <int M>
+__device__ int direct_sweep(int T, double* dws, double* sh, bool exact) {
+    using R = DRec<M>;
+    using Tr = Traits<M>;
+    constexpr int NX = R::NX, N = R::N, NG = R::NG, NU = R::NU, MB = R::MB, XZ = R::XZ, XH = R::XH;
+    static_assert(R::Scratch <= kDirectScratch, "per-warp scratch of the sweeps");
+    const int lane = threadIdx.x & 31;
+    double* X = sh;              // X_{t-1} = (S_{t-1}^-1)_xx, N x N
+    double* Pm = X + N * N;      // P_t, XH x N
+    double* U = Pm + XH * N;     // P_t X_{t-1}, XH x N  (Schur product U P_t' re-uses Pm)
+    double* Sc = U + XH * N;     // U P_t', XH x XH
+    double* prow = Sc + XH * XH; // pivot row / right-hand side broadcast, MB
+    double* yv = prow + MB;      // y_t, MB
+    double* wv = yv + MB;        // w_{t-1}, N
+    double* xn = wv + N;         // [lambda, eta_x] of stage t+1 in the backward sweep, XH
+    const double* par = dws + R::Par;
+    auto rec = [&](int t) -> double* { return dws + (long long)t * R::Stage; };
+    // P_t entry (r, b), r < XH: rows of A^-_{t-1}, then H_{t,t-1} (-W on the control
+    // diagonal from the rate cost, plus the curvature block of f_{t-1})
+    auto Pent = [&](int t, int r, int b) -> double {
+        if (r < XZ) return rec(t - 1)[R::Am + r * N + b];
+        const int j = r - XZ;
+        double h = (j == b && j >= NX) ? -par[j - NX] : 0.0;
+        if (exact) h += rec(t)[R::Cl + j * N + b];
+        return h;
+    };
+    auto Apd = [&](int t, int k, int j) -> double {   // A^+_t (k, j)
         if (j >= NX) return 0.0;
-        if (Traits<M>::IMPLICIT) return Amd(t)[k * N + j] - (k == j ? 2.0 : 0.0);
+        if (Tr::IMPLICIT) return rec(t)[R::Am + k * N + j] - (k == j ? 2.0 : 0.0);
         return k == j ? -1.0 : 0.0;
     };
-    // cost Hessian blocks plus, with the exact Hessian, the constraint curvature
-    auto Htt = [&](int t, int j, int jj) -> double {
-        double h = j == jj ? Hdiag<M>(c, t, j) : 0.0;
-        if (exact) {
-            const double* cv = dws + (long long)t * kDirectStage + kDirectCurv;
-            h += cv[j * N + jj] + (t > 0 ? cv[64 + j * N + jj] : 0.0);
-        }
-        return h;
-    };
-    auto Hlow = [&](int t, int j, int b) -> double {   // (t, t-1) block, t >= 1
-        double h = Hsub<M>(c, j, b);
-        if (exact) h += (dws + (long long)t * kDirectStage + kDirectCurv + 128)[j * N + b];
-        return h;
-    };
-    auto Gd = [&](int t, int q, int j) -> double {
-        const int s = Traits<M>::sel(q);
+    auto Gd = [&](const double* rt, int q, int j) -> double {
+        const int s = Tr::sel(q);
         if (s >= 0) return j == s ? 1.0 : 0.0;
-        return (dws + (long long)t * kDirectStage + kDirectJac + 48)[j];
+        return rt[R::G + j];
     };
+    // active-row positions of stage t's hard-active rows (pos[q] = -1 if not hard-active)
+    auto active = [&](const double* rt, int (&pos)[NG], int& myq) -> int {
+        int nact = 0;
+        myq = -1;
+#pragma unroll
+        for (int q = 0; q < NG; ++q) {
+            const double cd = rt[R::Code + q];
+            const bool hard = cd != 0.0 && fabs(cd) < 1.5;
+            pos[q] = hard ? nact : -1;
+            if (hard && lane == XH + nact) myq = q;
+            nact += hard ? 1 : 0;
+        }
+        return XH + nact;
+    };
+    int regularised = 0;
     for (int pass = 0; pass < 2; ++pass) {
         const double delta = pass == 0 ? 0.0 : 1e-10;
-        if (warp0) {
-            int singular = 0;
-            for (int t = 0; t < T; ++t) {
-                // ---- row `lane` of D_t ----
-                double a[MB], e[MB];
-#pragma unroll
-                for (int q = 0; q < MB; ++q) { a[q] = 0.0; e[q] = (q == lane) ? 1.0 : 0.0; }
-                if (row) {
-                    if (lane < XZ) {                         // lambda_t row k
-                        const int k = lane;
-#pragma unroll
-                        for (int j = 0; j < N; ++j)
-                            a[XZ + j] = t == 0 ? (j == k ? 1.0 : 0.0) : Apd(t - 1, k, j);
-                        a[k] = -delta;
-                    } else if (lane < XH) {                  // eta_x,t row j
-                        const int j = lane - XZ;
-#pragma unroll
-                        for (int k = 0; k < NX; ++k)
-                            a[k] = t == 0 ? (j == k ? 1.0 : 0.0) : Apd(t - 1, k, j);
-#pragma unroll
-                        for (int jj = 0; jj < N; ++jj) a[XZ + jj] = Htt(t, j, jj);
-#pragma unroll
-                        for (int q = 0; q < NG; ++q) {
-                            const float cd = code[t * NG + q];
-                            const double g = Gd(t, q, j);
-                            if (fabsf(cd) > 1.5f) {          // slack-active: gamma2 G_q' G_q
-#pragma unroll
-                                for (int jj = 0; jj < N; ++jj)
-                                    a[XZ + jj] += (double)c.gam2(q) * g * Gd(t, q, jj);
-                            } else if (cd != 0.f) {
-                                a[XH + q] = g;
-                            }
-                        }
-                    } else {                                 // eta_h,t row q
-                        const int q = lane - XH;
-                        const float cd = code[t * NG + q];
-                        if (cd != 0.f && fabsf(cd) < 1.5f) {
-#pragma unroll
-                            for (int j = 0; j < N; ++j) a[XZ + j] = Gd(t, q, j);
-                            a[lane] = -delta;
-                        } else {
-                            a[lane] = 1.0;
-                        }
-                    }
-                    // ---- Schur complement: - P_t X P_t' on the lambda / eta_x rows and columns ----
-                    if (t > 0 && lane < XH) {
-                        double pr[N];   // row `lane` of P_t
-#pragma unroll
-                        for (int b = 0; b < N; ++b)
-                            pr[b] = lane < XZ ? Amd(t - 1)[lane * N + b] : Hlow(t, lane - XZ, b);
-                        double u[N];
-#pragma unroll
-                        for (int b = 0; b < N; ++b) {
-                            double s = 0.0;
-#pragma unroll
-                            for (int q = 0; q < N; ++q) s += pr[q] * X[q * N + b];
-                            u[b] = s;
-                        }
-#pragma unroll
-                        for (int col = 0; col < XH; ++col) {
-                            double s = 0.0;
-#pragma unroll
-                            for (int b = 0; b < N; ++b)
-                                s += u[b] * (col < XZ ? Amd(t - 1)[col * N + b] : Hlow(t, col - XZ, b));
-                            a[col] -= s;
-                        }
-                    }
-                }
-                // ---- Gauss-Jordan with partial pivoting: [S_t | I] -> rows of S_t^-1 ----
-                double amax = 0.0;
-#pragma unroll
-                for (int q = 0; q < MB; ++q) amax = fmax(amax, fabs(a[q]));
-                for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-                const double tiny = 1e-13 * (amax > 0.0 ? amax : 1.0);
-                bool used = !row;
-                int mypiv = -1;
-#pragma unroll
-                for (int p = 0; p < MB; ++p) {
-                    double cand = used ? -1.0 : fabs(a[p]);
-                    int who = lane;
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const double oc = __shfl_xor_sync(0xffffffffu, cand, o);
-                        const int ow = __shfl_xor_sync(0xffffffffu, who, o);
-                        if (oc > cand || (oc == cand && ow < who)) { cand = oc; who = ow; }
-                    }
-                    if (!(cand > tiny)) singular = 1;
-                    if (lane == who) {
-                        used = true;
-                        mypiv = p;
-                        const double inv = (a[p] != 0.0) ? 1.0 / a[p] : 0.0;
-#pragma unroll
-                        for (int q = 0; q < MB; ++q) {
-                            a[q] *= inv;
-                            e[q] *= inv;
-                            prow[q] = a[q];
-                            prow[MB + q] = e[q];
-                        }
-                    }
-                    __syncwarp();
-                    if (row && lane != who) {
-                        const double f = a[p];
-#pragma unroll
-                        for (int q = 0; q < MB; ++q) {
-                            a[q] -= f * prow[q];
-                            e[q] -= f * prow[MB + q];
-                        }
-                    }
-                    __syncwarp();
-                }
-                // lane with pivot column p holds row p of S_t^-1
-                double* Sinv = dws + (long long)t * kDirectStage;
-                if (row) {
-#pragma unroll
-                    for (int q = 0; q < MB; ++q) Sinv[mypiv * MB + q] = e[q];
-                }
-                // ---- forward substitution: y_t = r_t - P_t w_{t-1} ----
-                if (row) {
-                    double y = 0.0;
-                    if (lane >= XZ && lane < XH) y = (double)bx[t * N + lane - XZ];
-                    if (t > 0 && lane < XH) {
-#pragma unroll
-                        for (int b = 0; b < N; ++b)
-                            y -= (lane < XZ ? Amd(t - 1)[lane * N + b] : Hlow(t, lane - XZ, b)) * wv[b];
-                    }
-                    yv[lane] = y;
-                    Sinv[MB * MB + lane] = y;
-                }
+        int singular = 0;
+        for (int t = 0; t < T; ++t) {
+            double* rt = rec(t);
+            int pos[NG], myq;
+            const int K = active(rt, pos, myq);
+            if (t > 0) {   // P_t, then U = P_t X_{t-1}, then Sc = U P_t' over all lanes
+                for (int e = lane; e < XH * N; e += 32) Pm[e] = Pent(t, e / N, e % N);
                 __syncwarp();
-                // w_t = (S_t^-1 y_t)_x and X_t = (S_t^-1)_xx (rows XZ..XH-1, columns XZ..XH-1)
-                if (row && mypiv >= XZ && mypiv < XH) {
+                for (int e = lane; e < XH * N; e += 32) {
+                    const int r = e / N, b = e % N;
                     double s = 0.0;
 #pragma unroll
-                    for (int q = 0; q < MB; ++q) s += e[q] * yv[q];
-                    wv[mypiv - XZ] = s;
-#pragma unroll
-                    for (int j = 0; j < N; ++j) X[(mypiv - XZ) * N + j] = e[XZ + j];
+                    for (int q = 0; q < N; ++q) s += Pm[r * N + q] * X[q * N + b];
+                    U[e] = s;
                 }
                 __syncwarp();
+                for (int e = lane; e < XH * XH; e += 32) {
+                    const int r = e / XH, cc = e % XH;
+                    double s = 0.0;
+#pragma unroll
+                    for (int b = 0; b < N; ++b) s += U[r * N + b] * Pm[cc * N + b];
+                    Sc[e] = s;
+                }
             }
-            // ---- backward sweep: x_t = S_t^-1 (y_t - P_{t+1}' x_{t+1}) ----
-            double* xnext = wv;   // eta_x,t+1 and lambda_{t+1} of the step before, in yv / wv
-            for (int t = T - 1; t >= 0; --t) {
-                const double* Sinv = dws + (long long)t * kDirectStage;
-                if (row) {
-                    double v = Sinv[MB * MB + lane];
-                    if (t < T - 1 && lane >= XZ && lane < XH) {
-                        const int b = lane - XZ;
-                        double s = 0.0;
+            // y_t = r_t - P_t w_{t-1} (row `lane`; r_t = b on the eta_x rows)
+            if (lane < K) {
+                double y = 0.0;
+                if (lane >= XZ && lane < XH) y = rt[R::B + lane - XZ];
+                if (t > 0 && lane < XH) {
 #pragma unroll
-                        for (int k = 0; k < NX; ++k) s += Amd(t)[k * N + b] * yv[k];
-#pragma unroll
-                        for (int j = 0; j < N; ++j) s += Hlow(t + 1, j, b) * xnext[j];
-                        v -= s;
-                    }
-                    prow[lane] = v;
+                    for (int b = 0; b < N; ++b) y -= Pm[lane * N + b] * wv[b];
                 }
-                __syncwarp();
-                double x = 0.0;
-                if (row) {
-#pragma unroll
-                    for (int q = 0; q < MB; ++q) x += Sinv[lane * MB + q] * prow[q];
-                }
-                __syncwarp();
-                if (row) {
-                    if (lane < XZ) { lam[t * NX + lane] = (float)x; yv[lane] = x; }
-                    else if (lane < XH) { ex[t * N + lane - XZ] = (float)x; xnext[lane - XZ] = x; }
-                    else {
-                        const float cd = code[t * NG + lane - XH];
-                        mu[t * NG + lane - XH] = (cd != 0.f && fabsf(cd) < 1.5f) ? (float)x : 0.f;
-                    }
-                }
-                __syncwarp();
+                yv[lane] = y;
+                rt[R::Y + lane] = y;
             }
-            if (lane == 0) *flag = singular;
+            __syncwarp();
+            // row `lane` of S_t = D_t - Sc (active-row order)
+            double v[MB];
+#pragma unroll
+            for (int q = 0; q < MB; ++q) v[q] = 0.0;
+            if (lane < XZ) {                        // lambda_t row k: [-delta e_k | A^+_{t-1}(k, :) | 0]
+#pragma unroll
+                for (int j = 0; j < N; ++j) v[XZ + j] = t == 0 ? (j == lane ? 1.0 : 0.0) : Apd(t - 1, lane, j);
+#pragma unroll
+                for (int q = 0; q < XZ; ++q)
+                    if (q == lane) v[q] = -delta;
+            } else if (lane < XH) {                 // eta_x,t row j
+                const int j = lane - XZ;
+#pragma unroll
+                for (int k = 0; k < NX; ++k) v[k] = t == 0 ? (j == k ? 1.0 : 0.0) : Apd(t - 1, k, j);
+#pragma unroll
+                for (int jj = 0; jj < N; ++jj) {
+                    double h = jj == j ? rt[R::Hd + j] : 0.0;
+                    if (exact) h += rt[R::Ct + j * N + jj] + (t > 0 ? rt[R::Cn + j * N + jj] : 0.0);
+                    v[XZ + jj] = h;
+                }
+#pragma unroll
+                for (int q = 0; q < NG; ++q) {
+                    const double cd = rt[R::Code + q];
+                    const double g = Gd(rt, q, j);
+                    if (fabs(cd) > 1.5) {           // slack-active: gamma2 G_q' G_q
+#pragma unroll
+                        for (int jj = 0; jj < N; ++jj) v[XZ + jj] += par[NU + q] * g * Gd(rt, q, jj);
+                    }
+#pragma unroll
+                    for (int m = 0; m < NG; ++m)
+                        if (pos[q] == m) v[XH + m] = g;
+                }
+            } else if (myq >= 0) {                  // eta_h row of hard-active row myq
+#pragma unroll
+                for (int j = 0; j < N; ++j) v[XZ + j] = Gd(rt, myq, j);
+#pragma unroll
+                for (int q = XH; q < MB; ++q)
+                    if (q == lane) v[q] = -delta;
+            }
+            if (t > 0 && lane < XH) {
+#pragma unroll
+                for (int cc = 0; cc < XH; ++cc) v[cc] -= Sc[lane * XH + cc];
+            }
+            singular |= sweep_block_k<M, 0>(K, v, rt, X, prow, yv, wv, lane);
+            if (pass == 0 && singular) break;   // warp-uniform: redo with the regularisation
         }
-        c.sync();
-        const bool sing = *flag != 0;
-        c.sync();
-        if (!sing) return pass > 0;
+        if (pass == 0 && singular) {
+            regularised = 1;
+            continue;
+        }
+        // backward sweep: x_t = S_t^-1 (y_t - P_{t+1}' x_{t+1})
+        for (int t = T - 1; t >= 0; --t) {
+            double* rt = rec(t);
+            int pos[NG], myq;
+            const int K = active(rt, pos, myq);
+            if (lane < K) {
+                double v = rt[R::Y + lane];
+                if (t < T - 1 && lane >= XZ && lane < XH) {
+                    const int b = lane - XZ;
+                    double s = 0.0;
+#pragma unroll
+                    for (int r = 0; r < XH; ++r) s += Pent(t + 1, r, b) * xn[r];
+                    v -= s;
+                }
+                prow[lane] = v;
+            }
+            __syncwarp();
+            double x = 0.0;
+            if (lane < K) {
+                const double* Si = rt + R::Inv + lane * MB;
+#pragma unroll
+                for (int q = 0; q < MB; ++q)
+                    if (q < K) x += Si[q] * prow[q];
+            }
+            __syncwarp();
+            if (lane < XH) {
+                xn[lane] = x;
+                rt[R::X + lane] = x;
+            } else if (myq >= 0) {
+                rt[R::X + XH + myq] = x;
+            }
+            if (lane < NG && lane >= 0) {
+                // inactive and slack-active rows carry no multiplier in this system
+                const double cd = rt[R::Code + lane];
+                if (!(cd != 0.0 && fabs(cd) < 1.5)) rt[R::X + XH + lane] = 0.0;
+            }
+            __syncwarp();
+        }
+        break;
     }
-    return true;
+    return regularised;
+}
+
+// The sweeps as a kernel of independent warps: each warp takes the next entry of
+// the group's instance order (longest first) from an atomic cursor and sweeps it
+// if the backward pass flagged it.  blockDim = kDirectWarps * 32.
+template <int M>
+__global__ void __launch_bounds__(kDirectWarps * 32, 1) direct_kernel(const int* N, const int* order, int count,
+                                                                      const int* flag, int* cursor, double* dws,
+                                                                      long long dstride, int exact) {
+    __shared__ double sh[kDirectWarps][kDirectScratch];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        int k = 0;
+        if (lane == 0) {
+            do {
+                k = atomicAdd(cursor, 1);
+            } while (k < count && !flag[order[k]]);
+        }
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= count) break;
+        const int i = order[k];
+        direct_sweep<M>(N[i] + 1, dws + (long long)i * dstride, sh[w], exact != 0);
+    }
 }
 
 }  // namespace fast

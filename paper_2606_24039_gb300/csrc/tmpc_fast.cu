@@ -3,6 +3,8 @@
 // kernel tables of tmpc_fast_di.cu, tmpc_fast_bicycle.cu and tmpc_fast_quad.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "../../include/tmpc.h"
 #include "tmpc_direct.cuh"
 #include "tmpc_fast.cuh"
@@ -24,7 +26,14 @@ long long arena_floats_host(int model, int T, int policy, int cluster) {
     return -1;
 }
 
-long long direct_ws_doubles(int T) { return (long long)T * kDirectStage; }
+long long direct_ws_doubles(int model, int T) {
+    switch (model) {
+        case MODEL_DI: return (long long)T * DRec<MODEL_DI>::Stage;
+        case MODEL_BICYCLE: return (long long)T * DRec<MODEL_BICYCLE>::Stage;
+        case MODEL_QUAD: return (long long)T * DRec<MODEL_QUAD>::Stage;
+    }
+    return 0;
+}
 
 bool supported(int model) { return model == MODEL_DI || model == MODEL_BICYCLE || model == MODEL_QUAD; }
 
@@ -124,7 +133,7 @@ cudaError_t launch_backward(int model, int cl, int grid, int threads, size_t sme
                             const KLayout& L, const KOpts& o, const KParams& p, const KSol& sol, float* gws,
                             long long gstride, const int* order, int count, int* queue, const float* x0,
                             int* gflags, const float* dLdz, const float* dLdxi, const KGrads& g, double* dws,
-                            long long dstride) {
+                            long long dstride, int* dq_flag, int* dq_ctr, int nsm) {
     const void* k = bwd_kernel_of(model, cl > 0);
     if (!k) return cudaErrorInvalidValue;
     if (cl > 0) {
@@ -145,11 +154,42 @@ cudaError_t launch_backward(int model, int cl, int grid, int threads, size_t sme
                         (void*)&dws, (void*)&dstride};
         return cudaLaunchKernelExC(&cfg, k, args);
     }
+    // CTA teams: instances that need the direct solve are flagged by the first pass,
+    // swept by the warp kernel and finished by a second pass of the backward kernel
+    // (dq_flag: one per instance, global index; dq_ctr: [1] sweep cursor, [2] queue
+    // of the finishing pass; all zeroed by the caller)
+    const bool direct = dws && dq_flag && dq_ctr && !(o.bwd_solver == 1 && !o.exact_hessian);
+    DirectQueue dq{direct ? dq_flag : nullptr};
+    int finish = 0;
     const long long sf = (long long)(smem_bytes / sizeof(float));
+    double* dw = direct ? dws : nullptr;
     void* args[] = {(void*)&L, (void*)&o, (void*)&p, (void*)&sol, (void*)&gws, (void*)&gstride, (void*)&order,
                     (void*)&count, (void*)&queue, (void*)&x0, (void*)&sf, (void*)&dLdz, (void*)&dLdxi, (void*)&g,
-                    (void*)&dws, (void*)&dstride};
-    return cudaLaunchKernel(k, dim3(grid), dim3(threads), args, smem_bytes, s);
+                    (void*)&dw, (void*)&dstride, (void*)&dq, (void*)&finish};
+    cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(threads), args, smem_bytes, s);
+    if (e != cudaSuccess || !direct) return e;
+    const KernelTable* t = table_of(model);
+    const int* Np = p.N;
+    const int* flg = dq_flag;
+    int* cursor = dq_ctr + 1;
+    int exact = o.exact_hessian ? 1 : 0;
+    // one CTA of kDirectWarps warps per SM (the occupancy limit), fewer for small groups
+    const int blocks = std::max(1, std::min(nsm, (count + kDirectWarps - 1) / kDirectWarps));
+    void* dargs[] = {(void*)&Np, (void*)&order, (void*)&count, (void*)&flg, (void*)&cursor, (void*)&dws,
+                     (void*)&dstride, (void*)&exact};
+    e = cudaLaunchKernel(t->direct, dim3(blocks), dim3(kDirectWarps * 32), dargs, 0, s);
+    if (e != cudaSuccess) return e;
+    finish = 1;
+    int* q2 = dq_ctr + 2;
+    void* fargs[] = {(void*)&L, (void*)&o, (void*)&p, (void*)&sol, (void*)&gws, (void*)&gstride, (void*)&order,
+                     (void*)&count, (void*)&q2, (void*)&x0, (void*)&sf, (void*)&dLdz, (void*)&dLdxi, (void*)&g,
+                     (void*)&dw, (void*)&dstride, (void*)&dq, (void*)&finish};
+    return cudaLaunchKernel(k, dim3(grid), dim3(threads), fargs, smem_bytes, s);
+}
+
+int backward_launches(int cl, const KOpts& o, bool have_dws) {
+    if (cl > 0 || !have_dws || (o.bwd_solver == 1 && !o.exact_hessian)) return 1;
+    return 3;
 }
 
 cudaError_t launch_plain(int model, int threads, cudaStream_t s, const KLayout& L, const KOpts& o, const KParams& p,

@@ -44,9 +44,12 @@ cudaError_t launch_backward(int model, int cl, int grid, int threads, size_t sme
                             const KLayout& L, const KOpts& o, const KParams& p, const KSol& sol, float* gws,
                             long long gstride, const int* order, int count, int* queue, const float* x0,
                             int* gflags, const float* dLdz, const float* dLdxi, const KGrads& g, double* dws,
-                            long long dstride);
+                            long long dstride, int* dq_flag, int* dq_ctr, int nsm);
+// kernels launch_backward enqueues (1, or 3 when the direct solve may run: the backward
+// pass, the sweep kernel and the finishing pass)
+int backward_launches(int cl, const KOpts& o, bool have_dws);
 // doubles of the direct backward's FP64 workspace per instance of T stages
-long long direct_ws_doubles(int T);
+long long direct_ws_doubles(int model, int T);
 
 // plain per-phase form: one launch per phase, fixed counts, one CTA per instance,
 // global arenas; kernels launched on s in host order (plain_launches of them)
@@ -62,6 +65,7 @@ struct KernelTable {
     const void* cluster[2];   // one thread-block cluster per instance, kCR / kLDL
     const void* backward;     // persistent backward kernel (cyclic reduction)
     const void* backward_cluster;
+    const void* direct;       // sweeps of the direct backward, one warp per instance
     cudaError_t (*plain)(int threads, cudaStream_t s, const KLayout& L, const KOpts& o, const KParams& p,
                          const KSol& out, float* gws, long long gstride, const int* order, int count,
                          const float* x0, int warm, PlainState* ps);

@@ -1197,7 +1197,7 @@ template <int M>
 __device__ __forceinline__ void backward_instance_team(Inst<M>& c, const KOpts& o, const Red& rs, const KLayout& L,
                                                        const KSol& sol, int inst, const float* dLdz_all,
                                                        const float* dLdxi_all, const KGrads& g, double* dws,
-                                                       double* dsh) {
+                                                       double* dsh, const DirectQueue& dq, bool finish) {
     using Tr = Traits<M>;
     constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NU = Inst<M>::NU, NG = Inst<M>::NG;
     const int T = c.T;
@@ -1262,108 +1262,121 @@ __device__ __forceinline__ void backward_instance_team(Inst<M>& c, const KOpts& 
     c.sync();
     // backward solver: 0 hybrid (refinement, then the direct solve where it did not
     // converge), 1 refinement only, 2 direct only; the exact Hessian needs the direct solve
-    const bool direct_ok = dws != nullptr;
+    const bool direct_ok = dws != nullptr && (dq.flag != nullptr || dsh != nullptr);
     const bool direct_only = direct_ok && (o.bwd_solver == 2 || o.exact_hessian);
-    bool refined_ok = true;
-    if (direct_only) {
-        // direct FP64 block LDL' of the interleaved active-set KKT system (tmpc_direct.cuh),
-        // its broadcast rows in the CTA's shared scratch dsh
-        direct_adjoint<M>(c, code, bx, ex, lam, mu, dws, dsh, c.tflags + 2, o.exact_hessian != 0);
+    if (finish) {
+        // the sweeps of the direct solve ran in the warp kernel: read the adjoint
+        direct_load<M>(c, dws, ex, lam, mu);
+        c.sync();
     } else {
-        // S_b = H + sigma_b I + rho_b C'C + G' diag(w) G; FP32 safeguard: lower rho_b up to three times
-        form_S<M>(c, o.bwd_sigma, rb, rb, gw);
-        bool ok = cr_factor<M>(c, c.tflags + 1);
-        for (int tries = 0; !ok && tries < 3; ++tries) {
-            rb *= 0.1f;
-            for (int e = c.tid; e < T * NG; e += c.nth)
-                if (code[e] != 0.f && fabsf(code[e]) < 1.5f) gw[e] = rb;
-            c.sync();
+        bool need_direct = direct_only;
+        if (!direct_only) {
+            // S_b = H + sigma_b I + rho_b C'C + G' diag(w) G; FP32 safeguard: lower rho_b up to three times
             form_S<M>(c, o.bwd_sigma, rb, rb, gw);
-            ok = cr_factor<M>(c, c.tflags + 1);
-        }
-        if (!ok && c.tid == 0) c.tflags[0] = 1;
-        top_inverse<M>(c);
-        // divergence guard (see tmpc_backward.cuh): growing steps lower rho_b and restart
-        float d0 = 0.f, dprev = kInf, dprev2 = kInf;
-        int restarts = 0;
-        for (int it = 0; it < o.bwd_iters; ++it) {
-            for (int e = c.tid; e < T * NG; e += c.nth) gz[e] = c.Gx(ex, e / NG, e % NG);
-            c.sync();
-            for (int e = c.tid; e < T * N; e += c.nth) {
-                const int t = e / N, j = e % N;
-                float sv = bx[e] - c.Pv(ex, t, j);
-                sv -= c.Ctv(t, j, [&](int row, int k) { return lam[row * NX + k]; });
-    #pragma unroll
-                for (int r = 0; r < NG; ++r) {
-                    const float cd = code[t * NG + r];
-                    if (fabsf(cd) > 1.5f) sv -= c.gam2(r) * c.Gval(t, r, j) * gz[t * NG + r];
-                    else if (cd != 0.f) sv -= c.Gval(t, r, j) * mu[t * NG + r];
-                }
-                c.r[e] = sv;
-            }
-            for (int e = c.tid; e < T * NX; e += c.nth) r2[e] = -c.Cx(ex, e / NX, e % NX);
-            for (int e = c.tid; e < T * NG; e += c.nth) {
-                const float cd = code[e];
-                r3[e] = (cd != 0.f && fabsf(cd) < 1.5f) ? -gz[e] : 0.f;
-            }
-            c.sync();
-            for (int e = c.tid; e < T * N; e += c.nth) {
-                const int t = e / N, j = e % N;
-                float sv = c.Ctv(t, j, [&](int row, int k) { return r2[row * NX + k]; });
-                sv += c.Gtw(t, j, [&](int r) { return r3[t * NG + r]; });
-                c.r[e] += rb * sv;
-            }
-            c.sync();
-            cr_solve<M>(c, c.r, c.dx);
-            for (int e = c.tid; e < T * NX; e += c.nth) lam[e] += rb * (c.Cx(c.dx, e / NX, e % NX) - r2[e]);
-            for (int e = c.tid; e < T * NG; e += c.nth) {
-                const float cd = code[e];
-                if (cd != 0.f && fabsf(cd) < 1.5f) mu[e] += rb * (c.Gx(c.dx, e / NG, e % NG) - r3[e]);
-            }
-            c.sync();
-            float dm[1] = {0.f};
-            for (int e = c.tid; e < T * N; e += c.nth) {
-                ex[e] += c.dx[e];
-                dm[0] = fmaxf(dm[0], fin(c.dx[e]));
-            }
-            team_max_k<M, 1>(c, dm, rs.red);
-            if (it == 0) d0 = dm[0];
-            const bool diverging = !(dm[0] < kInf) || (it >= 2 && dm[0] > 2.f * dprev && dm[0] > 1e-4f * d0);
-            if (diverging && restarts < 3) {
-                ++restarts;
+            bool ok = cr_factor<M>(c, c.tflags + 1);
+            for (int tries = 0; !ok && tries < 3; ++tries) {
                 rb *= 0.1f;
-                for (int e = c.tid; e < T * NG; e += c.nth) {
+                for (int e = c.tid; e < T * NG; e += c.nth)
                     if (code[e] != 0.f && fabsf(code[e]) < 1.5f) gw[e] = rb;
-                    mu[e] = 0.f;
-                }
-                for (int e = c.tid; e < T * NX; e += c.nth) lam[e] = 0.f;
-                for (int e = c.tid; e < T * N; e += c.nth) ex[e] = 0.f;
                 c.sync();
                 form_S<M>(c, o.bwd_sigma, rb, rb, gw);
-                if (!cr_factor<M>(c, c.tflags + 1) && c.tid == 0) c.tflags[0] = 1;
-                top_inverse<M>(c);
-                d0 = 0.f;
-                dprev = kInf;
-                it = -1;
-                continue;
+                ok = cr_factor<M>(c, c.tflags + 1);
             }
-            dprev2 = dprev;
-            dprev = dm[0];
+            if (!ok && c.tid == 0) c.tflags[0] = 1;
+            top_inverse<M>(c);
+            // divergence guard (see tmpc_backward.cuh): growing steps lower rho_b and restart
+            float d0 = 0.f, dprev = kInf, dprev2 = kInf;
+            int restarts = 0;
+            for (int it = 0; it < o.bwd_iters; ++it) {
+                for (int e = c.tid; e < T * NG; e += c.nth) gz[e] = c.Gx(ex, e / NG, e % NG);
+                c.sync();
+                for (int e = c.tid; e < T * N; e += c.nth) {
+                    const int t = e / N, j = e % N;
+                    float sv = bx[e] - c.Pv(ex, t, j);
+                    sv -= c.Ctv(t, j, [&](int row, int k) { return lam[row * NX + k]; });
+#pragma unroll
+                    for (int r = 0; r < NG; ++r) {
+                        const float cd = code[t * NG + r];
+                        if (fabsf(cd) > 1.5f) sv -= c.gam2(r) * c.Gval(t, r, j) * gz[t * NG + r];
+                        else if (cd != 0.f) sv -= c.Gval(t, r, j) * mu[t * NG + r];
+                    }
+                    c.r[e] = sv;
+                }
+                for (int e = c.tid; e < T * NX; e += c.nth) r2[e] = -c.Cx(ex, e / NX, e % NX);
+                for (int e = c.tid; e < T * NG; e += c.nth) {
+                    const float cd = code[e];
+                    r3[e] = (cd != 0.f && fabsf(cd) < 1.5f) ? -gz[e] : 0.f;
+                }
+                c.sync();
+                for (int e = c.tid; e < T * N; e += c.nth) {
+                    const int t = e / N, j = e % N;
+                    float sv = c.Ctv(t, j, [&](int row, int k) { return r2[row * NX + k]; });
+                    sv += c.Gtw(t, j, [&](int r) { return r3[t * NG + r]; });
+                    c.r[e] += rb * sv;
+                }
+                c.sync();
+                cr_solve<M>(c, c.r, c.dx);
+                for (int e = c.tid; e < T * NX; e += c.nth) lam[e] += rb * (c.Cx(c.dx, e / NX, e % NX) - r2[e]);
+                for (int e = c.tid; e < T * NG; e += c.nth) {
+                    const float cd = code[e];
+                    if (cd != 0.f && fabsf(cd) < 1.5f) mu[e] += rb * (c.Gx(c.dx, e / NG, e % NG) - r3[e]);
+                }
+                c.sync();
+                float dm[1] = {0.f};
+                for (int e = c.tid; e < T * N; e += c.nth) {
+                    ex[e] += c.dx[e];
+                    dm[0] = fmaxf(dm[0], fin(c.dx[e]));
+                }
+                team_max_k<M, 1>(c, dm, rs.red);
+                if (it == 0) d0 = dm[0];
+                const bool diverging = !(dm[0] < kInf) || (it >= 2 && dm[0] > 2.f * dprev && dm[0] > 1e-4f * d0);
+                if (diverging && restarts < 3) {
+                    ++restarts;
+                    rb *= 0.1f;
+                    for (int e = c.tid; e < T * NG; e += c.nth) {
+                        if (code[e] != 0.f && fabsf(code[e]) < 1.5f) gw[e] = rb;
+                        mu[e] = 0.f;
+                    }
+                    for (int e = c.tid; e < T * NX; e += c.nth) lam[e] = 0.f;
+                    for (int e = c.tid; e < T * N; e += c.nth) ex[e] = 0.f;
+                    c.sync();
+                    form_S<M>(c, o.bwd_sigma, rb, rb, gw);
+                    if (!cr_factor<M>(c, c.tflags + 1) && c.tid == 0) c.tflags[0] = 1;
+                    top_inverse<M>(c);
+                    d0 = 0.f;
+                    dprev = kInf;
+                    it = -1;
+                    continue;
+                }
+                dprev2 = dprev;
+                dprev = dm[0];
+                c.sync();
+            }
+            // convergence of the refinement: the last step at the FP32 floor of the solution, or a
+            // contraction whose geometric tail (last step q / (1 - q)) is below 1e-6 of it (the
+            // multipliers converge more slowly than eta_x, so the bound is kept tight)
+            float xm[1] = {0.f};
+            for (int e = c.tid; e < T * N; e += c.nth) xm[0] = fmaxf(xm[0], fin(ex[e]));
+            team_max_k<M, 1>(c, xm, rs.red);
+            const float q = dprev / fmaxf(dprev2, 1e-30f);
+            bool refined_ok = dprev <= 1e-6f * xm[0] || (q < 0.9f && dprev * q / (1.f - q) <= 1e-6f * xm[0]);
+            refined_ok = refined_ok && restarts == 0 && xm[0] < kInf;
+            need_direct = !refined_ok && direct_ok && o.bwd_solver == 0;
+        }
+        if (need_direct) {
+            // direct FP64 block LDL' of the interleaved active-set KKT system (tmpc_direct.cuh):
+            // the team fills the per-stage records, one warp runs the sweeps
+            direct_store<M>(c, code, bx, dws, o.exact_hessian != 0);
+            c.sync();
+            if (dq.flag) {   // sweeps in the warp kernel, gradients in the finishing pass
+                if (c.tid == 0) dq.flag[inst] = 1;
+                return;
+            }
+            if (c.tid < 32) direct_sweep<M>(T, dws, dsh, o.exact_hessian != 0);
+            c.sync();
+            direct_load<M>(c, dws, ex, lam, mu);
             c.sync();
         }
-        // convergence of the refinement: the last step at the FP32 floor of the solution, or a
-        // contraction whose geometric tail (last step q / (1 - q)) is below 1e-4 of it
-        float xm[1] = {0.f};
-        for (int e = c.tid; e < T * N; e += c.nth) xm[0] = fmaxf(xm[0], fin(ex[e]));
-        team_max_k<M, 1>(c, xm, rs.red);
-        const float q = dprev / fmaxf(dprev2, 1e-30f);
-        refined_ok = dprev <= 1e-6f * xm[0] || (q < 0.9f && dprev * q / (1.f - q) <= 1e-4f * xm[0]);
-        refined_ok = refined_ok && restarts == 0 && xm[0] < kInf;
-    }
-    if (!direct_only && !refined_ok && direct_ok && o.bwd_solver == 0) {
-        for (int e = c.tid; e < T * NG; e += c.nth) mu[e] = 0.f;
-        c.sync();
-        direct_adjoint<M>(c, code, bx, ex, lam, mu, dws, dsh, c.tflags + 2, false);
     }
     for (int e = c.tid; e < T * NG; e += c.nth) gz[e] = c.Gx(ex, e / NG, e % NG);
     c.sync();
@@ -1537,14 +1550,17 @@ __global__ void __launch_bounds__(256, 2) solve_kernel_cluster(KLayout L, KOpts 
 
 // Backward kernels (Algorithm 2) of the shared-memory path: persistent CTA
 // teams over a work queue, and one thread-block cluster per instance.
+// finish = 0: every instance of `order`; the ones that need the direct solve are
+// flagged in dq.flag after their records are filled (dq.flag may be null: no
+// direct solve).  finish = 1: the flagged instances, whose adjoint the sweep
+// kernel left in the records, take their gradients.
 template <int M>
 __global__ void __launch_bounds__(256, 2) backward_kernel(KLayout L, KOpts o, KParams p, KSol sol, float* gws,
                                                        long long gstride, const int* order, int count,
                                                        int* queue, const float* x0, long long smem_floats,
                                                        const float* dLdz, const float* dLdxi, KGrads g,
-                                                       double* dws, long long dstride) {
+                                                       double* dws, long long dstride, DirectQueue dq, int finish) {
     extern __shared__ __align__(16) float arena[];
-    __shared__ double dsh[kDirectScratch];
     __shared__ float red[32 * 8];
     __shared__ double redd[64];
     __shared__ double lsacc[2 * (kMaxLs + 1) + 2];
@@ -1552,7 +1568,13 @@ __global__ void __launch_bounds__(256, 2) backward_kernel(KLayout L, KOpts o, KP
     __shared__ int s_item;
     const Red rs{red, redd, lsacc, flags};
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+        if (threadIdx.x == 0) {
+            int k;
+            do {
+                k = atomicAdd(queue, 1);
+            } while (finish && k < count && !dq.flag[order[k]]);
+            s_item = k;
+        }
         __syncthreads();
         const int q = s_item;
         __syncthreads();
@@ -1568,7 +1590,7 @@ __global__ void __launch_bounds__(256, 2) backward_kernel(KLayout L, KOpts o, KP
         const long long need = arena_floats<M>(c.T, kCR);
         c.carve(need <= smem_floats ? arena : gws + (long long)i * gstride, kCR);
         backward_instance_team<M>(c, o, rs, L, sol, i, dLdz, dLdxi, g, dws ? dws + (long long)i * dstride : nullptr,
-                                  dsh);
+                                  nullptr, dq, finish != 0);
     }
 }
 
@@ -1600,7 +1622,7 @@ __global__ void __launch_bounds__(256, 2) backward_kernel_cluster(KLayout L, KOp
         c.tflags = gflags + 4LL * i;
         c.carve(gws + (long long)i * gstride, kCR, 1);
         backward_instance_team<M>(c, o, rs, L, sol, i, dLdz, dLdxi, g, dws ? dws + (long long)i * dstride : nullptr,
-                                  dsh);
+                                  dsh, DirectQueue{nullptr}, false);
         c.sync();
     }
 }

@@ -37,6 +37,7 @@ const KernelTable& kernel_table<TMPC_FAST_MODEL>() {
         {(const void*)solve_kernel_cluster<kM, kCR>, (const void*)solve_kernel_cluster<kM, kLDL>},
         (const void*)backward_kernel<kM>,
         (const void*)backward_kernel_cluster<kM>,
+        (const void*)direct_kernel<kM>,
         &launch_plain_model};
     return t;
 }
