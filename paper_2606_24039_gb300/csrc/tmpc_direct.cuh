@@ -72,6 +72,7 @@ struct DRec {
     // (XH N each), U P_t' (XH^2), pivot row (MB), y_t (MB), w_{t-1} (N), x_{t+1} (XH)
     static constexpr int Scratch = N * N + 2 * XH * N + XH * XH + 2 * MB + N + XH;
     static_assert(MB <= 32, "one lane per row of the block");
+    static_assert((N * N + 2 * XH * N + XH * XH) % 2 == 0, "pivot row on a 16-byte boundary");
 };
 
 // Largest per-warp scratch over the small models (the bicycle's)
@@ -316,14 +317,16 @@ __device__ __forceinline__ double recip_nr(double x) {
 }
 
 // In-place Gauss-Jordan inversion of the K x K block held one row per lane
-// (lanes K..31 idle), partial pivoting on the rows not yet pivoted.  Step p: the
-// pivot row is broadcast unscaled (its entry p replaced by 1) and every lane
-// applies one FMA per column, v = v inv on the pivot row, v -= (v_p inv) prow on
-// the others (the in-place form, entry p first set to 1 or 0).  On return the
-// lane that pivoted at step p holds row p of S^-1 with its entries in the order of
-// the pivot steps: v[j] = (S^-1)(p, pw[j]), pw[j] the lane (row) that pivoted at
-// step j.  Returns 1 if a pivot fell below 1e-13 of the block's largest entry
-// (numerically singular).
+// (lanes K..31 idle), partial pivoting on the rows not yet pivoted (the pivot is
+// the largest magnitude rounded to 18 bits, ties to the lower lane: one integer
+// warp reduction).  Step p: the pivot row is broadcast unscaled with its entry p
+// replaced by 1, and every lane applies one FMA per column, v -= g prow, with
+// g = v_p / pivot on the other rows (entry p first set to 0) and g = 1 - 1/pivot
+// on the pivot row (entry p first set to 1), which leaves it scaled by 1/pivot:
+// the in-place form.  On return the lane that pivoted at step p holds row p of
+// S^-1 with its entries in the order of the pivot steps: v[j] = (S^-1)(p, pw[j]),
+// pw[j] the lane (row) that pivoted at step j.  Returns 1 if a pivot fell below
+// 1e-13 of the block's largest entry (numerically singular).
 template <int MB, int K>
 __device__ __forceinline__ int gj_inplace(double (&v)[MB], int (&pw)[MB], int& mypiv, double* prow, int lane) {
     static_assert(K <= MB && K <= 32, "block size");
@@ -338,19 +341,12 @@ __device__ __forceinline__ int gj_inplace(double (&v)[MB], int (&pw)[MB], int& m
     mypiv = -1;
 #pragma unroll
     for (int p = 0; p < K; ++p) {
-        double cand = used ? -1.0 : fabs(v[p]);
-        int who = lane;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double oc = __shfl_xor_sync(0xffffffffu, cand, o);
-            const int ow = __shfl_xor_sync(0xffffffffu, who, o);
-            if (oc > cand || (oc == cand && ow < who)) { cand = oc; who = ow; }
-        }
+        const unsigned key = used ? 0u : ((__float_as_uint((float)fabs(v[p])) & ~31u) | (unsigned)(31 - lane));
+        const int who = 31 - (int)(__reduce_max_sync(0xffffffffu, key) & 31u);
         pw[p] = who;
-        const bool ok = cand > tiny;
-        if (!ok) singular = 1;
         const double piv = __shfl_sync(0xffffffffu, v[p], who);
         const double ap = fabs(piv);
+        if (!(ap > tiny)) singular = 1;
         const double inv = (ap > 1e-30 && ap < 1e30) ? recip_nr(piv) : (piv != 0.0 ? 1.0 / piv : 0.0);
         const bool me = lane == who;
         if (me) {
@@ -360,13 +356,15 @@ __device__ __forceinline__ int gj_inplace(double (&v)[MB], int (&pw)[MB], int& m
             for (int q = 0; q < K; ++q) prow[q] = q == p ? 1.0 : v[q];
         }
         __syncwarp();
-        const double g = me ? 0.0 : v[p] * inv;
+        const double g = me ? 1.0 - inv : v[p] * inv;
         v[p] = me ? 1.0 : 0.0;
 #pragma unroll
-        for (int q = 0; q < K; ++q) {
-            const double pq = prow[q];
-            v[q] = me ? v[q] * inv : fma(-g, pq, v[q]);
+        for (int q = 0; q + 1 < K; q += 2) {
+            const double2 pr = *reinterpret_cast<const double2*>(prow + q);
+            v[q] = fma(-g, pr.x, v[q]);
+            v[q + 1] = fma(-g, pr.y, v[q + 1]);
         }
+        if constexpr (K % 2 == 1) v[K - 1] = fma(-g, prow[K - 1], v[K - 1]);
         __syncwarp();
     }
     return singular;
@@ -605,7 +603,7 @@ template <int M>
 __global__ void __launch_bounds__(kDirectWarps * 32, 1) direct_kernel(const int* N, const int* order, int count,
                                                                       const int* flag, int* cursor, double* dws,
                                                                       long long dstride, int exact) {
-    __shared__ double sh[kDirectWarps][kDirectScratch];
+    __shared__ __align__(16) double sh[kDirectWarps][kDirectScratch];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (;;) {
         int k = 0;

@@ -1600,7 +1600,7 @@ __global__ void __launch_bounds__(256, 2) backward_kernel_cluster(KLayout L, KOp
                                                                const float* x0, int* gflags, const float* dLdz,
                                                                const float* dLdxi, KGrads g, double* dws,
                                                                long long dstride) {
-    __shared__ double dsh[kDirectScratch];
+    __shared__ __align__(16) double dsh[kDirectScratch];
     __shared__ float red[32 * 8];
     __shared__ double redd[64];
     __shared__ double lsacc[2 * (kMaxLs + 1) + 2];
