@@ -115,7 +115,7 @@ def parse():
 
 
 CPU_SAMPLE = {"racing": 128, "double_integrator": 512, "tracking": 96, "uneven": 160, "long_horizon": 16,
-              "linear_rl": 256}
+              "linear_rl": 256, "humanoid": 256}
 
 WORKLOADS = {
     # name: (generator, default batch, default horizon, seed, description)
@@ -127,8 +127,10 @@ WORKLOADS = {
     "double_integrator": ("double_integrator", 1, 20, 1001, "2-D double integrator, box bounds on u and v"),
     "linear_rl": ("linear_rl", 64, 40, 1006, "linear-system RL: x+ = A x + B u + b, nx=8 nu=4, |u| <= 1, "
                                              "Q = diag(theta), tolerance 1e-5 (<= 1000 ADMM per QP)"),
+    "humanoid": ("humanoid", 100, 20, 1007, "single-rigid-body humanoid balance, nx=12 nu=6, RK4 dt=0.025, "
+                                           "Q = diag(exp(theta)), box on the foot forces"),
 }
-SUITE = ("racing", "tracking", "long_horizon", "double_integrator", "linear_rl")
+SUITE = ("racing", "tracking", "long_horizon", "double_integrator", "linear_rl", "humanoid")
 LINEAR = ("tracking", "double_integrator", "linear_rl")
 
 
@@ -388,8 +390,9 @@ def kernel_name(pb, solver, forms=None):
 def launches_per_step(pb, solver, forms=None):
     """Kernels launched by one forward call and by one backward call: per fast-model
     group one persistent launch (the plain form: one per phase), one generic launch
-    for the other models; backward: one per cyclic-reduction group plus one generic
-    launch for the rest."""
+    for the other models; backward: per cyclic-reduction CTA group three (the
+    backward pass, the kernel of the direct solve's sweeps, the finishing pass),
+    per cluster group one, plus one generic launch for the rest."""
     models = set(int(m) for m in np.unique(pb.model))
     if solver == 1:
         return 1, 1
@@ -397,7 +400,8 @@ def launches_per_step(pb, solver, forms=None):
         forms = {m: (solver if solver >= 2 else 2) for m in models & set(FAST_MODELS)}
     other = bool(models - set(forms))
     fwd = sum(2 + pb.opts.max_sqp * (2 + pb.opts.max_admm) if f == 7 else 1 for f in forms.values()) + int(other)
-    bwd = sum(1 for f in forms.values() if f not in (4, 5)) + int(other or any(f in (4, 5) for f in forms.values()))
+    bwd = sum(1 if f == 6 else 3 for f in forms.values() if f not in (4, 5)) + \
+        int(other or any(f in (4, 5) for f in forms.values()))
     return fwd, bwd
 
 

@@ -69,9 +69,14 @@ enum {
     TMPC_MODEL_BICYCLE = 2,           /* nx=6 nu=2 ng=5, implicit midpoint.  dyn = [dt, L, ds, nt] */
     TMPC_MODEL_QUADROTOR = 3,         /* nx=6 nu=2 ng=2, RK4.  dyn = [dt, m, I, arm, g]            */
     TMPC_MODEL_BICYCLE_TRAP = 4,      /* as 2 with the trapezoidal constraint of Remark A1         */
-    TMPC_MODEL_BICYCLE_NEWTON = 5     /* as 2 with the explicit map x+ = Phi(x, u) that 3 Newton
+    TMPC_MODEL_BICYCLE_NEWTON = 5,    /* as 2 with the explicit map x+ = Phi(x, u) that 3 Newton
                                          steps on the midpoint rule define, Jacobians by the
                                          implicit function theorem (generic kernel only)          */
+    TMPC_MODEL_SRB = 6                /* single-rigid-body humanoid (App. humanoid SRB dynamics):
+                                         nx=12 (p, ZYX Euler angles, v, body rates) nu=6 (foot
+                                         forces f_L, f_R, world frame) ng=6 (box on the forces),
+                                         RK4.  dyn = [dt, m, Ixx, Iyy, Izz, r_L (3), r_R (3),
+                                         gravity] (generic kernel only)                           */
 };
 
 /* number of floats per instance in tmpc_solution.stats */

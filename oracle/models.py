@@ -21,7 +21,7 @@ import math
 import numpy as np
 
 from workloads import (BICYCLES, MODEL_BICYCLE, MODEL_BICYCLE_NEWTON, MODEL_BICYCLE_TRAP, MODEL_DI,
-                       MODEL_LINEAR, MODEL_QUAD)
+                       MODEL_LINEAR, MODEL_QUAD, MODEL_SRB)
 
 NEWTON_MAP_STEPS = 3   # Newton steps that define the explicit map of MODEL_BICYCLE_NEWTON
 
@@ -138,6 +138,82 @@ def quad_rk4(x, u, dyn):
     return phi, dphix, dphiu
 
 
+def srb_euler_rate_matrix(phi, th):
+    """T(Theta) of the ZYX Euler angles (Theta_dot = T omega, omega in the body
+    frame; App. humanoid SRB dynamics) and its derivatives with respect to roll
+    phi and pitch theta.  Arrays [T, 3, 3]."""
+    sp, cp, tt, ct = np.sin(phi), np.cos(phi), np.tan(th), np.cos(th)
+    one, zero = np.ones_like(phi), np.zeros_like(phi)
+    Tm = np.stack([np.stack([one, sp * tt, cp * tt], -1),
+                   np.stack([zero, cp, -sp], -1),
+                   np.stack([zero, sp / ct, cp / ct], -1)], -2)
+    dphi = np.stack([np.stack([zero, cp * tt, -sp * tt], -1),
+                     np.stack([zero, -sp, -cp], -1),
+                     np.stack([zero, cp / ct, -sp / ct], -1)], -2)
+    sec2 = 1.0 / ct**2
+    dth = np.stack([np.stack([zero, sp * sec2, cp * sec2], -1),
+                    np.stack([zero, zero, zero], -1),
+                    np.stack([zero, sp * tt / ct, cp * tt / ct], -1)], -2)
+    return Tm, dphi, dth
+
+
+def _cross_matrix(r):
+    """[r]_x with [r]_x a = r x a; r [..., 3]."""
+    z = np.zeros_like(r[..., 0])
+    return np.stack([np.stack([z, -r[..., 2], r[..., 1]], -1),
+                     np.stack([r[..., 2], z, -r[..., 0]], -1),
+                     np.stack([-r[..., 1], r[..., 0], z], -1)], -2)
+
+
+def srb_fc(x, u, dyn):
+    """Single-rigid-body centroidal dynamics (App. humanoid SRB dynamics):
+    state (p, Theta, v, omega), control (f_L, f_R) in the world frame,
+      p_dot = v,  Theta_dot = T(Theta) omega,  v_dot = (f_L + f_R) / m + g,
+      omega_dot = I^-1 (r_L x f_L + r_R x f_R - omega x (I omega)),
+    I = diag(Ixx, Iyy, Izz), g = (0, 0, -gravity), the torques as the paper
+    writes them.  dyn = [dt, m, Ixx, Iyy, Izz, r_L (3), r_R (3), gravity].
+    Returns f [T,12], df/dx [T,12,12], df/du [T,12,6]."""
+    m, Id, rL, rR, grav = dyn[1], np.asarray(dyn[2:5]), np.asarray(dyn[5:8]), np.asarray(dyn[8:11]), dyn[11]
+    T = x.shape[0]
+    Theta, v, w = x[:, 3:6], x[:, 6:9], x[:, 9:12]
+    fL, fR = u[:, 0:3], u[:, 3:6]
+    Tm, dphi, dth = srb_euler_rate_matrix(Theta[:, 0], Theta[:, 1])
+    Iw = w * Id
+    tau = np.cross(rL, fL) + np.cross(rR, fR) - np.cross(w, Iw)
+    f = np.concatenate([v, np.einsum("tij,tj->ti", Tm, w), (fL + fR) / m + np.array([0.0, 0.0, -grav]), tau / Id], axis=1)
+    Jx = np.zeros((T, 12, 12))
+    Jx[:, 0:3, 6:9] = np.eye(3)
+    Jx[:, 3:6, 3] = np.einsum("tij,tj->ti", dphi, w)
+    Jx[:, 3:6, 4] = np.einsum("tij,tj->ti", dth, w)
+    Jx[:, 3:6, 9:12] = Tm
+    # d(omega x I omega)/d omega = [omega]_x I - [I omega]_x
+    Jx[:, 9:12, 9:12] = -(_cross_matrix(w) * Id[None, None, :] - _cross_matrix(Iw)) / Id[None, :, None]
+    Ju = np.zeros((T, 12, 6))
+    Ju[:, 6:9, 0:3] = np.eye(3) / m
+    Ju[:, 6:9, 3:6] = np.eye(3) / m
+    Ju[:, 9:12, 0:3] = _cross_matrix(rL) / Id[:, None]
+    Ju[:, 9:12, 3:6] = _cross_matrix(rR) / Id[:, None]
+    return f, Jx, Ju
+
+
+def rk4(fc, x, u, dyn):
+    """Explicit RK4 step x+ = Phi(x, u) of the continuous dynamics fc (dt =
+    dyn[0]) with its Jacobians by the chain rule through the four stages.
+    Returns Phi [T,nx], dPhi/dx [T,nx,nx], dPhi/du [T,nx,nu]."""
+    dt = dyn[0]
+    T, nx = x.shape
+    I = np.broadcast_to(np.eye(nx), (T, nx, nx))
+    k1, J1, U1 = fc(x, u, dyn)
+    k2, J2, U2 = fc(x + 0.5 * dt * k1, u, dyn)
+    d2x, d2u = J2 @ (I + 0.5 * dt * J1), J2 @ (0.5 * dt * U1) + U2
+    k3, J3, U3 = fc(x + 0.5 * dt * k2, u, dyn)
+    d3x, d3u = J3 @ (I + 0.5 * dt * d2x), J3 @ (0.5 * dt * d2u) + U3
+    k4, J4, U4 = fc(x + dt * k3, u, dyn)
+    d4x, d4u = J4 @ (I + dt * d3x), J4 @ (dt * d3u) + U4
+    phi = x + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+    return phi, I + dt / 6.0 * (J1 + 2 * d2x + 2 * d3x + d4x), dt / 6.0 * (U1 + 2 * d2u + 2 * d3u + d4u)
+
+
 def di_matrices(dt):
     """Zero-order-hold double integrator in 2-D: position (2), velocity (2)."""
     I2 = np.eye(2)
@@ -170,9 +246,11 @@ def dynamics(inst, z):
     x, u = z[:, :nx], z[:, nx:]
     Am = np.zeros((N, nx, n))
     Ap = np.zeros((N, nx, n))
-    if model in (MODEL_DI, MODEL_LINEAR, MODEL_QUAD):
+    if model in (MODEL_DI, MODEL_LINEAR, MODEL_QUAD, MODEL_SRB):
         if model == MODEL_QUAD:
             phi, Jx, Ju = quad_rk4(x[:-1], u[:-1], inst["dyn"])
+        elif model == MODEL_SRB:
+            phi, Jx, Ju = rk4(srb_fc, x[:-1], u[:-1], inst["dyn"])
         else:
             A, B, b = (*di_matrices(inst["dyn"][0]), np.zeros(nx)) if model == MODEL_DI else linear_matrices(inst)
             phi = x[:-1] @ A.T + u[:-1] @ B.T + b
@@ -245,6 +323,8 @@ def rollout_guess(inst, x, u):
     model = inst["model"]
     if model == MODEL_QUAD:
         return quad_rk4(x[None], u[None], inst["dyn"])[0][0]
+    if model == MODEL_SRB:
+        return rk4(srb_fc, x[None], u[None], inst["dyn"])[0][0]
     if model == MODEL_DI:
         A, B = di_matrices(inst["dyn"][0])
         return A @ x + B @ u
@@ -273,8 +353,8 @@ def constraints(inst, z):
         g = np.stack([z[:, 4], z[:, 5], z[:, 2], z[:, 3]], axis=1)
         G[:, 0, 4] = G[:, 1, 5] = G[:, 2, 2] = G[:, 3, 3] = 1.0
         return g, G
-    if model == MODEL_LINEAR:
-        # rows: the controls (box constraints)
+    if model in (MODEL_LINEAR, MODEL_SRB):
+        # rows: the controls (box constraints; SRB: the friction cone as a box on the foot forces)
         g = z[:, nx:nx + ng].copy()
         for i in range(ng):
             G[:, i, nx + i] = 1.0

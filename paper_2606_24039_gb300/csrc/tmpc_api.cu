@@ -416,6 +416,7 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
             return TMPC_ERR_INVALID_ARG;
         if (is_bicycle(Mh[i]) && (d->n_track < 1 || d->n_dyn < 4)) return TMPC_ERR_INVALID_ARG;
         if (Mh[i] == MODEL_QUAD && d->n_dyn < 5) return TMPC_ERR_INVALID_ARG;
+        if (Mh[i] == MODEL_SRB && d->n_dyn < 12) return TMPC_ERR_INVALID_ARG;
     }
 
     tmpc_handle* h = new (std::nothrow) tmpc_handle();
@@ -959,6 +960,7 @@ __global__ void static_prologue(KLayout L, const int* N, const int* model, int* 
             if (m == MODEL_LINEAR) ok = ok && L.n_dyn >= L.nx * L.nx + L.nx * L.nu && L.ng <= L.nu;
             if (is_bicycle(m)) ok = ok && L.n_track >= 1 && L.n_dyn >= 4;
             if (m == MODEL_QUAD) ok = ok && L.n_dyn >= 5;
+            if (m == MODEL_SRB) ok = ok && L.n_dyn >= 12;
         }
         if (ok) {
             const int slot = atomicAdd(&s_valid, 1);

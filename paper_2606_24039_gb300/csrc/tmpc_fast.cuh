@@ -82,10 +82,12 @@ constexpr int kTeamMax = 16, kXchDoubles = 40;
 //   stage vectors:      x, r, dx, qv, zb, Pd      T x N   (kLDL: dx shares r)
 //   inequality rows:    zg, yg, xi, glo, ghi, xib, ygb, pg   T x NG
 //   equality rows:      yf, pf, cv, yfb, wf       T x NX  (wg: T x NG)
+//   refinement (cluster teams): rs, rd T x N, rcx T x NX, rgx T x NG
 //   cached weights:     par                       32 (W, gamma2, gamma1)
 //   Jacobians:          Am (A^- per stage, padded stride AMS; one block if LTI), Grow (dense G row)
-// Every array up to Pd has a multiple of 4 floats (N = 8), so rows of Am, Grow
-// and the stage vectors start on 16-byte boundaries (128-bit loads).
+// Every array up to rd has a multiple of 4 floats (N = 8), so rows of Am, Grow
+// and the stage vectors (the solves' right-hand sides and results among them)
+// start on 16-byte boundaries (128-bit loads).
 #define TMPC_FAST_ARENA(X)                                                       \
     X(Dm, (long long)T * BS) X(Um, (long long)T * BS)                            \
     X(Fa, P == kCR ? (long long)T * BS : 0LL)                                     \
@@ -97,10 +99,12 @@ constexpr int kTeamMax = 16, kXchDoubles = 40;
     X(Grow, (Traits<M>::DENSE_ROW >= 0 ? (long long)T * N : 0LL))                \
     X(x, T * N) X(r, T * N) X(dx, P == kCR ? T * N : 0) X(qv, T * N)             \
     X(zb, T * N) X(Pd, T * N)                                                    \
+    X(rs, CL ? T * N : 0) X(rd, CL ? T * N : 0)                                  \
     X(zg, T * NG) X(yg, T * NG) X(xi, T * NG) X(glo, T * NG) X(ghi, T * NG)      \
     X(xib, T * NG) X(ygb, T * NG) X(pg, T * NG)                                  \
     X(yf, T * NX) X(pf, T * NX) X(cv, T * NX) X(yfb, T * NX)                     \
     X(wf, T * NX) X(wg, T * NG)                                                  \
+    X(rcx, CL ? T * NX : 0) X(rgx, CL ? T * NG : 0)                              \
     X(par, 32)
 
 // CL: the arena of a cluster team (with the exchange area of its reductions)
@@ -140,6 +144,7 @@ struct Inst {
     float *zg, *yg, *xi, *glo, *ghi, *xib, *ygb, *pg;
     float *yf, *pf, *cv, *yfb;
     float *wf, *wg;  // right-hand-side row vectors y_f + rho_f p_f, y_g + rho_g p_g
+    float *rs, *rd, *rcx, *rgx;   // one step of iterative refinement of each solve (cluster teams)
     float *Am, *Grow, *par;  // par: W[NU], gamma2[NG], gamma1[NG] cached in the arena
 
     // barrier of the team: the CTA barrier, or the cluster barrier with release /

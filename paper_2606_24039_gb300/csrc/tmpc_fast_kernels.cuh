@@ -725,7 +725,7 @@ __device__ __forceinline__ void admm_rowvec(const Inst<M>& c, float rho_bar) {
 // inequality row (t, j < NG) relaxed, projected and dual-updated, and the
 // next iteration's w_f, w_g.  G x is tracked through p_g like C x through p_f.
 template <int M, int P>
-__device__ __forceinline__ void admm_iter(const Inst<M>& c, float rho_bar, float alpha) {
+__device__ __forceinline__ void admm_iter(const Inst<M>& c, float rho_bar, float alpha, float sigma) {
     using Tr = Traits<M>;
     constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NG = Inst<M>::NG;
     const int T = c.T;
@@ -754,8 +754,35 @@ __device__ __forceinline__ void admm_iter(const Inst<M>& c, float rho_bar, float
         for (int e = c.tid; e < T * N; e += c.nth) c.r[e] = rhs(e);
     }
     c.sync();
-    if (P == kCR) cr_solve<M>(c, c.r, c.dx);
-    else ldl_solve_warp<M>(c, c.r);   // dx shares r
+    if (P == kCR) {
+        if (c.cl > 1) {
+            // cluster teams (horizons of thousands of stages): one step of iterative
+            // refinement, dx += S^-1 (r - S dx) with S dx formed matrix-free, so that
+            // the FP32 solve through the many reduction levels stays accurate enough
+            // for ADMM (without it one long racing instance diverged in FP32)
+            for (int e = c.tid; e < T * N; e += c.nth) c.rs[e] = c.r[e];
+            c.sync();
+            cr_solve<M>(c, c.r, c.dx);
+            for (int e = c.tid; e < T * NX; e += c.nth) c.rcx[e] = c.Cx(c.dx, e / NX, e % NX);
+            for (int e = c.tid; e < T * NG; e += c.nth) c.rgx[e] = c.Gx(c.dx, e / NG, e % NG);
+            c.sync();
+            for (int e = c.tid; e < T * N; e += c.nth) {
+                const int t = e / N, j = e % N;
+                float sv = c.Pv(c.dx, t, j) + sigma * c.dx[e];
+                sv += rho_f * c.Ctv(t, j, [&](int row, int k) { return c.rcx[row * NX + k]; });
+                sv += rho_g * c.Gtw(t, j, [&](int r) { return c.rgx[t * NG + r]; });
+                c.rs[e] -= sv;
+            }
+            c.sync();
+            cr_solve<M>(c, c.rs, c.rd);
+            for (int e = c.tid; e < T * N; e += c.nth) c.dx[e] += c.rd[e];
+            c.sync();
+        } else {
+            cr_solve<M>(c, c.r, c.dx);
+        }
+    } else {
+        ldl_solve_warp<M>(c, c.r);   // dx shares r
+    }
     for (int e = c.tid; e < T * N; e += c.nth) {
         const int t = e / N, j = e % N;
         c.x[e] += alpha * c.dx[e];
@@ -1108,7 +1135,7 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
         admm_rowvec<M>(c, rho);
         int k = 0;
         for (k = 1; k <= o.max_admm; ++k) {
-            admm_iter<M, P>(c, rho, o.alpha);
+            admm_iter<M, P>(c, rho, o.alpha, o.sigma);
             const bool cc = o.early_exit && (k % o.check_every == 0);
             const bool cr = (k % o.k_rho_iter == 0) && k < o.max_admm;
             if (cc || cr || k == o.max_admm) {
@@ -1719,7 +1746,7 @@ __global__ void __launch_bounds__(256, 2) plain_admm(KLayout L, KOpts o, KParams
     __shared__ float red[32 * 8];
     float rho = ps[i].rho;
     int nf = 0;
-    admm_iter<M, kCR>(c, rho, o.alpha);
+    admm_iter<M, kCR>(c, rho, o.alpha, o.sigma);
     const bool cr = (k % o.k_rho_iter == 0) && k < o.max_admm;
     if (cr || k == o.max_admm) {
         const Res r = residuals<M>(c, red);

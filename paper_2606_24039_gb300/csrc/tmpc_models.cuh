@@ -14,7 +14,7 @@
 namespace tmpc {
 
 enum { MODEL_DI = 0, MODEL_LINEAR = 1, MODEL_BICYCLE = 2, MODEL_QUAD = 3, MODEL_BICYCLE_TRAP = 4,
-       MODEL_BICYCLE_NEWTON = 5, MODEL_COUNT = 6 };
+       MODEL_BICYCLE_NEWTON = 5, MODEL_SRB = 6, MODEL_COUNT = 7 };
 
 // the kinematic bicycle under its three time discretisations (Remark A1): implicit
 // midpoint, trapezoidal, and the explicit map defined by Newton steps on the midpoint rule
@@ -34,6 +34,7 @@ __host__ __device__ inline ModelDims model_dims(int model, int lnx, int lnu, int
         case MODEL_BICYCLE_TRAP:
         case MODEL_BICYCLE_NEWTON: return {6, 2, 5};
         case MODEL_QUAD: return {6, 2, 2};
+        case MODEL_SRB: return {12, 6, 6};
         default: return {lnx, lnu, lng};
     }
 }
@@ -205,6 +206,113 @@ __device__ inline void quad_rk4(const R* x, const R* u, const float* dyn, R* phi
         for (int i = 0; i < 6; ++i)
             for (int j = 0; j < 6; ++j) dPx[i * 6 + j] = (i == j ? R(1) : R(0)) + dt / R(6) * accx[i * 6 + j];
         for (int i = 0; i < 12; ++i) dPu[i] = dt / R(6) * accu[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// single-rigid-body humanoid (App. humanoid SRB dynamics): state (p, Theta =
+// ZYX (roll, pitch, yaw), v, omega body rates), control (f_L, f_R) in the world
+// frame; dyn = [dt, m, Ixx, Iyy, Izz, r_L (3), r_R (3), gravity]:
+//   p_dot = v, Theta_dot = T(Theta) omega, v_dot = (f_L + f_R) / m + g,
+//   omega_dot = I^-1 (r_L x f_L + r_R x f_R - omega x (I omega)).
+// ---------------------------------------------------------------------------
+template <class R>
+struct SrbTrig {
+    R sp, cp, tt, sc;   // sin / cos of roll, tan and 1 / cos of pitch
+};
+template <class R>
+__device__ __forceinline__ SrbTrig<R> srb_trig(const R* x) {
+    SrbTrig<R> q;
+    msincos(x[3], &q.sp, &q.cp);
+    q.tt = mtan(x[4]);
+    q.sc = R(1) / mcos(x[4]);
+    return q;
+}
+
+template <class R>
+__device__ __forceinline__ void srb_fc(const R* x, const R* u, const float* dyn, const SrbTrig<R>& q, R* f) {
+    const R m = dyn[1], Ix = dyn[2], Iy = dyn[3], Iz = dyn[4], g = dyn[11];
+    const float* rl = dyn + 5;
+    const float* rr = dyn + 8;
+    const R wx = x[9], wy = x[10], wz = x[11];
+    f[0] = x[6];
+    f[1] = x[7];
+    f[2] = x[8];
+    f[3] = wx + q.sp * q.tt * wy + q.cp * q.tt * wz;
+    f[4] = q.cp * wy - q.sp * wz;
+    f[5] = q.sp * q.sc * wy + q.cp * q.sc * wz;
+    f[6] = (u[0] + u[3]) / m;
+    f[7] = (u[1] + u[4]) / m;
+    f[8] = (u[2] + u[5]) / m - g;
+    // torque r_L x f_L + r_R x f_R - omega x (I omega)
+    const R hx = Ix * wx, hy = Iy * wy, hz = Iz * wz;
+    const R tx = (R)rl[1] * u[2] - (R)rl[2] * u[1] + (R)rr[1] * u[5] - (R)rr[2] * u[4] - (wy * hz - wz * hy);
+    const R ty = (R)rl[2] * u[0] - (R)rl[0] * u[2] + (R)rr[2] * u[3] - (R)rr[0] * u[5] - (wz * hx - wx * hz);
+    const R tz = (R)rl[0] * u[1] - (R)rl[1] * u[0] + (R)rr[0] * u[4] - (R)rr[1] * u[3] - (wx * hy - wy * hx);
+    f[9] = tx / Ix;
+    f[10] = ty / Iy;
+    f[11] = tz / Iz;
+}
+
+// directional derivative df = (df_c/dx) dx + (df_c/du) du at (x, u)
+template <class R>
+__device__ __forceinline__ void srb_jvp(const R* x, const float* dyn, const SrbTrig<R>& q, const R* dx, const R* du,
+                                        R* df) {
+    const R m = dyn[1], Ix = dyn[2], Iy = dyn[3], Iz = dyn[4];
+    const float* rl = dyn + 5;
+    const float* rr = dyn + 8;
+    const R wx = x[9], wy = x[10], wz = x[11];
+    const R dwx = dx[9], dwy = dx[10], dwz = dx[11], dph = dx[3], dth = dx[4];
+    const R sec2 = q.sc * q.sc;
+    df[0] = dx[6];
+    df[1] = dx[7];
+    df[2] = dx[8];
+    df[3] = dwx + q.sp * q.tt * dwy + q.cp * q.tt * dwz + dph * (q.cp * q.tt * wy - q.sp * q.tt * wz) +
+            dth * (q.sp * sec2 * wy + q.cp * sec2 * wz);
+    df[4] = q.cp * dwy - q.sp * dwz - dph * (q.sp * wy + q.cp * wz);
+    df[5] = q.sp * q.sc * dwy + q.cp * q.sc * dwz + dph * (q.cp * q.sc * wy - q.sp * q.sc * wz) +
+            dth * q.tt * q.sc * (q.sp * wy + q.cp * wz);
+    df[6] = (du[0] + du[3]) / m;
+    df[7] = (du[1] + du[4]) / m;
+    df[8] = (du[2] + du[5]) / m;
+    // d(omega x I omega) = d omega x I omega + omega x I d omega
+    const R hx = Ix * wx, hy = Iy * wy, hz = Iz * wz, dhx = Ix * dwx, dhy = Iy * dwy, dhz = Iz * dwz;
+    const R gx = (dwy * hz - dwz * hy) + (wy * dhz - wz * dhy);
+    const R gy = (dwz * hx - dwx * hz) + (wz * dhx - wx * dhz);
+    const R gz = (dwx * hy - dwy * hx) + (wx * dhy - wy * dhx);
+    df[9] = ((R)rl[1] * du[2] - (R)rl[2] * du[1] + (R)rr[1] * du[5] - (R)rr[2] * du[4] - gx) / Ix;
+    df[10] = ((R)rl[2] * du[0] - (R)rl[0] * du[2] + (R)rr[2] * du[3] - (R)rr[0] * du[5] - gy) / Iy;
+    df[11] = ((R)rl[0] * du[1] - (R)rl[1] * du[0] + (R)rr[0] * du[4] - (R)rr[1] * du[3] - gz) / Iz;
+}
+
+// RK4 step x+ = Phi(x, u) (dt = dyn[0]); with Am != nullptr also dPhi/d(x, u) (12 x 18,
+// row k at Am + k ld), column by column: each unit direction is carried through the
+// four stages by directional derivatives (forward mode).
+template <class R>
+__device__ inline void srb_rk4(const R* x, const R* u, const float* dyn, R* phi, R* Am, int ld) {
+    const R dt = dyn[0];
+    R xs[4][12], k[4][12];
+    SrbTrig<R> q[4];
+    const R cst[4] = {R(0), R(0.5), R(0.5), R(1)};
+    for (int st = 0; st < 4; ++st) {
+        for (int i = 0; i < 12; ++i) xs[st][i] = x[i] + (st ? cst[st] * dt * k[st - 1][i] : R(0));
+        q[st] = srb_trig<R>(xs[st]);
+        srb_fc<R>(xs[st], u, dyn, q[st], k[st]);
+    }
+    for (int i = 0; i < 12; ++i) phi[i] = x[i] + dt / R(6) * (k[0][i] + R(2) * k[1][i] + R(2) * k[2][i] + k[3][i]);
+    if (!Am) return;
+    for (int j = 0; j < 18; ++j) {
+        R d0[12], du[6], dxs[12], dk[12], acc[12];
+        for (int i = 0; i < 12; ++i) d0[i] = (i == j) ? R(1) : R(0);
+        for (int i = 0; i < 6; ++i) du[i] = (i + 12 == j) ? R(1) : R(0);
+        for (int i = 0; i < 12; ++i) acc[i] = R(0);
+        for (int st = 0; st < 4; ++st) {
+            for (int i = 0; i < 12; ++i) dxs[i] = d0[i] + (st ? cst[st] * dt * dk[i] : R(0));
+            srb_jvp<R>(xs[st], dyn, q[st], dxs, du, dk);
+            const R wgt = (st == 1 || st == 2) ? R(2) : R(1);
+            for (int i = 0; i < 12; ++i) acc[i] += wgt * dk[i];
+        }
+        for (int i = 0; i < 12; ++i) Am[i * ld + j] = d0[i] + dt / R(6) * acc[i];
     }
 }
 

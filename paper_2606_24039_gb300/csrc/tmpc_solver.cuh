@@ -226,6 +226,12 @@ __device__ inline void stage_dyn(const Ctx& c, int t, const float* zt, const flo
             }
             break;
         }
+        case MODEL_SRB: {
+            float phi[12];
+            srb_rk4<float>(zt, zt + 12, c.dyn, phi, Am, n);
+            for (int k = 0; k < 12; ++k) f[k] = phi[k] - zn[k];
+            break;
+        }
         case MODEL_BICYCLE_TRAP: {
             // f_t = x_t + dt/2 (f_c(z_t) + f_c(z_{t+1})) - x_{t+1}  (Remark A1)
             const float dt = c.dyn[0];
@@ -332,6 +338,12 @@ __device__ inline void stage_con(const Ctx& c, const float* z, float* g, float* 
             g[0] = z[6]; g[1] = z[7];
             if (G) { G[0 * n + 6] = 1.f; G[1 * n + 7] = 1.f; }
             break;
+        case MODEL_SRB:   // the friction cone as a box on the six foot-force components
+            for (int r = 0; r < 6; ++r) {
+                g[r] = z[12 + r];
+                if (G) G[r * n + 12 + r] = 1.f;
+            }
+            break;
         case MODEL_BICYCLE:
         case MODEL_BICYCLE_TRAP:
         case MODEL_BICYCLE_NEWTON: {  // accel, steer rate, speed, steering angle, lateral error
@@ -414,6 +426,7 @@ __device__ __forceinline__ int g_col(const Ctx& c, int r) {
         case MODEL_LINEAR: return c.nx + r;
         case MODEL_DI: return r == 0 ? 4 : r == 1 ? 5 : r == 2 ? 2 : 3;
         case MODEL_QUAD: return r == 0 ? 6 : 7;
+        case MODEL_SRB: return 12 + r;
     }
     return -1;
 }
@@ -422,6 +435,7 @@ __device__ __forceinline__ int g_row(const Ctx& c, int j) {
         case MODEL_LINEAR: return (j >= c.nx && j - c.nx < c.ng) ? j - c.nx : -1;
         case MODEL_DI: return j == 4 ? 0 : j == 5 ? 1 : j == 2 ? 2 : j == 3 ? 3 : -1;
         case MODEL_QUAD: return j == 6 ? 0 : j == 7 ? 1 : -1;
+        case MODEL_SRB: return j >= 12 && j < 18 ? j - 12 : -1;
     }
     return -1;
 }
@@ -460,6 +474,16 @@ __device__ inline void rollout(const Ctx& c, const KOpts& o) {
             }
             __syncthreads();
         }
+        return;
+    }
+    if (c.model == MODEL_SRB) {   // explicit RK4 map, one stage after the other
+        if (threadIdx.x == 0)
+            for (int t = 0; t < c.N; ++t) {
+                float xn[12];
+                srb_rk4<float>(c.zb + t * n, c.zb + t * n + 12, c.dyn, xn, nullptr, 0);
+                for (int k = 0; k < 12; ++k) c.zb[(t + 1) * n + k] = xn[k];
+            }
+        __syncthreads();
         return;
     }
     if (threadIdx.x == 0) {
@@ -561,7 +585,7 @@ __device__ inline void linearize(const Ctx& c) {
     } else {
         for (int t = threadIdx.x; t < N; t += blockDim.x) {
             float Apq[6 * 8];
-            float f[8];
+            float f[12];
             stage_dyn(c, t, c.zb + t * n, c.zb + (t + 1) * n, f, c.Am + t * c.amS,
                       cP ? Apq : c.Ap + t * c.apS);
             for (int k = 0; k < nx; ++k) c.fv[(t + 1) * nx + k] = f[k];

@@ -17,11 +17,13 @@ bench = pytest.importorskip("bench")
 def test_launches_follow_the_launch_form():
     pb = w.racing(B=4, N=50)
     bic = w.MODEL_BICYCLE
-    assert bench.launches_per_step(pb, 0) == (1, 1)                    # one persistent launch each way
+    # backward: the CTA pass, the sweep kernel of the direct solve, the finishing pass
+    assert bench.launches_per_step(pb, 0) == (1, 3)
     assert bench.launches_per_step(pb, 1) == (1, 1)                    # generic kernel
     assert bench.launches_per_step(pb, 0, {bic: 4}) == (1, 1)          # warp LDL': generic backward
     plain = 2 + pb.opts.max_sqp * (2 + pb.opts.max_admm)
-    assert bench.launches_per_step(pb, 0, {bic: 7}) == (plain, 1)      # one launch per phase
+    assert bench.launches_per_step(pb, 0, {bic: 7}) == (plain, 3)      # one launch per phase
+    assert bench.launches_per_step(pb, 0, {bic: 6}) == (1, 1)          # cluster: sweeps on its first warp
     assert plain == 522
 
 
@@ -30,7 +32,7 @@ def test_launches_of_a_mixed_batch():
     models = set(int(m) for m in np.unique(pb.model))
     fast = models & set(bench.FAST_MODELS)
     fwd, bwd = bench.launches_per_step(pb, 0)
-    assert fwd == len(fast) and bwd == len(fast)
+    assert fwd == len(fast) and bwd == 3 * len(fast)
     # warp LDL' groups share one generic backward launch
     fwd, bwd = bench.launches_per_step(pb, 0, {m: 4 for m in fast})
     assert fwd == len(fast) and bwd == 1

@@ -24,6 +24,8 @@ through unconverged inner loops and discrete line-search decisions):
     the residual bar adds the Lipschitz allowance 10 ||dz||_inf.
 """
 import dataclasses
+import json
+import os
 
 import numpy as np
 import pytest
@@ -154,8 +156,19 @@ def _replay_check(pb, i, st, opts=None, trials=2):
     return rep, max(REL_TOL, 10.0 * dev), None
 
 
+def _record(entry):
+    """With TMPC_PARITY_RECORD=<path>, append one JSON line per compared instance
+    (the bars each instance was held to; see the profiles directory)."""
+    path = os.environ.get("TMPC_PARITY_RECORD")
+    if path:
+        entry["test"] = os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]
+        with open(path, "a") as f:
+            f.write(json.dumps(entry) + "\n")
+
+
 def _compare(pb, sol, idx, allow_flips=0, opts=None, sensitivity=False):
     """Strict or sensitivity-mode comparison of instances idx (module docstring)."""
+    from paper_2606_24039_gb300._abi import ls_history
     errs, flips = [], []
     for i in idx:
         inst = pb.instance(i)
@@ -165,10 +178,20 @@ def _compare(pb, sol, idx, allow_flips=0, opts=None, sensitivity=False):
         assert np.all(sol["z"][i, N + 1:] == 0)
         assert np.all(sol["z"][i, :, n:] == 0)
         st = sol["stats"][i]
+        rec = {"workload": pb.name, "instance": int(i), "mode": "sensitivity" if sensitivity else "strict"}
         if sensitivity:
             o, bar, why = _replay_check(pb, i, st, opts)
+            if os.environ.get("TMPC_PARITY_RECORD"):
+                own = osqp.solve(pb.instance(i), opts or pb.opts, record=True)
+                steps = ls_history(st, st[0])
+                own_steps = [h.get("alpha") for h in own["history"]]
+                rec.update(gpu_steps=steps, oracle_steps=own_steps, steps_differ=int(sum(
+                    a != b for a, b in zip(steps, own_steps)) + abs(len(steps) - len(own_steps))),
+                    err_unreplayed=_rel(zg, own["z"]))
             if why is not None:
                 flips.append((i, why))
+                rec.update(flip=why)
+                _record(rec)
                 continue
         else:
             o, bar = _oracle(pb, i, opts), REL_TOL
@@ -180,6 +203,8 @@ def _compare(pb, sol, idx, allow_flips=0, opts=None, sensitivity=False):
         fp, fd = _fp32_floor(pb, i, o)
         res_ok = abs(st[2] - os_["r_prim"]) <= RES_TOL * max(1.0, os_["prim_norm"]) + fp + slack and \
                  abs(st[3] - os_["r_dual"]) <= RES_TOL * max(1.0, os_["dual_norm"]) + fd + slack
+        rec.update(err=e, bar=bar, res_slack=slack, fp32_floor=[fp, fd], ok=bool(e <= bar and res_ok))
+        _record(rec)
         if e > bar or not res_ok:
             flips.append((i, e, bar, st[2], os_["r_prim"], st[3], os_["r_dual"], st[4], os_["rho_bar"]))
     assert len(flips) <= allow_flips, f"instances off the oracle: {flips}"
@@ -361,6 +386,26 @@ def test_racing_full_batch_sampled():
     idx = np.random.default_rng(5).choice(pb.B, 12, replace=False)
     _compare(pb, sol, idx, sensitivity=True)
     assert np.all(np.isin(sol["status"], (0, 1)))
+
+
+def test_racing_strict_where_the_steps_agree():
+    """Strict mode on the racing model (32 instances, N = 50, 3 SQP x 50 ADMM):
+    no replay and no Lipschitz allowance.  Every instance takes exactly the
+    line-search steps of the oracle's own (unreplayed) run, the same SQP / ADMM
+    counts, and its solution is within 1e-4 of the oracle's."""
+    from paper_2606_24039_gb300._abi import ls_history
+    pb = w.racing(B=32, N=50, max_sqp=3, max_admm=50)
+    s, sol, _ = _run(pb)
+    errs = []
+    for i in range(pb.B):
+        st = sol["stats"][i]
+        o = osqp.solve(pb.instance(i), pb.opts, record=True)
+        assert ls_history(st, st[0]) == [h.get("alpha") for h in o["history"]], i
+        assert st[0] == o["stats"]["sqp_iters"] and st[1] == o["stats"]["admm_iters"]
+        e = _rel(sol["z"][i], o["z"])
+        _record({"workload": pb.name, "instance": i, "mode": "strict_racing", "err": e, "bar": REL_TOL})
+        errs.append(e)
+    assert max(errs) <= REL_TOL, max(errs)
 
 
 def test_tracking_full_batch_sampled():

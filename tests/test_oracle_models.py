@@ -26,6 +26,8 @@ def _instances():
         out.append(p.instance(0))
     p = w.tracking(B=1, nx=5, nu=3, N=4)
     out.append(p.instance(0))
+    p = w.humanoid(B=1, N=4)
+    out.append(p.instance(0))
     p = w.uneven(B=8, N_lo=4, N_hi=6, seed=3)
     for i in range(8):
         if p.model[i] == w.MODEL_QUAD:
@@ -143,3 +145,87 @@ def test_trapezoidal_rule_is_exact_for_uniform_motion():
     inst = dict(model=w.MODEL_BICYCLE_TRAP, nx=6, nu=2, dyn=dyn, track=tab)
     f, _, _ = models.dynamics(inst, z)
     assert np.max(np.abs(f)) < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# single-rigid-body humanoid (App. humanoid SRB dynamics): closed-form motions
+# ----------------------------------------------------------------------------
+def _srb_dyn():
+    return w.humanoid(B=1).dyn[0]
+
+
+def test_srb_standing_balance_is_an_equilibrium():
+    """Feet below the CoM in x, each carrying half the weight, at rest and level:
+    the net force and the net torque vanish, so every rate is zero."""
+    d = _srb_dyn()
+    m, g = d[1], d[11]
+    x = np.zeros(12)
+    x[2] = w.SRB_COM_HEIGHT
+    u = np.array([0.0, 0.0, 0.5 * m * g, 0.0, 0.0, 0.5 * m * g])
+    f, _, _ = models.srb_fc(x[None], u[None], d)
+    assert np.max(np.abs(f)) < 1e-12
+
+
+def test_srb_torque_free_body_follows_eulers_equations():
+    """No contact forces: free fall (v_dot = -g e_z) and Euler's equations of a
+    rigid body with principal moments (Ixx, Iyy, Izz), written out per axis."""
+    d = _srb_dyn()
+    Ix, Iy, Iz, g = d[2], d[3], d[4], d[11]
+    wx, wy, wz = 0.7, -1.3, 2.1
+    x = np.zeros(12)
+    x[6:9] = [0.2, -0.1, 0.4]
+    x[9:12] = [wx, wy, wz]
+    f, _, _ = models.srb_fc(x[None], np.zeros((1, 6)), d)
+    assert np.allclose(f[0, 0:3], [0.2, -0.1, 0.4], atol=0, rtol=1e-15)
+    assert np.allclose(f[0, 6:9], [0.0, 0.0, -g], atol=1e-15)
+    expect = [(Iy - Iz) / Ix * wy * wz, (Iz - Ix) / Iy * wz * wx, (Ix - Iy) / Iz * wx * wy]
+    assert np.allclose(f[0, 9:12], expect, rtol=1e-13, atol=1e-15)
+
+
+def test_srb_euler_angle_rates():
+    """ZYX Euler rates from body rates: identity when level; at zero roll
+    theta_dot = (wx + tan(pitch) wz, wy, wz / cos(pitch)); at zero pitch a
+    rotation of (wy, wz) by the roll angle."""
+    d = _srb_dyn()
+    om = np.array([0.3, -0.5, 0.9])
+    for ang, expect in (((0.0, 0.0, 0.4), om),
+                        ((0.0, 0.3, 0.0), [om[0] + np.tan(0.3) * om[2], om[1], om[2] / np.cos(0.3)]),
+                        ((0.4, 0.0, 0.0), [om[0], np.cos(0.4) * om[1] - np.sin(0.4) * om[2],
+                                           np.sin(0.4) * om[1] + np.cos(0.4) * om[2]])):
+        x = np.zeros(12)
+        x[3:6] = ang
+        x[9:12] = om
+        f, _, _ = models.srb_fc(x[None], np.zeros((1, 6)), d)
+        assert np.allclose(f[0, 3:6], expect, rtol=1e-14, atol=1e-15), ang
+
+
+def test_srb_foot_force_gives_r_cross_f():
+    """One horizontal force on the left foot: acceleration f / m and angular
+    acceleration (r_L x f) / I, the cross product written out."""
+    d = _srb_dyn()
+    m, Ix, Iy, Iz = d[1], d[2], d[3], d[4]
+    rx, ry, rz = d[5], d[6], d[7]
+    F = np.array([3.0, -2.0, 0.0])
+    u = np.concatenate([F, np.zeros(3)])
+    f, _, _ = models.srb_fc(np.zeros((1, 12)), u[None], d)
+    tau = [ry * F[2] - rz * F[1], rz * F[0] - rx * F[2], rx * F[1] - ry * F[0]]
+    assert np.allclose(f[0, 6:9], F / m + np.array([0, 0, -d[11]]), rtol=1e-14, atol=1e-15)
+    assert np.allclose(f[0, 9:12], np.array(tau) / [Ix, Iy, Iz], rtol=1e-14, atol=1e-15)
+
+
+def test_srb_rk4_is_exact_in_free_fall_and_constant_yaw_rate():
+    """RK4 integrates polynomials of degree <= 4 exactly: a ballistic CoM
+    (p + v dt - g dt^2 / 2 e_z) and a constant yaw rate at zero roll and pitch."""
+    d = _srb_dyn()
+    dt, g = d[0], d[11]
+    x = np.zeros(12)
+    x[0:3] = [0.1, 0.2, 0.7]
+    x[5] = 0.3
+    x[6:9] = [1.0, -0.5, 2.0]
+    x[11] = 0.8
+    phi, _, _ = models.rk4(models.srb_fc, x[None], np.zeros((1, 6)), d)
+    p = x[0:3] + x[6:9] * dt + 0.5 * np.array([0, 0, -g]) * dt**2
+    assert np.allclose(phi[0, 0:3], p, rtol=1e-14, atol=1e-15)
+    assert np.allclose(phi[0, 6:9], x[6:9] + np.array([0, 0, -g]) * dt, rtol=1e-14, atol=1e-15)
+    assert np.isclose(phi[0, 5], 0.3 + 0.8 * dt, rtol=1e-14)
+    assert np.allclose(phi[0, 9:12], x[9:12], atol=1e-15)

@@ -53,16 +53,18 @@ MODEL_QUAD = 3      # planar quadrotor, explicit RK4.       dyn = [dt, mass, ine
 MODEL_BICYCLE_TRAP = 4    # kinematic bicycle, trapezoidal rule (implicit).        dyn as MODEL_BICYCLE
 MODEL_BICYCLE_NEWTON = 5  # kinematic bicycle, explicit map x+ = Phi(x, u) defined by 3 Newton steps
                           # on the implicit midpoint rule, Jacobians by the implicit function theorem
+MODEL_SRB = 6       # single-rigid-body humanoid, explicit RK4. dyn = [dt, mass, Ixx, Iyy, Izz, r_L (3), r_R (3), gravity]
 
 MODEL_NAMES = {MODEL_DI: "double_integrator", MODEL_LINEAR: "linear",
                MODEL_BICYCLE: "bicycle", MODEL_QUAD: "planar_quadrotor",
-               MODEL_BICYCLE_TRAP: "bicycle_trapezoidal", MODEL_BICYCLE_NEWTON: "bicycle_newton_map"}
+               MODEL_BICYCLE_TRAP: "bicycle_trapezoidal", MODEL_BICYCLE_NEWTON: "bicycle_newton_map",
+               MODEL_SRB: "srb_humanoid"}
 BICYCLES = (MODEL_BICYCLE, MODEL_BICYCLE_TRAP, MODEL_BICYCLE_NEWTON)
 INTEGRATORS = {"midpoint": MODEL_BICYCLE, "trapezoidal": MODEL_BICYCLE_TRAP, "newton_map": MODEL_BICYCLE_NEWTON}
 
 # fixed (nx, nu, ng) of the nonlinear / fixed-size models
 MODEL_DIMS = {MODEL_DI: (4, 2, 4), MODEL_BICYCLE: (6, 2, 5), MODEL_QUAD: (6, 2, 2),
-              MODEL_BICYCLE_TRAP: (6, 2, 5), MODEL_BICYCLE_NEWTON: (6, 2, 5)}
+              MODEL_BICYCLE_TRAP: (6, 2, 5), MODEL_BICYCLE_NEWTON: (6, 2, 5), MODEL_SRB: (12, 6, 6)}
 
 INF = np.inf
 
@@ -547,4 +549,57 @@ def linear_rl(B=64, N=40, nx=8, nu=4, u_max=1.0, seed=1006, theta=None, tol=1e-5
     pb = ProblemBatch(nx, nu, ng, N, np.full(B, N, np.int32), np.full(B, MODEL_LINEAR, np.int32),
                       opts=opts, name=f"linear_rl_B{B}_N{N}_nx{nx}_nu{nu}_umax{u_max:g}", **a)
     pb.extra = dict(A=A, B=Bm, b=b, theta=th, u_max=u_max)
+    return pb
+
+
+# ----------------------------------------------------------------------------
+# humanoid standing balance with single-rigid-body MPC (the SRB model of the
+# paper's humanoid imitation-learning appendix)
+# ----------------------------------------------------------------------------
+SRB_MASS = 33.34                         # kg (paper)
+SRB_INERTIA = (1.6, 1.4, 0.35)           # kg m^2, body frame, diagonal (not given in the paper)
+SRB_COM_HEIGHT = 0.72                    # m above the feet (not given in the paper)
+SRB_FOOT_L = (0.0, 0.1, -SRB_COM_HEIGHT)  # contact points from the CoM (not given in the paper)
+SRB_FOOT_R = (0.0, -0.1, -SRB_COM_HEIGHT)
+SRB_U_MIN = (-240.0, -240.0, 0.0, -240.0, -240.0, 0.0)      # N (paper: friction cone as a box)
+SRB_U_MAX = (240.0, 240.0, 400.0, 240.0, 240.0, 400.0)
+SRB_THETA = np.log([50.0, 50.0, 100.0, 30.0, 30.0, 10.0, 5.0, 5.0, 5.0, 1.0, 1.0, 1.0])   # synthetic expert
+
+
+def humanoid(B=100, N=20, seed=1007, theta=None, max_sqp=5, max_admm=100, dt=0.025) -> ProblemBatch:
+    """Standing balance by SRB MPC: state (p, Theta (ZYX roll, pitch, yaw), v,
+    omega) in R^12, control the two foot forces (f_L, f_R) in the world frame,
+    RK4 at dt = 0.025, horizon N = 20.  Stage cost (x - x_ref)' Q(theta)
+    (x - x_ref) + (u - u_ref)' R (u - u_ref) with Q = diag(exp(theta)) and R =
+    1e-3 I (written with the 1/2 of the cost convention: Qd = 2 exp(theta), Rd
+    = 2e-3); x_ref the standing pose (CoM at SRB_COM_HEIGHT above the origin,
+    level, at rest), u_ref = m g / 2 upward on each foot; the friction cone as
+    the paper's box on the forces.  x0 = the standing pose perturbed uniformly
+    (position 3 cm, angles 0.1 rad, velocity 0.2 m/s, angular rate 0.5 rad/s).
+    theta defaults to SRB_THETA (one vector for every instance; a [B, 12] array
+    gives one per instance)."""
+    nx, nu, ng = 12, 6, 6
+    n_dyn = 12
+    th = np.broadcast_to(SRB_THETA if theta is None else np.asarray(theta, dtype=np.float64), (B, nx))
+    a = _empty(B, nx, nu, ng, N, n_dyn, 0)
+    a["z_init"] = np.zeros((B, N + 1, nx + nu))
+    xref = np.zeros(nx)
+    xref[2] = SRB_COM_HEIGHT
+    uref = np.array([0.0, 0.0, 0.5 * SRB_MASS * GRAVITY] * 2)
+    for i in range(B):
+        r = np.random.default_rng([seed, i])
+        a["x0"][i] = xref + r.uniform(-1, 1, nx) * np.repeat([0.03, 0.1, 0.2, 0.5], 3)
+        a["Qd"][i, :, :] = 2.0 * np.exp(th[i])
+        a["Rd"][i, :, :] = 2e-3
+        a["ref"][i, :, :nx] = xref
+        a["ref"][i, :, nx:] = uref
+        a["lo"][i, :, :] = SRB_U_MIN
+        a["hi"][i, :, :] = SRB_U_MAX
+        a["dyn"][i] = [dt, SRB_MASS, *SRB_INERTIA, *SRB_FOOT_L, *SRB_FOOT_R, GRAVITY]
+        a["z_init"][i, :, :nx] = a["x0"][i]
+        a["z_init"][i, :, nx:] = uref
+    opts = Options(max_sqp=max_sqp, max_admm=max_admm)
+    pb = ProblemBatch(nx, nu, ng, N, np.full(B, N, np.int32), np.full(B, MODEL_SRB, np.int32),
+                      opts=opts, name=f"humanoid_B{B}_N{N}", **a)
+    pb.extra = dict(theta=np.array(th), xref=xref, uref=uref)
     return pb
