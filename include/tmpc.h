@@ -277,7 +277,8 @@ typedef struct {
  * integrator, bicycle or quadrotor, times the group's forward solve from x0
  * [B][nx] (DEVICE) in each candidate form -- cyclic reduction with shared
  * arenas at 256 and 128 threads per CTA, the one-warp block LDL', cyclic
- * reduction with global arenas, the plain per-phase form, and one cluster per
+ * reduction with global arenas at 256 and 128 threads per CTA (the latter four
+ * CTAs per SM), the plain per-phase form, and one cluster per
  * instance when the group is at most about one wave of clusters -- and keeps the
  * fastest for later tmpc_solve / tmpc_backward calls.
  *   init       (DEVICE, may be NULL) warm start of the trials: z, xi, y_eq and

@@ -691,7 +691,7 @@ tmpc_status tmpc_autotune(tmpc_handle* h, const float* x0, const tmpc_solution* 
         const int def_form = G.form, def_threads = G.threads;
         const int t_full = h->o.threads > 0 ? h->o.threads : 256, t_half = h->o.threads > 0 ? h->o.threads : 128;
         std::vector<Cand> cands{{def_form, def_threads}};
-        std::vector<Cand> more{{2, t_full}, {2, t_half}, {4, t_half}, {3, t_full}, {7, t_full}};
+        std::vector<Cand> more{{2, t_full}, {2, t_half}, {4, t_half}, {3, t_full}, {3, t_half}, {7, t_full}};
         if ((long long)G.count * 8 <= 2LL * h->nsm) more.push_back({6, t_full});   // about one wave of clusters
         for (const Cand& c : more) {
             bool seen = false;

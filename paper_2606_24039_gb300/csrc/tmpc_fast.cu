@@ -173,8 +173,10 @@ cudaError_t launch_backward(int model, int cl, int grid, int threads, size_t sme
     const int* flg = dq_flag;
     int* cursor = dq_ctr + 1;
     int exact = o.exact_hessian ? 1 : 0;
-    // one CTA of kDirectWarps warps per SM (the occupancy limit), fewer for small groups
-    const int blocks = std::max(1, std::min(nsm, (count + kDirectWarps - 1) / kDirectWarps));
+    // one CTA of kDirectWarps warps on every SM (the occupancy limit): the sweeps are
+    // bound by each SM's FP64 pipe, so the instances are spread over all SMs (the
+    // warps take them from the cursor as they start), not packed eight to a CTA
+    const int blocks = std::max(1, std::min(nsm, count));
     void* dargs[] = {(void*)&Np, (void*)&order, (void*)&count, (void*)&flg, (void*)&cursor, (void*)&dws,
                      (void*)&dstride, (void*)&exact};
     e = cudaLaunchKernel(t->direct, dim3(blocks), dim3(kDirectWarps * 32), dargs, 0, s);
