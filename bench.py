@@ -28,8 +28,9 @@ solution back.  With the default workload the line also carries
 `--impl reference` times the FP64 CPU oracle (the baseline arm) on a bounded
 sample of the same workload on the host cores.
 
-Under torchrun (N > 1) every rank solves its own batch on its own GPU (weak
-scaling, no collective on the data path); rank 0 prints one JSON line with the
+Under torchrun (N > 1) every rank solves its longest-processing-time-first shard
+of a job batch N times the one-GPU batch on its own GPU (weak scaling, no
+collective on the data path); rank 0 prints one JSON line with the
 max-over-ranks time.
 """
 from __future__ import annotations
@@ -142,11 +143,23 @@ def make_batch(name, B, N, seed, **kw):
     return gen(B=B, N=N, seed=seed, **kw)
 
 
-def workload(args, rank=0, name=None):
+def workload(args, rank=0, name=None, world=1):
+    """The workload's batch for this rank.  Under torchrun (world > 1) the job's
+    batch is world times the one-GPU batch, drawn once with the same seed on every
+    rank, and each rank takes its longest-processing-time-first shard of it (work
+    (N+1) n^2 per instance): the per-GPU work stays that of the one-GPU run (weak
+    scaling), balanced across ranks."""
+    import workloads as w
     name = name or args.workload
     _, B0, N0, seed, _ = WORKLOADS[name]
-    return make_batch(name, (args.batch if name == args.workload else 0) or B0,
-                      (args.horizon if name == args.workload else 0) or N0, seed + 7919 * rank)
+    B = (args.batch if name == args.workload else 0) or B0
+    N = (args.horizon if name == args.workload else 0) or N0
+    if world <= 1:
+        return make_batch(name, B, N, seed)
+    from paper_2606_24039_gb300.shard import instance_work, shard_of
+    full = make_batch(name, B * world, N, seed)
+    n = np.array([sum(w.model_dims(int(m), full.nx, full.nu, full.ng)[:2]) for m in full.model])
+    return full.subset(shard_of(instance_work(full.N, n), world, rank))
 
 
 def describe(name, pb, world=1, solver=0):
@@ -758,7 +771,7 @@ def run_gpu(args):
     build.build()
     peak = fp32_peak(local)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    pb = workload(args, rank)
+    pb = workload(args, rank, world=world)
     suite = not args.no_suite and args.workload == "uneven" and world == 1
     if world > 1:
         dist.barrier()
@@ -771,7 +784,7 @@ def run_gpu(args):
         subs, conv = {}, {}
         if suite:
             for name in SUITE:
-                spb = workload(args, rank, name)
+                spb = workload(args, rank, name, world=world)
                 r = measure(name, spb, args, peak, flush, max(3, args.steps // 4), max(3, args.warmup // 2),
                             autotune=(name == "racing"), bwd=True)
                 if name == "linear_rl":
@@ -779,7 +792,7 @@ def run_gpu(args):
                 r.pop("_kkt", None)
                 subs[name] = r
             for name in ("uneven",) + SUITE:
-                cpb = converged_batch(name, workload(args, rank, name))
+                cpb = converged_batch(name, workload(args, rank, name, world=world))
                 r = measure(name, cpb, args, peak, flush, 2, 1, bwd=False)
                 kkt = r.pop("_kkt")
                 conv[name] = {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],

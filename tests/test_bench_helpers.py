@@ -46,3 +46,19 @@ def test_kernel_names_per_form():
     assert bench.kernel_name(pb, 0, {bic: 4}) == "fast::solve_kernel<MODEL_BICYCLE, kLDL>"
     assert bench.kernel_name(pb, 1) == "solve_kernel (generic)"
     assert bench.kernel_name(w.tracking(B=2), 0) == "solve_kernel (generic)"
+
+
+def test_ranks_take_balanced_shards_of_one_job_batch():
+    """Under torchrun every rank draws the same job batch (world x the one-GPU
+    batch) and takes its longest-processing-time-first shard: the shards cover
+    the job batch exactly once and their (N+1) n^2 work is balanced."""
+    import argparse
+    from paper_2606_24039_gb300.shard import instance_work
+    args = argparse.Namespace(workload="uneven", batch=64, horizon=0)
+    parts = [bench.workload(args, r, world=3) for r in range(3)]
+    full = bench.make_batch("uneven", 64 * 3, 0, bench.WORKLOADS["uneven"][3])
+    key = lambda pb: sorted(map(tuple, np.round(pb.x0, 12)))
+    assert sorted(sum((key(p) for p in parts), [])) == key(full)
+    n = lambda pb: np.array([sum(w.model_dims(int(m), pb.nx, pb.nu, pb.ng)[:2]) for m in pb.model])
+    loads = [float(instance_work(p.N, n(p)).sum()) for p in parts]
+    assert max(loads) - min(loads) <= float(instance_work(full.N, n(full)).max())
