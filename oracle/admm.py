@@ -183,3 +183,59 @@ def admm(qp, opts, x, zg, yf, yg, rho_bar, rho_schedule=None, perturb_S=None):
     return dict(x=x, zg=zg, xi=xi, yf=yf, yg=yg, rho_bar=rho_bar, iters=k,
                 r_prim=r_prim, r_dual=r_dual, prim_norm=pn, dual_norm=dn, refactors=refactors,
                 converged=converged, rho_events=rho_events)
+
+
+def pow2_floor(s):
+    """Largest power of two not above s > 0, taken from the FP32 value of s
+    (s = m 2^e with m in [0.5, 1) gives 2^(e-1)).  Scaling by powers of two is
+    exact in binary floating point, so the scaled QP carries no rounding of its
+    own."""
+    _, e = np.frexp(np.asarray(s, dtype=np.float32).astype(np.float64))
+    return np.ldexp(1.0, e - 1)
+
+
+def rescale_qp(qp, d, sel):
+    """The QP after the change of variables z = D zh that normalises the states
+    and controls (Remark 4, Section III-B).  The paper gives no recipe; the
+    reading built here:
+      D = diag(d) on every stage (d = pow2_floor of the caller's scales, one
+          per state and control component),
+      the dynamics rows (initial condition included) are divided by the scale
+          of the state component they define, E_f = D_x^-1 per stage, so that
+          A^+ = [-I 0] stays a unit block,
+      a row of g that bounds one variable z_j directly (sel[r] = j) is divided
+          by d_j (it stays a unit selector), any other row is left as it is.
+    With Sigma = diag(D, E_f, E_g) the scaled data are P^ = D P D, q^ = D q,
+    C^ = E_f C D, c^ = E_f c, G^ = E_g G D, bounds E_g lo, E_g hi, and the slack
+    penalty of row r in scaled units gamma2 / e_r^2, gamma1 / e_r.
+    Returns (scaled qp, Dv, Ef, Eg): the diagonal scales of every variable,
+    dynamics row and constraint row."""
+    N, n, nx, ng = qp["N"], qp["n"], qp["nx"], qp["ng"]
+    d = pow2_floor(d)
+    Dv = np.tile(d, N + 1)
+    Ef = 1.0 / np.tile(d[:nx], N + 1)
+    er = np.array([1.0 / d[j] if j >= 0 else 1.0 for j in sel])
+    Eg = np.tile(er, N + 1)
+    Dm, Efm, Egm = sp.diags(Dv), sp.diags(Ef), sp.diags(Eg)
+    out = dict(qp)
+    out.update(P=(Dm @ qp["P"] @ Dm).tocsr(), q=Dv * qp["q"],
+               C=(Efm @ qp["C"] @ Dm).tocsr(), c=Ef * qp["c"],
+               G=(Egm @ qp["G"] @ Dm).tocsr(), lo=Eg * qp["lo"], hi=Eg * qp["hi"],
+               gamma2=qp["gamma2"] / Eg ** 2, gamma1=qp["gamma1"] / Eg)
+    return out, Dv, Ef, Eg
+
+
+def admm_rescaled(qp, opts, d, sel, x, zg, yf, yg, rho_bar, **kw):
+    """Algorithm 3 run on the rescaled QP of `rescale_qp`, from the warm start
+    mapped into scaled units (xh = D^-1 x, zh_g = E_g z_g, yh_f = E_f^-1 y_f,
+    yh_g = E_g^-1 y_g), with its results mapped back (x = D xh, z_g = E_g^-1 zh_g,
+    xi = E_g^-1 xih, y_f = E_f yh_f, y_g = E_g yh_g).  rho, the residuals, the
+    termination test and the rho rule all act in scaled units; the returned
+    residuals are the scaled ones.  Parity: pinned by tests/test_oracle_rescale.py
+    (invariance of the converged solution and multipliers, unit scales, and a
+    uniform scale equal to a scaled cost at a fixed count)."""
+    sq, Dv, Ef, Eg = rescale_qp(qp, d, sel)
+    res = admm(sq, opts, x / Dv, Eg * zg, yf / Ef, yg / Eg, rho_bar, **kw)
+    res = dict(res)
+    res.update(x=Dv * res["x"], zg=res["zg"] / Eg, xi=res["xi"] / Eg, yf=Ef * res["yf"], yg=Eg * res["yg"])
+    return res

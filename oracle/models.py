@@ -380,6 +380,24 @@ def constraints(inst, z):
     raise ValueError(model)
 
 
+def selector_rows(inst):
+    """For each constraint row r of g_t, the index j of the stage variable it
+    bounds directly (g_t,r = z_t,j, as `constraints` defines the row), or -1
+    for a row that is a function of several variables (the bicycle's lateral
+    error).  Used by the rescaling of the QP (Remark 4) to divide a box row by
+    its variable's scale."""
+    model, nx, ng = inst["model"], inst["nx"], inst["ng"]
+    if model == MODEL_DI:
+        return np.array([4, 5, 2, 3])
+    if model in (MODEL_LINEAR, MODEL_SRB):
+        return np.arange(nx, nx + ng)
+    if model == MODEL_QUAD:
+        return np.array([6, 7])
+    if model in BICYCLES:
+        return np.array([6, 7, 3, 4, -1])
+    raise ValueError(model)
+
+
 # ----------------------------------------------------------------------------
 # cost (diagonal quadratic + control rate + linear term)
 # ----------------------------------------------------------------------------

@@ -7,7 +7,8 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
                   found from f_t(z_t, z_{t+1}) = 0 by `newton_steps` Newton
                   steps started from an explicit step (exact for explicit models);
   loop            convexify (oracle.qp) -> ADMM (oracle.admm, warm-started
-                  from the current primal-dual point and the previous rho)
+                  from the current primal-dual point and the previous rho; on
+                  the rescaled QP when the instance carries scales, Remark 4)
                   -> line search (Appendix D) -> convergence check (Eq. sqp_stop).
 
 Line search (Appendix D): direction (dz, dxi) = (z*, xi*) - (z, xi); merit
@@ -155,8 +156,13 @@ def solve(inst, opts, warm=None, replay=None, record=False, perturb_S=None):
         x0 = z.reshape(-1)
         zg0 = qp["G"] @ x0
         sched = None if replay is None or replay.get("rho") is None else replay["rho"][it]
-        res = admm_mod.admm(qp, opts, x0, zg0, yf.reshape(-1), yg.reshape(-1), rho_bar,
-                            rho_schedule=sched, perturb_S=perturb_S)
+        if inst.get("scale") is not None:   # normalised states and controls (Remark 4)
+            res = admm_mod.admm_rescaled(qp, opts, inst["scale"], models.selector_rows(inst), x0, zg0,
+                                         yf.reshape(-1), yg.reshape(-1), rho_bar,
+                                         rho_schedule=sched, perturb_S=perturb_S)
+        else:
+            res = admm_mod.admm(qp, opts, x0, zg0, yf.reshape(-1), yg.reshape(-1), rho_bar,
+                                rho_schedule=sched, perturb_S=perturb_S)
         rho_bar = res["rho_bar"]
         admm_iters += res["iters"]
         refactors += res["refactors"]

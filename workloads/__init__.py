@@ -66,6 +66,11 @@ INTEGRATORS = {"midpoint": MODEL_BICYCLE, "trapezoidal": MODEL_BICYCLE_TRAP, "ne
 MODEL_DIMS = {MODEL_DI: (4, 2, 4), MODEL_BICYCLE: (6, 2, 5), MODEL_QUAD: (6, 2, 2),
               MODEL_BICYCLE_TRAP: (6, 2, 5), MODEL_BICYCLE_NEWTON: (6, 2, 5), MODEL_SRB: (12, 6, 6)}
 
+# rows of g that bound one stage variable directly (its index), -1 for other rows;
+# the linear and SRB models bound their controls (index nx + r) and are not listed
+SELECTOR_ROWS = {MODEL_DI: (4, 5, 2, 3), MODEL_QUAD: (6, 7), MODEL_BICYCLE: (6, 7, 3, 4, -1),
+                 MODEL_BICYCLE_TRAP: (6, 7, 3, 4, -1), MODEL_BICYCLE_NEWTON: (6, 7, 3, 4, -1)}
+
 INF = np.inf
 
 
@@ -125,6 +130,7 @@ class ProblemBatch:
     opts: Options
     name: str = ""
     z_init: np.ndarray | None = None   # [B][Nm+1][n] initial primal guess (warm start), or None
+    scale: np.ndarray | None = None    # [B][n] characteristic magnitude of each state / control, or None
     extra: dict = dataclasses.field(default_factory=dict)
 
     @property
@@ -159,7 +165,8 @@ class ProblemBatch:
             nt = int(round(self.dyn[i, 3]))
             tr = self.track[i, :nt + 1].copy()
         z0 = None if self.z_init is None else self.z_init[i, :T, :nx + nu].copy()
-        return dict(model=int(self.model[i]), N=Ni, nx=nx, nu=nu, ng=ng, z_init=z0,
+        sc = None if self.scale is None else self.scale[i, :nx + nu].copy()
+        return dict(model=int(self.model[i]), N=Ni, nx=nx, nu=nu, ng=ng, z_init=z0, scale=sc,
                     x0=self.x0[i, :nx].copy(), Qd=self.Qd[i, :T, :nx].copy(),
                     Rd=self.Rd[i, :T, :nu].copy(), Wd=self.Wd[i, :nu].copy(),
                     ref=ref, lin=lin, lo=self.lo[i, :T, :ng].copy(),
@@ -174,7 +181,35 @@ class ProblemBatch:
             self, N=s(self.N), model=s(self.model), x0=s(self.x0), Qd=s(self.Qd),
             Rd=s(self.Rd), Wd=s(self.Wd), ref=s(self.ref), lin=s(self.lin), lo=s(self.lo),
             hi=s(self.hi), gamma2=s(self.gamma2), gamma1=s(self.gamma1), dyn=s(self.dyn),
-            track=s(self.track), z_init=s(self.z_init), extra=dict(self.extra))
+            track=s(self.track), z_init=s(self.z_init), scale=s(self.scale), extra=dict(self.extra))
+
+
+def magnitude_scales(pb: "ProblemBatch", floor: float = 1.0) -> np.ndarray:
+    """Characteristic magnitude of every state and control of each instance:
+    the largest |value| the component takes in the initial guess (z_init, else
+    x0 for the states), or the largest finite bound of a row that bounds the
+    component alone, floored at `floor`.  Input data for the solver's optional
+    normalisation of states and controls (a user's choice of units, like the
+    bounds themselves); [B][n]."""
+    B, n = pb.B, pb.n
+    out = np.full((B, n), float(floor))
+    for i in range(B):
+        nx, nu, ng = pb.dims_of(i)
+        T = int(pb.N[i]) + 1
+        mag = np.zeros(n)
+        if pb.z_init is not None:
+            mag[:nx + nu] = np.max(np.abs(pb.z_init[i, :T, :nx + nu]), axis=0)
+        else:
+            mag[:nx] = np.abs(pb.x0[i, :nx])
+        for r, j in enumerate(SELECTOR_ROWS.get(int(pb.model[i]), ())):
+            if j < 0 or r >= ng:
+                continue
+            b = np.concatenate([pb.lo[i, :T, r], pb.hi[i, :T, r]])
+            b = np.abs(b[np.isfinite(b)])
+            if b.size:
+                mag[j] = max(mag[j], float(np.max(b)))
+        out[i] = np.maximum(mag, floor)
+    return out
 
 
 def _empty(B, nx, nu, ng, N_max, n_dyn, n_track):
