@@ -166,7 +166,21 @@ typedef struct {
  *   lo, hi [B][Nmax+1][ng]                     bounds of g_t; +-inf = no bound
  *   gamma2, gamma1 [B][ng]                     L2 / L1 slack weights; gamma2 = +inf: hard row
  *   dyn [B][n_dyn]                             model parameters
- *   track [B][n_track+1][4]                    centreline table (x_c, y_c, psi_c, kappa) */
+ *   track [B][n_track+1][4]                    centreline table (x_c, y_c, psi_c, kappa)
+ *   scale [B][nx+nu]                           optional: characteristic magnitude of each state
+ *                                              and control (Remark 4, problem rescaling).
+ *     When given, every ADMM solve runs on the QP in normalised variables z = D zh, with
+ *     D = diag(d) on every stage and d_j the largest power of two not above scale_j (an
+ *     entry that is not positive and finite counts as 1); the dynamics rows are divided by
+ *     the scale of the state they define and a bound row of one variable by that
+ *     variable's scale, the other rows are left as they are.  Powers of two make the
+ *     change of variables exact.  rho, the ADMM residuals, the termination test and the
+ *     rho rule act in the normalised units; the SQP iterate, the line search, the KKT
+ *     test, the returned solution and multipliers and tmpc_backward stay in physical
+ *     units.  Built on the shared-memory kernels (double integrator, bicycle, quadrotor;
+ *     solver 0 or 2..7); a call that would run a scaled instance on the generic kernel,
+ *     and tmpc_solve_static with a scale, return TMPC_ERR_INVALID_ARG before any work
+ *     is enqueued.  NULL = no rescaling. */
 typedef struct {
     const int32_t* N;
     const int32_t* model;
@@ -181,6 +195,7 @@ typedef struct {
     const float* gamma1;
     const float* dyn;
     const float* track;
+    const float* scale;
 } tmpc_params;
 
 /* Solution (z, xi, y) of Algorithm 1 and per-instance diagnostics; DEVICE pointers.

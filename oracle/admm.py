@@ -189,9 +189,11 @@ def pow2_floor(s):
     """Largest power of two not above s > 0, taken from the FP32 value of s
     (s = m 2^e with m in [0.5, 1) gives 2^(e-1)).  Scaling by powers of two is
     exact in binary floating point, so the scaled QP carries no rounding of its
-    own."""
-    _, e = np.frexp(np.asarray(s, dtype=np.float32).astype(np.float64))
-    return np.ldexp(1.0, e - 1)
+    own.  An entry that is not positive and finite counts as 1."""
+    s32 = np.asarray(s, dtype=np.float32).astype(np.float64)
+    ok = np.isfinite(s32) & (s32 > 0.0)
+    _, e = np.frexp(np.where(ok, s32, 1.0))
+    return np.where(ok, np.ldexp(1.0, e - 1), 1.0)
 
 
 def rescale_qp(qp, d, sel):

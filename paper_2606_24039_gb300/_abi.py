@@ -44,7 +44,7 @@ class Params(ctypes.Structure):
                 ("Rd", ctypes.c_void_p), ("Wd", ctypes.c_void_p), ("ref", ctypes.c_void_p),
                 ("lin", ctypes.c_void_p), ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p),
                 ("gamma2", ctypes.c_void_p), ("gamma1", ctypes.c_void_p), ("dyn", ctypes.c_void_p),
-                ("track", ctypes.c_void_p)]
+                ("track", ctypes.c_void_p), ("scale", ctypes.c_void_p)]
 
 
 class Solution(ctypes.Structure):
@@ -140,7 +140,7 @@ def check(code: int, what: str):
         lib = load()
         msg = lib.tmpc_status_string(code).decode()
         extra = lib.tmpc_last_error().decode()
-        raise TmpcError(f"{what} failed: {msg}" + (f" ({extra})" if extra and code == 2 else ""))
+        raise TmpcError(f"{what} failed: {msg}" + (f" ({extra})" if extra and code in (1, 2) else ""))
 
 
 def default_options() -> Options:

@@ -57,6 +57,7 @@ KParams to_kparams(const tmpc_params& p) {
     k.N = p.N; k.model = p.model; k.x0 = nullptr; k.Qd = p.Qd; k.Rd = p.Rd; k.Wd = p.Wd; k.ref = p.ref;
     k.lin = p.lin; k.lo = p.lo; k.hi = p.hi; k.g2 = p.gamma2; k.g1 = p.gamma1; k.dyn = p.dyn;
     k.track = p.track;
+    k.scale = p.scale;
     return k;
 }
 
@@ -238,7 +239,7 @@ static bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3
 static tmpc_status check_params(const tmpc_dims& d, const tmpc_params* p) {
     if (!p || !p->N || !p->model || !p->Qd || !p->Rd || !p->lo || !p->hi || !p->dyn) return TMPC_ERR_INVALID_ARG;
     const void* ptrs[] = {p->N, p->model, p->Qd, p->Rd, p->Wd, p->ref, p->lin, p->lo, p->hi,
-                          p->gamma2, p->gamma1, p->dyn, p->track};
+                          p->gamma2, p->gamma1, p->dyn, p->track, p->scale};
     for (const void* q : ptrs)
         if (q && !aligned4(q)) return TMPC_ERR_INVALID_ARG;
     if (d.n_track > 0 && !p->track) return TMPC_ERR_INVALID_ARG;
@@ -532,10 +533,12 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
         sizeof(float) * B * d->nx,                                          // x0
         sizeof(float) * B * T * n, sizeof(float) * B * T * d->ng,           // z, xi
         sizeof(float) * B * T * d->nx, sizeof(float) * B * T * d->ng,       // y_eq, y_ineq
-        sizeof(int) * B, sizeof(float) * B * TMPC_STATS};                   // status, stats
+        sizeof(int) * B, sizeof(float) * B * TMPC_STATS,                   // status, stats
+        sizeof(float) * B * n};                                             // scale
+    constexpr int kStaged = sizeof(sz) / sizeof(sz[0]);
     size_t tot = 0;
-    size_t offs[20];
-    for (int k = 0; k < 20; ++k) { offs[k] = tot; tot += (sz[k] + 255) & ~size_t(255); }
+    size_t offs[kStaged];
+    for (int k = 0; k < kStaged; ++k) { offs[k] = tot; tot += (sz[k] + 255) & ~size_t(255); }
     e = cudaMalloc(&h->stage, tot);
     if (e != cudaSuccess) { set_err("cudaMalloc(staging)", e); tmpc_destroy(h); return TMPC_ERR_OOM; }
     h->stage_bytes = tot;
@@ -560,6 +563,7 @@ tmpc_status tmpc_setup(tmpc_handle** hp, const tmpc_dims* d, const tmpc_options*
     h->ss.y_ineq = reinterpret_cast<float*>(sb + offs[17]);
     h->ss.status = reinterpret_cast<int*>(sb + offs[18]);
     h->ss.stats = reinterpret_cast<float*>(sb + offs[19]);
+    h->sp.scale = reinterpret_cast<float*>(sb + offs[20]);
     *hp = h;
     return TMPC_OK;
 }
@@ -610,8 +614,25 @@ static bool timing_ok(cudaStream_t s) {
     return cs == cudaStreamCaptureStatusNone;
 }
 
+// rescaling (params.scale) is built on the shared-memory kernels only: refuse a
+// call that would send an instance to the generic kernel with a scale
+static bool scale_supported(const tmpc_handle* h, const void* scale) {
+    g_last_error[0] = '\0';
+    if (!scale) return true;
+    for (int g = 0; g < h->n_groups; ++g)
+        if (h->groups[g].model < 0 && h->groups[g].count > 0) {
+            snprintf(g_last_error, sizeof(g_last_error),
+                     "params.scale: the rescaled ADMM runs on the shared-memory kernels (double integrator, "
+                     "bicycle, quadrotor with solver 0 or 2..7); %d instance(s) of this handle use the generic kernel",
+                     h->groups[g].count);
+            return false;
+        }
+    return true;
+}
+
 static tmpc_status launch_solve(tmpc_handle* h, const tmpc_params& p, const float* x0,
                                 const tmpc_solution& out, int warm, cudaStream_t s) {
+    if (!scale_supported(h, p.scale)) return TMPC_ERR_INVALID_ARG;
     KSol ks{out.z, out.xi, out.y_eq, out.y_ineq, out.status, out.stats};
     TMPC_CUDA(cudaMemsetAsync(h->queue, 0, sizeof(int) * 5, s));
     const KOpts ko = to_kopts(h->o);
@@ -809,6 +830,7 @@ tmpc_status tmpc_solve_host(tmpc_handle* h, const tmpc_params* hp, const float* 
     if (!h) return TMPC_ERR_NOT_SETUP;
     if (!hp || !x0 || !ho || !ho->z || !ho->xi || !ho->y_eq || !ho->y_ineq) return TMPC_ERR_INVALID_ARG;
     if (!hp->N || !hp->model || !hp->Qd || !hp->Rd || !hp->lo || !hp->hi || !hp->dyn) return TMPC_ERR_INVALID_ARG;
+    if (!scale_supported(h, hp->scale)) return TMPC_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const tmpc_dims& d = h->d;
     const long long B = d.batch, T = d.N_max + 1, n = d.nx + d.nu;
@@ -830,6 +852,7 @@ tmpc_status tmpc_solve_host(tmpc_handle* h, const tmpc_params* hp, const float* 
     TMPC_CUDA(h2d(hp->dyn, dp.dyn, sizeof(float) * B * d.n_dyn));
     if (hp->track && d.n_track > 0) TMPC_CUDA(h2d(hp->track, dp.track, sizeof(float) * B * (d.n_track + 1) * 4));
     else dp.track = nullptr;
+    if (hp->scale) TMPC_CUDA(h2d(hp->scale, dp.scale, sizeof(float) * B * n)); else dp.scale = nullptr;
     TMPC_CUDA(h2d(x0, h->s_x0, sizeof(float) * B * d.nx));
     tmpc_solution ds = h->ss;
     if (z_init) {
@@ -993,6 +1016,11 @@ tmpc_status tmpc_solve_static(const tmpc_dims* d, const tmpc_options* o, const t
     if (n > 72 || d->nx > 64 || d->ng > 64) return TMPC_ERR_UNSUPPORTED;
     if (check_options(o) != TMPC_OK || check_params(*d, p) != TMPC_OK) return TMPC_ERR_INVALID_ARG;
     if (o->solver != 0 && o->solver != 1) return TMPC_ERR_INVALID_ARG;
+    if (p->scale) {   // the generic kernel has no rescaled ADMM
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "tmpc_solve_static: params.scale is not supported (the generic kernel has no rescaled ADMM)");
+        return TMPC_ERR_INVALID_ARG;
+    }
     if (!aligned4(x0) || !aligned4(out->z) || !aligned4(out->xi) || !aligned4(out->y_eq) ||
         !aligned4(out->y_ineq) || !aligned4(out->status) || (out->stats && !aligned4(out->stats)))
         return TMPC_ERR_INVALID_ARG;

@@ -71,6 +71,8 @@ __host__ __device__ constexpr int top_blocks(int T, int B) {
 constexpr int kCR = 0, kLDL = 1;
 // largest team (CTAs of a cluster) and doubles exchanged per CTA in a team reduction
 constexpr int kTeamMax = 16, kXchDoubles = 40;
+// first entry of the per-variable scales d_j in the cached-weights area par (N <= 8 entries)
+constexpr int kParScale = 16;
 
 // Per-instance arena: one list (name, floats) drives both the layout (carve)
 // and its size (arena_floats), so the two cannot disagree.
@@ -83,7 +85,8 @@ constexpr int kTeamMax = 16, kXchDoubles = 40;
 //   inequality rows:    zg, yg, xi, glo, ghi, xib, ygb, pg   T x NG
 //   equality rows:      yf, pf, cv, yfb, wf       T x NX  (wg: T x NG)
 //   refinement (cluster teams): rs, rd T x N, rcx T x NX, rgx T x NG
-//   cached weights:     par                       32 (W, gamma2, gamma1)
+//   cached weights:     par                       32 (W, gamma2, gamma1; from kParScale on the
+//                                                 power-of-two scales of a rescaled instance)
 //   Jacobians:          Am (A^- per stage, padded stride AMS; one block if LTI), Grow (dense G row)
 // Every array up to rd has a multiple of 4 floats (N = 8), so rows of Am, Grow
 // and the stage vectors (the solves' right-hand sides and results among them)
@@ -137,6 +140,7 @@ struct Inst {
     int* tflags;    // team-visible flags (shared memory for one CTA, global for a cluster)
     double* xch;    // exchange area of the team reductions (global, cluster teams only)
     const float *x0, *Qd, *Rd, *Wd, *ref, *lin, *lo, *hi, *g2, *g1, *dyn, *track;
+    const float* scl;   // magnitudes of the instance's variables for the rescaled ADMM, or nullptr
     float *Dm, *Um, *Fa, *Fb, *Xt, *Wk, *Xc;
     int TD;     // leading dimension of Xt
     int topb;   // most blocks of the reduced top system (kTopBlocks or kTopBlocksCluster)
@@ -166,7 +170,10 @@ struct Inst {
         if (P == kLDL) dx = r;   // the sweep solves in place
         xch = CL ? reinterpret_cast<double*>(Xc) : nullptr;
     }
-    // copy the per-instance weights used in the inner loop into the arena
+    // copy the per-instance weights used in the inner loop into the arena, and the
+    // scales of a rescaled instance: d_j = the largest power of two not above the
+    // caller's magnitude (s = m 2^e, m in [0.5, 1): d = 2^(e-1)); 1 for an entry
+    // that is not positive and finite
     __device__ void cache_params() {
         for (int k = tid; k < NU + 2 * NG; k += nth) {
             float v;
@@ -175,6 +182,13 @@ struct Inst {
             else v = g1 ? g1[k - NU - NG] : 0.f;
             par[k] = v;
         }
+        if (scl)
+            for (int j = tid; j < N; j += nth) {
+                const float v = scl[j];
+                int e = 0;
+                frexpf(v, &e);
+                par[kParScale + j] = (v > 0.f && v < kInf) ? ldexpf(1.f, e - 1) : 1.f;
+            }
     }
     __device__ __forceinline__ const float* Amt(int t) const { return Tr::LTI ? Am : Am + t * AMS; }
     __device__ __forceinline__ float W(int k) const { return par[k]; }

@@ -704,6 +704,76 @@ __device__ __forceinline__ void linearize(const Inst<M>& c) {
 }
 
 // ---------------------------------------------------------------------------
+// Problem rescaling (Remark 4): the ADMM of an instance with scales runs on the
+// QP in normalised variables z = D zh, D = diag(d) on every stage, d_j a power
+// of two.  The dynamics rows are divided by the scale of the state they define
+// (E_f = D_x^-1, so that A^+ keeps its [-I 0] / [A^-_x - 2I, 0] form), a bound
+// row of one variable by that variable's scale (it stays a unit selector), the
+// dense row is left as it is (e = 1).  In scaled units:
+//   A^- -> D_x^-1 A^- D,  G row -> e G D,  P -> D P D (Pd and the rate weight W),
+//   q -> D q,  c -> E_f c,  bounds -> e lo, e hi,  gamma2 -> gamma2 / e^2,
+//   gamma1 -> gamma1 / e,  z -> D^-1 z,  xi -> e xi,  y_f -> E_f^-1 y_f,
+//   y_g -> y_g / e,  z_g -> e z_g.
+// back = false maps the linearisation, the SQP iterate and its multipliers into
+// scaled units before the factorisation; back = true maps everything, the ADMM
+// result included, back to physical units before the line search.  Every factor
+// is a power of two, so both directions are exact.
+// ---------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ void rescale(const Inst<M>& c, bool back) {
+    using Tr = Traits<M>;
+    constexpr int N = Inst<M>::N, NX = Inst<M>::NX, NU = Inst<M>::NU, NG = Inst<M>::NG, AMS = Inst<M>::AMS;
+    const int T = c.T;
+    const float* d = c.par + kParScale;
+    // u_j: the factor of a quantity that scales like d_j (q, a column of C or G)
+    auto u = [&](int j) { return back ? 1.f / d[j] : d[j]; };
+    const int nam = (Tr::LTI ? 1 : c.Nh) * NX * N;
+    for (int e = c.tid; e < nam; e += c.nth) {
+        const int kj = e % (NX * N), k = kj / N, j = kj % N;
+        c.Am[(e / (NX * N)) * AMS + kj] *= u(j) / u(k);
+    }
+    for (int e = c.tid; e < T * N; e += c.nth) {
+        const float f = u(e % N);
+        c.Pd[e] *= f * f;
+        c.qv[e] *= f;
+        c.zb[e] /= f;
+        c.x[e] /= f;
+        if (Tr::DENSE_ROW >= 0) c.Grow[e] *= f;
+    }
+    for (int e = c.tid; e < T * NX; e += c.nth) {
+        const float f = u(e % NX);
+        c.cv[e] /= f;
+        c.yfb[e] *= f;
+        c.yf[e] *= f;
+    }
+    for (int e = c.tid; e < T * NG; e += c.nth) {
+        const int s = Tr::sel(e % NG);
+        if (s >= 0) {
+            const float f = u(s);   // 1 / e of the row
+            c.glo[e] /= f;
+            c.ghi[e] /= f;
+            c.xib[e] /= f;
+            c.xi[e] /= f;
+            c.zg[e] /= f;
+            c.ygb[e] *= f;
+            c.yg[e] *= f;
+        }
+    }
+    if (c.tid == 0) {   // the loops above read only the scales of par, not these weights
+        float* par = c.par;
+        for (int k = 0; k < NU; ++k) par[k] *= u(NX + k) * u(NX + k);
+        for (int r = 0; r < NG; ++r) {
+            const int s = Tr::sel(r);
+            if (s >= 0) {
+                par[NU + r] *= u(s) * u(s);   // gamma2 (infinite on a hard row: stays infinite)
+                par[NU + NG + r] *= u(s);     // gamma1
+            }
+        }
+    }
+    c.sync();
+}
+
+// ---------------------------------------------------------------------------
 // one ADMM iteration in increment form (see tmpc_solver.cuh admm_iter)
 // ---------------------------------------------------------------------------
 // Row vectors of the right-hand side, w_f = y_f + rho_f p_f and
@@ -1121,6 +1191,7 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
         if (it > 0 && o.early_exit) {
             if (kkt<M>(c, rs.red) <= o.eps_c) break;
         }
+        if (c.scl) rescale<M>(c, false);
         ++nfact;
         if (!factor<M, P>(c, o, rho, c.tflags + 1)) note_factor_failure<M>(c, rs.red);
         for (int e = c.tid; e < T * N; e += c.nth) c.x[e] = 0.f;
@@ -1161,6 +1232,7 @@ __device__ __forceinline__ void solve_instance(Inst<M>& c, const KOpts& o, const
             }
         }
         admm_total += (k > o.max_admm) ? o.max_admm : k;
+        if (c.scl) rescale<M>(c, true);
         float ys[1] = {0.f};
         for (int e = c.tid; e < T * NX; e += c.nth) ys[0] = fmaxf(ys[0], fin(c.yf[e]));
         for (int e = c.tid; e < T * NG; e += c.nth) ys[0] = fmaxf(ys[0], fin(c.yg[e]));
@@ -1498,6 +1570,7 @@ __device__ __forceinline__ void bind_instance(Inst<M>& c, const KLayout& L, cons
     c.g1 = p.g1 ? p.g1 + (long long)i * L.ng : nullptr;
     c.dyn = p.dyn + (long long)i * L.n_dyn;
     c.track = p.track ? p.track + (long long)i * (L.n_track + 1) * 4 : nullptr;
+    c.scl = p.scale ? p.scale + (long long)i * L.n : nullptr;
     c.nt = 0;
     if (M == MODEL_BICYCLE) {
         const float ntf = c.dyn[3];
@@ -1726,6 +1799,7 @@ __global__ void __launch_bounds__(256, 2) plain_sqp_begin(KLayout L, KOpts o, KP
     const int T = c.T;
     const float rho = ps[i].rho;
     linearize<M>(c);
+    if (c.scl) rescale<M>(c, false);
     if (!factor<M, kCR>(c, o, rho, c.tflags + 1)) note_factor_failure<M>(c, red);
     for (int e = c.tid; e < T * N; e += c.nth) c.x[e] = 0.f;
     for (int e = c.tid; e < T * NX; e += c.nth) { c.yf[e] = c.yfb[e]; c.pf[e] = -c.cv[e]; }
@@ -1792,6 +1866,7 @@ __global__ void __launch_bounds__(256, 2) plain_sqp_end(KLayout L, KOpts o, KPar
     __shared__ double lsacc[2 * (kMaxLs + 1) + 2];
     const Red rs{red, redd, lsacc, nullptr};
     const int T = c.T;
+    if (c.scl) rescale<M>(c, true);
     float ys[1] = {0.f};
     for (int e = c.tid; e < T * NX; e += c.nth) ys[0] = fmaxf(ys[0], fin(c.yf[e]));
     for (int e = c.tid; e < T * NG; e += c.nth) ys[0] = fmaxf(ys[0], fin(c.yg[e]));

@@ -49,6 +49,7 @@ struct KParams {
     const int* model;
     const float* x0;
     const float *Qd, *Rd, *Wd, *ref, *lin, *lo, *hi, *g2, *g1, *dyn, *track;
+    const float* scale;   // [B][n] magnitudes of the normalised variables (shared-memory kernels), or nullptr
 };
 
 struct KSol {

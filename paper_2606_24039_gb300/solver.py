@@ -12,7 +12,7 @@ import torch
 
 from . import _abi
 
-PARAM_KEYS = ("Qd", "Rd", "Wd", "ref", "lin", "lo", "hi", "gamma2", "gamma1", "dyn", "track")
+PARAM_KEYS = ("Qd", "Rd", "Wd", "ref", "lin", "lo", "hi", "gamma2", "gamma1", "dyn", "track", "scale")
 GRAD_KEYS = ("x0", "Qd", "Rd", "Wd", "ref", "lin", "lo", "hi", "gamma2", "gamma1")
 
 
@@ -45,7 +45,7 @@ def tensors_from_batch(pb, device="cuda") -> dict:
     """Device tensors (FP32 / int32, contiguous) of a problem batch object with
     the attributes of the ABI parameter struct (N, model, x0, Qd, ...)."""
     f = lambda a: None if a is None else torch.as_tensor(a, dtype=torch.float32).contiguous().to(device)
-    out = {k: f(getattr(pb, k)) for k in PARAM_KEYS}
+    out = {k: f(getattr(pb, k, None)) for k in PARAM_KEYS}
     out["x0"] = f(pb.x0)
     out["z_init"] = f(getattr(pb, "z_init", None))
     out["N"] = torch.as_tensor(pb.N, dtype=torch.int32).contiguous().to(device)

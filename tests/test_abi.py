@@ -148,3 +148,15 @@ def test_group_time_mirror_matches_the_header():
     assert [(n, ctype[t]) for t, n in fields] == list(_abi.GroupTime._fields_)
     lib = _abi.load()
     assert lib.tmpc_group_times(None, None, None) == 4
+
+
+def test_params_mirror_matches_the_header():
+    """The ctypes mirror of tmpc_params lists the header's pointers, in order."""
+    from paper_2606_24039_gb300 import _abi
+    src = open(os.path.join(ROOT, "include", "tmpc.h")).read()
+    end = src.index("} tmpc_params;")
+    body = src[src.rindex("typedef struct {", 0, end) + len("typedef struct {"):end]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"\bconst\s+(?:int32_t|float)\s*\*\s*(\w+);", body)
+    assert names == [f for f, _ in _abi.Params._fields_]
+    assert names[-1] == "scale"

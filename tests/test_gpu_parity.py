@@ -166,8 +166,10 @@ def _record(entry):
             f.write(json.dumps(entry) + "\n")
 
 
-def _compare(pb, sol, idx, allow_flips=0, opts=None, sensitivity=False):
-    """Strict or sensitivity-mode comparison of instances idx (module docstring)."""
+def _compare(pb, sol, idx, allow_flips=0, opts=None, sensitivity=False, floor=None):
+    """Strict or sensitivity-mode comparison of instances idx (module docstring).
+    floor: the FP32 residual floor (pb, i, oracle result) -> (primal, dual);
+    default `_fp32_floor` (residuals in the QP's own units)."""
     from paper_2606_24039_gb300._abi import ls_history
     errs, flips = [], []
     for i in idx:
@@ -200,7 +202,7 @@ def _compare(pb, sol, idx, allow_flips=0, opts=None, sensitivity=False):
         os_ = o["stats"]
         assert st[0] == os_["sqp_iters"] and st[1] == os_["admm_iters"]
         slack = 10.0 * float(np.max(np.abs(zg - o["z"]))) if sensitivity else 0.0
-        fp, fd = _fp32_floor(pb, i, o)
+        fp, fd = (floor or _fp32_floor)(pb, i, o)
         res_ok = abs(st[2] - os_["r_prim"]) <= RES_TOL * max(1.0, os_["prim_norm"]) + fp + slack and \
                  abs(st[3] - os_["r_dual"]) <= RES_TOL * max(1.0, os_["dual_norm"]) + fd + slack
         rec.update(err=e, bar=bar, res_slack=slack, fp32_floor=[fp, fd], ok=bool(e <= bar and res_ok))
