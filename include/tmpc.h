@@ -145,7 +145,13 @@ typedef struct {
      * dependent); 0 = the refinement, then the direct solve for every instance whose
      * refinement did not converge by its own step test.  The direct solve exists for
      * the small models and, on the generic kernel, when nx + (nx + nu) + ng <= 32;
-     * elsewhere 0 and 2 mean 1. */
+     * elsewhere 0 and 2 mean 1.  3 = the reduced adjoint QP of Appendix E (the
+     * paper's ADMM-based backward, kept for comparison): every hard active row is
+     * absorbed into the Hessian as a penalty of weight bwd_gamma, leaving an
+     * equality-only QP in eta_x that the refinement solves (multipliers on the
+     * dynamics rows only); its gradient is biased by O(1 / bwd_gamma) against the
+     * exact adjoint of 0-2, and the multiplier it returns for a hard active row is
+     * bwd_gamma G_A eta_x.  Not combinable with exact_hessian. */
     int32_t bwd_solver;
     /* 1: the direct backward uses the exact Lagrangian Hessian H = Hessian of
      * l + y_f' f + y_A' g_A (App. E) at the solution, the constraint curvature by FP64
@@ -153,6 +159,7 @@ typedef struct {
      * Hessian approximation; exact for linear dynamics).  Implies the direct solve
      * (small models). */
     int32_t exact_hessian;
+    float bwd_gamma;     /* penalty weight of the hard active rows when bwd_solver = 3   */
 } tmpc_options;
 
 /* Problem parameters theta (the OCP of Appendix A with the cost of Eq. (cost)).

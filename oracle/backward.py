@@ -20,6 +20,13 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
    approximation" option) or, with exact_hessian, the Hessian of
    l + y_f'f + y_A'g_A whose constraint curvature is obtained by central
    differences of the analytic Jacobians.
+   With `penalty` = gamma_xi, the reduced adjoint QP of Appendix E instead: each
+   hard active row is absorbed into the Hessian as the penalty
+   gamma_xi/2 (G_A eta_x)^2, i.e. its row of the KKT matrix gets -1/gamma_xi on
+   the diagonal of its multiplier (eliminating eta_A = gamma_xi G_A eta_x leaves
+   H + gamma_xi G_A'G_A with the dynamics rows as the only constraints); the
+   soft active rows keep their exact slack blocks.  The paper notes this
+   variant's bias against the exact adjoint; it tends to it as gamma_xi grows.
 3. The VJP of Eq. (loss_gradient): grad_theta L = -(dF/dtheta)' eta for
    theta = x_init, diagonal cost weights Q, R, W, references, linear cost
    term, active bounds, and the slack weights (gamma2, gamma1).
@@ -72,9 +79,11 @@ def _constraint_curvature(inst, z, yf, yg, active, h=1e-6):
     return 0.5 * (Hc + Hc.T)
 
 
-def backward(inst, sol, dLdz, dLdxi=None, eps_g=1e-4, exact_hessian=False):
+def backward(inst, sol, dLdz, dLdxi=None, eps_g=1e-4, exact_hessian=False, penalty=None):
     """Gradients of L with respect to the problem parameters (see module doc).
-    sol: dict(z, xi, yf, yg).  Returns (grads dict, info dict)."""
+    sol: dict(z, xi, yf, yg).  penalty: None for the exact active-set adjoint, or
+    gamma_xi for the reduced adjoint QP of Appendix E.  Returns (grads dict,
+    info dict)."""
     nx, nu, ng, N = inst["nx"], inst["nu"], inst["ng"], inst["N"]
     n = nx + nu
     z, xi, yf, yg = sol["z"], sol["xi"], sol["yf"], sol["yg"]
@@ -103,6 +112,11 @@ def backward(inst, sol, dLdz, dLdxi=None, eps_g=1e-4, exact_hessian=False):
                  [q["C"], None, None, None],
                  [GA, E.T if ns else None, None, None]], format="csc") if ns else \
         sp.bmat([[H, q["C"].T, GA.T], [q["C"], None, None], [GA, None, None]], format="csc")
+    if penalty is not None:
+        # hard active rows (active, no slack) become penalties: -1/gamma_xi on their diagonal
+        hard = np.array([r not in set(slk_idx.tolist()) for r in act_idx], dtype=bool)
+        d = np.concatenate([np.zeros(nz + ns + nf), np.where(hard, -1.0 / penalty, 0.0)])
+        K = (K + sp.diags(d)).tocsc()
     rhs = np.concatenate([dLdz.reshape(-1), dLdxi.reshape(-1)[slk_idx], np.zeros(nf + na)])
     singular = False
     with np.errstate(all="ignore"):

@@ -36,7 +36,7 @@ class Options(ctypes.Structure):
                 ("threads", ctypes.c_int32), ("solver", ctypes.c_int32),
                 ("force_pivot_failure", ctypes.c_int32), ("wait_polls", ctypes.c_int32),
                 ("force_wait_timeout", ctypes.c_int32), ("bwd_solver", ctypes.c_int32),
-                ("exact_hessian", ctypes.c_int32)]
+                ("exact_hessian", ctypes.c_int32), ("bwd_gamma", ctypes.c_float)]
 
 
 class Params(ctypes.Structure):

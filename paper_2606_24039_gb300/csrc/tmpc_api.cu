@@ -48,6 +48,7 @@ KOpts to_kopts(const tmpc_options& o) {
     k.force_timeout = o.force_wait_timeout;
     k.bwd_solver = o.bwd_solver;
     k.exact_hessian = o.exact_hessian;
+    k.bwd_gamma = o.bwd_gamma;
     if (k.k_rho_iter < 1) k.k_rho_iter = 1 << 30;
     return k;
 }
@@ -206,6 +207,7 @@ void tmpc_default_options(tmpc_options* o) {
     o->newton_steps = 3; o->early_exit = 0; o->check_every = 25;
     o->bwd_rho = 1e4f; o->bwd_sigma = 1e-6f; o->bwd_iters = 30;
     o->bwd_solver = 2;
+    o->bwd_gamma = 1e4f;
     o->threads = 0; o->solver = 0;
 }
 
@@ -230,7 +232,9 @@ static tmpc_status check_options(const tmpc_options* o) {
     if (o->threads < 0 || o->threads > 256 || (o->threads % 32) != 0) return TMPC_ERR_INVALID_ARG;
     if (o->solver < 0 || o->solver > 7) return TMPC_ERR_INVALID_ARG;
     if (o->force_pivot_failure < 0 || o->wait_polls < 0) return TMPC_ERR_INVALID_ARG;
-    if (o->bwd_solver < 0 || o->bwd_solver > 2) return TMPC_ERR_INVALID_ARG;
+    if (o->bwd_solver < 0 || o->bwd_solver > 3) return TMPC_ERR_INVALID_ARG;
+    if (o->bwd_solver == 3 && (o->exact_hessian || !(o->bwd_gamma > 0.f) || !(o->bwd_gamma < 1e30f)))
+        return TMPC_ERR_INVALID_ARG;
     return TMPC_OK;
 }
 

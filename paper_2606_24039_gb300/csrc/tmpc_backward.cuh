@@ -31,7 +31,10 @@ struct KGrads {
 };
 
 // codes stored per inequality row: 0 inactive, 1/-1 hard active upper/lower,
-// 2/-2 soft active upper/lower
+// 2/-2 soft active upper/lower, 3/-3 hard active rows that bwd_solver 3 (the
+// reduced adjoint QP of Appendix E) absorbs into the Hessian as penalties of
+// weight bwd_gamma: they enter S_b and the residual like soft rows (weight in
+// gw), carry no multiplier iteration, and report bwd_gamma G_A eta_x as eta_A
 __device__ __forceinline__ float active_code(float y, float val, float lo, float hi, float xi,
                                              bool soft, float eg) {
     const bool lower = (lo > -kInf) && ((y < -eg) || (fabsf(y) < eg && val - lo <= eg * fmaxf(1.f, fabsf(lo))));
@@ -63,10 +66,11 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
     float* r3 = c.glo;    // -G_H eta_x
     for (int e = threadIdx.x; e < T * ng; e += blockDim.x) {
         const int t = e / ng, r = e % ng;
-        const float cd = active_code(c.ygb[e], c.gv[e] + c.xib[e], c.lob(t, r), c.hib(t, r), c.xib[e],
-                                     c.gam2(r) < kInf, o.eps_g);
+        float cd = active_code(c.ygb[e], c.gv[e] + c.xib[e], c.lob(t, r), c.hib(t, r), c.xib[e],
+                               c.gam2(r) < kInf, o.eps_g);
+        if (o.bwd_solver == 3 && cd != 0.f && fabsf(cd) < 1.5f) cd *= 3.f;   // hard row absorbed as a penalty
         code[e] = cd;
-        c.gw[e] = (cd == 0.f) ? 0.f : (fabsf(cd) > 1.5f ? c.gam2(r) : rb);
+        c.gw[e] = (cd == 0.f) ? 0.f : (fabsf(cd) > 2.5f ? o.bwd_gamma : (fabsf(cd) > 1.5f ? c.gam2(r) : rb));
         mu[e] = 0.f;
     }
     for (int e = threadIdx.x; e < T * nx; e += blockDim.x) lam[e] = 0.f;
@@ -76,8 +80,10 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
         float b = dLdz[t * L.n + j];
         if (dLdxi) {
             const float* G = c.Gt(t);
-            for (int r = 0; r < ng; ++r)
-                if (fabsf(code[t * ng + r]) > 1.5f) b -= G[r * n + j] * dLdxi[t * L.ng + r];
+            for (int r = 0; r < ng; ++r) {
+                const float cd = fabsf(code[t * ng + r]);
+                if (cd > 1.5f && cd < 2.5f) b -= G[r * n + j] * dLdxi[t * L.ng + r];
+            }
         }
         bx[e] = b;
         ex[e] = 0.f;
@@ -126,7 +132,7 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
                     const int r = g_row(c, j);   // selector rows of the linear model
                     if (r >= 0) {
                         const float cd = code[t * ng + r];
-                        if (fabsf(cd) > 1.5f) s -= c.gam2(r) * gz[t * ng + r];
+                        if (fabsf(cd) > 1.5f) s -= c.gw[t * ng + r] * gz[t * ng + r];
                         else if (cd != 0.f) s -= mu[t * ng + r];
                         s += rb * r3[t * ng + r];
                     }
@@ -150,13 +156,13 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
                 if (g_is_selector(c)) {
                     const int r = g_row(c, j);
                     const float cd = r >= 0 ? code[t * ng + r] : 0.f;
-                    if (fabsf(cd) > 1.5f) s -= c.gam2(r) * gz[t * ng + r];
+                    if (fabsf(cd) > 1.5f) s -= c.gw[t * ng + r] * gz[t * ng + r];
                     else if (cd != 0.f) s -= mu[t * ng + r];
                 } else {
                     const float* G = c.Gt(t);
                     for (int r = 0; r < ng; ++r) {
                         const float cd = code[t * ng + r];
-                        if (fabsf(cd) > 1.5f) s -= c.gam2(r) * G[r * n + j] * gz[t * ng + r];
+                        if (fabsf(cd) > 1.5f) s -= c.gw[t * ng + r] * G[r * n + j] * gz[t * ng + r];
                         else if (cd != 0.f) s -= G[r * n + j] * mu[t * ng + r];
                     }
                 }
@@ -264,7 +270,8 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
             const int q = t * ng + r;
             const float cd = code[q];
             float eA = 0.f;
-            if (fabsf(cd) > 1.5f) eA = (dLdxi ? dLdxi[t * L.ng + r] : 0.f) + c.gam2(r) * gz[q];
+            if (fabsf(cd) > 2.5f) eA = c.gw[q] * gz[q];   // penalty row of the reduced adjoint QP
+            else if (fabsf(cd) > 1.5f) eA = (dLdxi ? dLdxi[t * L.ng + r] : 0.f) + c.gam2(r) * gz[q];
             else if (cd != 0.f) eA = mu[q];
             if (cd > 0.f) ghi = eA;
             if (cd < 0.f) glo = eA;
@@ -290,7 +297,7 @@ __device__ inline void backward_instance(const Ctx& c, const KOpts& o, const Sme
             if (r < ng)
                 for (int t = threadIdx.x; t < T; t += blockDim.x) {
                     const int q = t * ng + r;
-                    if (fabsf(code[q]) > 1.5f) {
+                    if (fabsf(code[q]) > 1.5f && fabsf(code[q]) < 2.5f) {
                         const float exi = -gz[q];
                         const float xv = c.xib[q];
                         s2 += (double)xv * exi;

@@ -158,7 +158,7 @@ cudaError_t launch_backward(int model, int cl, int grid, int threads, size_t sme
     // swept by the warp kernel and finished by a second pass of the backward kernel
     // (dq_flag: one per instance, global index; dq_ctr: [1] sweep cursor, [2] queue
     // of the finishing pass; all zeroed by the caller)
-    const bool direct = dws && dq_flag && dq_ctr && !(o.bwd_solver == 1 && !o.exact_hessian);
+    const bool direct = dws && dq_flag && dq_ctr && !((o.bwd_solver == 1 || o.bwd_solver == 3) && !o.exact_hessian);
     DirectQueue dq{direct ? dq_flag : nullptr};
     int finish = 0;
     const long long sf = (long long)(smem_bytes / sizeof(float));
@@ -190,7 +190,7 @@ cudaError_t launch_backward(int model, int cl, int grid, int threads, size_t sme
 }
 
 int backward_launches(int cl, const KOpts& o, bool have_dws) {
-    if (cl > 0 || !have_dws || (o.bwd_solver == 1 && !o.exact_hessian)) return 1;
+    if (cl > 0 || !have_dws || ((o.bwd_solver == 1 || o.bwd_solver == 3) && !o.exact_hessian)) return 1;
     return 3;
 }
 

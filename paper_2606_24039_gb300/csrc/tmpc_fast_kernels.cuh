@@ -1341,9 +1341,10 @@ __device__ __forceinline__ void backward_instance_team(Inst<M>& c, const KOpts& 
         if (lower || upper) {
             const float side = upper ? 1.f : -1.f;
             cd = (c.gam2(r) < kInf && fabsf(xv) > eg) ? 2.f * side : side;
+            if (o.bwd_solver == 3 && fabsf(cd) < 1.5f) cd = 3.f * side;   // hard row absorbed as a penalty
         }
         code[e] = cd;
-        gw[e] = (cd == 0.f) ? 0.f : (fabsf(cd) > 1.5f ? c.gam2(r) : rb);
+        gw[e] = (cd == 0.f) ? 0.f : (fabsf(cd) > 2.5f ? o.bwd_gamma : (fabsf(cd) > 1.5f ? c.gam2(r) : rb));
         mu[e] = 0.f;
     }
     for (int e = c.tid; e < T * NX; e += c.nth) lam[e] = 0.f;
@@ -1353,14 +1354,17 @@ __device__ __forceinline__ void backward_instance_team(Inst<M>& c, const KOpts& 
         float b = dLdz[t * L.n + j];
         if (dLdxi)
 #pragma unroll
-            for (int r = 0; r < NG; ++r)
-                if (fabsf(code[t * NG + r]) > 1.5f) b -= c.Gval(t, r, j) * dLdxi[t * L.ng + r];
+            for (int r = 0; r < NG; ++r) {
+                const float cd = fabsf(code[t * NG + r]);
+                if (cd > 1.5f && cd < 2.5f) b -= c.Gval(t, r, j) * dLdxi[t * L.ng + r];
+            }
         bx[e] = b;
         ex[e] = 0.f;
     }
     c.sync();
     // backward solver: 0 hybrid (refinement, then the direct solve where it did not
-    // converge), 1 refinement only, 2 direct only; the exact Hessian needs the direct solve
+    // converge), 1 refinement only, 2 direct only, 3 the reduced adjoint QP (hard active
+    // rows as penalties, code +-3; refinement only); the exact Hessian needs the direct solve
     const bool direct_ok = dws != nullptr && (dq.flag != nullptr || dsh != nullptr);
     const bool direct_only = direct_ok && (o.bwd_solver == 2 || o.exact_hessian);
     if (finish) {
@@ -1396,7 +1400,7 @@ __device__ __forceinline__ void backward_instance_team(Inst<M>& c, const KOpts& 
 #pragma unroll
                     for (int r = 0; r < NG; ++r) {
                         const float cd = code[t * NG + r];
-                        if (fabsf(cd) > 1.5f) sv -= c.gam2(r) * c.Gval(t, r, j) * gz[t * NG + r];
+                        if (fabsf(cd) > 1.5f) sv -= gw[t * NG + r] * c.Gval(t, r, j) * gz[t * NG + r];
                         else if (cd != 0.f) sv -= c.Gval(t, r, j) * mu[t * NG + r];
                     }
                     c.r[e] = sv;
@@ -1508,7 +1512,8 @@ __device__ __forceinline__ void backward_instance_team(Inst<M>& c, const KOpts& 
             const int q = t * NG + r;
             const float cd = code[q];
             float eA = 0.f;
-            if (fabsf(cd) > 1.5f) eA = (dLdxi ? dLdxi[t * L.ng + r] : 0.f) + c.gam2(r) * gz[q];
+            if (fabsf(cd) > 2.5f) eA = gw[q] * gz[q];   // penalty row of the reduced adjoint QP
+            else if (fabsf(cd) > 1.5f) eA = (dLdxi ? dLdxi[t * L.ng + r] : 0.f) + c.gam2(r) * gz[q];
             else if (cd != 0.f) eA = mu[q];
             if (cd > 0.f) ghi = eA;
             if (cd < 0.f) glo = eA;
@@ -1533,7 +1538,7 @@ __device__ __forceinline__ void backward_instance_team(Inst<M>& c, const KOpts& 
             if (r < NG)
                 for (int t = c.tid; t < T; t += c.nth) {
                     const int q = t * NG + r;
-                    if (fabsf(code[q]) > 1.5f) {
+                    if (fabsf(code[q]) > 1.5f && fabsf(code[q]) < 2.5f) {
                         const float exi = -gz[q];
                         const float xv = c.xib[q];
                         s2 += (double)xv * exi;

@@ -37,6 +37,7 @@ struct KOpts {
     int force_timeout;   // nonzero: every bounded wait gives up at once (test hook)
     int bwd_solver;      // backward: 0 hybrid (refinement, direct where it does not converge), 1 refinement, 2 direct
     int exact_hessian;   // 1: the direct backward adds the constraint curvature of the Lagrangian
+    float bwd_gamma;     // bwd_solver 3: penalty weight of the hard active rows (reduced adjoint QP)
 };
 
 struct KLayout {

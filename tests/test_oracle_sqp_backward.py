@@ -142,3 +142,65 @@ def test_backward_x0_matches_riccati_sensitivity():
             g += (-K[t] @ Phi).T @ dLdz[t, nx:]
             Phi = (A - B @ K[t]) @ Phi
     assert np.allclose(gr["x0"], g, atol=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# The reduced adjoint QP of Appendix E (hard active rows as penalties gamma_xi)
+# ---------------------------------------------------------------------------
+def _hard_active_instance():
+    p = w.tracking(B=1, nx=6, nu=3, N=8, seed=11)
+    inst = p.instance(0)
+    inst["x0"] = inst["x0"] * 6.0                          # controls on |u| <= 1
+    sol = sqp.solve(inst, tight(p.opts, iters=60000, eps=1e-12))
+    return inst, sol
+
+
+def test_adjoint_qp_penalty_tends_to_the_exact_adjoint():
+    """The bias of the penalised adjoint against the exact one (pinned by finite
+    differences above) falls like 1 / gamma_xi."""
+    inst, sol = _hard_active_instance()
+    rng = np.random.default_rng(4)
+    dLdz = rng.normal(size=sol["z"].shape)
+    exact, info = backward.backward(inst, sol, dLdz, eps_g=1e-7)
+    assert (info["lower"] | info["upper"]).sum() >= 3 and not info["slack"].any()
+    errs = []
+    for gam in (1e2, 1e4, 1e6):
+        pen, _ = backward.backward(inst, sol, dLdz, eps_g=1e-7, penalty=gam)
+        keys = ("x0", "Qd", "Rd", "ref", "lo", "hi")
+        errs.append(max(np.linalg.norm(pen[k] - exact[k]) / max(np.linalg.norm(exact[k]), 1e-12) for k in keys))
+    assert errs[0] > 1e-4
+    assert 3e-3 < errs[1] / errs[0] < 3e-2 and 3e-3 < errs[2] / errs[1] < 3e-2
+
+
+def test_adjoint_qp_penalty_equals_slack_rows_of_that_weight():
+    """Eliminating a penalty row's multiplier (-1/gamma on its diagonal) is the
+    same as giving the row an active slack of L2 weight gamma: the oracle's
+    slack blocks (a separate assembly) reproduce the penalised adjoint."""
+    inst, sol = _hard_active_instance()
+    rng = np.random.default_rng(6)
+    dLdz = rng.normal(size=sol["z"].shape)
+    gam = 300.0
+    pen, _ = backward.backward(inst, sol, dLdz, eps_g=1e-7, penalty=gam)
+    lower, upper, _ = backward.active_set(inst, sol["z"], sol["xi"], sol["yg"], 1e-7)
+    soft = dict(inst, gamma2=np.full_like(inst["gamma2"], gam), gamma1=np.zeros_like(inst["gamma1"]))
+    orig = backward.active_set
+    try:
+        backward.active_set = lambda *a, **k: (lower, upper, lower | upper)
+        via_slack, _ = backward.backward(soft, sol, dLdz, eps_g=1e-7)
+    finally:
+        backward.active_set = orig
+    for k in ("x0", "Qd", "Rd", "ref", "lo", "hi", "lin", "Wd"):
+        assert np.allclose(pen[k], via_slack[k], rtol=1e-9, atol=1e-12), k
+
+
+def test_adjoint_qp_without_hard_active_rows_is_the_exact_adjoint():
+    p = w.tracking(B=1, nx=6, nu=3, N=8, seed=11)
+    inst = p.instance(0)
+    inst["x0"] = inst["x0"] * 0.1                           # small x0: no bound active
+    sol = sqp.solve(inst, tight(p.opts, iters=20000, eps=1e-12))
+    dLdz = np.random.default_rng(8).normal(size=sol["z"].shape)
+    a, info = backward.backward(inst, sol, dLdz, eps_g=1e-7)
+    b, _ = backward.backward(inst, sol, dLdz, eps_g=1e-7, penalty=10.0)
+    assert not (info["lower"] | info["upper"]).any()
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k

@@ -105,6 +105,7 @@ class Options:
     bwd_rho: float = 1e4
     bwd_sigma: float = 1e-6
     bwd_iters: int = 30
+    bwd_gamma: float = 1e4      # penalty weight of hard active rows in the reduced adjoint QP
 
 
 @dataclasses.dataclass
