@@ -526,11 +526,48 @@ def mean_group_times(samples):
     return out
 
 
+BACKENDS = {2: "direct", 0: "hybrid", 1: "refinement", 3: "adjoint_qp"}
+
+
+def backward_backends(s, pb, sol, dLdz, flush, steps):
+    """The backward solvers on the same forward solution: time of one tmpc_backward
+    call (CUDA events, L2 flushed before each) and the relative deviation of each
+    backend's gradients (x0, Q, R, ref) from the direct solve's."""
+    import torch
+    from paper_2606_24039_gb300 import options_from
+    stream = torch.cuda.current_stream()
+    keep = s.options
+    out, ref = {}, None
+    for b, label in BACKENDS.items():
+        s.tmpc_set_options(options_from(keep, bwd_solver=b))
+        g = s.tmpc_backward(s.x0, sol, dLdz)
+        times = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g = s.tmpc_backward(s.x0, sol, dLdz)
+            e.record(stream)
+            e.synchronize()
+            times.append(a.elapsed_time(e))
+        vec = torch.cat([g[k].reshape(pb.B, -1) for k in ("x0", "Qd", "Rd", "ref")], dim=1).double()
+        if ref is None:
+            ref = vec
+        dev = ((vec - ref).norm(dim=1) / ref.norm(dim=1).clamp_min(1e-12)).cpu().numpy()
+        fin = lambda v: float(v) if np.isfinite(v) else None
+        out[label] = {"ms": float(np.mean(times)), "grad_dev_median": fin(np.median(dev)),
+                      "grad_dev_p99": fin(np.percentile(dev, 99)), "nonfinite": int(np.sum(~np.isfinite(dev)))}
+    s.tmpc_set_options(keep)
+    return out
+
+
 def measure(name, pb, args, peak, flush, steps, warmup, autotune=False, plain=False, e2e=False, bwd=True,
-            solver=0, world=1):
+            solver=0, world=1, backends=False):
     """Time one workload: forward steps and forward + backward steps (CUDA events
     on the caller's stream, L2 flushed before each), the per-group kernel times
-    (events on the launching streams), quality of the returned points."""
+    (events on the launching streams), quality of the returned points; with
+    backends, the backward solvers compared on the last forward solution."""
     import torch
     from paper_2606_24039_gb300 import Solver, tensors_from_batch
     s = Solver.from_batch(pb, device="cuda", solver=solver, threads=args.threads)
@@ -610,6 +647,8 @@ def measure(name, pb, args, peak, flush, steps, warmup, autotune=False, plain=Fa
                     "factorizations_mean": float(stats[:, 5].mean())},
     })
     rec["_kkt"] = kkt
+    if backends and bwd:
+        rec["backward_backends"] = backward_backends(s, pb, sol, dLdz, flush, max(3, steps // 4))
     if plain and solver in (0, 2) and set(int(m) for m in np.unique(pb.model)) <= set(FAST_MODELS):
         rec["plain_form"] = plain_form(pb, args, flush, ms_f, kkt)
     if e2e:
@@ -779,7 +818,8 @@ def run_gpu(args):
         t0 = time.time()
         head = measure(args.workload, pb, args, peak, flush, args.steps, args.warmup,
                        autotune=(args.solver == 0 and not args.no_autotune), plain=not args.no_plain,
-                       e2e=not args.skip_e2e, bwd=not args.skip_bwd, solver=args.solver, world=world)
+                       e2e=not args.skip_e2e, bwd=not args.skip_bwd, solver=args.solver, world=world,
+                       backends=suite)
         t1 = time.time()
         subs, conv = {}, {}
         if suite:
@@ -830,6 +870,7 @@ def run_gpu(args):
             "plain_form": head.get("plain_form"),
             "autotune": head.get("autotune"),
             "quality": head["quality"],
+            "backward_backends": head.get("backward_backends"),
             "fp32_peak": {"tflops": peak[0], "sms": peak[1], "sm_max_mhz": peak[2]},
         }
         if suite:

@@ -83,6 +83,15 @@ def test_rescaled_racing_equal_iterations(solver):
     _compare(pb, sol, range(8), sensitivity=True, floor=_scaled_floor)
 
 
+def test_rescaled_model_mix():
+    """Double integrator, bicycle and quadrotor (thrust bounds [0, 10] scaled by 8)
+    in one batch, each model group on its shared-memory kernel."""
+    pb = w.uneven(B=12, N_lo=10, N_hi=40, seed=77, max_sqp=1, max_admm=100)
+    pb.scale = w.magnitude_scales(pb)
+    s, sol, _ = _run(pb, solver=2)
+    _compare(pb, sol, range(pb.B), sensitivity=True, floor=_scaled_floor)
+
+
 def test_rescaled_forms_agree_bitwise():
     pb = w.racing(B=8, N=40, max_sqp=3, max_admm=30)
     pb.N[:] = [40, 7, 33, 1, 40, 20, 12, 39]
