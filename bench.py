@@ -452,6 +452,16 @@ def fp32_peak(gpu_index):
     return sms * FP32_LANES_PER_SM * 2.0 * mhz * 1e6 / 1e12, sms, mhz
 
 
+def fp32_probe():
+    """FP32 FMA throughput measured by the library's probe (eight independent FMA
+    chains per thread on every SM); TFLOP/s, or None if the probe failed."""
+    import ctypes
+    from paper_2606_24039_gb300 import _abi
+    t, ms = ctypes.c_float(0.0), ctypes.c_float(0.0)
+    code = _abi.load().tmpc_fp32_fma_probe(ctypes.byref(t), ctypes.byref(ms))
+    return float(t.value) if code == 0 else None
+
+
 GROUP_MODELS = {0: "MODEL_DI", 2: "MODEL_BICYCLE", 3: "MODEL_QUAD"}
 
 
@@ -809,6 +819,7 @@ def run_gpu(args):
     from paper_2606_24039_gb300 import build
     build.build()
     peak = fp32_peak(local)
+    fma_measured = fp32_probe()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     pb = workload(args, rank, world=world)
     suite = not args.no_suite and args.workload == "uneven" and world == 1
@@ -871,7 +882,9 @@ def run_gpu(args):
             "autotune": head.get("autotune"),
             "quality": head["quality"],
             "backward_backends": head.get("backward_backends"),
-            "fp32_peak": {"tflops": peak[0], "sms": peak[1], "sm_max_mhz": peak[2]},
+            "fp32_peak": {"tflops": peak[0], "sms": peak[1], "sm_max_mhz": peak[2],
+                          "measured_tflops": fma_measured,
+                          "measured_note": "FMA-chain probe (tmpc_fp32_fma_probe), at the clock of the moment"},
         }
         if suite:
             line["workloads"] = subs

@@ -342,6 +342,16 @@ typedef struct {
  * Errors: NOT_SETUP, INVALID_ARG (out or n_out NULL). */
 tmpc_status tmpc_group_times(tmpc_handle* h, tmpc_group_time* out, int32_t* n_out);
 
+/* Measurement helper with no counterpart in the paper: the FP32 FMA throughput of
+ * the current device (TFLOP/s, an FMA counted as 2 flop), the denominator of the
+ * roofline of the solve kernels, which are bound by FP32 issue.  Eight CTAs of 256
+ * threads per SM each run eight independent FMA chains; three warm-up launches,
+ * then the fastest of five, timed by CUDA events on a private stream.  tflops
+ * (HOST, required) receives the rate, ms (HOST, may be NULL) the launch time.
+ * Synchronous; allocates and frees a small device buffer.  Errors: INVALID_ARG
+ * for a NULL tflops, OOM, CUDA. */
+tmpc_status tmpc_fp32_fma_probe(float* tflops, float* ms);
+
 /* End-to-end forward pass from HOST memory: copies the parameter arrays of
  * host_p and x0 (HOST pointers, pinned memory recommended) into device
  * buffers owned by the handle, solves, copies z, xi, y_eq, y_ineq, status and

@@ -115,6 +115,8 @@ def load(path: str | None = None):
     lib.tmpc_autotune.restype = ctypes.c_int
     lib.tmpc_group_times.argtypes = [vp, ctypes.POINTER(GroupTime), ctypes.POINTER(ctypes.c_int32)]
     lib.tmpc_group_times.restype = ctypes.c_int
+    lib.tmpc_fp32_fma_probe.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
+    lib.tmpc_fp32_fma_probe.restype = ctypes.c_int
     lib.tmpc_destroy.argtypes = [vp]
     lib.tmpc_destroy.restype = None
     lib.tmpc_status_string.argtypes = [ctypes.c_int]

@@ -16,7 +16,7 @@ LIBDIR = os.path.join(PKG, "lib")
 LIBNAME = "libtmpc.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # the heavy kernels sit in translation units of their own so that they compile in parallel
-SOURCES = ["tmpc_api.cu", "tmpc_generic_fwd.cu", "tmpc_generic_bwd.cu", "tmpc_fast.cu",
+SOURCES = ["tmpc_api.cu", "tmpc_probe.cu", "tmpc_generic_fwd.cu", "tmpc_generic_bwd.cu", "tmpc_fast.cu",
            "tmpc_fast_di.cu", "tmpc_fast_bicycle.cu", "tmpc_fast_quad.cu"]
 
 
