@@ -178,7 +178,8 @@ typedef struct {
  *                                              and control (Remark 4, problem rescaling).
  *     When given, every ADMM solve runs on the QP in normalised variables z = D zh, with
  *     D = diag(d) on every stage and d_j the largest power of two not above scale_j (an
- *     entry that is not positive and finite counts as 1); the dynamics rows are divided by
+ *     entry that is not positive and finite counts as 1; keep the magnitudes within
+ *     2^-30 .. 2^30, as the normalised data must stay in FP32 range); the dynamics rows are divided by
  *     the scale of the state they define and a bound row of one variable by that
  *     variable's scale, the other rows are left as they are.  Powers of two make the
  *     change of variables exact.  rho, the ADMM residuals, the termination test and the

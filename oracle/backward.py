@@ -114,7 +114,8 @@ def backward(inst, sol, dLdz, dLdxi=None, eps_g=1e-4, exact_hessian=False, penal
         sp.bmat([[H, q["C"].T, GA.T], [q["C"], None, None], [GA, None, None]], format="csc")
     if penalty is not None:
         # hard active rows (active, no slack) become penalties: -1/gamma_xi on their diagonal
-        hard = np.array([r not in set(slk_idx.tolist()) for r in act_idx], dtype=bool)
+        slack_rows = set(slk_idx.tolist())
+        hard = np.array([r not in slack_rows for r in act_idx], dtype=bool)
         d = np.concatenate([np.zeros(nz + ns + nf), np.where(hard, -1.0 / penalty, 0.0)])
         K = (K + sp.diags(d)).tocsc()
     rhs = np.concatenate([dLdz.reshape(-1), dLdxi.reshape(-1)[slk_idx], np.zeros(nf + na)])
