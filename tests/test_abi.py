@@ -57,10 +57,40 @@ def test_setup_rejects_bad_arguments_without_a_gpu(lib):
     o2 = _abi.default_options()
     o2.alpha = 2.5
     assert lib.tmpc_setup(ctypes.byref(h), ctypes.byref(d), ctypes.byref(o2), ctypes.byref(p)) == 1
-    for field, value in (("solver", 8), ("threads", 48), ("threads", 512), ("n_ls", 17), ("max_admm", 0)):
+    for field, value in (("solver", 8), ("threads", 48), ("threads", 512), ("n_ls", 17), ("max_admm", 0),
+                         ("bwd_solver", 4), ("bwd_solver", -1)):
         o3 = _abi.default_options()
         setattr(o3, field, value)
         assert lib.tmpc_setup(ctypes.byref(h), ctypes.byref(d), ctypes.byref(o3), ctypes.byref(p)) == 1, field
+    assert abs(_abi.default_options().bwd_gamma - 1e4) < 1e-3
+
+
+def test_backward_options_are_validated_before_any_device_work(lib):
+    """The option check alone rejects a backward solver outside 0..3 and a reduced
+    adjoint QP (3) with a non-positive or infinite penalty or with the exact
+    Hessian: the no-allocation entry point, given well-formed parameters and a
+    batch too large for its scratch, stops at the option check for these (no
+    scratch message) and reaches the capacity check with the defaults."""
+    from paper_2606_24039_gb300 import _abi
+    d = _abi.Dims(4096, 30, 6, 2, 5, 4, 800)
+    fake = 0x10000
+    p = _abi.Params(*([fake] * 13))
+    s = _abi.Solution(*([fake] * 6))
+
+    def call(o):
+        code = lib.tmpc_solve_static(ctypes.byref(d), ctypes.byref(o), ctypes.byref(p), fake, ctypes.byref(s), 0, None)
+        return code, lib.tmpc_last_error().decode()
+
+    code, msg = call(_abi.default_options())
+    assert code == 1 and "static scratch" in msg
+    for bwd, exact, gamma in ((4, 0, 1e4), (-1, 0, 1e4), (3, 1, 1e4), (3, 0, 0.0), (3, 0, float("inf"))):
+        o = _abi.default_options()
+        o.bwd_solver, o.exact_hessian, o.bwd_gamma = bwd, exact, gamma
+        code, msg = call(o)
+        assert code == 1 and "static scratch" not in msg, (bwd, exact, gamma)
+    o = _abi.default_options()
+    o.bwd_solver = 3
+    assert "static scratch" in call(o)[1]
     # calls on a null handle
     assert lib.tmpc_solve(None, None, None, 0, None) == 4
     assert lib.tmpc_backward(None, None, None, None, None, None, None) == 4
