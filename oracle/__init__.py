@@ -16,11 +16,15 @@ Modules (each function cites the passage of the paper it follows):
             adaptive rho rule of Eq. (rho:update).  The primal system
             S x = eta is formed as P + sigma I + A' rho A and solved by a
             library banded Cholesky (a plain definition, no block formulas).
+            Optionally on the QP in normalised states and controls
+            (problem rescaling, Remark 4).
   sqp       Algorithm 1 with the backtracking line search of Appendix D and
             the stopping test of Eq. (sqp_stop).
   backward  Algorithm 2: active set (Appendix E), the full active-set KKT
             system of Eq. (bwd:slack_adjoint) assembled sparse and solved by
-            a library LU, and the vector-Jacobian product of Eq. (loss_gradient).
+            a library LU, and the vector-Jacobian product of Eq. (loss_gradient);
+            optionally the reduced adjoint QP of Appendix E (hard active rows
+            as penalties).
 
 Parity status of each function is stated in its docstring; all of them are
 pinned by `tests/test_oracle_*.py` except where a docstring says
