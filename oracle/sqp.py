@@ -22,8 +22,11 @@ Line search (Appendix D): direction (dz, dxi) = (z*, xi*) - (z, xi); merit
 The floor ||y*||_inf + 1e-4 on mu (the exact-penalty condition) is this
 implementation's reading where the printed ratio is not positive.
 Parity: one SQP step of an LQ problem is pinned (a second step is a no-op,
-the Armijo condition holds for the accepted step); the nonlinear SQP path as a
-whole is otherwise "parity unpinned" beyond the algorithm itself.
+the Armijo condition holds for the accepted step), a worked line search by
+hand (tests/test_oracle_pins.py), and the converged nonlinear loop against an
+independent NLP solver on small bicycle and quadrotor OCPs
+(tests/test_oracle_nlp.py); the path at fixed counts is pinned only by the
+algorithm itself.
 """
 from __future__ import annotations
 

@@ -1,0 +1,76 @@
+"""Pin of the oracle's nonlinear SQP loop (Algorithm 1: linearisation, QP in
+absolute coordinates, ADMM, merit line search, multiplier steps) as a whole:
+run to convergence on small nonlinear OCPs with active hard bounds, it must
+reach the minimiser that an independent NLP solver (SciPy's SLSQP on the same
+cost, dynamics and bounds, written from the model functions that the
+finite-difference pins of test_oracle_models.py fix) finds, and its KKT
+residual of Eq. (sqp_stop) must vanish.  A mistake in the QP's coordinates,
+the step or the multiplier update moves the fixed point or stops convergence.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+from scipy.optimize import minimize
+
+import workloads as w
+from oracle import models, sqp
+
+
+def _nlp_minimiser(inst, z_start):
+    N, nx, n = inst["N"], inst["nx"], inst["nx"] + inst["nu"]
+    unpack = lambda v: v.reshape(N + 1, n)
+
+    def eq(v):
+        z = unpack(v)
+        f, _, _ = models.dynamics(inst, z)
+        return np.concatenate([z[0, :nx] - inst["x0"], f.reshape(-1)])
+
+    def ineq(v):
+        g, _ = models.constraints(inst, unpack(v))
+        lo, hi = inst["lo"], inst["hi"]
+        return np.concatenate([(hi - g)[np.isfinite(hi)], (g - lo)[np.isfinite(lo)]])
+
+    r = minimize(lambda v: models.cost(inst, unpack(v)), z_start.reshape(-1),
+                 jac=lambda v: models.cost_grad(inst, unpack(v)).reshape(-1), method="SLSQP",
+                 constraints=[{"type": "eq", "fun": eq}, {"type": "ineq", "fun": ineq}],
+                 options=dict(maxiter=3000, ftol=1e-15))
+    assert r.success, r.message
+    return unpack(r.x)
+
+
+def _tight(opts, sqp_iters):
+    return dataclasses.replace(opts, max_sqp=sqp_iters, max_admm=40000, early_exit=1, eps_abs=1e-11,
+                               eps_rel=1e-11, eps_c=1e-9, check_every=25)
+
+
+def _active(inst, z):
+    g, _ = models.constraints(inst, z)
+    return int(np.sum(np.isclose(g, inst["hi"], atol=1e-6) | np.isclose(g, inst["lo"], atol=1e-6)))
+
+
+def test_sqp_reaches_the_nlp_minimiser_bicycle():
+    """Implicit-midpoint bicycle on a short track, every row hard, the speed bound
+    active below the initial speed."""
+    pb = w.racing(B=1, N=6, track_length=60.0)
+    inst = pb.instance(0)
+    inst["gamma2"] = np.full_like(inst["gamma2"], np.inf)
+    inst["gamma1"] = np.zeros_like(inst["gamma1"])
+    inst["hi"][1:, 2] = inst["z_init"][0, 3] - 0.1
+    o = sqp.solve(inst, _tight(pb.opts, 80))
+    ref = _nlp_minimiser(inst, inst["z_init"])
+    assert o["stats"]["kkt"] < 1e-9
+    assert _active(inst, o["z"]) >= 1
+    assert np.max(np.abs(o["z"] - ref)) / max(1.0, np.max(np.abs(ref))) < 1e-6
+
+
+def test_sqp_reaches_the_nlp_minimiser_quadrotor():
+    """RK4 planar quadrotor pushed off hover, with a thrust bound active."""
+    pb = w.uneven(B=40, N_lo=6, N_hi=6, seed=21)
+    inst = pb.instance(int(np.flatnonzero(pb.model == w.MODEL_QUAD)[0]))
+    inst["x0"] = inst["x0"] + np.array([0.3, -0.2, 0.2, 0.5, -0.3, 0.1])
+    o = sqp.solve(inst, _tight(pb.opts, 60))
+    ref = _nlp_minimiser(inst, sqp.rollout(inst))
+    assert o["stats"]["kkt"] < 1e-6
+    assert _active(inst, o["z"]) >= 1
+    assert np.max(np.abs(o["z"] - ref)) / max(1.0, np.max(np.abs(ref))) < 1e-5
