@@ -74,3 +74,20 @@ def test_sqp_reaches_the_nlp_minimiser_quadrotor():
     assert o["stats"]["kkt"] < 1e-6
     assert _active(inst, o["z"]) >= 1
     assert np.max(np.abs(o["z"] - ref)) / max(1.0, np.max(np.abs(ref))) < 1e-5
+
+
+def test_rescaled_sqp_reaches_the_same_minimiser():
+    """With the ADMM on the rescaled QP (normalised states and controls), the
+    converged SQP point is still the NLP minimiser: the rescaling changes the
+    inner iteration, not the problem."""
+    pb = w.racing(B=1, N=6, track_length=60.0)
+    inst = pb.instance(0)
+    inst["gamma2"] = np.full_like(inst["gamma2"], np.inf)
+    inst["gamma1"] = np.zeros_like(inst["gamma1"])
+    inst["hi"][1:, 2] = inst["z_init"][0, 3] - 0.1
+    pb.scale = w.magnitude_scales(pb)
+    inst["scale"] = pb.scale[0]
+    o = sqp.solve(inst, _tight(pb.opts, 80))
+    ref = _nlp_minimiser(inst, inst["z_init"])
+    assert o["stats"]["kkt"] < 1e-7     # the inner tolerance now acts in scaled units
+    assert np.max(np.abs(o["z"] - ref)) / max(1.0, np.max(np.abs(ref))) < 1e-6
