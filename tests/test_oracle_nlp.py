@@ -26,14 +26,34 @@ def _nlp_minimiser(inst, z_start):
         f, _, _ = models.dynamics(inst, z)
         return np.concatenate([z[0, :nx] - inst["x0"], f.reshape(-1)])
 
+    def eq_jac(v):   # [I 0] on x_0, then df_t / d(z_t, z_t+1) per stage
+        _, Am, Ap = models.dynamics(inst, unpack(v))
+        J = np.zeros((nx * (N + 1), n * (N + 1)))
+        J[:nx, :nx] = np.eye(nx)
+        for t in range(N):
+            J[nx * (t + 1):nx * (t + 2), n * t:n * (t + 1)] = Am[t]
+            J[nx * (t + 1):nx * (t + 2), n * (t + 1):n * (t + 2)] = Ap[t]
+        return J
+
+    lo, hi = inst["lo"], inst["hi"]
+    mh, ml = np.isfinite(hi), np.isfinite(lo)
+
     def ineq(v):
         g, _ = models.constraints(inst, unpack(v))
-        lo, hi = inst["lo"], inst["hi"]
-        return np.concatenate([(hi - g)[np.isfinite(hi)], (g - lo)[np.isfinite(lo)]])
+        return np.concatenate([(hi - g)[mh], (g - lo)[ml]])
+
+    def ineq_jac(v):
+        _, G = models.constraints(inst, unpack(v))
+        ng = G.shape[1]
+        J = np.zeros(((N + 1) * ng, (N + 1) * n))
+        for t in range(N + 1):
+            J[ng * t:ng * (t + 1), n * t:n * (t + 1)] = G[t]
+        return np.vstack([-J[mh.reshape(-1)], J[ml.reshape(-1)]])
 
     r = minimize(lambda v: models.cost(inst, unpack(v)), z_start.reshape(-1),
                  jac=lambda v: models.cost_grad(inst, unpack(v)).reshape(-1), method="SLSQP",
-                 constraints=[{"type": "eq", "fun": eq}, {"type": "ineq", "fun": ineq}],
+                 constraints=[{"type": "eq", "fun": eq, "jac": eq_jac},
+                              {"type": "ineq", "fun": ineq, "jac": ineq_jac}],
                  options=dict(maxiter=3000, ftol=1e-15))
     assert r.success, r.message
     return unpack(r.x)
@@ -90,4 +110,21 @@ def test_rescaled_sqp_reaches_the_same_minimiser():
     o = sqp.solve(inst, _tight(pb.opts, 80))
     ref = _nlp_minimiser(inst, inst["z_init"])
     assert o["stats"]["kkt"] < 1e-7     # the inner tolerance now acts in scaled units
+    assert np.max(np.abs(o["z"] - ref)) / max(1.0, np.max(np.abs(ref))) < 1e-6
+
+
+@pytest.mark.parametrize("integrator", ["trapezoidal", "newton_map"])
+def test_sqp_reaches_the_nlp_minimiser_other_time_discretisations(integrator):
+    """The bicycle under the trapezoidal constraint (A^+ with a control block) and
+    under the explicit map that 3 Newton steps on the midpoint rule define (IFT
+    Jacobians)."""
+    pb = w.racing(B=1, N=6, track_length=60.0, integrator=integrator)
+    inst = pb.instance(0)
+    inst["gamma2"] = np.full_like(inst["gamma2"], np.inf)
+    inst["gamma1"] = np.zeros_like(inst["gamma1"])
+    inst["hi"][1:, 2] = inst["z_init"][0, 3] - 0.1
+    o = sqp.solve(inst, _tight(pb.opts, 80))
+    ref = _nlp_minimiser(inst, inst["z_init"])
+    assert o["stats"]["kkt"] < 1e-6
+    assert _active(inst, o["z"]) >= 1
     assert np.max(np.abs(o["z"] - ref)) / max(1.0, np.max(np.abs(ref))) < 1e-6
