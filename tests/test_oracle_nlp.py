@@ -128,3 +128,18 @@ def test_sqp_reaches_the_nlp_minimiser_other_time_discretisations(integrator):
     assert o["stats"]["kkt"] < 1e-6
     assert _active(inst, o["z"]) >= 1
     assert np.max(np.abs(o["z"] - ref)) / max(1.0, np.max(np.abs(ref))) < 1e-6
+
+
+def test_sqp_reaches_the_nlp_minimiser_srb_humanoid():
+    """Single-rigid-body humanoid (RK4, n = 18) with the vertical foot forces capped
+    below the weight, so that the cap is active on every stage."""
+    pb = w.humanoid(B=1, N=5)
+    inst = pb.instance(0)
+    inst["hi"][:, 2] = 150.0
+    inst["hi"][:, 5] = 150.0
+    o = sqp.solve(inst, _tight(pb.opts, 60))
+    z0 = inst["z_init"] if inst.get("z_init") is not None else sqp.rollout(inst)
+    ref = _nlp_minimiser(inst, z0)
+    assert o["stats"]["kkt"] < 1e-6
+    assert _active(inst, o["z"]) >= 6
+    assert np.max(np.abs(o["z"] - ref)) / max(1.0, np.max(np.abs(ref))) < 1e-6
