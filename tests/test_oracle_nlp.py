@@ -143,3 +143,67 @@ def test_sqp_reaches_the_nlp_minimiser_srb_humanoid():
     assert o["stats"]["kkt"] < 1e-6
     assert _active(inst, o["z"]) >= 6
     assert np.max(np.abs(o["z"] - ref)) / max(1.0, np.max(np.abs(ref))) < 1e-6
+
+
+def _nlp_minimiser_with_slacks(inst, z_start):
+    """The same NLP with the L1 + L2 slack of every soft row, the slack split as
+    xi = p - m with p, m >= 0 so that gamma1 |xi| = gamma1 (p + m) is smooth:
+    min l(z) + sum gamma2/2 xi^2 + gamma1 (p + m)  s.t. dynamics, lo <= g + xi <= hi."""
+    N, nx, n = inst["N"], inst["nx"], inst["nx"] + inst["nu"]
+    ks = np.flatnonzero(np.isfinite(inst["gamma2"]))
+    ns = len(ks)
+    nz, nsl = n * (N + 1), ns * (N + 1)
+    g2, g1 = inst["gamma2"][ks], inst["gamma1"][ks]
+    lo, hi = inst["lo"], inst["hi"]
+    mh, ml = np.isfinite(hi), np.isfinite(lo)
+
+    def split(v):
+        return v[:nz].reshape(N + 1, n), v[nz:nz + nsl].reshape(N + 1, ns), v[nz + nsl:].reshape(N + 1, ns)
+
+    def obj(v):
+        z, p, m = split(v)
+        xi = p - m
+        return models.cost(inst, z) + np.sum(0.5 * g2 * xi ** 2 + g1 * (p + m))
+
+    def obj_grad(v):
+        z, p, m = split(v)
+        xi = p - m
+        return np.concatenate([models.cost_grad(inst, z).reshape(-1), (g2 * xi + g1).reshape(-1),
+                               (-g2 * xi + g1).reshape(-1)])
+
+    def eq(v):
+        z = split(v)[0]
+        f, _, _ = models.dynamics(inst, z)
+        return np.concatenate([z[0, :nx] - inst["x0"], f.reshape(-1)])
+
+    def ineq(v):
+        z, p, m = split(v)
+        g, _ = models.constraints(inst, z)
+        g = g.copy()
+        g[:, ks] += p - m
+        return np.concatenate([(hi - g)[mh], (g - lo)[ml]])
+
+    v0 = np.concatenate([z_start.reshape(-1), np.zeros(2 * nsl)])
+    r = minimize(obj, v0, jac=obj_grad, method="SLSQP", bounds=[(None, None)] * nz + [(0.0, None)] * (2 * nsl),
+                 constraints=[{"type": "eq", "fun": eq}, {"type": "ineq", "fun": ineq}],
+                 options=dict(maxiter=5000, ftol=1e-15))
+    z, p, m = split(r.x)
+    xi = np.zeros((N + 1, inst["ng"]))
+    xi[:, ks] = p - m
+    return z, xi
+
+
+def test_sqp_reaches_the_nlp_minimiser_with_l1_l2_slacks():
+    """The racing track row kept soft (gamma2 = 100, gamma1 = 10) and narrowed so
+    that its slack is used: the SQP's converged point and slacks equal the
+    minimiser of the NLP with explicit slack variables."""
+    pb = w.racing(B=1, N=4, track_length=60.0)
+    inst = pb.instance(0)
+    inst["lo"][1:, 4], inst["hi"][1:, 4] = -0.05, 0.05   # state rows bound t >= 1 (x_0 is fixed)
+    inst["x0"] = inst["x0"] + np.array([0.0, 0.4, 0.05, 0.0, 0.0, 0.0])
+    o = sqp.solve(inst, _tight(pb.opts, 80))
+    z, xi = _nlp_minimiser_with_slacks(inst, inst["z_init"])
+    assert o["stats"]["kkt"] < 1e-6
+    assert np.max(np.abs(o["xi"])) > 1e-2
+    assert np.max(np.abs(o["z"] - z)) / max(1.0, np.max(np.abs(z))) < 1e-5
+    assert np.max(np.abs(o["xi"] - xi)) < 1e-5 * max(1.0, np.max(np.abs(xi)))
