@@ -180,3 +180,17 @@ def test_rescaled_blocks_keep_their_unit_structure():
                 if j >= 0:
                     e = np.zeros(n); e[j] = 1.0
                     assert np.array_equal(G[t * ng + r, t * n:(t + 1) * n], e)
+
+
+def test_magnitude_scales_of_the_workloads():
+    """The input helper: per component the largest |value| in the initial guess
+    or of a finite bound on a row that bounds the component alone, floored at 1."""
+    pb = w.racing(B=2, N=10, track_length=80.0)
+    m = w.magnitude_scales(pb)
+    for i in range(pb.B):
+        T = int(pb.N[i]) + 1
+        guess = np.max(np.abs(pb.z_init[i, :T, :8]), axis=0)
+        assert m[i, 3] == max(1.0, guess[3], 30.0)          # speed: bound 30 m/s
+        assert m[i, 6] == max(1.0, guess[6], 4.0)           # acceleration: |a| <= 4
+        assert m[i, 0] == max(1.0, guess[0])                # x position: no bound row
+        assert np.all(m[i] >= 1.0)
